@@ -1,0 +1,228 @@
+"""CPU FP64 oracle of the 3DGS^3 low-resolution render (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg may
+import this package. The product path (``paper_2605_11489_gb300``) never does,
+and the two share no code: the only common module is the seeded input generator
+``paper_2605_11489_gb300.synth``, which holds none of the render arithmetic.
+
+The C source (``oracle.c``) is a plain, per-pixel, untiled reference renderer:
+FP64 continuous math, plus an fp32 round-to-nearest sequence for the discrete
+decisions (depth key, support rectangle). Every function here is a thin ctypes
+wrapper around it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Scene(C.Structure):
+    _fields_ = [("n", C.c_int64), ("stride", C.c_int64), ("deg", C.c_int32), ("_pad", C.c_int32),
+                ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("viewmat", C.c_double * 12), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("near_plane", C.c_double),
+                ("width", C.c_int32), ("height", C.c_int32), ("bg", C.c_double * 3)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            P = C.c_void_p
+            L.or_spec_exp.restype = C.c_float
+            L.or_spec_exp.argtypes = [C.c_float]
+            L.or_spec_log.restype = C.c_float
+            L.or_spec_log.argtypes = [C.c_float]
+            L.or_sh_basis.argtypes = [C.c_int, P, P, P]
+            L.or_cov3d.argtypes = [P, P, P, P]
+            L.or_project.argtypes = [P, P, C.c_int32] + [P] * 10
+            L.or_render.argtypes = [P, P, C.c_int] + [P] * 8
+            L.or_render_pixels.argtypes = [P, P, C.c_int64, P, P, P, P]
+            L.or_count_instances.restype = C.c_int64
+            L.or_count_instances.argtypes = [P, P, C.c_int32]
+            L.or_keys.argtypes = [P, P, C.c_int32, C.c_int64, P, P, P]
+            L.or_backward.argtypes = [P, P] + [P] * 11
+            L.or_max_threads.restype = C.c_int
+            L.or_set_threads.argtypes = [C.c_int]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class OScene:
+    """FP64 copy of a ``synth.SceneArrays`` (the fp32 values promoted exactly)."""
+
+    def __init__(self, s):
+        self.n, self.deg = s.n, s.deg
+        self.stride = s.n_pad
+        self.means = np.ascontiguousarray(s.means, dtype=np.float64)
+        self.log_scales = np.ascontiguousarray(s.log_scales, dtype=np.float64)
+        self.quats = np.ascontiguousarray(s.quats, dtype=np.float64)
+        self.logits = np.ascontiguousarray(s.logits, dtype=np.float64)
+        self.sh = np.ascontiguousarray(s.sh, dtype=np.float64)
+
+    def struct(self):
+        return _Scene(self.n, self.stride, self.deg, 0, _ptr(self.means), _ptr(self.log_scales),
+                      _ptr(self.quats), _ptr(self.logits), _ptr(self.sh))
+
+
+def _as_oscene(s):
+    return s if isinstance(s, OScene) else OScene(s)
+
+
+def _cam(cam, bg=(0.0, 0.0, 0.0)):
+    c = _Camera()
+    for k in range(12):
+        c.viewmat[k] = float(cam.viewmat[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.near_plane = float(cam.near)
+    c.width, c.height = int(cam.width), int(cam.height)
+    for k in range(3):
+        c.bg[k] = float(bg[k])
+    return c
+
+
+def spec_exp(x: float) -> float:
+    return lib().or_spec_exp(float(x))
+
+
+def spec_log(x: float) -> float:
+    return lib().or_spec_log(float(x))
+
+
+def sh_basis(deg: int, d) -> tuple[np.ndarray, np.ndarray]:
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    k = (deg + 1) ** 2
+    y = np.zeros(k)
+    dy = np.zeros((k, 3))
+    lib().or_sh_basis(deg, _ptr(d), _ptr(y), _ptr(dy))
+    return y, dy
+
+
+def cov3d(s, q):
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    sig = np.zeros(9)
+    R = np.zeros(9)
+    lib().or_cov3d(_ptr(s), _ptr(q), _ptr(sig), _ptr(R))
+    return sig.reshape(3, 3), R.reshape(3, 3)
+
+
+def project(scene, cam, tile: int = 16) -> dict:
+    """Per-Gaussian projection: discrete fields (visible, z32, rect, ntiles) and
+    FP64 continuous fields (uv, conic, opacity, rgb, depth, cov2d)."""
+    s = _as_oscene(scene)
+    n = s.n
+    out = dict(visible=np.zeros(n, np.int32), z32=np.zeros(n, np.float32), rect=np.zeros((n, 4), np.int32),
+               ntiles=np.zeros(n, np.int32), uv=np.zeros((n, 2)), conic=np.zeros((n, 3)),
+               opacity=np.zeros(n), rgb=np.zeros((n, 3)), depth=np.zeros(n), cov2d=np.zeros((n, 3)))
+    st, cm = s.struct(), _cam(cam)
+    lib().or_project(C.byref(st), C.byref(cm), tile, *[_ptr(out[k]) for k in
+                     ("visible", "z32", "rect", "ntiles", "uv", "conic", "opacity", "rgb", "depth", "cov2d")])
+    return out
+
+
+def render(scene, cam, bg=(0.0, 0.0, 0.0), mode: str = "binned") -> dict:
+    """Full-frame FP64 render. Returns planar rgb/dcdx/dcdy [3,H,W], depth,
+    alpha, final_T [H,W], n_blended [H,W] and the per-pixel decision signature."""
+    s = _as_oscene(scene)
+    H, W = cam.height, cam.width
+    out = dict(rgb=np.zeros((3, H, W)), dcdx=np.zeros((3, H, W)), dcdy=np.zeros((3, H, W)),
+               depth=np.zeros((H, W)), alpha=np.zeros((H, W)), final_T=np.zeros((H, W)),
+               n_blended=np.zeros((H, W), np.int32), sig=np.zeros((H, W), np.uint32))
+    st, cm = s.struct(), _cam(cam, bg)
+    rc = lib().or_render(C.byref(st), C.byref(cm), 1 if mode == "binned" else 0,
+                         *[_ptr(out[k]) for k in ("rgb", "dcdx", "dcdy", "depth", "alpha", "final_T",
+                                                  "n_blended", "sig")])
+    if rc != 0:
+        raise RuntimeError("or_render failed: %d" % rc)
+    return out
+
+
+def render_pixels(scene, cam, px, py, bg=(0.0, 0.0, 0.0)) -> tuple[np.ndarray, np.ndarray]:
+    """Brute-force render of sampled pixels. Returns ([n, 11] = rgb, dcdx, dcdy,
+    depth, alpha; n_blended)."""
+    s = _as_oscene(scene)
+    px = np.ascontiguousarray(px, dtype=np.int32)
+    py = np.ascontiguousarray(py, dtype=np.int32)
+    out = np.zeros((len(px), 11))
+    nb = np.zeros(len(px), np.int32)
+    st, cm = s.struct(), _cam(cam, bg)
+    rc = lib().or_render_pixels(C.byref(st), C.byref(cm), len(px), _ptr(px), _ptr(py), _ptr(out), _ptr(nb))
+    if rc != 0:
+        raise RuntimeError("or_render_pixels failed: %d" % rc)
+    return out, nb
+
+
+def keys(scene, cam, tile: int = 16) -> dict:
+    """Sorted (tile, depth) instance list: keys u64, vals u32, ranges [n_tiles, 2]."""
+    s = _as_oscene(scene)
+    st, cm = s.struct(), _cam(cam)
+    L = lib()
+    K = L.or_count_instances(C.byref(st), C.byref(cm), tile)
+    tw = (cam.width + tile - 1) // tile
+    th = (cam.height + tile - 1) // tile
+    k = np.zeros(max(K, 1), np.uint64)
+    v = np.zeros(max(K, 1), np.uint32)
+    r = np.zeros((tw * th, 2), np.uint32)
+    rc = L.or_keys(C.byref(st), C.byref(cm), tile, K, _ptr(k), _ptr(v), _ptr(r))
+    if rc != 0:
+        raise RuntimeError("or_keys failed: %d" % rc)
+    return dict(keys=k[:K], vals=v[:K], ranges=r, n_tiles=tw * th)
+
+
+def backward(scene, cam, g_rgb=None, g_dcdx=None, g_dcdy=None, g_depth=None, g_alpha=None,
+             bg=(0.0, 0.0, 0.0)) -> dict:
+    """FP64 adjoint of L = sum <g_*, output_*>. Returns planar grads shaped like the
+    scene's planes (means [3,n_pad], log_scales, quats, logits, sh) and the 2D
+    adjoints g2d [n, 10] = (u, v, conic a, b, c, opacity, depth, r, g, b)."""
+    s = _as_oscene(scene)
+    S = s.stride
+    f64 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    ups = [f64(g_rgb), f64(g_dcdx), f64(g_dcdy), f64(g_depth), f64(g_alpha)]
+    out = dict(means=np.zeros((3, S)), log_scales=np.zeros((3, S)), quats=np.zeros((4, S)),
+               logits=np.zeros(S), sh=np.zeros(((s.deg + 1) ** 2, 3, S)), g2d=np.zeros((s.n, 10)))
+    st, cm = s.struct(), _cam(cam, bg)
+    rc = lib().or_backward(C.byref(st), C.byref(cm), *[_ptr(a) for a in ups],
+                           *[_ptr(out[k]) for k in ("means", "log_scales", "quats", "logits", "sh", "g2d")])
+    if rc != 0:
+        raise RuntimeError("or_backward failed: %d" % rc)
+    return out
+
+
+def max_threads() -> int:
+    return lib().or_max_threads()
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
