@@ -1,0 +1,340 @@
+"""Benchmark of the low-resolution 3DGS render hot path on GB300.
+
+A step renders one frame of the workload's camera path through the whole hot
+path (projection + SH colour, scan, key duplication, radix sort, tile ranges,
+compositing with dC/dx, dC/dy, depth and alpha), replayed as a captured CUDA
+graph with the frame's camera (the fixed-resolution stream path). The scene is
+resident in HBM before timing starts and is larger than L2, so steps do not
+reuse each other's inputs from cache.
+
+Prints one JSON line. Default workload: 1M clustered Gaussians, SH degree 3,
+960x540, 60-frame orbit (steps cycle over the orbit).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload large|ultra|ultra_lr|tiny]
+
+With --gpus N > 1 (launched by torchrun) every rank renders the same workload
+as an independent replica (the render has no cross-GPU exchange); value is the
+pixels of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "render+grad Mpix/s"
+WORKLOADS = {
+    "large": dict(desc="1M Gaussians (64 clusters, 100x100x20 m), SH degree 3, 960x540, 60-frame orbit",
+                  n=1_000_000, width=960, height=540, path="orbit"),
+    "ultra": dict(desc="6M Gaussians (64 clusters, 300x300x40 m), SH degree 3, 1920x1080, 60-frame fly-through",
+                  n=6_000_000, width=1920, height=1080, path="fly"),
+    "ultra_lr": dict(desc="6M Gaussians (300x300x40 m), SH degree 3, 480x270, 60-frame fly-through",
+                     n=6_000_000, width=480, height=270, path="fly"),
+    "tiny": dict(desc="4,096 Gaussians in [-1,1]^3, SH degree 0, 256x144, 64 jittered cameras",
+                 n=4096, width=256, height=144, path="tiny"),
+}
+GS_CAMERA_BYTES = 76  # sizeof(gs_camera): the per-step host input
+
+
+def make_workload(name):
+    from paper_2605_11489_gb300 import synth
+
+    w = WORKLOADS[name]
+    if name == "large":
+        sc = synth.large_scene(w["n"], 1)
+        cams = synth.orbit_cameras(60, w["width"], w["height"])
+    elif name in ("ultra", "ultra_lr"):
+        sc = synth.ultra_scene(w["n"], 2)
+        cams = synth.flythrough_cameras(60, w["width"], w["height"])
+    else:
+        sc = synth.tiny_scene(w["n"], 0)
+        cams = [synth.tiny_camera()] + synth.jittered_tiny_cameras(63, 1)
+    return sc, cams
+
+
+def dist_env():
+    n = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), n
+
+
+def start_clock_sampler(path, gpu_index):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                              "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except (OSError, FileNotFoundError):
+        return None, None
+
+
+def read_clocks(path):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+    except OSError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), d.get("sm_max_mhz", 2070.0), "measured"
+    except (OSError, ValueError):
+        return 6800.0, 2070.0, "fallback"
+
+
+def cpu_baseline(sc, cams, name, max_seconds=20.0):
+    """The oracle as it stands (binned FP64 mode) on the host cores, over a bounded
+    sample: whole frames of the same camera path until ~max_seconds."""
+    import oracle
+
+    oracle.build()
+    osc = oracle.OScene(sc)
+    cores = oracle.max_threads()
+    px = 0
+    t0 = time.perf_counter()
+    frames = 0
+    while frames < len(cams):
+        cam = cams[frames]
+        if name.startswith("ultra") and cam.width * cam.height > 600_000 and frames == 0:
+            # 1920x1080 over 6M Gaussians: one band of rows keeps the sample bounded
+            oracle.render_band(osc, cam, 0, cam.height // 8)
+            px += cam.width * (cam.height // 8)
+        else:
+            oracle.render(osc, cam)
+            px += cam.width * cam.height
+        frames += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "sample": "%d frame(s) of the %s camera path (%d px) in %.1f s, FP64 binned oracle" % (
+                frames, name, px, dt)}
+
+
+def run_reference(args):
+    """--impl reference: the CPU FP64 oracle timed on the same workload, metric and
+    unit; each step renders a band of rows of one frame (bounded)."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    sc, cams = make_workload(args.workload)
+    osc = oracle.OScene(sc)
+    cores = oracle.max_threads()
+    band = max(1, cams[0].height // 16)
+
+    def step(i):
+        cam = cams[i % len(cams)]
+        y0 = (i * band) % cam.height
+        oracle.render_band(osc, cam, y0, min(cam.height, y0 + band))
+        return cam.width * (min(cam.height, y0 + band) - y0)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    px = 0
+    for i in range(args.steps):
+        px += step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    v = px / dt / 1e6
+    line = {"metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
+                       "step": "one band of %d rows of a frame" % band},
+            "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d steps x %d rows" % (args.steps, band)},
+            "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def algorithmic(stage, w, deg, n, K_avg, V_avg, passes, pixels, pairs):
+    """Algorithmic work of one launch of `stage` (bytes, or FP32 ops for compositing)."""
+    sh_bytes = 12 * (deg + 1) ** 2
+    if stage == "project":
+        return "hbm", 12.0 * n + (12 + 16 + 4 + sh_bytes + 48) * V_avg
+    if stage == "sort":
+        return "hbm", K_avg * (8 + 24 * passes)
+    if stage == "duplicate":
+        return "hbm", 16.0 * V_avg + 12.0 * K_avg + 4.0 * n
+    if stage == "ranges":
+        return "hbm", 8.0 * K_avg
+    if stage == "scan":
+        return "hbm", 8.0 * n / 1024
+    # composite: FP32 operations of the per-pair work
+    return "alu", pairs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2605_11489_gb300 import abi, api, synth  # noqa: F401
+
+    sc, cams = make_workload(args.workload)
+    W, H = cams[0].width, cams[0].height
+    stream = torch.cuda.Stream()
+    ctx = api.Context(local_rank)
+    with torch.cuda.stream(stream):
+        scene = api.Scene.from_arrays(sc)
+        out = api.alloc_outputs(W, H)
+    stream.synchronize()
+    # pre-pass (untimed): plain renders of every camera for the instance counts
+    for cam in cams:
+        ctx.forward(scene, cam, out=out, stream=stream)
+    pre = ctx.stats(reset=True, stream=stream)
+    capacity = int(pre["instances_max"] * 1.25) + 4096
+    graph = ctx.graph(scene, cams[0], out, capacity=capacity, timed=True, stream=stream)
+    for i in range(args.warmup):
+        graph.render(cams[i % len(cams)], stream=stream)
+    graph.stats(reset=True, stream=stream)
+
+    clk_path = os.path.join(tempfile.gettempdir(), "gsr_clocks_%d_%d.csv" % (os.getpid(), rank))
+    smi, smi_f = start_clock_sampler(clk_path, local_rank)
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        graph.render(cams[(args.warmup + i) % len(cams)], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        torch.distributed.barrier()
+    if smi:
+        smi.terminate()
+        smi.wait()
+        smi_f.close()
+    clocks = read_clocks(clk_path)
+    st = graph.stats(reset=True, stream=stream)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    pixels = W * H * args.steps * world
+    value = pixels / (ms * 1e-3) / 1e6
+
+    # per-stage times from events recorded inside the timed replays
+    stage_ms = st["stage_ms"]
+    frames = max(st["frames"], 1)
+    K_avg = st["instances_total"] / frames
+    V_avg = st["visible_total"] / frames
+    n_tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    passes = math.ceil((32 + max(1, math.ceil(math.log2(max(n_tiles, 2))))) / 8)
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    hbm_peak, sm_max_mhz, peak_src = measured_peaks()
+    bound, amount = algorithmic(dom, (W, H), sc.deg, sc.n, K_avg, V_avg, passes, W * H, 0.0)
+    if bound == "hbm":
+        achieved = amount / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": amount, "launch_ms": stage_ms[dom]}
+    else:
+        roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "launch_ms": stage_ms[dom]}
+
+    # end to end through the public API: camera in from the host, planes out to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in out.items()}
+        e2e_steps = min(args.steps, 30)
+        for i in range(2):
+            ctx.forward_to_host(scene, cams[i], host, stream=stream)
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            ctx.forward_to_host(scene, cams[i % len(cams)], host, stream=stream)
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": W * H * e2e_steps * world / dt / 1e6, "unit": "Mpix/s",
+               "h2d_bytes_per_step": GS_CAMERA_BYTES, "d2h_bytes_per_step": 11 * W * H * 4,
+               "path": "gs_render_forward_to_host (plain forward + D2H of rgb, dC/dx, dC/dy, depth, alpha)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc, cams, args.workload)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
+                           "width": W, "height": H, "gaussians": sc.n, "sh_degree": sc.deg,
+                           "tile": 16, "batch": 64, "path": "CUDA graph replay per frame",
+                           "l2": "inputs larger than L2 (scene %.0f MB)" % (sc.nbytes() / 1e6),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "frames_per_s": 1e3 * args.steps * world / ms,
+                "stage_ms": stage_ms, "instances_per_frame": K_avg, "visible_per_frame": V_avg,
+                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+                "gpu_launches": args.steps * (6 + passes)}
+        print(json.dumps(line), flush=True)
+    graph.close()
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

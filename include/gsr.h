@@ -1,0 +1,244 @@
+/*
+ * gsr.h -- C ABI of the GB300 low-resolution 3D Gaussian Splatting render core
+ * (the render that feeds the super-sampling and frame-interpolation networks of
+ * 3DGS^3, arXiv 2605.11489).
+ *
+ * What it computes (paper Sec. 3, "Preliminaries"):
+ *   - Gaussians G(x) = exp(-1/2 (x - xc)^T Sigma^-1 (x - xc))              (Eq. 1)
+ *     with Sigma = R S S^T R^T (R from a quaternion, S = diag(exp(log_scale)))
+ *   - EWA splatting to screen-space conics, plus a 0.3 px^2 low-pass
+ *   - view-dependent colour c_i from SH coefficients (degree 0..3, +0.5, >= 0)
+ *   - depth sort: instances keyed by (tile id, fp32 depth), radix sorted
+ *   - front-to-back alpha blending I = sum_i c_i a_i T_i                   (Eq. 2)
+ *     a_i = min(0.99, opacity * G), skipped below 1/255, stop before T < 1e-4
+ *   - in the same pass, the analytic screen-space image gradients           (Eq. 3)
+ *     dI/dx = sum_i c_i (dT_i/dx a_i + T_i da_i/dx) with                    (Eq. 4)
+ *     dT_i/dx = -da_{i-1}/dx T_{i-1} + (1 - a_{i-1}) dT_{i-1}/dx (same in y),
+ *     plus depth = sum_i z_i a_i T_i and alpha = 1 - T_final.
+ *
+ * Conventions shared by every call:
+ *   - Device memory: every float pointer in gs_scene, gs_outputs and
+ *     gs_scene_grads is a CUDA device pointer owned by the caller. Planes are
+ *     fp32, attribute-planar (structure of arrays) with row stride n_pad
+ *     (n_pad % 4 == 0, n_pad >= n) and every base pointer 16-byte aligned.
+ *   - Image planes are planar fp32: rgb/dcdx/dcdy are [3][H][W], depth/alpha
+ *     [H][W], row-major, pixel (i, j) sampled at (i + 0.5, j + 0.5).
+ *   - Camera: OpenCV axes (x right, y down, z forward); viewmat is the
+ *     world->camera transform as a row-major 3x4 [R | t].
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream) unless stated otherwise.
+ *   - Every call returns a gs_status and never aborts. On error the contents
+ *     of the output buffers are unspecified; gs_last_error() returns a
+ *     thread-local message describing the last failure on the calling thread.
+ *   - A context is used by one host thread, and its calls go to one stream
+ *     (or the caller orders the streams it uses). The server is thread safe.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_NOT_READY = 1,          /* gs_server_poll: request still in flight */
+    GS_ERR_INVALID_ARG = -1,   /* bad pointer, size, alignment or option */
+    GS_ERR_OOM = -2,           /* device or host allocation failed */
+    GS_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    GS_ERR_TIMEOUT = -4,       /* a bounded device wait gave up */
+    GS_ERR_CAPACITY = -5,      /* instance list exceeded a fixed capacity */
+    GS_ERR_CANCELLED = -6      /* request cancelled or server shut down */
+} gs_status;
+
+typedef struct gs_context gs_context;
+typedef struct gs_fwd_state gs_fwd_state;
+typedef struct gs_graph gs_graph;
+typedef struct gs_server gs_server;
+typedef void *gs_stream; /* cudaStream_t */
+
+/* Gaussians (Sec. 3: mean, rotation + scale, opacity, SH coefficients). */
+typedef struct {
+    int64_t n;                    /* number of Gaussians (>= 0) */
+    int64_t n_pad;                /* plane stride, multiple of 4, >= n */
+    int32_t sh_degree;            /* 0..3; (sh_degree+1)^2 coefficients per channel */
+    int32_t _reserved;
+    const float *means;           /* [3][n_pad]  x, y, z */
+    const float *log_scales;      /* [3][n_pad]  log of per-axis scale */
+    const float *quats;           /* [4][n_pad]  w, x, y, z, any nonzero norm */
+    const float *opacity_logits;  /* [n_pad]     opacity = sigmoid(logit) */
+    const float *sh;              /* [(deg+1)^2][3][n_pad], l-major, m = -l..l */
+} gs_scene;
+
+/* Pinhole camera and output resolution. */
+typedef struct {
+    float viewmat[12];            /* world -> camera, row-major 3x4 [R | t] */
+    float fx, fy, cx, cy;         /* focal lengths and principal point, pixels */
+    float near_plane;             /* Gaussians with camera z <= near are culled */
+    int32_t width, height;        /* 1..65535 */
+} gs_camera;
+
+enum {
+    GS_EMIT_BWD_STATE = 1u,       /* keep what gs_render_backward needs */
+    GS_TIME_STAGES = 2u           /* record CUDA events at every stage boundary (see gs_frame_stats) */
+};
+
+typedef struct {
+    int32_t tile;                 /* tile side: 8, 16 or 32; 0 = autotuned/default */
+    int32_t batch;                /* Gaussians per shared-memory batch: 32/64/128/256; 0 = default */
+    float bg[3];                  /* background colour */
+    uint32_t flags;               /* GS_EMIT_* */
+} gs_render_opts;
+
+/* Caller-owned device outputs; a NULL plane is not written (and, for dcdx and
+ * dcdy both NULL, the gradient recursion is not evaluated). */
+typedef struct {
+    float *rgb;    /* [3][H][W] */
+    float *dcdx;   /* [3][H][W]  dI/dx, Eq. 3 */
+    float *dcdy;   /* [3][H][W]  dI/dy */
+    float *depth;  /* [H][W]     sum z_i a_i T_i */
+    float *alpha;  /* [H][W]     1 - T_final */
+} gs_outputs;
+
+/* Per-parameter gradients, same layout and stride as gs_scene (caller-owned,
+ * accumulated with +=, so the caller zeroes them). NULL planes are skipped. */
+typedef struct {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logits;
+    float *sh;
+} gs_scene_grads;
+
+/* Read-only view of a forward state's device buffers (inspection and tests). */
+typedef struct {
+    int64_t n_instances;          /* K: (Gaussian, tile) pairs */
+    int64_t n_visible;            /* Gaussians that survived culling */
+    int32_t n_tiles, tiles_x, tiles_y, tile;
+    const uint64_t *keys;         /* [K] sorted (tile << 32) | fp32 bits of depth */
+    const uint32_t *vals;         /* [K] Gaussian index of each sorted key */
+    const uint32_t *ranges;       /* [n_tiles][2] [start, end) into keys */
+    const uint32_t *ntiles;       /* [n] tiles touched by each Gaussian (0 = culled) */
+    const float *records;         /* [n][12] u, v, conic a, b, c, opacity, depth, r, g, b, rect, rect */
+    const float *final_T;         /* [H][W] (with GS_EMIT_BWD_STATE) */
+    const uint32_t *n_contrib;    /* [H][W] list positions walked up to the last blended one */
+} gs_state_view;
+
+/* Counters of the frames rendered since the last reset, and (with
+ * GS_TIME_STAGES) the mean per-frame device time of each stage, from CUDA
+ * events recorded on the launch stream at the stage boundaries:
+ * [0] projection + SH (K1), [1] scan (K2), [2] key duplication (K3),
+ * [3] radix sort (K4), [4] tile ranges (K5), [5] compositing + gradients (K6). */
+typedef struct {
+    int64_t frames;               /* frames since the last reset */
+    int64_t instances_total;      /* sum over those frames of K, the (Gaussian, tile) instances */
+    int64_t visible_total;        /* sum of Gaussians that survived culling */
+    int64_t instances_max;        /* largest K */
+    double stage_ms[6];
+    int64_t timed_frames;         /* frames that carried stage events */
+} gs_frame_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a render context on CUDA device `device`. The context owns its
+ * workspace (per-Gaussian records, instance keys, sort buffers), grown on
+ * demand with cudaMalloc and freed by gs_context_destroy. */
+gs_status gs_context_create(int device, gs_context **ctx);
+gs_status gs_context_destroy(gs_context *ctx);
+
+/* Forward render (Eq. 1-4). Enqueues projection + SH colour, tile-key
+ * duplication, the (tile, depth) radix sort, tile ranges and the
+ * compositing+gradient pass on `stream`. It synchronises `stream` once,
+ * after the instance count is known, to size the sort buffers.
+ * If `state` is non-NULL a gs_fwd_state is returned that owns the buffers the
+ * backward pass needs (free with gs_state_free); GS_EMIT_BWD_STATE must be set.
+ * Errors: GS_ERR_INVALID_ARG (NULL scene/camera/opts/outputs, misaligned or
+ * negative sizes, unsupported tile/batch/degree), GS_ERR_OOM, GS_ERR_CUDA,
+ * GS_ERR_TIMEOUT (a bounded device wait gave up). */
+gs_status gs_render_forward(gs_context *ctx, const gs_scene *scene, const gs_camera *cam,
+                            const gs_render_opts *opts, const gs_outputs *out, gs_fwd_state **state,
+                            gs_stream stream);
+
+/* Same as gs_render_forward, but the outputs are HOST buffers (pinned memory
+ * recommended): the call renders into context-owned device planes, copies
+ * them to the host and synchronises `stream` before returning. */
+gs_status gs_render_forward_to_host(gs_context *ctx, const gs_scene *scene, const gs_camera *cam,
+                                    const gs_render_opts *opts, const gs_outputs *host_out,
+                                    gs_stream stream);
+
+/* Backward of gs_render_forward: the reverse walk of Eq. 2-4 with the upstream
+ * gradients of rgb, dcdx, dcdy, depth and alpha (`grad_in` planes, device,
+ * same layout as the outputs; NULL = zero), then the chain rule to means,
+ * log-scales, quaternions, opacity logits and SH coefficients. Adds into
+ * `grads` (caller zeroes). `scene` must be the one given to the forward.
+ * Errors: GS_ERR_INVALID_ARG (state without GS_EMIT_BWD_STATE, NULL args),
+ * GS_ERR_CUDA. */
+gs_status gs_render_backward(gs_context *ctx, const gs_fwd_state *state, const gs_scene *scene,
+                             const gs_outputs *grad_in, const gs_scene_grads *grads, gs_stream stream);
+
+gs_status gs_state_view_get(const gs_fwd_state *state, gs_state_view *view);
+/* Synchronises `stream` and returns the context's frame statistics (plain
+ * forward calls); `reset` != 0 clears them afterwards. */
+gs_status gs_context_stats(gs_context *ctx, gs_stream stream, int reset, gs_frame_stats *stats);
+gs_status gs_state_free(gs_fwd_state *state);
+
+/* ---------------------------------------------------------------- CUDA graphs
+ * A graph replays the whole forward (same scene, resolution, options and
+ * output buffers) with a new camera per frame and no host synchronisation.
+ * The instance buffers have a fixed `capacity` (0 = 4 * n); a frame whose
+ * instance count exceeds it renders incompletely and is reported by
+ * gs_graph_check as GS_ERR_CAPACITY. */
+gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camera *cam,
+                          const gs_render_opts *opts, const gs_outputs *out, int64_t capacity,
+                          gs_stream stream, gs_graph **graph);
+/* Replay with camera `cam` (same width/height as at creation). Asynchronous. */
+gs_status gs_graph_render(gs_graph *graph, const gs_camera *cam, gs_stream stream);
+/* Synchronises `stream`; GS_ERR_CAPACITY if any replay since the last check
+ * overflowed; `max_instances` (nullable) receives the largest count seen. */
+gs_status gs_graph_check(gs_graph *graph, gs_stream stream, int64_t *max_instances);
+/* Synchronises `stream` and returns the statistics of the replays since the
+ * last reset (stage times if the graph was created with GS_TIME_STAGES);
+ * returns the replays' error status like gs_graph_check. */
+gs_status gs_graph_stats(gs_graph *graph, gs_stream stream, int reset, gs_frame_stats *stats);
+gs_status gs_graph_destroy(gs_graph *graph);
+
+/* ---------------------------------------------------------------- autotuner
+ * Times the forward for every tile in {8, 16, 32} and batch in
+ * {32, 64, 128, 256} (CUDA events, `iters` frames each, after one warm-up)
+ * and records the fastest in the context's cache, keyed by (W, H, N bucket,
+ * SH degree); later calls with tile = 0 / batch = 0 use it. Synchronous. */
+gs_status gs_autotune(gs_context *ctx, const gs_scene *scene, const gs_camera *cam,
+                      const gs_outputs *out, int iters, gs_stream stream, int32_t *best_tile,
+                      int32_t *best_batch, float *best_ms);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching over resident scenes: requests (scene, camera, options,
+ * caller-owned device outputs) are queued by gs_server_submit; a scheduler
+ * thread admits them as in-flight slots and sort-buffer memory free up,
+ * projects and sorts each on its own stream, and composites every ready
+ * request's tiles in one persistent launch driven by a (request, tile) work
+ * list, so new requests' preparation overlaps other requests' compositing. */
+gs_status gs_server_create(int device, size_t sort_budget_bytes, int max_inflight, gs_server **srv);
+/* Copies the scene (device pointers) into server-owned memory. */
+gs_status gs_server_load_scene(gs_server *srv, const gs_scene *scene, int32_t *scene_id);
+gs_status gs_server_submit(gs_server *srv, int32_t scene_id, const gs_camera *cam,
+                           const gs_render_opts *opts, const gs_outputs *out, uint64_t *req_id);
+/* GS_OK (done, latency in ms since submit), GS_NOT_READY, or the request's
+ * error. A finished request is forgotten after the first GS_OK/error poll. */
+gs_status gs_server_poll(gs_server *srv, uint64_t req_id, double *latency_ms);
+gs_status gs_server_cancel(gs_server *srv, uint64_t req_id);
+/* Blocks until every submitted request has finished. */
+gs_status gs_server_drain(gs_server *srv);
+gs_status gs_server_destroy(gs_server *srv);
+
+/* ---------------------------------------------------------------- misc */
+const char *gs_last_error(void);
+const char *gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSR_H */

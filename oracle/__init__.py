@@ -65,6 +65,7 @@ def lib():
             L.or_project.argtypes = [P, P, C.c_int32] + [P] * 10
             L.or_render.argtypes = [P, P, C.c_int] + [P] * 8
             L.or_render_pixels.argtypes = [P, P, C.c_int64, P, P, P, P]
+            L.or_render_band.argtypes = [P, P, C.c_int, C.c_int, P, P, P, P, P]
             L.or_count_instances.restype = C.c_int64
             L.or_count_instances.argtypes = [P, P, C.c_int32]
             L.or_keys.argtypes = [P, P, C.c_int32, C.c_int64, P, P, P]
@@ -166,6 +167,20 @@ def render(scene, cam, bg=(0.0, 0.0, 0.0), mode: str = "binned") -> dict:
                                                   "n_blended", "sig")])
     if rc != 0:
         raise RuntimeError("or_render failed: %d" % rc)
+    return out
+
+
+def render_band(scene, cam, y0: int, y1: int, bg=(0.0, 0.0, 0.0)) -> dict:
+    """Binned FP64 render of rows [y0, y1) (rest of the planes left at zero)."""
+    s = _as_oscene(scene)
+    H, W = cam.height, cam.width
+    out = dict(rgb=np.zeros((3, H, W)), dcdx=np.zeros((3, H, W)), dcdy=np.zeros((3, H, W)),
+               depth=np.zeros((H, W)), alpha=np.zeros((H, W)))
+    st, cm = s.struct(), _cam(cam, bg)
+    rc = lib().or_render_band(C.byref(st), C.byref(cm), int(y0), int(y1),
+                              *[_ptr(out[k]) for k in ("rgb", "dcdx", "dcdy", "depth", "alpha")])
+    if rc != 0:
+        raise RuntimeError("or_render_band failed: %d" % rc)
     return out
 
 

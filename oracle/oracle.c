@@ -617,8 +617,28 @@ static int64_t max_bucket(const or_buckets *B)
 
 /* Full-frame render. mode 0 = brute force, 1 = binned. Planar outputs:
  * rgb/dcdx/dcdy [3][H][W], depth/alpha/final_T [H][W]; any may be NULL. */
+static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y0, int y1, double *rgb,
+                       double *dcdx, double *dcdy, double *depth, double *alpha, double *final_T,
+                       int32_t *n_blended, uint32_t *sig);
+
 int or_render(const or_scene *sc, const or_camera *cam, int mode, double *rgb, double *dcdx, double *dcdy,
               double *depth, double *alpha, double *final_T, int32_t *n_blended, uint32_t *sig)
+{
+    return render_rows(sc, cam, mode, 0, cam->height, rgb, dcdx, dcdy, depth, alpha, final_T, n_blended, sig);
+}
+
+/* Rows [y0, y1) of the frame (binned mode), written into full-size planes. */
+int or_render_band(const or_scene *sc, const or_camera *cam, int y0, int y1, double *rgb, double *dcdx,
+                   double *dcdy, double *depth, double *alpha)
+{
+    if (y0 < 0) y0 = 0;
+    if (y1 > cam->height) y1 = cam->height;
+    return render_rows(sc, cam, 1, y0, y1, rgb, dcdx, dcdy, depth, alpha, NULL, NULL, NULL);
+}
+
+static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y0, int y1, double *rgb,
+                       double *dcdx, double *dcdy, double *depth, double *alpha, double *final_T,
+                       int32_t *n_blended, uint32_t *sig)
 {
     const int W = cam->width, H = cam->height;
     const int64_t HW = (int64_t)W * H;
@@ -636,7 +656,7 @@ int or_render(const or_scene *sc, const or_camera *cam, int mode, double *rgb, d
         or_cand *buf = (or_cand *)malloc(sizeof(or_cand) * (size_t)(cap > 0 ? cap : 1));
         if (!buf) rc = -2;
 #pragma omp for schedule(dynamic, 1)
-        for (int py = 0; py < H; ++py) {
+        for (int py = y0; py < y1; ++py) {
             if (!buf) continue;
             for (int px = 0; px < W; ++px) {
                 int64_t len = mode == 1 ? pixel_list_binned(&F, &B, px, py, buf) : pixel_list_brute(&F, px, py, buf);

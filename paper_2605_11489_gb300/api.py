@@ -1,0 +1,384 @@
+"""Torch-facing wrapper of the C ABI: device memory and streams come from
+PyTorch, every computation runs in libgsr.so.
+
+    ctx = Context()                       # gs_context on the current device
+    scene = Scene.from_arrays(synth.tiny_scene())
+    out = ctx.forward(scene, cam)         # dict of planar fp32 tensors
+    rgb, dcdx, dcdy, depth, alpha = render(ctx, scene.params(), cam)   # autograd
+
+Layouts (include/gsr.h): scene planes [rows, n_pad] fp32 (16-byte aligned,
+n_pad % 4 == 0); images planar [3, H, W] / [H, W] fp32.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import glob
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import abi
+from .abi import GsCamera, GsOutputs, GsRenderOpts, GsScene, GsSceneGrads, GsStateView, check
+
+OUTPUT_KEYS = ("rgb", "dcdx", "dcdy", "depth", "alpha")
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+@dataclass
+class Scene:
+    """Gaussians resident on the device, attribute-planar (see include/gsr.h)."""
+    n: int
+    deg: int
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    logits: torch.Tensor
+    sh: torch.Tensor
+
+    @property
+    def n_pad(self) -> int:
+        return self.means.shape[1]
+
+    @staticmethod
+    def from_arrays(s, device="cuda") -> "Scene":
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        return Scene(s.n, s.deg, t(s.means), t(s.log_scales), t(s.quats), t(s.logits), t(s.sh))
+
+    @staticmethod
+    def from_tensors(n, deg, means, log_scales, quats, logits, sh) -> "Scene":
+        return Scene(n, deg, means, log_scales, quats, logits, sh)
+
+    def params(self):
+        return self.means, self.log_scales, self.quats, self.logits, self.sh
+
+    def struct(self) -> GsScene:
+        for t in self.params():
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError("scene planes must be contiguous fp32 CUDA tensors")
+        return GsScene(self.n, self.n_pad, self.deg, 0, _ptr(self.means), _ptr(self.log_scales), _ptr(self.quats),
+                       _ptr(self.logits), _ptr(self.sh))
+
+    def zeros_like_grads(self):
+        return tuple(torch.zeros_like(t) for t in self.params())
+
+
+def camera_struct(cam) -> GsCamera:
+    c = GsCamera()
+    for k in range(12):
+        c.viewmat[k] = float(cam.viewmat[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.near_plane = float(cam.near)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def opts_struct(tile=0, batch=0, bg=(0.0, 0.0, 0.0), state=False, timed=False) -> GsRenderOpts:
+    o = GsRenderOpts()
+    o.tile, o.batch = int(tile), int(batch)
+    for k in range(3):
+        o.bg[k] = float(bg[k])
+    o.flags = (abi.GS_EMIT_BWD_STATE if state else 0) | (abi.GS_TIME_STAGES if timed else 0)
+    return o
+
+
+def _stats_dict(st) -> dict:
+    return dict(frames=st.frames, instances_total=st.instances_total, visible_total=st.visible_total,
+                instances_max=st.instances_max, timed_frames=st.timed_frames,
+                stage_ms={k: st.stage_ms[i] for i, k in enumerate(abi.STAGES)})
+
+
+def alloc_outputs(width, height, keys=OUTPUT_KEYS, device="cuda") -> dict:
+    shp = {"rgb": (3, height, width), "dcdx": (3, height, width), "dcdy": (3, height, width),
+           "depth": (height, width), "alpha": (height, width)}
+    return {k: torch.empty(shp[k], dtype=torch.float32, device=device) for k in keys}
+
+
+def outputs_struct(out: dict) -> GsOutputs:
+    return GsOutputs(*[_ptr(out.get(k)) for k in OUTPUT_KEYS])
+
+
+# ----------------------------------------------------------------------------- raw device copies (inspection)
+_cudart = None
+
+
+def _cudart_lib():
+    global _cudart
+    if _cudart is None:
+        cands = []
+        tdir = os.path.dirname(torch.__file__)
+        cands += glob.glob(os.path.join(os.path.dirname(tdir), "nvidia", "cu*", "lib", "libcudart.so*"))
+        cands += glob.glob(os.path.join(os.path.dirname(tdir), "nvidia", "cuda_runtime", "lib", "libcudart.so*"))
+        cands += glob.glob(os.path.join(tdir, "lib", "libcudart*.so*"))
+        cands += glob.glob("/usr/local/cuda/lib64/libcudart.so*")
+        for c in cands:
+            try:
+                _cudart = C.CDLL(c)
+                break
+            except OSError:
+                continue
+        if _cudart is None:
+            raise RuntimeError("libcudart not found")
+        _cudart.cudaMemcpy.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
+        _cudart.cudaMemcpy.restype = C.c_int
+    return _cudart
+
+
+def device_to_numpy(ptr: int, count: int, dtype) -> np.ndarray:
+    """Copy `count` elements of `dtype` from a raw device pointer (synchronous)."""
+    torch.cuda.synchronize()
+    a = np.empty(max(int(count), 0), dtype=dtype)
+    if count > 0:
+        rc = _cudart_lib().cudaMemcpy(a.ctypes.data, ptr, a.nbytes, 2)
+        if rc != 0:
+            raise RuntimeError("cudaMemcpy failed: %d" % rc)
+    return a
+
+
+# ----------------------------------------------------------------------------- context
+class State:
+    """Buffers a forward kept for the backward pass (gs_fwd_state)."""
+
+    def __init__(self, handle: int, cam):
+        self.handle = C.c_void_p(handle)
+        self.cam = cam
+
+    def view(self) -> dict:
+        v = GsStateView()
+        check(abi.lib().gs_state_view_get(self.handle, C.byref(v)))
+        K = v.n_instances
+        hw = self.cam.width * self.cam.height
+        out = dict(n_instances=K, n_tiles=v.n_tiles, tiles_x=v.tiles_x, tiles_y=v.tiles_y, tile=v.tile,
+                   keys=device_to_numpy(v.keys, K, np.uint64), vals=device_to_numpy(v.vals, K, np.uint32),
+                   ranges=device_to_numpy(v.ranges, 2 * v.n_tiles, np.uint32).reshape(-1, 2))
+        if v.final_T:
+            out["final_T"] = device_to_numpy(v.final_T, hw, np.float32).reshape(self.cam.height, self.cam.width)
+            out["n_contrib"] = device_to_numpy(v.n_contrib, hw, np.uint32).reshape(self.cam.height, self.cam.width)
+        out["_records_ptr"] = v.records
+        out["_ntiles_ptr"] = v.ntiles
+        return out
+
+    def records(self, n: int) -> np.ndarray:
+        v = GsStateView()
+        check(abi.lib().gs_state_view_get(self.handle, C.byref(v)))
+        return device_to_numpy(v.records, 12 * n, np.float32).reshape(n, 12)
+
+    def ntiles(self, n: int) -> np.ndarray:
+        v = GsStateView()
+        check(abi.lib().gs_state_view_get(self.handle, C.byref(v)))
+        return device_to_numpy(v.ntiles, n, np.uint32)
+
+    def free(self):
+        if self.handle:
+            abi.lib().gs_state_free(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """A gs_context: owns the render workspace on one device."""
+
+    def __init__(self, device: int | None = None):
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = C.c_void_p()
+        check(abi.lib().gs_context_create(self.device, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            abi.lib().gs_context_destroy(self.h)
+            self.h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, scene: Scene, cam, tile=0, batch=0, bg=(0.0, 0.0, 0.0), keys=OUTPUT_KEYS, out=None,
+                state=False, timed=False, stream=None):
+        """Render; returns the output dict (and a State if state=True)."""
+        if out is None:
+            out = alloc_outputs(cam.width, cam.height, keys)
+        sc, cm = scene.struct(), camera_struct(cam)
+        op, ou = opts_struct(tile, batch, bg, state, timed), outputs_struct(out)
+        hs = C.c_void_p()
+        check(abi.lib().gs_render_forward(self.h, C.byref(sc), C.byref(cm), C.byref(op), C.byref(ou),
+                                          C.byref(hs) if state else None, _stream_ptr(stream)))
+        if state:
+            return out, State(hs.value, cam)
+        return out
+
+    def forward_to_host(self, scene: Scene, cam, host_out: dict, tile=0, batch=0, bg=(0.0, 0.0, 0.0), stream=None):
+        """Render into HOST tensors (pinned recommended); synchronous."""
+        for t in host_out.values():
+            if t.is_cuda or not t.is_contiguous() or t.dtype != torch.float32:
+                raise ValueError("host outputs must be contiguous fp32 CPU tensors")
+        sc, cm, op, ou = scene.struct(), camera_struct(cam), opts_struct(tile, batch, bg), outputs_struct(host_out)
+        check(abi.lib().gs_render_forward_to_host(self.h, C.byref(sc), C.byref(cm), C.byref(op), C.byref(ou),
+                                                  _stream_ptr(stream)))
+        return host_out
+
+    def backward(self, state: State, scene: Scene, grads_in: dict, grads=None, stream=None):
+        """Adds d(sum <grads_in, outputs>)/d(params) into `grads` (zeros if None)."""
+        if grads is None:
+            grads = scene.zeros_like_grads()
+        gi = outputs_struct(grads_in)
+        go = GsSceneGrads(*[_ptr(g) for g in grads])
+        sc = scene.struct()
+        check(abi.lib().gs_render_backward(self.h, state.handle, C.byref(sc), C.byref(gi), C.byref(go),
+                                           _stream_ptr(stream)))
+        return grads
+
+    def stats(self, reset=False, stream=None) -> dict:
+        st = abi.GsFrameStats()
+        check(abi.lib().gs_context_stats(self.h, _stream_ptr(stream), int(reset), C.byref(st)))
+        return _stats_dict(st)
+
+    def graph(self, scene: Scene, cam, out: dict, capacity=0, tile=0, batch=0, bg=(0.0, 0.0, 0.0), timed=False,
+              stream=None):
+        return Graph(self, scene, cam, out, capacity, tile, batch, bg, stream, timed)
+
+    def autotune(self, scene: Scene, cam, out: dict, iters=3, stream=None):
+        t, b, ms = C.c_int32(), C.c_int32(), C.c_float()
+        sc, cm, ou = scene.struct(), camera_struct(cam), outputs_struct(out)
+        check(abi.lib().gs_autotune(self.h, C.byref(sc), C.byref(cm), C.byref(ou), int(iters), _stream_ptr(stream),
+                                    C.byref(t), C.byref(b), C.byref(ms)))
+        return t.value, b.value, ms.value
+
+
+class Graph:
+    """Captured whole-frame forward replayed with a new camera per frame."""
+
+    def __init__(self, ctx: Context, scene: Scene, cam, out: dict, capacity, tile, batch, bg, stream, timed=False):
+        self.ctx, self.scene, self.out = ctx, scene, out  # keep the buffers alive
+        sc, cm = scene.struct(), camera_struct(cam)
+        op, ou = opts_struct(tile, batch, bg, timed=timed), outputs_struct(out)
+        h = C.c_void_p()
+        check(abi.lib().gs_graph_create(ctx.h, C.byref(sc), C.byref(cm), C.byref(op), C.byref(ou), int(capacity),
+                                        _stream_ptr(stream), C.byref(h)))
+        self.h = h
+
+    def render(self, cam, stream=None):
+        cm = camera_struct(cam)
+        check(abi.lib().gs_graph_render(self.h, C.byref(cm), _stream_ptr(stream)))
+
+    def check(self, stream=None) -> int:
+        mx = C.c_int64()
+        check(abi.lib().gs_graph_check(self.h, _stream_ptr(stream), C.byref(mx)))
+        return mx.value
+
+    def stats(self, reset=False, stream=None) -> dict:
+        st = abi.GsFrameStats()
+        check(abi.lib().gs_graph_stats(self.h, _stream_ptr(stream), int(reset), C.byref(st)))
+        return _stats_dict(st)
+
+    def close(self):
+        if self.h:
+            abi.lib().gs_graph_destroy(self.h)
+            self.h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching render server (gs_server_*)."""
+
+    def __init__(self, device: int | None = None, sort_budget_bytes: int = 1 << 30, max_inflight: int = 8):
+        dev = torch.cuda.current_device() if device is None else int(device)
+        h = C.c_void_p()
+        check(abi.lib().gs_server_create(dev, C.c_size_t(int(sort_budget_bytes)), int(max_inflight), C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def load_scene(self, scene: Scene) -> int:
+        sid = C.c_int32()
+        sc = scene.struct()
+        torch.cuda.synchronize()
+        check(abi.lib().gs_server_load_scene(self.h, C.byref(sc), C.byref(sid)))
+        return sid.value
+
+    def submit(self, scene_id: int, cam, out: dict, bg=(0.0, 0.0, 0.0)) -> int:
+        rid = C.c_uint64()
+        cm, op, ou = camera_struct(cam), opts_struct(0, 0, bg), outputs_struct(out)
+        check(abi.lib().gs_server_submit(self.h, int(scene_id), C.byref(cm), C.byref(op), C.byref(ou), C.byref(rid)))
+        self._keep[rid.value] = out
+        return rid.value
+
+    def poll(self, rid: int):
+        """Returns (status, latency_ms); status GS_NOT_READY while in flight."""
+        lat = C.c_double()
+        st = abi.lib().gs_server_poll(self.h, C.c_uint64(rid), C.byref(lat))
+        if st != abi.GS_NOT_READY:
+            self._keep.pop(rid, None)
+        return st, lat.value
+
+    def cancel(self, rid: int) -> int:
+        return abi.lib().gs_server_cancel(self.h, C.c_uint64(rid))
+
+    def drain(self):
+        check(abi.lib().gs_server_drain(self.h))
+
+    def close(self):
+        if self.h:
+            abi.lib().gs_server_destroy(self.h)
+            self.h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- autograd
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, means, log_scales, quats, logits, sh, gctx, n, deg, cam, bg, tile, batch):
+        scene = Scene(n, deg, means.contiguous(), log_scales.contiguous(), quats.contiguous(), logits.contiguous(),
+                      sh.contiguous())
+        out, state = gctx.forward(scene, cam, tile=tile, batch=batch, bg=bg, state=True)
+        fctx.gctx, fctx.state, fctx.scene = gctx, state, scene
+        fctx.mark_non_differentiable()
+        return tuple(out[k] for k in OUTPUT_KEYS)
+
+    @staticmethod
+    def backward(fctx, g_rgb, g_dcdx, g_dcdy, g_depth, g_alpha):
+        gi = {}
+        for k, g in zip(OUTPUT_KEYS, (g_rgb, g_dcdx, g_dcdy, g_depth, g_alpha)):
+            if g is not None:
+                gi[k] = g.contiguous()
+        grads = fctx.gctx.backward(fctx.state, fctx.scene, gi)
+        fctx.state.free()
+        return (*grads, None, None, None, None, None, None, None)
+
+
+def render(gctx: Context, params, cam, n: int | None = None, deg: int | None = None, bg=(0.0, 0.0, 0.0), tile=0,
+           batch=0):
+    """Differentiable render: params = (means [3,n_pad], log_scales [3,n_pad], quats [4,n_pad],
+    logits [n_pad], sh [K,3,n_pad]); returns (rgb, dcdx, dcdy, depth, alpha)."""
+    means, log_scales, quats, logits, sh = params
+    if n is None:
+        n = means.shape[1]
+    if deg is None:
+        deg = int(round(sh.shape[0] ** 0.5)) - 1
+    return _RenderFn.apply(means, log_scales, quats, logits, sh, gctx, int(n), int(deg), cam, tuple(bg), int(tile),
+                           int(batch))

@@ -1,0 +1,163 @@
+// Tile binning: instance offsets (K2), (tile, depth) key duplication (K3) and
+// per-tile ranges of the sorted keys (K5). The depth sort itself (paper Sec. 3:
+// "the resulting 2D Gaussians are depth-sorted") is a radix sort over these
+// keys (sort.cu); binning by tile lets compositing walk only the Gaussians
+// whose support reaches each tile.
+//
+// The scan is split to avoid a separate pass over the per-Gaussian counts: the
+// projection kernel already reduced tiles-touched per block of 1024 Gaussians;
+// K2 scans those block sums in one CTA; K3 re-reads the counts it needs anyway
+// and finishes the scan inside each block.
+#include "gsr_internal.cuh"
+
+namespace gsr {
+namespace {
+
+constexpr int kScanThreads = 1024;
+
+// Exclusive scan of per-block tile counts; writes offsets, K = total, and the
+// capacity-clamped K used downstream (with an overflow bit if clamped).
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const uint32_t *__restrict__ sums, int nb,
+                                                              uint32_t *__restrict__ offs, uint32_t *counters,
+                                                              unsigned long long capacity)
+{
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    const int per = (nb + kScanThreads - 1) / kScanThreads;
+    const int b0 = threadIdx.x * per;
+    unsigned long long local = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nb) local += sums[b0 + k];
+    // inclusive warp scan
+    unsigned long long v = local;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long run = v - local + (warp > 0 ? s_warp[warp - 1] : 0ull);
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nb) {
+            offs[b0 + k] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
+            run += sums[b0 + k];
+        }
+    if (threadIdx.x == kScanThreads - 1) {
+        const unsigned long long total = run;
+        counters[kCntTotal] = (uint32_t)(total & 0xffffffffull);
+        counters[kCntTotalHi] = (uint32_t)(total >> 32);
+        const unsigned long long eff = total < capacity ? total : capacity;
+        counters[kCntEff] = (uint32_t)eff;
+        if (total > capacity) atomicOr(&counters[kCntErr], kErrCapacity);
+        atomicMax(&counters[kCntMaxTotal], (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull));
+        atomicAdd(reinterpret_cast<unsigned long long *>(counters + kCntSumK), total);
+        atomicAdd(&counters[kCntFrames], 1u);
+    }
+}
+
+// One thread per quad of Gaussians (same partition as the projection); emits
+// key = (tile id << 32) | fp32 bits of depth, val = Gaussian index, for every
+// tile of each Gaussian's support rectangle, in index order.
+__global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__restrict__ ntiles,
+                                                            const uint4 *__restrict__ bin,
+                                                            const uint32_t *__restrict__ block_offs, int64_t n,
+                                                            int tile_shift, int tiles_x, uint64_t *__restrict__ keys,
+                                                            uint32_t *__restrict__ vals, unsigned long long capacity,
+                                                            uint32_t *counters)
+{
+    __shared__ uint32_t s_warp[kProjThreads / 32];
+    const int64_t i0 = ((int64_t)blockIdx.x * kProjThreads + threadIdx.x) * 4;
+    uint4 nt = make_uint4(0, 0, 0, 0);
+    if (i0 < n) nt = *reinterpret_cast<const uint4 *>(ntiles + i0);
+    const uint32_t mine = nt.x + nt.y + nt.z + nt.w;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t v = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += s_warp[w];
+    unsigned long long off = (unsigned long long)block_offs[blockIdx.x] + before + (v - mine);
+    if (mine == 0) return;
+    const uint32_t cnt[4] = {nt.x, nt.y, nt.z, nt.w};
+    bool overflow = false;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        if (cnt[g] == 0) continue;
+        const uint4 b = bin[i0 + g];
+        const int x0 = (b.y & 0xFFFFu) >> tile_shift, y0 = (b.y >> 16) >> tile_shift;
+        const int x1 = (b.z & 0xFFFFu) >> tile_shift, y1 = (b.z >> 16) >> tile_shift;
+        const uint32_t idx = (uint32_t)(i0 + g);
+        for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx) {
+                if (off < capacity) {
+                    keys[off] = ((uint64_t)(uint32_t)(ty * tiles_x + tx) << 32) | (uint64_t)b.x;
+                    vals[off] = idx;
+                } else {
+                    overflow = true;
+                }
+                ++off;
+            }
+    }
+    if (overflow) atomicOr(&counters[kCntErr], kErrCapacity);
+}
+
+__global__ void k_ranges(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ counters, uint2 *ranges)
+{
+    const uint32_t K = counters[kCntEff];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    const uint32_t t = (uint32_t)(keys[i] >> 32);
+    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = i;
+    if (i == K - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = i + 1;
+}
+
+}  // namespace
+
+cudaError_t launch_scan_blocks(const uint32_t *block_sums, int nblocks, uint32_t *block_offsets, uint32_t *counters,
+                               int64_t capacity, cudaStream_t s)
+{
+    k_scan_blocks<<<1, kScanThreads, 0, s>>>(block_sums, nblocks, block_offsets, counters,
+                                              (unsigned long long)capacity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_duplicate(const uint32_t *ntiles, const uint4 *bin, const uint32_t *block_offsets, int64_t n,
+                             int tile_shift, int tiles_x, uint64_t *keys, uint32_t *vals, int64_t capacity,
+                             uint32_t *counters, cudaStream_t s)
+{
+    const int nb = project_blocks(n);
+    if (nb == 0) return cudaSuccess;
+    k_duplicate<<<nb, kProjThreads, 0, s>>>(ntiles, bin, block_offsets, n, tile_shift, tiles_x, keys, vals,
+                                            (unsigned long long)capacity, counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const uint64_t *keys, const uint32_t *counters, int64_t max_k, uint2 *ranges, int n_tiles,
+                          cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
+    if (e != cudaSuccess) return e;
+    if (max_k <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t nb = (max_k + threads - 1) / threads;
+    k_ranges<<<(unsigned)nb, threads, 0, s>>>(keys, counters, ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace gsr

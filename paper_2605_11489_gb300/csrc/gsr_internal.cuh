@@ -1,0 +1,255 @@
+// Internal declarations shared by the render core's translation units.
+// Nothing here is part of the C ABI (include/gsr.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gsr.h"
+
+namespace gsr {
+
+// ---------------------------------------------------------------- constants
+// Rasterizer conventions (3DGS, which the paper builds on; Sec. 3 and Eq. 2):
+constexpr float kAlphaCap = 0.99f;          // a_i = min(0.99, o G)
+constexpr float kAlphaMin = 1.0f / 255.0f;  // skip a_i < 1/255
+constexpr float kTMin = 1e-4f;              // stop before T would fall below 1e-4
+constexpr int kProjThreads = 256;           // projection block: 256 threads x 4 Gaussians
+constexpr int kProjPerBlock = kProjThreads * 4;
+
+// Error bits written by kernels into a device status word.
+enum : uint32_t {
+    kErrSortTimeout = 1u,       // radix-sort lookback gave up waiting
+    kErrTmaTimeout = 2u,        // compositing waited too long for a staged batch
+    kErrCapacity = 4u,          // instance list exceeded the buffers' capacity
+    kErrQueueTimeout = 8u,      // serving work list wait gave up
+};
+
+// ---------------------------------------------------------------- device-side camera
+struct CamParams {
+    float vm[12];      // world -> camera [R | t], row-major
+    float fx, fy, cx, cy;
+    float near_plane;
+    float campos[3];   // camera centre in world space, -R^T t
+    int32_t width, height;
+    int32_t tile_shift;  // log2(tile)
+    int32_t tiles_x, tiles_y;
+};
+
+// Per-Gaussian compositing record, 48 bytes (3 x float4), written by the
+// projection kernel for visible Gaussians and gathered by compositing:
+//   r0 = (u, v, conic_a, conic_b)       projected centre, conic (Sigma2D^-1)
+//   r1 = (conic_c, opacity, depth, red)
+//   r2 = (green, blue, rect_lo, rect_hi)   rect as bits: x | y << 16 (inclusive)
+struct __align__(16) GaussRec {
+    float4 r0, r1, r2;
+};
+static_assert(sizeof(GaussRec) == 48, "record must be 48 bytes");
+
+// Per-Gaussian binning entry: (depth bits, rect_lo, rect_hi, 0).
+// Counters block (device, u32 words):
+enum CounterSlot : int {
+    kCntTotal = 0,      // K (instances) reported by the scan, before clamping
+    kCntTotalHi = 1,
+    kCntEff = 2,        // min(K, capacity): what sort/ranges/compositing use
+    kCntVisible = 3,    // visible Gaussians
+    kCntErr = 4,        // error bits
+    kCntMaxTotal = 5,   // largest K seen (graph replays)
+    kCntSumK = 6,       // u64 (slots 6-7): sum of K over frames since reset
+    kCntSumV = 8,       // u64 (slots 8-9): sum of visible Gaussians over frames since reset
+    kCntFrames = 10,    // frames since reset
+    kCntSlots = 16,
+    kCntPerFrame = 4,   // slots 0..3 are cleared at the start of every frame
+};
+
+// ---------------------------------------------------------------- status plumbing
+void set_error(const std::string &msg);
+gs_status fail(gs_status st, const std::string &msg);
+gs_status cuda_fail(cudaError_t e, const char *what);
+
+#define GSR_CUDA(call)                                     \
+    do {                                                   \
+        cudaError_t e__ = (call);                          \
+        if (e__ != cudaSuccess) return ::gsr::cuda_fail(e__, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------- shared host helpers (render.cu)
+CamParams make_cam(const gs_camera &c, int tile);
+gs_status check_scene(const gs_scene *s);
+gs_status check_cam(const gs_camera *c);
+int ilog2(int v);
+
+// ---------------------------------------------------------------- launchers
+struct ProjectArgs {
+    const float *means, *log_scales, *quats, *logits, *sh;
+    int64_t n, n_pad;
+    int deg;
+    CamParams cam;
+    GaussRec *rec;
+    uint4 *bin;
+    uint32_t *ntiles;
+    uint32_t *block_sums;
+    uint32_t *counters;  // visible count accumulates into kCntVisible / kCntSumV
+};
+int project_blocks(int64_t n);
+cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s);
+
+// scan of the projection's per-block sums -> per-block offsets and K
+cudaError_t launch_scan_blocks(const uint32_t *block_sums, int nblocks, uint32_t *block_offsets,
+                               uint32_t *counters, int64_t capacity, cudaStream_t s);
+// (tile, depth) key duplication
+cudaError_t launch_duplicate(const uint32_t *ntiles, const uint4 *bin, const uint32_t *block_offsets,
+                             int64_t n, int tile_shift, int tiles_x, uint64_t *keys, uint32_t *vals,
+                             int64_t capacity, uint32_t *counters, cudaStream_t s);
+// per-tile [start, end) from sorted keys
+cudaError_t launch_ranges(const uint64_t *keys, const uint32_t *counters, int64_t max_k, uint2 *ranges,
+                          int n_tiles, cudaStream_t s);
+
+// onesweep LSD radix sort of (keys, vals) on the low `bits` bits, K from counters[kCntEff]
+struct SortScratch {
+    uint32_t *hist;      // [8][256]
+    uint32_t *status;    // [passes][max_parts][256]
+    uint32_t *part_ctr;  // [8]
+    int64_t max_parts;
+};
+size_t sort_scratch_bytes(int64_t capacity);
+void sort_scratch_carve(void *base, int64_t capacity, SortScratch *s);
+int sort_passes(int bits);
+// Sorts keys[0]/vals[0] into the buffer pair returned in *result (0 or 1).
+cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *counters, uint32_t *err_word,
+                        int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s);
+
+struct CompositeArgs {
+    const GaussRec *rec;
+    const uint32_t *vals;
+    const uint2 *ranges;
+    int32_t width, height, tiles_x, tiles_y;
+    float bg[3];
+    float *rgb, *dcdx, *dcdy, *depth, *alpha;
+    float *final_T, *final_Tx, *final_Ty;  // backward state (nullable)
+    uint32_t *n_contrib;
+    uint32_t *err_word;
+};
+bool composite_supported(int tile, int batch);
+cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, cudaStream_t s);
+
+// serving: tiles of several requests from one (request, tile) work list
+struct ServeItem {  // one request's compositing description (device copy)
+    CompositeArgs args;
+    uint32_t first_item;  // prefix of tiles over the batch's requests
+    uint32_t n_items;
+};
+cudaError_t launch_composite_persistent(const ServeItem *reqs, int n_reqs, uint32_t total_items, int tile,
+                                        int batch, uint32_t *work_counter, int grid, cudaStream_t s);
+int composite_persistent_grid(int tile, int batch);
+
+// backward
+struct BackwardArgs {
+    // compositing side
+    const GaussRec *rec;
+    const uint32_t *vals;
+    const uint2 *ranges;
+    int32_t width, height, tiles_x, tiles_y, tile;
+    float bg[3];
+    const float *final_T, *final_Tx, *final_Ty;
+    const uint32_t *n_contrib;
+    const float *g_rgb, *g_dcdx, *g_dcdy, *g_depth, *g_alpha;
+    float *g2d;  // [n][10] per-Gaussian 2D adjoints: u, v, ca, cb, cc, o, z, r, g, b
+};
+cudaError_t launch_composite_backward(const BackwardArgs &a, cudaStream_t s);
+
+struct ProjectBwdArgs {
+    const float *means, *log_scales, *quats, *logits, *sh;
+    int64_t n, n_pad;
+    int deg;
+    CamParams cam;
+    const uint32_t *ntiles;
+    const float *g2d;
+    float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh;
+};
+cudaError_t launch_project_backward(const ProjectBwdArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase. Returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t max_tries)
+{
+    for (uint32_t t = 0; t < max_tries; ++t)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// TMA bulk copy (non-tensor) global -> this CTA's shared memory, completing
+// `bytes` transactions on `bar`. Both addresses 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void tma_bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Alpha of a Gaussian record at pixel centre (pxc, pyc), with every operation
+// spelled out so that the forward and backward kernels make identical
+// skip/cap decisions. ex, ey = conic * d (the pixel-derivative factors).
+struct AlphaEval {
+    float dx, dy, ex, ey, al;
+    bool capped;
+};
+__device__ __forceinline__ AlphaEval eval_alpha(const float4 &r0, const float4 &r1, float pxc, float pyc)
+{
+    AlphaEval e;
+    e.dx = __fsub_rn(pxc, r0.x);
+    e.dy = __fsub_rn(pyc, r0.y);
+    e.ex = __fmaf_rn(r0.z, e.dx, __fmul_rn(r0.w, e.dy));
+    e.ey = __fmaf_rn(r0.w, e.dx, __fmul_rn(r1.x, e.dy));
+    const float Q = __fmaf_rn(e.dx, e.ex, __fmul_rn(e.dy, e.ey));
+    const float al = __fmul_rn(r1.y, ex2_approx(__fmul_rn(Q, -0.72134752044448170f)));
+    e.capped = al > kAlphaCap;
+    e.al = e.capped ? kAlphaCap : al;
+    return e;
+}
+
+__device__ __forceinline__ bool rect_contains(const float4 &r2, uint32_t px, uint32_t py)
+{
+    const uint32_t lo = __float_as_uint(r2.z), hi = __float_as_uint(r2.w);
+    return px >= (lo & 0xFFFFu) && px <= (hi & 0xFFFFu) && py >= (lo >> 16) && py <= (hi >> 16);
+}
+
+}  // namespace gsr

@@ -1,0 +1,348 @@
+// K1: projection, culling and SH colour of 3D Gaussians (paper Sec. 3).
+//
+// Per Gaussian: activations (scale = exp(log_scale), unit quaternion, opacity =
+// sigmoid(logit)), Sigma = R S S^T R^T, camera transform, EWA local-affine
+// projection Sigma2D = J W Sigma W^T J^T plus a 0.3 px^2 low-pass, the conic
+// Sigma2D^-1, the support rectangle (exact bounding box of the ellipse where
+// opacity * G >= 1/255), the number of tiles it touches, and the view-dependent
+// colour from real SH (Condon-Shortley phase, degree 0..3, +0.5, clamped at 0).
+//
+// The depth key and the support rectangle decide culling, tiling and sort
+// order, so they are computed by a fixed sequence of IEEE fp32 round-to-nearest
+// operations (explicit __f*_rn intrinsics, never contracted), including a
+// Cody-Waite exp and an atanh-series log written from their published methods.
+// Any other fp32 implementation of the same sequence reproduces them bit for
+// bit.
+//
+// Layout: one thread owns 4 consecutive Gaussians and reads every attribute
+// plane with one 16-byte load per plane (planes are 16-byte aligned, stride a
+// multiple of 4), so a warp moves 512 contiguous bytes per plane. SH planes are
+// read only for quads with at least one surviving Gaussian.
+#include "gsr_internal.cuh"
+
+namespace gsr {
+namespace {
+
+__device__ __forceinline__ float A(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float S(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float M(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float D(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float F(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// e^x: n = rint(x log2 e), r = x - n ln2 (ln2 as 0.693359375 + lo, two FMAs),
+// e^r by its degree-7 Taylor polynomial (Horner, FMA), times 2^n built exactly.
+__device__ float rn_exp(float x)
+{
+    if (x != x) return x;
+    x = fminf(fmaxf(x, -87.0f), 88.0f);
+    const float n = rintf(M(x, 1.44269502e+00f));
+    float r = F(-n, 0.693359375f, x);
+    r = F(-n, -2.12194442e-04f, r);
+    float p = 1.98412701e-04f;
+    p = F(p, r, 1.38888892e-03f);
+    p = F(p, r, 8.33333377e-03f);
+    p = F(p, r, 4.16666679e-02f);
+    p = F(p, r, 1.66666672e-01f);
+    p = F(p, r, 0.5f);
+    p = F(p, r, 1.0f);
+    p = F(p, r, 1.0f);
+    return M(p, __int_as_float(((int)n + 127) << 23));
+}
+
+// ln x for normal x > 0: x = m 2^e, m in [sqrt(1/2), sqrt(2)]; ln m = 2 atanh(s)
+// with s = (m - 1)/(m + 1) by the odd series through s^11.
+__device__ float rn_log(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    int e = (int)((b >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+    if (m > 1.41421354e+00f) {
+        m = M(m, 0.5f);
+        e += 1;
+    }
+    const float s = D(S(m, 1.0f), A(m, 1.0f));
+    const float w = M(s, s);
+    float p = 9.09090936e-02f;
+    p = F(p, w, 1.11111112e-01f);
+    p = F(p, w, 1.42857149e-01f);
+    p = F(p, w, 2.00000003e-01f);
+    p = F(p, w, 3.33333343e-01f);
+    const float t = M(2.0f, s);
+    const float lm = F(M(t, w), p, t);
+    const float ef = (float)e;
+    return F(ef, 0.693359375f, F(ef, -2.12194442e-04f, lm));
+}
+
+struct Proj {
+    bool vis;
+    float u, v, ca, cb, cc, o, z;
+    uint32_t rlo, rhi, nt;
+};
+
+__device__ __forceinline__ void project_one(const CamParams &c, float mx, float my, float mz, float ls0, float ls1,
+                                            float ls2, float qw, float qx, float qy, float qz, float logit,
+                                            Proj &P)
+{
+    P.vis = false;
+    P.nt = 0;
+    const float *vm = c.vm;
+    const float tz = A(A(A(M(vm[8], mx), M(vm[9], my)), M(vm[10], mz)), vm[11]);
+    if (!(tz > c.near_plane)) return;
+    const float tx = A(A(A(M(vm[0], mx), M(vm[1], my)), M(vm[2], mz)), vm[3]);
+    const float ty = A(A(A(M(vm[4], mx), M(vm[5], my)), M(vm[6], mz)), vm[7]);
+    const float s0 = rn_exp(ls0), s1 = rn_exp(ls1), s2 = rn_exp(ls2);
+    const float qn = __fsqrt_rn(A(A(A(M(qw, qw), M(qx, qx)), M(qy, qy)), M(qz, qz)));
+    if (!(qn > 0.0f)) return;
+    const float w = D(qw, qn), x = D(qx, qn), y = D(qy, qn), z = D(qz, qn);
+    float R[9];
+    R[0] = S(1.0f, M(2.0f, A(M(y, y), M(z, z))));
+    R[1] = M(2.0f, S(M(x, y), M(w, z)));
+    R[2] = M(2.0f, A(M(x, z), M(w, y)));
+    R[3] = M(2.0f, A(M(x, y), M(w, z)));
+    R[4] = S(1.0f, M(2.0f, A(M(x, x), M(z, z))));
+    R[5] = M(2.0f, S(M(y, z), M(w, x)));
+    R[6] = M(2.0f, S(M(x, z), M(w, y)));
+    R[7] = M(2.0f, A(M(y, z), M(w, x)));
+    R[8] = S(1.0f, M(2.0f, A(M(x, x), M(y, y))));
+    float Mx[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        Mx[3 * r + 0] = M(R[3 * r + 0], s0);
+        Mx[3 * r + 1] = M(R[3 * r + 1], s1);
+        Mx[3 * r + 2] = M(R[3 * r + 2], s2);
+    }
+    float Sg[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = r; q < 3; ++q) {
+            const float v = A(A(M(Mx[3 * r], Mx[3 * q]), M(Mx[3 * r + 1], Mx[3 * q + 1])), M(Mx[3 * r + 2], Mx[3 * q + 2]));
+            Sg[3 * r + q] = v;
+            Sg[3 * q + r] = v;
+        }
+    const float limx = M(1.29999995f, D(M(0.5f, (float)c.width), c.fx));
+    const float limy = M(1.29999995f, D(M(0.5f, (float)c.height), c.fy));
+    const float txc = M(fminf(limx, fmaxf(-limx, D(tx, tz))), tz);
+    const float tyc = M(fminf(limy, fmaxf(-limy, D(ty, tz))), tz);
+    const float tz2 = M(tz, tz);
+    const float J00 = D(c.fx, tz), J02 = -D(M(c.fx, txc), tz2);
+    const float J11 = D(c.fy, tz), J12 = -D(M(c.fy, tyc), tz2);
+    float T3[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T3[k] = A(M(J00, vm[k]), M(J02, vm[8 + k]));
+        T3[3 + k] = A(M(J11, vm[4 + k]), M(J12, vm[8 + k]));
+    }
+    float U[6];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            U[3 * r + k] = A(A(M(T3[3 * r], Sg[k]), M(T3[3 * r + 1], Sg[3 + k])), M(T3[3 * r + 2], Sg[6 + k]));
+    const float Aa = A(A(A(M(U[0], T3[0]), M(U[1], T3[1])), M(U[2], T3[2])), 3.00000012e-01f);
+    const float Bb = A(A(M(U[0], T3[3]), M(U[1], T3[4])), M(U[2], T3[5]));
+    const float Cc = A(A(A(M(U[3], T3[3]), M(U[4], T3[4])), M(U[5], T3[5])), 3.00000012e-01f);
+    const float det = S(M(Aa, Cc), M(Bb, Bb));
+    if (!(det > 0.0f)) return;
+    const float o = D(1.0f, A(1.0f, rn_exp(-logit)));
+    if (!(M(255.0f, o) >= 1.0f)) return;
+    const float kk = M(2.0f, rn_log(M(255.0f, o)));
+    const float ex = __fsqrt_rn(M(kk, Aa)), ey = __fsqrt_rn(M(kk, Cc));
+    const float u = A(D(M(c.fx, tx), tz), c.cx);
+    const float v = A(D(M(c.fy, ty), tz), c.cy);
+    const float xlo = S(S(u, ex), 0.5f), xhi = S(A(u, ex), 0.5f);
+    const float ylo = S(S(v, ey), 0.5f), yhi = S(A(v, ey), 0.5f);
+    const float wm1 = (float)(c.width - 1), hm1 = (float)(c.height - 1);
+    if (!(xhi >= 0.0f) || !(xlo <= wm1) || !(yhi >= 0.0f) || !(ylo <= hm1)) return;
+    const int x0 = (int)fmaxf(0.0f, ceilf(xlo)), x1 = (int)fminf(wm1, floorf(xhi));
+    const int y0 = (int)fmaxf(0.0f, ceilf(ylo)), y1 = (int)fminf(hm1, floorf(yhi));
+    if (x0 > x1 || y0 > y1) return;
+    P.vis = true;
+    P.u = u;
+    P.v = v;
+    P.ca = D(Cc, det);
+    P.cb = -D(Bb, det);
+    P.cc = D(Aa, det);
+    P.o = o;
+    P.z = tz;
+    P.rlo = (uint32_t)x0 | ((uint32_t)y0 << 16);
+    P.rhi = (uint32_t)x1 | ((uint32_t)y1 << 16);
+    const int sh = c.tile_shift;
+    P.nt = (uint32_t)(((x1 >> sh) - (x0 >> sh) + 1) * ((y1 >> sh) - (y0 >> sh) + 1));
+}
+
+__device__ __forceinline__ float lane4(const float4 &v, int g)
+{
+    return g == 0 ? v.x : g == 1 ? v.y : g == 2 ? v.z : v.w;
+}
+
+// Real SH basis value k (l-major, m = -l..l, Condon-Shortley phase) at unit (x, y, z).
+template <int K>
+__device__ __forceinline__ float sh_basis(float x, float y, float z)
+{
+    constexpr float c0 = 0.28209479177387814f;   // sqrt(1/(4 pi))
+    constexpr float c1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
+    constexpr float c2a = 1.0925484305920792f;   // sqrt(15/(4 pi))
+    constexpr float c2b = 0.31539156525252005f;  // sqrt(5/(16 pi))
+    constexpr float c2c = 0.54627421529603959f;  // sqrt(15/(16 pi))
+    constexpr float c3a = 0.59004358992664352f;  // sqrt(35/(32 pi))
+    constexpr float c3b = 2.8906114426405538f;   // sqrt(105/(4 pi))
+    constexpr float c3c = 0.45704579946446572f;  // sqrt(21/(32 pi))
+    constexpr float c3d = 0.37317633259011540f;  // sqrt(7/(16 pi))
+    constexpr float c3e = 1.4453057213202769f;   // sqrt(105/(16 pi))
+    if (K == 0) return c0;
+    if (K == 1) return -c1 * y;
+    if (K == 2) return c1 * z;
+    if (K == 3) return -c1 * x;
+    if (K == 4) return c2a * x * y;
+    if (K == 5) return -c2a * y * z;
+    if (K == 6) return c2b * (2.f * z * z - x * x - y * y);
+    if (K == 7) return -c2a * x * z;
+    if (K == 8) return c2c * (x * x - y * y);
+    if (K == 9) return -c3a * y * (3.f * x * x - y * y);
+    if (K == 10) return c3b * x * y * z;
+    if (K == 11) return -c3c * y * (4.f * z * z - x * x - y * y);
+    if (K == 12) return c3d * z * (2.f * z * z - 3.f * x * x - 3.f * y * y);
+    if (K == 13) return -c3c * x * (4.f * z * z - x * x - y * y);
+    if (K == 14) return c3e * z * (x * x - y * y);
+    return -c3a * x * (x * x - 3.f * y * y);
+}
+
+template <int K, int NK>
+struct ShAccum {
+    __device__ __forceinline__ static void run(const float *__restrict__ sh, int64_t n_pad, int64_t i0,
+                                               const float (&dx)[4], const float (&dy)[4], const float (&dz)[4],
+                                               float (&col)[4][3])
+    {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float4 c4 = __ldg(reinterpret_cast<const float4 *>(sh + (int64_t)(K * 3 + ch) * n_pad + i0));
+#pragma unroll
+            for (int g = 0; g < 4; ++g) col[g][ch] = fmaf(sh_basis<K>(dx[g], dy[g], dz[g]), lane4(c4, g), col[g][ch]);
+        }
+        ShAccum<K + 1, NK>::run(sh, n_pad, i0, dx, dy, dz, col);
+    }
+};
+template <int NK>
+struct ShAccum<NK, NK> {
+    __device__ __forceinline__ static void run(const float *, int64_t, int64_t, const float (&)[4], const float (&)[4],
+                                               const float (&)[4], float (&)[4][3])
+    {
+    }
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads) k_project(ProjectArgs a)
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    const int64_t q = (int64_t)blockIdx.x * kProjThreads + threadIdx.x;
+    const int64_t i0 = q * 4;
+    uint32_t my_tiles = 0, my_vis = 0;
+    if (i0 < a.n) {
+        const int64_t np = a.n_pad;
+        auto ld4 = [&](const float *base, int row) {
+            return __ldg(reinterpret_cast<const float4 *>(base + (int64_t)row * np + i0));
+        };
+        const float4 mx = ld4(a.means, 0), my = ld4(a.means, 1), mz = ld4(a.means, 2);
+        const float4 l0 = ld4(a.log_scales, 0), l1 = ld4(a.log_scales, 1), l2 = ld4(a.log_scales, 2);
+        const float4 qw = ld4(a.quats, 0), qx = ld4(a.quats, 1), qy = ld4(a.quats, 2), qz = ld4(a.quats, 3);
+        const float4 lg = ld4(a.logits, 0);
+        Proj P[4];
+        bool any = false;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            if (i0 + g < a.n) {
+                project_one(a.cam, lane4(mx, g), lane4(my, g), lane4(mz, g), lane4(l0, g), lane4(l1, g), lane4(l2, g),
+                            lane4(qw, g), lane4(qx, g), lane4(qy, g), lane4(qz, g), lane4(lg, g), P[g]);
+            } else {
+                P[g].vis = false;
+                P[g].nt = 0;
+            }
+            any |= P[g].vis;
+        }
+        if (any) {
+            float dx[4], dy[4], dz[4], col[4][3];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const float ex = lane4(mx, g) - a.cam.campos[0], ey = lane4(my, g) - a.cam.campos[1],
+                            ez = lane4(mz, g) - a.cam.campos[2];
+                const float rn = rsqrtf(ex * ex + ey * ey + ez * ez);
+                dx[g] = ex * rn;
+                dy[g] = ey * rn;
+                dz[g] = ez * rn;
+                col[g][0] = col[g][1] = col[g][2] = 0.0f;
+            }
+            ShAccum<0, NK>::run(a.sh, np, i0, dx, dy, dz, col);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                if (!P[g].vis) continue;
+                GaussRec r;
+                r.r0 = make_float4(P[g].u, P[g].v, P[g].ca, P[g].cb);
+                r.r1 = make_float4(P[g].cc, P[g].o, P[g].z, fmaxf(col[g][0] + 0.5f, 0.0f));
+                r.r2 = make_float4(fmaxf(col[g][1] + 0.5f, 0.0f), fmaxf(col[g][2] + 0.5f, 0.0f),
+                                   __uint_as_float(P[g].rlo), __uint_as_float(P[g].rhi));
+                a.rec[i0 + g] = r;
+                a.bin[i0 + g] = make_uint4(__float_as_uint(P[g].z), P[g].rlo, P[g].rhi, 0u);
+            }
+        }
+        *reinterpret_cast<uint4 *>(a.ntiles + i0) = make_uint4(P[0].nt, P[1].nt, P[2].nt, P[3].nt);
+        my_tiles = P[0].nt + P[1].nt + P[2].nt + P[3].nt;
+        my_vis = (uint32_t)P[0].vis + (uint32_t)P[1].vis + (uint32_t)P[2].vis + (uint32_t)P[3].vis;
+    }
+    // block sum of tiles touched -> per-block sums for the instance-offset scan
+    __shared__ uint32_t s_warp[2][kProjThreads / 32];
+    uint32_t v = my_tiles, c = my_vis;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_warp[0][threadIdx.x >> 5] = v;
+        s_warp[1][threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0, cv = 0;
+#pragma unroll
+        for (int w = 0; w < kProjThreads / 32; ++w) {
+            t += s_warp[0][w];
+            cv += s_warp[1][w];
+        }
+        a.block_sums[blockIdx.x] = t;
+        if (cv) {
+            atomicAdd(&a.counters[kCntVisible], cv);
+            atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kCntSumV), (unsigned long long)cv);
+        }
+    }
+}
+
+}  // namespace
+
+int project_blocks(int64_t n) { return (int)((n + kProjPerBlock - 1) / kProjPerBlock); }
+
+// The projection kernel's entry, to find its node in a captured graph.
+const void *project_kernel_ptr(int deg)
+{
+    switch (deg) {
+    case 0: return reinterpret_cast<const void *>(k_project<0>);
+    case 1: return reinterpret_cast<const void *>(k_project<1>);
+    case 2: return reinterpret_cast<const void *>(k_project<2>);
+    default: return reinterpret_cast<const void *>(k_project<3>);
+    }
+}
+
+cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
+{
+    const int nb = project_blocks(a.n);
+    if (nb == 0) return cudaSuccess;
+    switch (a.deg) {
+    case 0: k_project<0><<<nb, kProjThreads, 0, s>>>(a); break;
+    case 1: k_project<1><<<nb, kProjThreads, 0, s>>>(a); break;
+    case 2: k_project<2><<<nb, kProjThreads, 0, s>>>(a); break;
+    default: k_project<3><<<nb, kProjThreads, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gsr

@@ -1,0 +1,265 @@
+// K4: stable LSD radix sort of the (tile, depth) keys with their Gaussian
+// indices, "onesweep" style (Adinets & Merrill, 2022): one pass over the keys
+// builds every digit's global histogram, then each 8-bit digit is sorted in a
+// single pass over the data, with partitions publishing their per-digit counts
+// and resolving their global offsets by decoupled lookback.
+//
+// Only the low `bits` bits are sorted: 32 bits of fp32 depth (positive, so its
+// bit pattern orders like the value) plus ceil(log2(n_tiles)) tile bits.
+// Stability (equal keys keep index order) gives the (depth, index) tie-break.
+//
+// Partition ids are taken from an atomic ticket, so a partition only ever waits
+// for partitions that are already running. Every wait is still bounded: a
+// partition that gives up sets kErrSortTimeout and publishes what it has.
+#include <algorithm>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;
+constexpr int kPart = kThreads * kItems;  // 4096 keys per partition
+constexpr int kRadix = 256;
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPre = 2u << 30;
+constexpr uint32_t kFlagMask = 3u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr uint32_t kMaxSpins = 1u << 22;
+constexpr size_t kPassSmem = (size_t)kPart * 8 + (size_t)kPart * 4 + (size_t)kWarps * kRadix * 4;
+
+__device__ __forceinline__ uint32_t ld_vol(const uint32_t *p) { return *reinterpret_cast<const volatile uint32_t *>(p); }
+__device__ __forceinline__ void st_vol(uint32_t *p, uint32_t v) { *reinterpret_cast<volatile uint32_t *>(p) = v; }
+
+__global__ void __launch_bounds__(kThreads) k_sort_hist(const uint64_t *__restrict__ keys,
+                                                        const uint32_t *__restrict__ counters, int passes,
+                                                        uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t sh[8 * kRadix];
+    for (int i = threadIdx.x; i < 8 * kRadix; i += kThreads) sh[i] = 0;
+    __syncthreads();
+    const uint32_t K = counters[kCntEff];
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp_global = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
+    for (uint32_t base = warp_global * 32; base < K; base += nwarps * 32) {
+        const uint32_t idx = base + lane;
+        const bool valid = idx < K;
+        const uint64_t key = valid ? keys[idx] : 0ull;
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = valid ? (uint32_t)(key >> (8 * p)) & 0xFFu : 0x100u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh[p * kRadix + d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += kThreads)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// Exclusive scan of two per-thread values over the 256 threads of the block.
+__device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_t &ea, uint32_t &eb, uint32_t *s_tmp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += ta;
+            ib += tb;
+        }
+    }
+    if (lane == 31) {
+        s_tmp[warp] = ia;
+        s_tmp[kWarps + warp] = ib;
+    }
+    __syncthreads();
+    uint32_t pa = 0, pb = 0;
+    for (int w = 0; w < warp; ++w) {
+        pa += s_tmp[w];
+        pb += s_tmp[kWarps + w];
+    }
+    ea = pa + ia - a;
+    eb = pb + ib - b;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sort_pass(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                        uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                        const uint32_t *__restrict__ counters, int shift,
+                                                        const uint32_t *__restrict__ hist, uint32_t *status,
+                                                        uint32_t *part_ctr, uint32_t *err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(smem + (size_t)kPart * 8);
+    uint32_t *s_whist = reinterpret_cast<uint32_t *>(smem + (size_t)kPart * 12);
+    __shared__ uint32_t s_base[kRadix];
+    __shared__ uint32_t s_start[kRadix];
+    __shared__ uint32_t s_tmp[2 * kWarps];
+    __shared__ uint32_t s_part;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t K = counters[kCntEff];
+    const uint32_t nparts = (K + kPart - 1) / kPart;
+    if (tid == 0) s_part = atomicAdd(part_ctr, 1u);
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
+    __syncthreads();
+    const uint32_t part = s_part;
+    if (part >= nparts) return;
+    const uint32_t base = part * kPart;
+
+    uint64_t k[kItems];
+    uint32_t v[kItems], rk[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const uint32_t idx = base + warp * (kItems * 32) + j * 32 + lane;
+        if (idx < K) {
+            k[j] = kin[idx];
+            v[j] = vin[idx];
+        } else {
+            k[j] = ~0ull;
+            v[j] = 0u;
+        }
+    }
+    // warp-level stable ranking: items are ordered (warp, j, lane)
+    uint32_t *wh = s_whist + warp * kRadix;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const uint32_t idx = base + warp * (kItems * 32) + j * 32 + lane;
+        const bool valid = idx < K;
+        const uint32_t d = valid ? (uint32_t)(k[j] >> shift) & 0xFFu : 0x100u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t prev = 0;
+        if (lane == leader && valid) {
+            prev = wh[d];
+            wh[d] = prev + (uint32_t)__popc(peers);
+        }
+        prev = __shfl_sync(0xffffffffu, prev, leader);
+        rk[j] = prev + (uint32_t)__popc(peers & lt_mask);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive offsets across warps and the partition's count
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = s_whist[w * kRadix + tid];
+        s_whist[w * kRadix + tid] = cnt;
+        cnt += c;
+    }
+    uint32_t cexcl, hexcl;
+    block_excl_scan2(cnt, hist[tid], cexcl, hexcl, s_tmp);
+    // decoupled lookback for this digit
+    uint32_t *st = status + (size_t)part * kRadix + tid;
+    uint32_t excl = 0;
+    if (part == 0) {
+        st_vol(st, kFlagPre | cnt);
+    } else {
+        st_vol(st, kFlagAgg | cnt);
+        int p = (int)part - 1;
+        uint32_t spins = 0;
+        while (p >= 0) {
+            const uint32_t s = ld_vol(status + (size_t)p * kRadix + tid);
+            const uint32_t f = s & kFlagMask;
+            if (f == 0u) {
+                if (++spins > kMaxSpins) {
+                    atomicOr(err, kErrSortTimeout);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            excl += s & kValMask;
+            if (f == kFlagPre) break;
+            --p;
+        }
+        st_vol(st, kFlagPre | ((excl + cnt) & kValMask));
+    }
+    s_base[tid] = hexcl + excl;
+    s_start[tid] = cexcl;
+    __syncthreads();
+    // stable local scatter into shared memory, then coalesced global writes
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const uint32_t idx = base + warp * (kItems * 32) + j * 32 + lane;
+        if (idx < K) {
+            const uint32_t d = (uint32_t)(k[j] >> shift) & 0xFFu;
+            const uint32_t pos = s_start[d] + s_whist[warp * kRadix + d] + rk[j];
+            s_keys[pos] = k[j];
+            s_vals[pos] = v[j];
+        }
+    }
+    __syncthreads();
+    const uint32_t nval = min((uint32_t)kPart, K - base);
+    for (uint32_t i = tid; i < nval; i += kThreads) {
+        const uint64_t key = s_keys[i];
+        const uint32_t d = (uint32_t)(key >> shift) & 0xFFu;
+        const uint32_t g = s_base[d] + (i - s_start[d]);
+        kout[g] = key;
+        vout[g] = s_vals[i];
+    }
+}
+
+}  // namespace
+
+int sort_passes(int bits) { return (bits + 7) / 8; }
+
+static int64_t parts_for(int64_t k) { return (k + kPart - 1) / kPart; }
+
+size_t sort_scratch_bytes(int64_t capacity)
+{
+    const int64_t parts = parts_for(capacity) + 1;
+    return sizeof(uint32_t) * (8 * kRadix + 8 + (size_t)8 * parts * kRadix) + 256;
+}
+
+void sort_scratch_carve(void *base, int64_t capacity, SortScratch *s)
+{
+    uint32_t *p = reinterpret_cast<uint32_t *>(base);
+    s->hist = p;
+    s->part_ctr = p + 8 * kRadix;
+    s->status = p + 8 * kRadix + 8;
+    s->max_parts = parts_for(capacity) + 1;
+}
+
+cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *counters, uint32_t *err_word,
+                        int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s)
+{
+    const int passes = sort_passes(bits);
+    *result = passes & 1;
+    if (max_k <= 0) return cudaSuccess;
+    const int64_t parts = parts_for(max_k);
+    if (parts > scr.max_parts || passes > 8) return cudaErrorInvalidValue;
+    // once per device, outside any stream capture (the first sort on a device is never captured)
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    e = cudaMemsetAsync(scr.hist, 0, sizeof(uint32_t) * (8 * kRadix + 8), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(scr.status, 0, sizeof(uint32_t) * (size_t)passes * parts * kRadix, s);
+    if (e != cudaSuccess) return e;
+    const int64_t hist_blocks = std::min<int64_t>((max_k + kThreads * 8 - 1) / (kThreads * 8), 152 * 8);
+    k_sort_hist<<<(unsigned)hist_blocks, kThreads, 0, s>>>(keys[0], counters, passes, scr.hist);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int p = 0; p < passes; ++p) {
+        const int src = p & 1, dst = src ^ 1;
+        k_sort_pass<<<(unsigned)parts, kThreads, kPassSmem, s>>>(keys[src], vals[src], keys[dst], vals[dst], counters,
+                                                                 8 * p, scr.hist + p * kRadix,
+                                                                 scr.status + (size_t)p * parts * kRadix,
+                                                                 scr.part_ctr + p, err_word);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace gsr

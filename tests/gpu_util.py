@@ -1,0 +1,53 @@
+"""Helpers shared by the GPU parity tests: tolerance checks between the CUDA
+render (fp32) and the FP64 oracle.
+
+Tolerances (stated for the render's outputs):
+  colour (rgb, and alpha, which is 1 - T on the same scale): |gpu - ref| <= 2e-4
+      on >= 99.99 % of values and <= 5e-3 on all; the excess is the alpha = 1/255
+      cut flipping under fp32 rounding (a flip moves a pixel by at most about
+      c * 1/255).
+  depth: the same, scaled by max(1, |ref depth|).
+  gradient channels: |g - g_ref| <= 1e-3 * max(|g_ref|, 1e-2 * rms(g_ref)) per
+      channel, on pixels whose colour is within 2e-4 (i.e. no discrete flip).
+"""
+import numpy as np
+
+COLOUR_TOL = 2e-4
+COLOUR_TOL_ALL = 5e-3
+COLOUR_FRAC = 0.9999
+GRAD_REL = 1e-3
+
+
+def check_colour(got, ref, name, scale=None, frac=COLOUR_FRAC, tol_all=COLOUR_TOL_ALL):
+    got = np.asarray(got, dtype=np.float64)
+    err = np.abs(got - ref)
+    if scale is not None:
+        err = err / scale
+    ok = err <= COLOUR_TOL
+    assert ok.mean() >= frac, "%s: %.5f%% within %.0e (max err %.3g)" % (name, 100 * ok.mean(), COLOUR_TOL, err.max())
+    assert err.max() <= tol_all, "%s: max err %.3g > %.0e" % (name, err.max(), tol_all)
+    return ok
+
+
+def check_grad(got, ref, mask, name, rel=GRAD_REL):
+    got = np.asarray(got, dtype=np.float64)
+    for c in range(ref.shape[0]):
+        r = ref[c]
+        rms = np.sqrt(np.mean(r ** 2)) if r.size else 0.0
+        bound = rel * np.maximum(np.abs(r), 1e-2 * rms) + 1e-7
+        bad = (np.abs(got[c] - r) > bound) & mask
+        assert not bad.any(), "%s[%d]: %d pixels out of tolerance, worst %.3g vs bound %.3g" % (
+            name, c, bad.sum(), np.abs(got[c] - r)[bad].max(), bound[bad].min())
+
+
+def check_render(out, ref, frac=COLOUR_FRAC):
+    """out: dict of torch tensors from the GPU; ref: oracle.render dict."""
+    g = {k: v.detach().cpu().numpy() for k, v in out.items()}
+    ok_rgb = check_colour(g["rgb"], ref["rgb"], "rgb", frac=frac)
+    check_colour(g["alpha"], ref["alpha"], "alpha", frac=frac)
+    check_colour(g["depth"], ref["depth"], "depth", scale=np.maximum(1.0, np.abs(ref["depth"])), frac=frac,
+                 tol_all=COLOUR_TOL_ALL)
+    mask = ok_rgb.all(axis=0)
+    check_grad(g["dcdx"], ref["dcdx"], mask, "dcdx")
+    check_grad(g["dcdy"], ref["dcdy"], mask, "dcdy")
+    return mask

@@ -1,0 +1,69 @@
+"""CPU-side checks of the C ABI library: it builds for sm_103a, loads, and
+exports every entry point include/gsr.h declares (no GPU calls)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_2605_11489_gb300 import abi
+
+    return abi
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "gsr.h")).read()
+    return sorted(set(re.findall(r"^(?:gs_status|const char \*)\s*(gs_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_header_entry_points_match_binding(built):
+    assert _declared() == sorted(built.ENTRY_POINTS)
+
+
+def test_library_exports_every_declared_symbol(built):
+    L = built.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_version_string_without_gpu(built):
+    assert b"sm_103a" in built.lib().gs_version()
+
+
+def test_library_is_sm103a_only(built):
+    # the fatbin embeds exactly one cubin arch; check via the build flags we pass
+    from paper_2605_11489_gb300 import build as b
+
+    assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert "--use_fast_math" not in b.FLAGS
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path, built):
+    import importlib
+
+    from paper_2605_11489_gb300 import abi
+
+    mod = importlib.reload(abi)
+    try:
+        mod._lib = None
+        with pytest.raises(RuntimeError):
+            mod.lib(str(tmp_path / "missing.so"))
+    finally:
+        importlib.reload(abi)
+
+
+def test_product_never_imports_oracle():
+    pkg = os.path.join(ROOT, "paper_2605_11489_gb300")
+    for dp, _, fs in os.walk(pkg):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "oracle.c" not in txt, f

@@ -1,0 +1,222 @@
+"""GPU parity of the forward render (K1-K6) against the FP64 oracle, through
+the C ABI. Sort keys and tile ranges must match bit for bit; colours, depth,
+alpha and the gradient channels within the tolerances in gpu_util."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_11489_gb300 import synth
+
+from gpu_util import check_colour, check_render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__ as g
+
+    g.build()
+    import oracle
+    from paper_2605_11489_gb300 import api
+
+    torch.cuda.set_device(0)
+    return api, oracle, api.Context(0)
+
+
+def _render(api, ctx, sc, cam, **kw):
+    scene = api.Scene.from_arrays(sc)
+    return ctx.forward(scene, cam, **kw)
+
+
+def test_keys_and_ranges_bit_exact_tiny(env):
+    api, O, ctx = env
+    sc = synth.tiny_scene()
+    for cam in [synth.tiny_camera()] + synth.jittered_tiny_cameras(4, 1):
+        out, st = _render(api, ctx, sc, cam, state=True)
+        v = st.view()
+        ref = O.keys(sc, cam, 16)
+        assert v["n_instances"] == len(ref["keys"])
+        assert np.array_equal(v["keys"], ref["keys"])
+        assert np.array_equal(v["vals"], ref["vals"])
+        assert np.array_equal(v["ranges"], ref["ranges"])
+        st.free()
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_keys_bit_exact_every_tile_size(env, tile):
+    api, O, ctx = env
+    sc = synth.tiny_scene(4096, 3)
+    cam = synth.jittered_tiny_cameras(2, 9)[1]
+    out, st = _render(api, ctx, sc, cam, state=True, tile=tile)
+    v = st.view()
+    ref = O.keys(sc, cam, tile)
+    assert np.array_equal(v["keys"], ref["keys"]) and np.array_equal(v["vals"], ref["vals"])
+    assert np.array_equal(v["ranges"], ref["ranges"])
+    st.free()
+
+
+def test_projection_records_match_oracle(env):
+    api, O, ctx = env
+    sc = synth.tiny_scene()
+    cam = synth.tiny_camera()
+    out, st = _render(api, ctx, sc, cam, state=True)
+    p = O.project(sc, cam, 16)
+    nt = st.ntiles(sc.n)
+    assert np.array_equal(nt.astype(np.int64), p["ntiles"].astype(np.int64))
+    rec = st.records(sc.n)
+    vis = p["visible"].astype(bool)
+    r = rec[vis]
+    rect = r[:, 10:12].copy().view(np.uint32)
+    assert np.array_equal(rect[:, 0] & 0xFFFF, p["rect"][vis, 0])
+    assert np.array_equal(rect[:, 0] >> 16, p["rect"][vis, 1])
+    assert np.array_equal(rect[:, 1] & 0xFFFF, p["rect"][vis, 2])
+    assert np.array_equal(rect[:, 1] >> 16, p["rect"][vis, 3])
+    assert np.array_equal(r[:, 6], p["z32"][vis])  # depth key value, bit-exact
+    np.testing.assert_allclose(r[:, 0:2], p["uv"][vis], rtol=0, atol=2e-4)
+    np.testing.assert_allclose(r[:, 2:5], p["conic"][vis], rtol=2e-5, atol=1e-6)
+    np.testing.assert_allclose(r[:, 5], p["opacity"][vis], rtol=2e-6, atol=1e-7)
+    np.testing.assert_allclose(np.stack([r[:, 7], r[:, 8], r[:, 9]], 1), p["rgb"][vis], rtol=0, atol=2e-6)
+    st.free()
+
+
+def test_forward_parity_tiny(env):
+    api, O, ctx = env
+    sc = synth.tiny_scene()
+    for cam in [synth.tiny_camera()] + synth.jittered_tiny_cameras(6, 2):
+        out = _render(api, ctx, sc, cam)
+        ref = O.render(sc, cam)
+        check_render(out, ref)
+
+
+def test_forward_parity_background_and_ragged_image(env):
+    api, O, ctx = env
+    sc = synth.tiny_scene(777, 12)  # n not a multiple of 4
+    cam = synth.tiny_camera(203, 117)  # partial tiles on both edges
+    bg = (0.2, 0.7, 0.35)
+    for tile in (8, 16, 32):
+        out = _render(api, ctx, sc, cam, bg=bg, tile=tile)
+        ref = O.render(sc, cam, bg=bg)
+        check_render(out, ref)
+
+
+def test_tile_and_batch_invariance_bitwise(env):
+    """The support rectangle decides which pixels a Gaussian reaches, so tile size
+    and batch size change nothing in the per-pixel arithmetic."""
+    api, O, ctx = env
+    import torch
+
+    sc = synth.tiny_scene(4096, 5)
+    cam = synth.jittered_tiny_cameras(3, 3)[2]
+    base = _render(api, ctx, sc, cam, tile=16, batch=64)
+    for tile in (8, 16, 32):
+        for batch in (32, 64, 128, 256):
+            o = _render(api, ctx, sc, cam, tile=tile, batch=batch)
+            for k in base:
+                assert torch.equal(o[k], base[k]), (tile, batch, k)
+
+
+def test_single_gaussian_closed_form_on_gpu(env):
+    """One isotropic Gaussian on the optical axis against its closed form."""
+    api, O, ctx = env
+    cam = synth.tiny_camera(96, 64)
+    s = synth.empty_scene(1, 0)
+    s.quats[:, 0] = (0.3, -0.5, 0.7, 0.2)
+    s.log_scales[:, 0] = np.float32(-2.5)
+    s.logits[0] = np.float32(1.0)
+    s.sh[0, :, 0] = np.float32([1.2, -0.4, 0.1])
+    out = _render(api, ctx, s, cam)
+    sig2 = (cam.fx * math.exp(float(np.float32(-2.5))) / 4.0) ** 2 + 0.3
+    o = 1 / (1 + math.exp(-1.0))
+    X, Y = np.meshgrid(np.arange(cam.width) + 0.5, np.arange(cam.height) + 0.5)
+    a = np.minimum(0.99, o * np.exp(-((X - cam.cx) ** 2 + (Y - cam.cy) ** 2) / (2 * sig2)))
+    a = a * (a >= 1 / 255)
+    col = np.maximum(s.sh[0, :, 0].astype(np.float64) * 0.5 / math.sqrt(math.pi) + 0.5, 0)
+    check_colour(out["rgb"].cpu().numpy(), col[:, None, None] * a, "rgb")
+    check_colour(out["alpha"].cpu().numpy(), a, "alpha")
+    ref_dx = -col[:, None, None] * a * (X - cam.cx) / sig2
+    assert np.abs(out["dcdx"].cpu().numpy() - ref_dx).max() < 2e-4
+
+
+def test_empty_and_culled_scenes(env):
+    api, O, ctx = env
+    import torch
+
+    cam = synth.tiny_camera(64, 48)
+    bg = (0.1, 0.2, 0.3)
+    # n = 0
+    s0 = synth.empty_scene(0, 0)
+    out = _render(api, ctx, s0, cam, bg=bg)
+    for c in range(3):
+        assert torch.all(out["rgb"][c] == bg[c])
+    assert torch.all(out["alpha"] == 0) and torch.all(out["dcdx"] == 0) and torch.all(out["depth"] == 0)
+    # every Gaussian behind the camera
+    s1 = synth.tiny_scene(100, 1)
+    s1.means[2, :100] = 10.0
+    out = _render(api, ctx, s1, cam, bg=bg, state=True)
+    out, st = out
+    assert st.view()["n_instances"] == 0
+    assert torch.all(out["alpha"] == 0)
+    st.free()
+    # a single Gaussian, n = 1 (ragged quad)
+    s2 = synth.tiny_scene(1, 4)
+    s2.means[:, 0] = 0.0
+    s2.log_scales[:, 0] = -2.0
+    out = _render(api, ctx, s2, cam)
+    check_render(out, O.render(s2, cam))
+
+
+def test_large_gaussian_many_tiles_and_saturation(env):
+    """Screen-filling, opaque Gaussians: thousands of tiles per Gaussian, capped
+    alpha, early termination in every pixel."""
+    api, O, ctx = env
+    rng = np.random.default_rng(17)
+    n = 64
+    s = synth.empty_scene(n, 1)
+    s.means[:, :n] = rng.uniform(-0.5, 0.5, (3, n))
+    s.log_scales[:, :n] = rng.uniform(-1.0, 0.5, (3, n))
+    s.quats[:, :n] = rng.normal(size=(4, n))
+    s.logits[:n] = rng.uniform(2.0, 8.0, n)
+    s.sh[:, :, :n] = rng.normal(0, 0.5, (4, 3, n))
+    cam = synth.tiny_camera(320, 180)
+    out = _render(api, ctx, s, cam)
+    check_render(out, O.render(s, cam))
+
+
+def test_forward_to_host_matches_device(env):
+    api, O, ctx = env
+    import torch
+
+    sc = synth.tiny_scene()
+    cam = synth.tiny_camera()
+    dev = _render(api, ctx, sc, cam)
+    host = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in dev.items()}
+    ctx.forward_to_host(api.Scene.from_arrays(sc), cam, host)
+    for k in dev:
+        assert torch.equal(host[k], dev[k].cpu()), k
+
+
+def test_invalid_arguments_rejected(env):
+    api, O, ctx = env
+    from paper_2605_11489_gb300 import abi
+
+    sc = synth.tiny_scene(16, 0)
+    scene = api.Scene.from_arrays(sc)
+    bad = synth.tiny_camera(64, 48)
+    bad.width = 0
+    with pytest.raises(abi.GsError) as e:
+        ctx.forward(scene, bad)
+    assert e.value.status == abi.GS_ERR_INVALID_ARG
+    with pytest.raises(abi.GsError):
+        ctx.forward(scene, synth.tiny_camera(64, 48), tile=12)
+    # misaligned plane pointer
+    import torch
+
+    means = torch.zeros(3 * 16 + 1, device="cuda")[1:].view(3, 16)
+    s2 = api.Scene(16, 0, means, scene.log_scales, scene.quats, scene.logits, scene.sh)
+    with pytest.raises(abi.GsError) as e:
+        ctx.forward(s2, synth.tiny_camera(64, 48))
+    assert e.value.status == abi.GS_ERR_INVALID_ARG
