@@ -204,6 +204,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--tile", type=int, default=0, help="tile side 8/16/32 (0 = autotune)")
+    ap.add_argument("--batch", type=int, default=0, help="Gaussians per shared-memory batch (0 = autotune)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

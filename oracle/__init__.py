@@ -63,7 +63,7 @@ def lib():
             L.or_sh_basis.argtypes = [C.c_int, P, P, P]
             L.or_cov3d.argtypes = [P, P, P, P]
             L.or_project.argtypes = [P, P, C.c_int32] + [P] * 10
-            L.or_render.argtypes = [P, P, C.c_int] + [P] * 8
+            L.or_render.argtypes = [P, P, C.c_int] + [P] * 10
             L.or_render_pixels.argtypes = [P, P, C.c_int64, P, P, P, P]
             L.or_render_band.argtypes = [P, P, C.c_int, C.c_int, P, P, P, P, P]
             L.or_count_instances.restype = C.c_int64
@@ -155,16 +155,20 @@ def project(scene, cam, tile: int = 16) -> dict:
 
 def render(scene, cam, bg=(0.0, 0.0, 0.0), mode: str = "binned") -> dict:
     """Full-frame FP64 render. Returns planar rgb/dcdx/dcdy [3,H,W], depth,
-    alpha, final_T [H,W], n_blended [H,W] and the per-pixel decision signature."""
+    alpha, final_T [H,W], n_blended [H,W], the per-pixel decision signature, and
+    `amb`: 1 where a discrete decision (alpha cap 0.99, cut 1/255, stop at
+    T < 1e-4) lies within 1e-5 relative of its threshold, so that fp32
+    rounding elsewhere may decide it the other way."""
     s = _as_oscene(scene)
     H, W = cam.height, cam.width
     out = dict(rgb=np.zeros((3, H, W)), dcdx=np.zeros((3, H, W)), dcdy=np.zeros((3, H, W)),
                depth=np.zeros((H, W)), alpha=np.zeros((H, W)), final_T=np.zeros((H, W)),
-               n_blended=np.zeros((H, W), np.int32), sig=np.zeros((H, W), np.uint32))
+               n_blended=np.zeros((H, W), np.int32), sig=np.zeros((H, W), np.uint32),
+               amb=np.zeros((H, W), np.int32), gabs=np.zeros((2, 3, H, W)))
     st, cm = s.struct(), _cam(cam, bg)
     rc = lib().or_render(C.byref(st), C.byref(cm), 1 if mode == "binned" else 0,
                          *[_ptr(out[k]) for k in ("rgb", "dcdx", "dcdy", "depth", "alpha", "final_T",
-                                                  "n_blended", "sig")])
+                                                  "n_blended", "sig", "amb", "gabs")])
     if rc != 0:
         raise RuntimeError("or_render failed: %d" % rc)
     return out

@@ -434,9 +434,13 @@ typedef struct {
 
 typedef struct {
     double rgb[3], gx[3], gy[3], depth, alpha, T, Tx, Ty;
+    double gx_abs[3], gy_abs[3]; /* sum of |terms| of Eq. 3 (incl. the bg term): the scale of dI/dx, dI/dy */
     int32_t n_blended;
     uint32_t sig;
+    int32_t amb; /* a discrete decision (cap, cut, stop) lies within 1e-5 relative of its threshold */
 } or_pix;
+
+#define OR_AMB_REL 1e-5
 
 /* Eq. 2-4 for one pixel over the depth-ordered candidate list. */
 static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, int px, int py,
@@ -444,8 +448,8 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
 {
     const double X = px + 0.5, Yp = py + 0.5;
     double T = 1.0, Tx = 0.0, Ty = 0.0, D = 0.0;
-    double C[3] = {0, 0, 0}, Cx[3] = {0, 0, 0}, Cy[3] = {0, 0, 0};
-    int32_t nb = 0;
+    double C[3] = {0, 0, 0}, Cx[3] = {0, 0, 0}, Cy[3] = {0, 0, 0}, Ax[3] = {0, 0, 0}, Ay[3] = {0, 0, 0};
+    int32_t nb = 0, amb = 0;
     uint32_t sig = 2166136261u;
     int64_t nt = 0;
     for (int64_t k = 0; k < len; ++k) {
@@ -453,9 +457,12 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
         double dx = X - g->u, dy = Yp - g->v;
         double Q = g->ca * dx * dx + 2.0 * g->cb * dx * dy + g->cc * dy * dy;
         double a = g->o * exp(-0.5 * Q);
+        if (fabs(a - OR_ALPHA_CAP) <= OR_AMB_REL * OR_ALPHA_CAP || fabs(a - OR_ALPHA_MIN) <= OR_AMB_REL * OR_ALPHA_MIN)
+            amb = 1;
         int capped = 0;
         if (a > OR_ALPHA_CAP) { a = OR_ALPHA_CAP; capped = 1; }
         if (a < OR_ALPHA_MIN) continue;
+        if (fabs(T * (1.0 - a) - OR_T_MIN) <= OR_AMB_REL * OR_T_MIN) amb = 1;
         if (T * (1.0 - a) < OR_T_MIN) { sig = (sig ^ 0xA5A5A5A5u) * 16777619u; break; }
         double ax = capped ? 0.0 : -a * (g->ca * dx + g->cb * dy);
         double ay = capped ? 0.0 : -a * (g->cb * dx + g->cc * dy);
@@ -469,6 +476,8 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
             C[c] += g->rgb[c] * a * T;                 /* Eq. 2 */
             Cx[c] += g->rgb[c] * (Tx * a + T * ax);    /* Eq. 3 */
             Cy[c] += g->rgb[c] * (Ty * a + T * ay);
+            Ax[c] += fabs(g->rgb[c] * Tx * a) + fabs(g->rgb[c] * T * ax);
+            Ay[c] += fabs(g->rgb[c] * Ty * a) + fabs(g->rgb[c] * T * ay);
         }
         D += g->z * a * T;
         Tx = -ax * T + (1.0 - a) * Tx;                 /* Eq. 4 */
@@ -481,12 +490,15 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
         out->rgb[c] = C[c] + T * bg[c];
         out->gx[c] = Cx[c] + bg[c] * Tx;
         out->gy[c] = Cy[c] + bg[c] * Ty;
+        out->gx_abs[c] = Ax[c] + fabs(bg[c] * Tx);
+        out->gy_abs[c] = Ay[c] + fabs(bg[c] * Ty);
     }
     out->depth = D;
     out->alpha = 1.0 - T;
     out->T = T; out->Tx = Tx; out->Ty = Ty;
     out->n_blended = nb;
     out->sig = sig;
+    out->amb = amb;
     if (n_trace) *n_trace = nt;
 }
 
@@ -619,12 +631,12 @@ static int64_t max_bucket(const or_buckets *B)
  * rgb/dcdx/dcdy [3][H][W], depth/alpha/final_T [H][W]; any may be NULL. */
 static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y0, int y1, double *rgb,
                        double *dcdx, double *dcdy, double *depth, double *alpha, double *final_T,
-                       int32_t *n_blended, uint32_t *sig);
+                       int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs);
 
 int or_render(const or_scene *sc, const or_camera *cam, int mode, double *rgb, double *dcdx, double *dcdy,
-              double *depth, double *alpha, double *final_T, int32_t *n_blended, uint32_t *sig)
+              double *depth, double *alpha, double *final_T, int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs)
 {
-    return render_rows(sc, cam, mode, 0, cam->height, rgb, dcdx, dcdy, depth, alpha, final_T, n_blended, sig);
+    return render_rows(sc, cam, mode, 0, cam->height, rgb, dcdx, dcdy, depth, alpha, final_T, n_blended, sig, amb, gabs);
 }
 
 /* Rows [y0, y1) of the frame (binned mode), written into full-size planes. */
@@ -633,12 +645,12 @@ int or_render_band(const or_scene *sc, const or_camera *cam, int y0, int y1, dou
 {
     if (y0 < 0) y0 = 0;
     if (y1 > cam->height) y1 = cam->height;
-    return render_rows(sc, cam, 1, y0, y1, rgb, dcdx, dcdy, depth, alpha, NULL, NULL, NULL);
+    return render_rows(sc, cam, 1, y0, y1, rgb, dcdx, dcdy, depth, alpha, NULL, NULL, NULL, NULL, NULL);
 }
 
 static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y0, int y1, double *rgb,
                        double *dcdx, double *dcdy, double *depth, double *alpha, double *final_T,
-                       int32_t *n_blended, uint32_t *sig)
+                       int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs)
 {
     const int W = cam->width, H = cam->height;
     const int64_t HW = (int64_t)W * H;
@@ -673,6 +685,12 @@ static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y
                 if (final_T) final_T[p] = o.T;
                 if (n_blended) n_blended[p] = o.n_blended;
                 if (sig) sig[p] = o.sig;
+                if (amb) amb[p] = o.amb;
+                if (gabs)
+                    for (int c = 0; c < 3; ++c) {
+                        gabs[c * HW + p] = o.gx_abs[c];
+                        gabs[(3 + c) * HW + p] = o.gy_abs[c];
+                    }
             }
         }
         free(buf);

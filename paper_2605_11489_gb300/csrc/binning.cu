@@ -117,7 +117,12 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
     if (overflow) atomicOr(&counters[kCntErr], kErrCapacity);
 }
 
-__global__ void k_ranges(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ counters, uint2 *ranges)
+// Per-tile [start, end) of the sorted keys and, in the same pass, the records
+// gathered into sorted (instance) order, so compositing stages each batch of a
+// tile's list with one contiguous bulk copy.
+__global__ void k_ranges(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                         const uint32_t *__restrict__ counters, const GaussRec *__restrict__ rec,
+                         GaussRec *__restrict__ rec_sorted, uint2 *ranges)
 {
     const uint32_t K = counters[kCntEff];
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,9 +130,51 @@ __global__ void k_ranges(const uint64_t *__restrict__ keys, const uint32_t *__re
     const uint32_t t = (uint32_t)(keys[i] >> 32);
     if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = i;
     if (i == K - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = i + 1;
+    if (rec_sorted) {
+        const GaussRec *src = rec + vals[i];
+        GaussRec r;
+        r.r0 = __ldg(&src->r0);
+        r.r1 = __ldg(&src->r1);
+        r.r2 = __ldg(&src->r2);
+        rec_sorted[i] = r;
+    }
+}
+
+// Tiles ordered by decreasing list length, bucketed by floor(log2(length)), so
+// compositing dispatches the heaviest tiles first and the light ones fill in.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, int n_tiles,
+                                                     uint32_t *__restrict__ order)
+{
+    __shared__ uint32_t s_cnt[33];
+    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    auto bucket = [&](int t) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+        return len == 0 ? 32 : __clz(len);  // longer lists -> smaller bucket index
+    };
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&s_cnt[bucket(t)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < 33; ++b) {
+            const uint32_t c = s_cnt[b];
+            s_cnt[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(t)], 1u)] = (uint32_t)t;
 }
 
 }  // namespace
+
+cudaError_t launch_tile_order(const uint2 *ranges, int n_tiles, uint32_t *order, cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    k_tile_order<<<1, 1024, 0, s>>>(ranges, n_tiles, order);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_scan_blocks(const uint32_t *block_sums, int nblocks, uint32_t *block_offsets, uint32_t *counters,
                                int64_t capacity, cudaStream_t s)
@@ -148,15 +195,15 @@ cudaError_t launch_duplicate(const uint32_t *ntiles, const uint4 *bin, const uin
     return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const uint64_t *keys, const uint32_t *counters, int64_t max_k, uint2 *ranges, int n_tiles,
-                          cudaStream_t s)
+cudaError_t launch_ranges(const uint64_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
+                          const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess) return e;
     if (max_k <= 0) return cudaSuccess;
     const int threads = 256;
     const int64_t nb = (max_k + threads - 1) / threads;
-    k_ranges<<<(unsigned)nb, threads, 0, s>>>(keys, counters, ranges);
+    k_ranges<<<(unsigned)nb, threads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges);
     return cudaGetLastError();
 }
 

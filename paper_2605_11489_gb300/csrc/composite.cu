@@ -13,23 +13,28 @@
 // tile size.
 //
 // GB300 layout: one CTA per TILE x TILE tile, one pixel per thread. The tile's
-// Gaussian records (48 B each) are gathered into shared memory in batches of
-// BATCH by TMA bulk copies (cp.async.bulk, one per record, completion counted
-// on an mbarrier), double-buffered so batch b+1 lands while batch b is blended.
-// Every lane of the warp reads the same record (a shared-memory broadcast).
-// Warps whose pixels are all saturated skip the batch (warp ballot); the CTA
-// stops loading once every pixel is done. Waits on the mbarrier are bounded.
+// records (48 B each, already gathered into sorted order, so a tile's list is
+// contiguous) are staged into shared memory in batches of BATCH by one TMA
+// bulk copy per batch (cp.async.bulk, completion counted on an mbarrier), in a
+// ring of NSTAGE buffers so that NSTAGE-1 batches are in flight while one is
+// blended. Every lane of a warp reads the same record (shared-memory
+// broadcast). Per landed batch each warp builds, with one ballot per 32
+// records, the mask of records whose rectangle reaches its pixel rows, and
+// visits only those, in order. Warps whose pixels are all saturated skip
+// (warp ballot); the CTA stops loading once every pixel is done. Tiles are
+// dispatched heaviest first. Waits on the mbarriers are bounded.
 #include "gsr_internal.cuh"
 
 namespace gsr {
 namespace {
 
 constexpr uint32_t kWaitTries = 1u << 22;
+constexpr int kStages = 3;
 
 template <int TILE, int BATCH>
 struct TileSmem {
-    GaussRec rec[2][BATCH];
-    uint64_t bar[2];
+    GaussRec rec[kStages][BATCH];
+    uint64_t bar[kStages];
 };
 
 struct PixelAcc {
@@ -39,29 +44,32 @@ struct PixelAcc {
     bool done;
 };
 
-// Composites one tile. `phase` carries the two mbarriers' parities across
-// tiles (persistent use). Returns false if a bounded wait gave up.
+// Composites one tile. `phase` carries the mbarriers' parities across tiles
+// (persistent use). Returns false if a bounded wait gave up.
 template <int TILE, int BATCH, bool GRAD, bool STATE>
 __device__ __forceinline__ bool composite_tile(const CompositeArgs &a, int tile_x, int tile_y,
-                                               TileSmem<TILE, BATCH> &sm, uint32_t (&phase)[2])
+                                               TileSmem<TILE, BATCH> &sm, uint32_t (&phase)[kStages])
 {
-    constexpr int NT = TILE * TILE;
-    const int tid = threadIdx.x;
-    const int lx = tid % TILE, ly = tid / TILE;
-    const int px = tile_x * TILE + lx, py = tile_y * TILE + ly;
+    // each warp owns an 8 x 4 pixel block of the tile, so a small Gaussian's
+    // support covers a large share of the warp's lanes and misses most warps
+    constexpr int WX = 8, WY = 4, WPR = TILE / WX;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bx0 = tile_x * TILE + (warp % WPR) * WX, by0 = tile_y * TILE + (warp / WPR) * WY;
+    const int px = bx0 + (lane % WX), py = by0 + (lane / WX);
     const bool inside = px < a.width && py < a.height;
     const uint2 range = a.ranges[tile_y * a.tiles_x + tile_x];
     const uint32_t total = range.y > range.x ? range.y - range.x : 0u;
     const int nbatches = (int)((total + BATCH - 1) / BATCH);
 
+    // batch b -> buffer b % kStages; one bulk copy of the batch's contiguous records
     auto issue = [&](int b) {
-        const int buf = b & 1;
-        const uint32_t start = range.x + (uint32_t)b * BATCH;
-        const uint32_t cnt = min((uint32_t)BATCH, range.y - start);
-        if (tid == 0) mbar_arrive_expect_tx(&sm.bar[buf], cnt * (uint32_t)sizeof(GaussRec));
-        for (uint32_t t = tid; t < cnt; t += NT) {
-            const uint32_t idx = a.vals[start + t];
-            tma_bulk_g2s(&sm.rec[buf][t], a.rec + idx, (uint32_t)sizeof(GaussRec), &sm.bar[buf]);
+        if (tid == 0) {
+            const int buf = b % kStages;
+            const uint32_t start = range.x + (uint32_t)b * BATCH;
+            const uint32_t cnt = min((uint32_t)BATCH, range.y - start);
+            const uint32_t bytes = cnt * (uint32_t)sizeof(GaussRec);
+            mbar_arrive_expect_tx(&sm.bar[buf], bytes);
+            tma_bulk_g2s(&sm.rec[buf][0], a.rec + start, bytes, &sm.bar[buf]);
         }
     };
 
@@ -74,55 +82,73 @@ __device__ __forceinline__ bool composite_tile(const CompositeArgs &a, int tile_
     s.done = !inside;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
     const uint32_t upx = (uint32_t)px, upy = (uint32_t)py;
+    const uint32_t wx0 = (uint32_t)bx0, wx1 = (uint32_t)(bx0 + WX - 1);
+    const uint32_t wy0 = (uint32_t)by0, wy1 = (uint32_t)(by0 + WY - 1);
     bool ok = true;
 
-    if (nbatches > 0) issue(0);
+    for (int b = 0; b < kStages - 1 && b < nbatches; ++b) issue(b);
     int b = 0;
     for (; b < nbatches; ++b) {
-        const int buf = b & 1;
-        if (b + 1 < nbatches) issue(b + 1);
+        const int buf = b % kStages;
+        if (b + kStages - 1 < nbatches) issue(b + kStages - 1);
         if (!mbar_wait_bounded(&sm.bar[buf], phase[buf], kWaitTries)) ok = false;
         phase[buf] ^= 1u;
         const uint32_t cnt = min((uint32_t)BATCH, range.y - (range.x + (uint32_t)b * BATCH));
         const bool warp_idle = __all_sync(0xffffffffu, s.done || !ok);
         if (ok && !warp_idle) {
             const GaussRec *recs = sm.rec[buf];
-            for (uint32_t k = 0; k < cnt && !s.done; ++k) {
-                const float4 r2 = recs[k].r2;
-                if (!rect_contains(r2, upx, upy)) continue;
-                const float4 r0 = recs[k].r0;
-                const float4 r1 = recs[k].r1;
-                const AlphaEval e = eval_alpha(r0, r1, pxc, pyc);
-                const float al = e.al;
-                const bool capped = e.capped;
-                const float ex = e.ex, ey = e.ey;
-                if (al < kAlphaMin) continue;
-                const float om = __fsub_rn(1.0f, al);
-                const float nT = __fmul_rn(s.T, om);
-                if (nT < kTMin) {
-                    s.done = true;
-                    break;
+            // which of the batch's records reach this warp's pixel block (one ballot per 32 records)
+            uint32_t rows_mask[BATCH / 32];
+#pragma unroll
+            for (int w = 0; w < BATCH / 32; ++w) {
+                const uint32_t k = (uint32_t)w * 32u + (uint32_t)lane;
+                bool hit = false;
+                if (k < cnt) {
+                    const uint32_t lo = __float_as_uint(recs[k].r2.z), hi = __float_as_uint(recs[k].r2.w);
+                    hit = (hi >> 16) >= wy0 && (lo >> 16) <= wy1 && (hi & 0xFFFFu) >= wx0 && (lo & 0xFFFFu) <= wx1;
                 }
-                const float w = __fmul_rn(al, s.T);
-                const float col[3] = {r1.w, r2.x, r2.y};
+                rows_mask[w] = __ballot_sync(0xffffffffu, hit);
+            }
 #pragma unroll
-                for (int c = 0; c < 3; ++c) s.C[c] = __fmaf_rn(col[c], w, s.C[c]);
-                s.D = __fmaf_rn(r1.z, w, s.D);
-                if (GRAD) {
-                    const float ax = capped ? 0.0f : -__fmul_rn(al, ex);
-                    const float ay = capped ? 0.0f : -__fmul_rn(al, ey);
-                    const float wx = __fmaf_rn(s.Tx, al, __fmul_rn(s.T, ax));
-                    const float wy = __fmaf_rn(s.Ty, al, __fmul_rn(s.T, ay));
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        s.Cx[c] = __fmaf_rn(col[c], wx, s.Cx[c]);
-                        s.Cy[c] = __fmaf_rn(col[c], wy, s.Cy[c]);
+            for (int w = 0; w < BATCH / 32; ++w) {
+                uint32_t m = s.done ? 0u : rows_mask[w];
+                while (m) {
+                    const uint32_t k = (uint32_t)w * 32u + (uint32_t)(__ffs(m) - 1);
+                    m &= m - 1u;
+                    const float4 r2 = recs[k].r2;
+                    if (!rect_contains(r2, upx, upy)) continue;
+                    const float4 r0 = recs[k].r0;
+                    const float4 r1 = recs[k].r1;
+                    const AlphaEval e = eval_alpha(r0, r1, pxc, pyc);
+                    const float al = e.al;
+                    if (al < kAlphaMin) continue;
+                    const float om = __fsub_rn(1.0f, al);
+                    const float nT = __fmul_rn(s.T, om);
+                    if (nT < kTMin) {
+                        s.done = true;
+                        break;
                     }
-                    s.Tx = __fmaf_rn(-ax, s.T, __fmul_rn(om, s.Tx));
-                    s.Ty = __fmaf_rn(-ay, s.T, __fmul_rn(om, s.Ty));
+                    const float wgt = __fmul_rn(al, s.T);
+                    const float col[3] = {r1.w, r2.x, r2.y};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) s.C[c] = __fmaf_rn(col[c], wgt, s.C[c]);
+                    s.D = __fmaf_rn(r1.z, wgt, s.D);
+                    if (GRAD) {
+                        const float ax = e.capped ? 0.0f : -__fmul_rn(al, e.ex);
+                        const float ay = e.capped ? 0.0f : -__fmul_rn(al, e.ey);
+                        const float wx = __fmaf_rn(s.Tx, al, __fmul_rn(s.T, ax));
+                        const float wy = __fmaf_rn(s.Ty, al, __fmul_rn(s.T, ay));
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            s.Cx[c] = __fmaf_rn(col[c], wx, s.Cx[c]);
+                            s.Cy[c] = __fmaf_rn(col[c], wy, s.Cy[c]);
+                        }
+                        s.Tx = __fmaf_rn(-ax, s.T, __fmul_rn(om, s.Tx));
+                        s.Ty = __fmaf_rn(-ay, s.T, __fmul_rn(om, s.Ty));
+                    }
+                    s.T = nT;
+                    if (STATE) s.last = (uint32_t)b * BATCH + k + 1u;
                 }
-                s.T = nT;
-                if (STATE) s.last = (uint32_t)b * BATCH + k + 1u;
             }
         }
         if (!ok) s.done = true;
@@ -131,10 +157,10 @@ __device__ __forceinline__ bool composite_tile(const CompositeArgs &a, int tile_
             break;
         }
     }
-    // a batch issued ahead of an early exit must land before its buffer is reused or the CTA exits
-    if (b < nbatches) {
-        if (!mbar_wait_bounded(&sm.bar[b & 1], phase[b & 1], kWaitTries)) ok = false;
-        phase[b & 1] ^= 1u;
+    // batches issued ahead of an early exit must land before their buffers are reused or the CTA exits
+    for (int q = b; q < nbatches && q < b + kStages - 1; ++q) {
+        if (!mbar_wait_bounded(&sm.bar[q % kStages], phase[q % kStages], kWaitTries)) ok = false;
+        phase[q % kStages] ^= 1u;
     }
     if (inside) {
         const int64_t HW = (int64_t)a.width * a.height;
@@ -162,18 +188,27 @@ __device__ __forceinline__ bool composite_tile(const CompositeArgs &a, int tile_
     return ok;
 }
 
+template <int TILE, int BATCH>
+__device__ __forceinline__ void init_barriers(TileSmem<TILE, BATCH> &sm)
+{
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < kStages; ++s) mbar_init(&sm.bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
 template <int TILE, int BATCH, bool GRAD, bool STATE>
 __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
 {
     __shared__ TileSmem<TILE, BATCH> sm;
-    if (threadIdx.x == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    uint32_t phase[2] = {0u, 0u};
-    const bool ok = composite_tile<TILE, BATCH, GRAD, STATE>(a, blockIdx.x, blockIdx.y, sm, phase);
+    init_barriers(sm);
+    uint32_t phase[kStages] = {};
+    // heaviest tiles first: CTAs are dispatched roughly in blockIdx order
+    const uint32_t t = a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x;
+    const int tx = (int)(t % (uint32_t)a.tiles_x), ty = (int)(t / (uint32_t)a.tiles_x);
+    const bool ok = composite_tile<TILE, BATCH, GRAD, STATE>(a, tx, ty, sm, phase);
     if (!ok && threadIdx.x == 0) atomicOr(a.err_word, kErrTmaTimeout);
 }
 
@@ -190,14 +225,9 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_persistent(const Serve
     __shared__ uint32_t s_first[kMaxServeReqs + 1];
     __shared__ uint32_t s_item;
     for (int r = threadIdx.x; r < n_reqs; r += blockDim.x) s_first[r] = reqs[r].first_item;
-    if (threadIdx.x == 0) {
-        s_first[n_reqs] = total_items;
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    uint32_t phase[2] = {0u, 0u};
+    if (threadIdx.x == 0) s_first[n_reqs] = total_items;
+    init_barriers(sm);
+    uint32_t phase[kStages] = {};
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(work_counter, 1u);
         __syncthreads();
@@ -211,7 +241,8 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_persistent(const Serve
             else hi = mid - 1;
         }
         const CompositeArgs &a = reqs[lo].args;
-        const uint32_t t = item - s_first[lo];
+        uint32_t t = item - s_first[lo];
+        if (a.tile_order) t = a.tile_order[t];
         const int tx = (int)(t % (uint32_t)a.tiles_x), ty = (int)(t / (uint32_t)a.tiles_x);
         bool ok;
         if (a.dcdx || a.dcdy) ok = composite_tile<TILE, BATCH, true, false>(a, tx, ty, sm, phase);
@@ -224,7 +255,7 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_persistent(const Serve
 template <int TILE, int BATCH>
 cudaError_t launch_tb(const CompositeArgs &a, cudaStream_t s)
 {
-    const dim3 grid(a.tiles_x, a.tiles_y);
+    const dim3 grid(a.tiles_x * a.tiles_y);
     const bool grad = a.dcdx || a.dcdy;
     const bool state = a.final_T != nullptr;
     if (grad && state) k_composite<TILE, BATCH, true, true><<<grid, TILE * TILE, 0, s>>>(a);
@@ -276,9 +307,9 @@ cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, cudaSt
 int composite_persistent_grid(int tile, int batch)
 {
     (void)batch;
-    if (tile == 8) return persistent_grid<8, 64>();
-    if (tile == 32) return persistent_grid<32, 64>();
-    return persistent_grid<16, 64>();
+    if (tile == 8) return persistent_grid<8, 128>();
+    if (tile == 32) return persistent_grid<32, 128>();
+    return persistent_grid<16, 128>();
 }
 
 cudaError_t launch_composite_persistent(const ServeItem *reqs, int n_reqs, uint32_t total_items, int tile, int batch,
@@ -287,9 +318,9 @@ cudaError_t launch_composite_persistent(const ServeItem *reqs, int n_reqs, uint3
     (void)batch;
     if (n_reqs <= 0 || total_items == 0) return cudaSuccess;
     if (n_reqs > kMaxServeReqs) return cudaErrorInvalidValue;
-    if (tile == 8) k_composite_persistent<8, 64><<<grid, 64, 0, s>>>(reqs, n_reqs, total_items, work_counter);
-    else if (tile == 32) k_composite_persistent<32, 64><<<grid, 1024, 0, s>>>(reqs, n_reqs, total_items, work_counter);
-    else k_composite_persistent<16, 64><<<grid, 256, 0, s>>>(reqs, n_reqs, total_items, work_counter);
+    if (tile == 8) k_composite_persistent<8, 128><<<grid, 64, 0, s>>>(reqs, n_reqs, total_items, work_counter);
+    else if (tile == 32) k_composite_persistent<32, 128><<<grid, 1024, 0, s>>>(reqs, n_reqs, total_items, work_counter);
+    else k_composite_persistent<16, 128><<<grid, 256, 0, s>>>(reqs, n_reqs, total_items, work_counter);
     return cudaGetLastError();
 }
 

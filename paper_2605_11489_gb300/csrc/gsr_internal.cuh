@@ -103,9 +103,9 @@ cudaError_t launch_scan_blocks(const uint32_t *block_sums, int nblocks, uint32_t
 cudaError_t launch_duplicate(const uint32_t *ntiles, const uint4 *bin, const uint32_t *block_offsets,
                              int64_t n, int tile_shift, int tiles_x, uint64_t *keys, uint32_t *vals,
                              int64_t capacity, uint32_t *counters, cudaStream_t s);
-// per-tile [start, end) from sorted keys
-cudaError_t launch_ranges(const uint64_t *keys, const uint32_t *counters, int64_t max_k, uint2 *ranges,
-                          int n_tiles, cudaStream_t s);
+// per-tile [start, end) from sorted keys, plus the records gathered into sorted order
+cudaError_t launch_ranges(const uint64_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
+                          const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, cudaStream_t s);
 
 // onesweep LSD radix sort of (keys, vals) on the low `bits` bits, K from counters[kCntEff]
 struct SortScratch {
@@ -122,7 +122,7 @@ cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *co
                         int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s);
 
 struct CompositeArgs {
-    const GaussRec *rec;
+    const GaussRec *rec;  // records in sorted (instance) order: tile t's list is rec[ranges[t].x, ranges[t].y)
     const uint32_t *vals;
     const uint2 *ranges;
     int32_t width, height, tiles_x, tiles_y;
@@ -131,7 +131,10 @@ struct CompositeArgs {
     float *final_T, *final_Tx, *final_Ty;  // backward state (nullable)
     uint32_t *n_contrib;
     uint32_t *err_word;
+    const uint32_t *tile_order;  // tiles by decreasing list length (nullable = row-major)
 };
+// order tiles by decreasing list length (power-of-two buckets)
+cudaError_t launch_tile_order(const uint2 *ranges, int n_tiles, uint32_t *order, cudaStream_t s);
 bool composite_supported(int tile, int batch);
 cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, cudaStream_t s);
 

@@ -78,8 +78,8 @@ struct Buf {
 // All per-frame device buffers. Owned by a context (pooled), a state or a graph.
 struct Frame {
     Buf rec, bin, ntiles, bsums, boffs;
-    Buf keys[2], vals[2], sort_scr;
-    Buf ranges;
+    Buf keys[2], vals[2], sort_scr, rec_sorted;
+    Buf ranges, order;
     Buf fT, fTx, fTy, ncontrib;
     Buf counters;
     int64_t n = 0, K = 0, key_cap = 0;
@@ -120,10 +120,14 @@ struct StageTimer {
     {
         cudaEvent_t *e = &ev[(size_t)slot * kBounds];
         cudaEventSynchronize(e[kBounds - 1]);
-        for (int k = 0; k < kBounds - 1; ++k) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, e[k], e[k + 1]) == cudaSuccess) sum_ms[k] += ms;
+        bool ok = true;
+        float ms[kBounds - 1];
+        for (int k = 0; k < kBounds - 1 && ok; ++k) ok = cudaEventElapsedTime(&ms[k], e[k], e[k + 1]) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();  // do not leave the failure for the next launch check
+            return;
         }
+        for (int k = 0; k < kBounds - 1; ++k) sum_ms[k] += ms[k];
         ++folded;
     }
     // events of the next frame slot (the slot's previous frame is folded first)
@@ -307,6 +311,7 @@ gs_status frame_setup(Frame *f, const gs_scene *s, const gs_camera *c, const gs_
     GSR_CUDA(f->bsums.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
     GSR_CUDA(f->boffs.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
     GSR_CUDA(f->ranges.ensure(sizeof(uint2) * (size_t)f->n_tiles));
+    GSR_CUDA(f->order.ensure(sizeof(uint32_t) * (size_t)f->n_tiles));
     GSR_CUDA(f->counters.ensure(sizeof(uint32_t) * kCntSlots));
     const size_t hw = (size_t)f->W * f->H;
     if (state) {
@@ -326,6 +331,7 @@ gs_status frame_keys(Frame *f, int64_t cap)
     GSR_CUDA(f->vals[0].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(cap, 1)));
     GSR_CUDA(f->vals[1].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(cap, 1)));
     GSR_CUDA(f->sort_scr.ensure(sort_scratch_bytes(std::max<int64_t>(cap, 1))));
+    GSR_CUDA(f->rec_sorted.ensure(sizeof(GaussRec) * (size_t)std::max<int64_t>(cap, 1)));
     f->key_cap = cap;
     return GS_OK;
 }
@@ -353,7 +359,7 @@ ProjectArgs proj_args(Frame *f, const gs_scene *s)
 CompositeArgs comp_args(Frame *f, const gs_outputs *out)
 {
     CompositeArgs c{};
-    c.rec = f->rec.as<GaussRec>();
+    c.rec = f->rec_sorted.as<GaussRec>();
     c.vals = f->vals[f->sorted].as<uint32_t>();
     c.ranges = f->ranges.as<uint2>();
     c.width = f->W;
@@ -373,6 +379,7 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
         c.n_contrib = f->ncontrib.as<uint32_t>();
     }
     c.err_word = f->counters.as<uint32_t>() + kCntErr;
+    c.tile_order = f->order.as<uint32_t>();
     return c;
 }
 
@@ -400,7 +407,9 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     GSR_CUDA(launch_sort(kk, vv, cnt, cnt + kCntErr, max_k, f->bits, scr, &res, st));
     f->sorted = res;
     GSR_CUDA(mark(ev, 4, st, capture));
-    GSR_CUDA(launch_ranges(f->keys[res].as<uint64_t>(), cnt, max_k, f->ranges.as<uint2>(), f->n_tiles, st));
+    GSR_CUDA(launch_ranges(f->keys[res].as<uint64_t>(), f->vals[res].as<uint32_t>(), cnt, max_k, f->rec.as<GaussRec>(),
+                           f->rec_sorted.as<GaussRec>(), f->ranges.as<uint2>(), f->n_tiles, st));
+    GSR_CUDA(launch_tile_order(f->ranges.as<uint2>(), f->n_tiles, f->order.as<uint32_t>(), st));
     GSR_CUDA(mark(ev, 5, st, capture));
     const CompositeArgs ca = comp_args(f, out);
     GSR_CUDA(launch_composite(ca, f->tile, f->batch, st));
@@ -502,6 +511,7 @@ gs_status gs_render_forward(gs_context *ctx, const gs_scene *scene, const gs_cam
     if (state && !(opts->flags & GS_EMIT_BWD_STATE))
         return fail(GS_ERR_INVALID_ARG, "a backward state needs GS_EMIT_BWD_STATE");
     GSR_CUDA(cudaSetDevice(ctx->device));
+    cudaGetLastError();  // a stale non-sticky error must not be charged to this call's launches
     Frame *f = ctx->acquire();
     r = forward_plain(ctx, scene, cam, opts, out, f, (cudaStream_t)stream);
     if (r != GS_OK) {
@@ -534,6 +544,7 @@ gs_status gs_render_forward_to_host(gs_context *ctx, const gs_scene *scene, cons
     gs_status r = check_cam(cam);
     if (r != GS_OK) return r;
     GSR_CUDA(cudaSetDevice(ctx->device));
+    cudaGetLastError();  // a stale non-sticky error must not be charged to this call's launches
     const size_t hw = (size_t)cam->width * cam->height;
     GSR_CUDA(ctx->host_planes.ensure(sizeof(float) * hw * 11));
     float *d = ctx->host_planes.as<float>();
@@ -568,6 +579,7 @@ gs_status gs_render_backward(gs_context *ctx, const gs_fwd_state *state, const g
     if (scene->n != state->n || scene->n_pad != state->n_pad || scene->sh_degree != f->deg)
         return fail(GS_ERR_INVALID_ARG, "scene does not match the forward state");
     GSR_CUDA(cudaSetDevice(ctx->device));
+    cudaGetLastError();  // a stale non-sticky error must not be charged to this call's launches
     cudaStream_t st = (cudaStream_t)stream;
     if (f->n == 0) return GS_OK;
     GSR_CUDA(ctx->g2d.ensure(sizeof(float) * 10 * (size_t)f->n));
@@ -656,6 +668,7 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
     if ((r = check_cam(cam)) != GS_OK) return r;
     if (opts->flags & GS_EMIT_BWD_STATE) return fail(GS_ERR_INVALID_ARG, "graphs do not keep backward state");
     GSR_CUDA(cudaSetDevice(ctx->device));
+    cudaGetLastError();  // a stale non-sticky error must not be charged to this call's launches
     int tile, batch;
     pick_tile_batch(ctx, scene, cam, opts, &tile, &batch);
     if (!composite_supported(tile, batch)) return fail(GS_ERR_INVALID_ARG, "unsupported tile/batch");
@@ -750,6 +763,7 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
                 }
                 for (int k = 0; k < StageTimer::kBounds; ++k)
                     if (!g->ev_node[k]) r = fail(GS_ERR_CUDA, "stage event node not found in captured graph");
+                g->timer.reset();  // the capture-time event set was never recorded
             }
         }
     }

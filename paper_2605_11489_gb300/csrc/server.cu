@@ -155,7 +155,8 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_scan = nullptr, ev_sorted = nullptr;
-    DevBuf rec, bin, ntiles, bsums, boffs, ranges, counters;
+    DevBuf rec, bin, ntiles, bsums, boffs, ranges, order, counters;
+    GaussRec *rec_sorted = nullptr;  // in the sort memory
     uint32_t *h_counters = nullptr;  // pinned
     void *sort_mem = nullptr;        // from the arena
     Request *req = nullptr;
@@ -233,7 +234,8 @@ size_t sort_bytes(int64_t K)
 {
     const int64_t k = std::max<int64_t>(K, 1);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return 2 * up(sizeof(uint64_t) * k) + 2 * up(sizeof(uint32_t) * k) + up(sort_scratch_bytes(k));
+    return 2 * up(sizeof(uint64_t) * k) + 2 * up(sizeof(uint32_t) * k) + up(sizeof(GaussRec) * k) +
+           up(sort_scratch_bytes(k));
 }
 
 // Stage 1: projection + scan on the slot's stream; K copied back.
@@ -255,6 +257,7 @@ gs_status admit(gs_server *S, int si, Request *r)
     GSR_CUDA(sl.bsums.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
     GSR_CUDA(sl.boffs.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
     GSR_CUDA(sl.ranges.ensure(sizeof(uint2) * (size_t)sl.n_tiles));
+    GSR_CUDA(sl.order.ensure(sizeof(uint32_t) * (size_t)sl.n_tiles));
     GSR_CUDA(sl.counters.ensure(sizeof(uint32_t) * kCntSlots));
     uint32_t *cnt = static_cast<uint32_t *>(sl.counters.p);
     GSR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * kCntSlots, sl.stream));
@@ -301,6 +304,8 @@ gs_status enqueue_sort(gs_server *S, Slot &sl)
     p += up(sizeof(uint32_t) * k1);
     sl.vals[1] = reinterpret_cast<uint32_t *>(p);
     p += up(sizeof(uint32_t) * k1);
+    sl.rec_sorted = reinterpret_cast<GaussRec *>(p);
+    p += up(sizeof(GaussRec) * k1);
     GSR_CUDA(launch_duplicate(static_cast<uint32_t *>(sl.ntiles.p), static_cast<uint4 *>(sl.bin.p),
                               static_cast<uint32_t *>(sl.boffs.p), s.n, sl.cam.tile_shift, sl.cam.tiles_x, sl.keys[0],
                               sl.vals[0], K, cnt, sl.stream));
@@ -309,7 +314,10 @@ gs_status enqueue_sort(gs_server *S, Slot &sl)
     int res = 0;
     GSR_CUDA(launch_sort(sl.keys, sl.vals, cnt, cnt + kCntErr, K, sl.bits, scr, &res, sl.stream));
     sl.sorted = res;
-    GSR_CUDA(launch_ranges(sl.keys[res], cnt, K, static_cast<uint2 *>(sl.ranges.p), sl.n_tiles, sl.stream));
+    GSR_CUDA(launch_ranges(sl.keys[res], sl.vals[res], cnt, K, static_cast<const GaussRec *>(sl.rec.p), sl.rec_sorted,
+                           static_cast<uint2 *>(sl.ranges.p), sl.n_tiles, sl.stream));
+    GSR_CUDA(launch_tile_order(static_cast<const uint2 *>(sl.ranges.p), sl.n_tiles, static_cast<uint32_t *>(sl.order.p),
+                               sl.stream));
     GSR_CUDA(cudaEventRecord(sl.ev_sorted, sl.stream));
     r->stage = Stage::Sorted;
     return GS_OK;
@@ -319,8 +327,9 @@ CompositeArgs slot_comp_args(Slot &sl)
 {
     Request *r = sl.req;
     CompositeArgs c{};
-    c.rec = static_cast<const GaussRec *>(sl.rec.p);
+    c.rec = sl.rec_sorted;
     c.vals = sl.vals[sl.sorted];
+    c.tile_order = static_cast<const uint32_t *>(sl.order.p);
     c.ranges = static_cast<const uint2 *>(sl.ranges.p);
     c.width = r->cam.width;
     c.height = r->cam.height;
@@ -637,6 +646,7 @@ gs_status gs_server_destroy(gs_server *S)
         sl.bsums.release();
         sl.boffs.release();
         sl.ranges.release();
+        sl.order.release();
         sl.counters.release();
     }
     for (SceneRes &s : S->scenes)

@@ -1,0 +1,162 @@
+"""Continuous-batching server through the C ABI: every request's output is
+the same alone and in a mixed stream, admission respects the sort-buffer
+budget, cancellation and not-ready polls work, and a host-injected failure
+ends only its own request. No test faults or hangs the GPU: failures are
+injected on the host (GSR_FAULT) and every wait has a deadline."""
+import os
+import time
+
+import numpy as np
+import pytest
+
+from paper_2605_11489_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_2605_11489_gb300 import api
+
+    torch.cuda.set_device(0)
+    return api, api.Context(0)
+
+
+def _wait(srv, rid, deadline_s=60.0):
+    from paper_2605_11489_gb300 import abi
+
+    t0 = time.time()
+    while True:
+        st, lat = srv.poll(rid)
+        if st != abi.GS_NOT_READY:
+            return st, lat
+        assert time.time() - t0 < deadline_s, "request %d not done after %.0f s" % (rid, deadline_s)
+        time.sleep(0.001)
+
+
+def _mixed_requests(n, seed):
+    rng = np.random.default_rng(seed)
+    res = [(64, 48), (256, 144), (203, 117), (480, 270)]
+    cams = []
+    for _ in range(n):
+        w, h = res[rng.integers(len(res))]
+        eye = np.array([0.0, 0.0, 4.0]) + rng.normal(0, 0.5, 3)
+        cams.append((int(rng.integers(2)), synth.make_camera(eye, (0, 0, 0), (0, 1, 0), w, h)))
+    return cams
+
+
+def test_requests_same_alone_and_in_the_mix(env):
+    api, ctx = env
+    import torch
+
+    scenes = [api.Scene.from_arrays(synth.tiny_scene(4096, 0)),
+              api.Scene.from_arrays(synth.clustered_scene(20_000, 5, (2.0, 2.0, 2.0), 8, 3))]
+    srv = api.Server(sort_budget_bytes=256 << 20, max_inflight=6)
+    ids = [srv.load_scene(s) for s in scenes]
+    reqs = _mixed_requests(40, 1)
+    bg = (0.1, 0.2, 0.3)
+    outs, rids = [], []
+    for sid, cam in reqs:
+        o = api.alloc_outputs(cam.width, cam.height)
+        outs.append(o)
+        rids.append(srv.submit(ids[sid], cam, o, bg=bg))
+    lats = []
+    for rid in rids:
+        st, lat = _wait(srv, rid)
+        assert st == 0
+        lats.append(lat)
+    assert min(lats) > 0
+    for (sid, cam), o in zip(reqs, outs):
+        ref = ctx.forward(scenes[sid], cam, tile=16, bg=bg)
+        for k in ref:
+            assert torch.equal(o[k], ref[k]), k
+    srv.close()
+
+
+def test_poll_before_ready_and_drain(env):
+    api, ctx = env
+    from paper_2605_11489_gb300 import abi
+
+    scene = api.Scene.from_arrays(synth.clustered_scene(200_000, 6, (2.0, 2.0, 2.0), 8, 3))
+    srv = api.Server(sort_budget_bytes=512 << 20, max_inflight=4)
+    sid = srv.load_scene(scene)
+    cam = synth.make_camera((0.5, 0.3, 4.0), (1, 1, 1), (0, 1, 0), 480, 270)
+    rids = [srv.submit(sid, cam, api.alloc_outputs(480, 270)) for _ in range(16)]
+    st0, _ = srv.poll(rids[-1])
+    assert st0 == abi.GS_NOT_READY
+    srv.drain()
+    for rid in rids:
+        st, lat = srv.poll(rid)
+        assert st == 0 and lat > 0
+    with pytest.raises(Exception):
+        abi.check(abi.lib().gs_server_poll(srv.h, 10_000_000, None))
+    srv.close()
+
+
+def test_cancel_queued_request(env):
+    api, ctx = env
+    from paper_2605_11489_gb300 import abi
+
+    scene = api.Scene.from_arrays(synth.clustered_scene(200_000, 7, (2.0, 2.0, 2.0), 8, 3))
+    srv = api.Server(sort_budget_bytes=512 << 20, max_inflight=1)
+    sid = srv.load_scene(scene)
+    cam = synth.make_camera((0.0, 0.0, 4.0), (1, 1, 1), (0, 1, 0), 480, 270)
+    rids = [srv.submit(sid, cam, api.alloc_outputs(480, 270)) for _ in range(12)]
+    srv.cancel(rids[-1])
+    st, _ = _wait(srv, rids[-1])
+    assert st in (abi.GS_ERR_CANCELLED, 0)
+    srv.drain()
+    srv.close()
+
+
+def test_admission_waits_for_budget_and_rejects_oversized(env):
+    api, ctx = env
+    import torch
+
+    from paper_2605_11489_gb300 import abi
+
+    scene = api.Scene.from_arrays(synth.tiny_scene(4096, 8))
+    cam = synth.tiny_camera()
+    # about 6,700 instances * ~75 B: one request's sort memory is ~0.5 MB
+    srv = api.Server(sort_budget_bytes=1 << 20, max_inflight=8)
+    sid = srv.load_scene(scene)
+    outs = [api.alloc_outputs(cam.width, cam.height) for _ in range(10)]
+    rids = [srv.submit(sid, cam, o) for o in outs]
+    for rid in rids:
+        assert _wait(srv, rid)[0] == 0
+    ref = ctx.forward(scene, cam, tile=16)
+    for o in outs:
+        assert torch.equal(o["rgb"], ref["rgb"])
+    srv.close()
+    tiny = api.Server(sort_budget_bytes=4096, max_inflight=2)
+    sid = tiny.load_scene(scene)
+    rid = tiny.submit(sid, cam, api.alloc_outputs(cam.width, cam.height))
+    assert _wait(tiny, rid)[0] == abi.GS_ERR_OOM
+    tiny.close()
+
+
+@pytest.mark.parametrize("fault", ["alloc:1", "enqueue:2"])
+def test_injected_host_failure_ends_only_its_request(env, fault):
+    api, ctx = env
+    scene = api.Scene.from_arrays(synth.tiny_scene(4096, 9))
+    cam = synth.tiny_camera()
+    old = os.environ.get("GSR_FAULT")
+    os.environ["GSR_FAULT"] = fault
+    try:
+        srv = api.Server(sort_budget_bytes=64 << 20, max_inflight=1)
+    finally:
+        if old is None:
+            del os.environ["GSR_FAULT"]
+        else:
+            os.environ["GSR_FAULT"] = old
+    sid = srv.load_scene(scene)
+    rids = [srv.submit(sid, cam, api.alloc_outputs(cam.width, cam.height)) for _ in range(5)]
+    sts = [_wait(srv, r)[0] for r in rids]
+    assert sum(1 for s in sts if s != 0) == 1, sts
+    assert sts[int(fault.split(":")[1])] != 0
+    srv.close()
