@@ -206,6 +206,7 @@ def main():
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--tile", type=int, default=0, help="tile side 8/16/32 (0 = autotune)")
     ap.add_argument("--batch", type=int, default=0, help="Gaussians per shared-memory batch (0 = autotune)")
+    ap.add_argument("--chunk", type=int, default=0, help="records per chunk of a split tile list (0 = autotune)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -235,12 +236,18 @@ def main():
         scene = api.Scene.from_arrays(sc)
         out = api.alloc_outputs(W, H)
     stream.synchronize()
-    # pre-pass (untimed): plain renders of every camera for the instance counts
+    # untimed: the autotuner's choice of tile / batch / chunk (unless given), then
+    # plain renders of every camera for the instance counts that size the graph
+    tile, batch, chunk = args.tile, args.batch, args.chunk
+    if not (tile and batch and chunk):
+        t, b, c, _ = ctx.autotune(scene, cams[0], out, iters=3, stream=stream)
+        tile, batch, chunk = tile or t, batch or b, chunk or c
     for cam in cams:
-        ctx.forward(scene, cam, out=out, stream=stream)
+        ctx.forward(scene, cam, out=out, tile=tile, batch=batch, chunk=chunk, stream=stream)
     pre = ctx.stats(reset=True, stream=stream)
     capacity = int(pre["instances_max"] * 1.25) + 4096
-    graph = ctx.graph(scene, cams[0], out, capacity=capacity, timed=True, stream=stream)
+    graph = ctx.graph(scene, cams[0], out, capacity=capacity, tile=tile, batch=batch, chunk=chunk, timed=True,
+                      stream=stream)
     for i in range(args.warmup):
         graph.render(cams[i % len(cams)], stream=stream)
     graph.stats(reset=True, stream=stream)
@@ -279,7 +286,7 @@ def main():
     frames = max(st["frames"], 1)
     K_avg = st["instances_total"] / frames
     V_avg = st["visible_total"] / frames
-    n_tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    n_tiles = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
     passes = math.ceil((32 + max(1, math.ceil(math.log2(max(n_tiles, 2))))) / 8)
     dom = max(stage_ms, key=lambda k: stage_ms[k])
     hbm_peak, sm_max_mhz, peak_src = measured_peaks()
@@ -299,12 +306,12 @@ def main():
         host = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in out.items()}
         e2e_steps = min(args.steps, 30)
         for i in range(2):
-            ctx.forward_to_host(scene, cams[i], host, stream=stream)
+            ctx.forward_to_host(scene, cams[i], host, tile=tile, batch=batch, stream=stream)
         if world > 1:
             torch.distributed.barrier()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
-            ctx.forward_to_host(scene, cams[i % len(cams)], host, stream=stream)
+            ctx.forward_to_host(scene, cams[i % len(cams)], host, tile=tile, batch=batch, stream=stream)
         dt = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([dt], device="cuda")
@@ -324,7 +331,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
                            "width": W, "height": H, "gaussians": sc.n, "sh_degree": sc.deg,
-                           "tile": 16, "batch": 64, "path": "CUDA graph replay per frame",
+                           "tile": tile, "batch": batch, "chunk": chunk, "path": "CUDA graph replay per frame",
                            "l2": "inputs larger than L2 (scene %.0f MB)" % (sc.nbytes() / 1e6),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "frames_per_s": 1e3 * args.steps * world / ms,

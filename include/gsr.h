@@ -91,6 +91,9 @@ typedef struct {
     int32_t batch;                /* Gaussians per shared-memory batch: 32/64/128/256; 0 = default */
     float bg[3];                  /* background colour */
     uint32_t flags;               /* GS_EMIT_* */
+    int32_t chunk;                /* a tile list longer than this is split into chunks composited in
+                                     parallel and merged exactly; multiple of 256, 0 = default 2048 */
+    int32_t _reserved;
 } gs_render_opts;
 
 /* Caller-owned device outputs; a NULL plane is not written (and, for dcdx and
@@ -206,13 +209,15 @@ gs_status gs_graph_stats(gs_graph *graph, gs_stream stream, int reset, gs_frame_
 gs_status gs_graph_destroy(gs_graph *graph);
 
 /* ---------------------------------------------------------------- autotuner
- * Times the forward for every tile in {8, 16, 32} and batch in
- * {32, 64, 128, 256} (CUDA events, `iters` frames each, after one warm-up)
- * and records the fastest in the context's cache, keyed by (W, H, N bucket,
- * SH degree); later calls with tile = 0 / batch = 0 use it. Synchronous. */
+ * Times the forward for every tile in {8, 16, 32}, batch in {32, 64, 128, 256}
+ * (pairs whose per-warp staging rings fit shared memory) and chunk in
+ * {512, 2048, 8192} (CUDA events, `iters` frames each, after one warm-up) and
+ * records the fastest in the context's cache, keyed by (W, H, N bucket, SH
+ * degree); later calls with tile / batch / chunk = 0 use it. Synchronous.
+ * Any output pointer may be NULL. */
 gs_status gs_autotune(gs_context *ctx, const gs_scene *scene, const gs_camera *cam,
                       const gs_outputs *out, int iters, gs_stream stream, int32_t *best_tile,
-                      int32_t *best_batch, float *best_ms);
+                      int32_t *best_batch, int32_t *best_chunk, float *best_ms);
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching over resident scenes: requests (scene, camera, options,

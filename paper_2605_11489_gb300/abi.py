@@ -50,7 +50,8 @@ class GsCamera(C.Structure):
 
 
 class GsRenderOpts(C.Structure):
-    _fields_ = [("tile", C.c_int32), ("batch", C.c_int32), ("bg", C.c_float * 3), ("flags", C.c_uint32)]
+    _fields_ = [("tile", C.c_int32), ("batch", C.c_int32), ("bg", C.c_float * 3), ("flags", C.c_uint32),
+                ("chunk", C.c_int32), ("_reserved", C.c_int32)]
 
 
 class GsOutputs(C.Structure):
@@ -106,7 +107,7 @@ def _declare(L):
         "gs_graph_stats": [P, P, C.c_int, C.POINTER(GsFrameStats)],
         "gs_context_stats": [P, P, C.c_int, C.POINTER(GsFrameStats)],
         "gs_autotune": [P, C.POINTER(GsScene), C.POINTER(GsCamera), C.POINTER(GsOutputs), C.c_int, P,
-                        C.POINTER(I32), C.POINTER(I32), C.POINTER(C.c_float)],
+                        C.POINTER(I32), C.POINTER(I32), C.POINTER(I32), C.POINTER(C.c_float)],
         "gs_server_create": [C.c_int, C.c_size_t, C.c_int, C.POINTER(P)],
         "gs_server_load_scene": [P, C.POINTER(GsScene), C.POINTER(I32)],
         "gs_server_submit": [P, I32, C.POINTER(GsCamera), C.POINTER(GsRenderOpts), C.POINTER(GsOutputs),

@@ -167,7 +167,106 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
     for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(t)], 1u)] = (uint32_t)t;
 }
 
+// Compositing work plan. A tile whose list is longer than `chunk` is split into
+// depth-contiguous chunks of `chunk` records; each chunk is a work item whose
+// per-pixel partial state goes to its own slot, and the split tile is merged
+// front to back afterwards. Items: all chunks first (slot order), then the
+// whole tiles, longest lists first. One CTA; tiles scanned in index order.
+//   items[i]       = (tile, start, end, slot | kWholeTile)
+//   split_tiles[s] = tile id of the s-th split tile, split_slot0[s] = its first slot
+//   counts         = (n_items, n_split, n_slots)
+__global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges, int n_tiles, uint32_t chunk,
+                                               uint4 *__restrict__ items, uint32_t *__restrict__ split_tiles,
+                                               uint32_t *__restrict__ split_slot0, uint32_t *__restrict__ counts)
+{
+    __shared__ uint32_t s_a[1024], s_b[1024];
+    __shared__ uint32_t s_cnt[33];
+    __shared__ uint32_t s_tot[2];
+    const int per = (n_tiles + 1023) / 1024;
+    const int t0 = threadIdx.x * per, t1 = min(n_tiles, t0 + per);
+    auto nch = [&](int t) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+        return len > chunk ? (len + chunk - 1) / chunk : 1u;
+    };
+    uint32_t my_split = 0, my_slots = 0;
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t c = nch(t);
+        if (c > 1) {
+            ++my_split;
+            my_slots += c;
+        }
+    }
+    s_a[threadIdx.x] = my_split;
+    s_b[threadIdx.x] = my_slots;
+    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // exclusive scans of 1024 per-thread totals
+        uint32_t ra = 0, rb = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const uint32_t a = s_a[i], b = s_b[i];
+            s_a[i] = ra;
+            s_b[i] = rb;
+            ra += a;
+            rb += b;
+        }
+        s_tot[0] = ra;
+        s_tot[1] = rb;
+    }
+    __syncthreads();
+    uint32_t sp = s_a[threadIdx.x], slot = s_b[threadIdx.x];
+    const uint32_t n_split = s_tot[0], n_slots = s_tot[1];
+    for (int t = t0; t < t1; ++t) {
+        const uint2 r = ranges[t];
+        const uint32_t c = nch(t);
+        if (c > 1) {
+            split_tiles[sp] = (uint32_t)t;
+            split_slot0[sp] = slot;
+            ++sp;
+            for (uint32_t k = 0; k < c; ++k) {
+                const uint32_t s0 = r.x + k * chunk;
+                items[slot + k] = make_uint4((uint32_t)t, s0, min(r.y, s0 + chunk), slot + k);
+            }
+            slot += c;
+        } else {
+            const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+            atomicAdd(&s_cnt[len == 0 ? 32 : __clz(len)], 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = n_slots;
+        for (int b = 0; b < 33; ++b) {
+            const uint32_t c = s_cnt[b];
+            s_cnt[b] = run;
+            run += c;
+        }
+        counts[0] = run;
+        counts[1] = n_split;
+        counts[2] = n_slots;
+    }
+    __syncthreads();
+    for (int t = t0; t < t1; ++t) {
+        if (nch(t) > 1) continue;
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+        const uint32_t pos = atomicAdd(&s_cnt[len == 0 ? 32 : __clz(len)], 1u);
+        items[pos] = make_uint4((uint32_t)t, r.x, r.x + len, kWholeTile);
+    }
+}
+
 }  // namespace
+
+int64_t plan_max_slots(int64_t max_k, int chunk) { return 2 * (max_k / chunk) + 2; }
+int64_t plan_max_items(int n_tiles, int64_t max_k, int chunk) { return n_tiles + plan_max_slots(max_k, chunk); }
+
+cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, uint4 *items, uint32_t *split_tiles,
+                        uint32_t *split_slot0, uint32_t *counts, cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 3, s);
+    k_plan<<<1, 1024, 0, s>>>(ranges, n_tiles, (uint32_t)chunk, items, split_tiles, split_slot0, counts);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tile_order(const uint2 *ranges, int n_tiles, uint32_t *order, cudaStream_t s)
 {

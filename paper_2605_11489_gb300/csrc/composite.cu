@@ -12,17 +12,28 @@
 // both skips most of a tile's pairs and makes the image independent of the
 // tile size.
 //
-// GB300 layout: one CTA per TILE x TILE tile, one pixel per thread. The tile's
-// records (48 B each, already gathered into sorted order, so a tile's list is
-// contiguous) are staged into shared memory in batches of BATCH by one TMA
-// bulk copy per batch (cp.async.bulk, completion counted on an mbarrier), in a
-// ring of NSTAGE buffers so that NSTAGE-1 batches are in flight while one is
-// blended. Every lane of a warp reads the same record (shared-memory
-// broadcast). Per landed batch each warp builds, with one ballot per 32
-// records, the mask of records whose rectangle reaches its pixel rows, and
-// visits only those, in order. Warps whose pixels are all saturated skip
-// (warp ballot); the CTA stops loading once every pixel is done. Tiles are
-// dispatched heaviest first. Waits on the mbarriers are bounded.
+// GB300 layout: one CTA per work item (a tile, or a chunk of a long tile
+// list), one pixel per thread, and every warp an independent 8x4 pixel block
+// with its own shared-memory ring of kStages batches of BATCH records and its
+// own mbarriers. Lane 0 stages the next batches of the tile's (contiguous,
+// sorted) records with one TMA bulk copy per batch (cp.async.bulk, completion
+// counted on the warp's mbarrier) while the warp blends the current one; the
+// warp builds, with one ballot per 32 records, the mask of records whose
+// rectangle reaches its block and visits only those, in order. No barrier
+// spans warps: a warp whose pixels are all saturated stops on its own. The
+// tile's list is read once per warp from L2 (DRAM once). Waits are bounded.
+//
+// Load balance: a tile whose list is longer than `chunk` records is split into
+// depth-contiguous chunks, one work item each, composited from the identity
+// state into per-pixel partial states (C, C_x, C_y, D, T, T_x, T_y). The merge
+// folds them front to back with the exact composition of two segments a, b:
+//   C = Ca + Ta Cb,  C_x = Cxa + Txa Cb + Ta Cxb,  D = Da + Ta Db,
+//   T = Ta Tb,       T_x = Txa Tb + Ta Txb                     (product rule)
+// which equals the sequential result as long as no Gaussian of the tile was
+// cut off by the T < 1e-4 stop. T only decreases, so the stop falls inside
+// chunk c exactly when c stopped locally or prefix T * chunk T < 1e-4; that
+// chunk is then re-walked from the exact prefix state, so the stop rule is
+// applied exactly as in one sequential pass.
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -30,60 +41,132 @@ namespace {
 
 constexpr uint32_t kWaitTries = 1u << 22;
 constexpr int kStages = 3;
+constexpr int kPartialVals = 16;  // floats per pixel in a partial state
+constexpr int kMaxSmem = 227 * 1024;
 
-template <int TILE, int BATCH>
-struct TileSmem {
+template <int BATCH>
+struct WarpRing {
     GaussRec rec[kStages][BATCH];
     uint64_t bar[kStages];
 };
+
+template <int TILE, int BATCH>
+constexpr size_t smem_bytes()
+{
+    return sizeof(WarpRing<BATCH>) * (size_t)(TILE * TILE / 32);
+}
 
 struct PixelAcc {
     float T, Tx, Ty, D;
     float C[3], Cx[3], Cy[3];
     uint32_t last;
-    bool done;
+    bool done, stopped;
 };
 
-// Composites one tile. `phase` carries the mbarriers' parities across tiles
-// (persistent use). Returns false if a bounded wait gave up.
-template <int TILE, int BATCH, bool GRAD, bool STATE>
-__device__ __forceinline__ bool composite_tile(const CompositeArgs &a, int tile_x, int tile_y,
-                                               TileSmem<TILE, BATCH> &sm, uint32_t (&phase)[kStages])
+__device__ __forceinline__ void acc_init(PixelAcc &s, bool inside)
 {
-    // each warp owns an 8 x 4 pixel block of the tile, so a small Gaussian's
-    // support covers a large share of the warp's lanes and misses most warps
-    constexpr int WX = 8, WY = 4, WPR = TILE / WX;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int bx0 = tile_x * TILE + (warp % WPR) * WX, by0 = tile_y * TILE + (warp / WPR) * WY;
-    const int px = bx0 + (lane % WX), py = by0 + (lane / WX);
-    const bool inside = px < a.width && py < a.height;
-    const uint2 range = a.ranges[tile_y * a.tiles_x + tile_x];
-    const uint32_t total = range.y > range.x ? range.y - range.x : 0u;
-    const int nbatches = (int)((total + BATCH - 1) / BATCH);
-
-    // batch b -> buffer b % kStages; one bulk copy of the batch's contiguous records
-    auto issue = [&](int b) {
-        if (tid == 0) {
-            const int buf = b % kStages;
-            const uint32_t start = range.x + (uint32_t)b * BATCH;
-            const uint32_t cnt = min((uint32_t)BATCH, range.y - start);
-            const uint32_t bytes = cnt * (uint32_t)sizeof(GaussRec);
-            mbar_arrive_expect_tx(&sm.bar[buf], bytes);
-            tma_bulk_g2s(&sm.rec[buf][0], a.rec + start, bytes, &sm.bar[buf]);
-        }
-    };
-
-    PixelAcc s;
     s.T = 1.0f;
     s.Tx = s.Ty = s.D = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) s.C[c] = s.Cx[c] = s.Cy[c] = 0.0f;
     s.last = 0;
     s.done = !inside;
+    s.stopped = false;
+}
+
+// Pixel of thread `tid`: warps own 8x4 blocks, row-major over the tile.
+template <int TILE>
+__device__ __forceinline__ void tile_pixel(int tid, int tile_x, int tile_y, int &px, int &py, int &bx0, int &by0)
+{
+    constexpr int WX = 8, WY = 4, WPR = TILE / WX;
+    const int warp = tid >> 5, lane = tid & 31;
+    bx0 = tile_x * TILE + (warp % WPR) * WX;
+    by0 = tile_y * TILE + (warp / WPR) * WY;
+    px = bx0 + (lane % WX);
+    py = by0 + (lane / WX);
+}
+
+// One Gaussian record at one pixel (Eq. 2-4). Returns true when the pixel
+// stops (the record would take T below 1e-4; it is not blended).
+template <bool GRAD, bool STATE>
+__device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float4 &r1, const float4 &r2, float pxc,
+                                      float pyc, uint32_t pos)
+{
+    const AlphaEval e = eval_alpha(r0, r1, pxc, pyc);
+    const float al = e.al;
+    if (al < kAlphaMin) return false;
+    const float om = __fsub_rn(1.0f, al);
+    const float nT = __fmul_rn(s.T, om);
+    if (nT < kTMin) return true;
+    const float wgt = __fmul_rn(al, s.T);
+    const float col[3] = {r1.w, r2.x, r2.y};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s.C[c] = __fmaf_rn(col[c], wgt, s.C[c]);
+    s.D = __fmaf_rn(r1.z, wgt, s.D);
+    if (GRAD) {
+        const float ax = e.capped ? 0.0f : -__fmul_rn(al, e.ex);
+        const float ay = e.capped ? 0.0f : -__fmul_rn(al, e.ey);
+        const float wx = __fmaf_rn(s.Tx, al, __fmul_rn(s.T, ax));
+        const float wy = __fmaf_rn(s.Ty, al, __fmul_rn(s.T, ay));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            s.Cx[c] = __fmaf_rn(col[c], wx, s.Cx[c]);
+            s.Cy[c] = __fmaf_rn(col[c], wy, s.Cy[c]);
+        }
+        s.Tx = __fmaf_rn(-ax, s.T, __fmul_rn(om, s.Tx));
+        s.Ty = __fmaf_rn(-ay, s.T, __fmul_rn(om, s.Ty));
+    }
+    s.T = nT;
+    if (STATE) s.last = pos;
+    return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <int BATCH>
+__device__ __forceinline__ void ring_init(WarpRing<BATCH> &ring)
+{
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int s = 0; s < kStages; ++s) mbar_init(&ring.bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+}
+
+// Warp-level: composites records [s0, s1) of the sorted list onto this lane's
+// pixel state. (px, py) is the lane's pixel, (bx0, by0) the warp's 8x4 block,
+// pos0 the list position of s0 within its tile. The warp's ring carries its
+// mbarrier parities in `phase`. Returns false if a bounded wait gave up.
+template <int BATCH, bool GRAD, bool STATE>
+__device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py, int bx0, int by0, uint32_t s0,
+                                          uint32_t s1, uint32_t pos0, WarpRing<BATCH> &ring,
+                                          uint32_t (&phase)[kStages], PixelAcc &s)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t total = s1 > s0 ? s1 - s0 : 0u;
+    const int nbatches = (int)((total + BATCH - 1) / BATCH);
+    if (__all_sync(0xffffffffu, s.done) || nbatches == 0) return true;
+
+    // batch b -> ring slot b % kStages; lane 0 issues one bulk copy per batch
+    auto issue = [&](int b) {
+        if (lane == 0) {
+            const int buf = b % kStages;
+            const uint32_t start = s0 + (uint32_t)b * BATCH;
+            const uint32_t cnt = min((uint32_t)BATCH, s1 - start);
+            const uint32_t bytes = cnt * (uint32_t)sizeof(GaussRec);
+            fence_proxy_async_smem();  // this warp's earlier reads of the slot precede the async write
+            mbar_arrive_expect_tx(&ring.bar[buf], bytes);
+            tma_bulk_g2s(&ring.rec[buf][0], a.rec + start, bytes, &ring.bar[buf]);
+        }
+    };
+
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
     const uint32_t upx = (uint32_t)px, upy = (uint32_t)py;
-    const uint32_t wx0 = (uint32_t)bx0, wx1 = (uint32_t)(bx0 + WX - 1);
-    const uint32_t wy0 = (uint32_t)by0, wy1 = (uint32_t)(by0 + WY - 1);
+    const uint32_t wx0 = (uint32_t)bx0, wx1 = (uint32_t)(bx0 + 7), wy0 = (uint32_t)by0, wy1 = (uint32_t)(by0 + 3);
     bool ok = true;
 
     for (int b = 0; b < kStages - 1 && b < nbatches; ++b) issue(b);
@@ -91,148 +174,239 @@ __device__ __forceinline__ bool composite_tile(const CompositeArgs &a, int tile_
     for (; b < nbatches; ++b) {
         const int buf = b % kStages;
         if (b + kStages - 1 < nbatches) issue(b + kStages - 1);
-        if (!mbar_wait_bounded(&sm.bar[buf], phase[buf], kWaitTries)) ok = false;
+        if (!mbar_wait_bounded(&ring.bar[buf], phase[buf], kWaitTries)) ok = false;
         phase[buf] ^= 1u;
-        const uint32_t cnt = min((uint32_t)BATCH, range.y - (range.x + (uint32_t)b * BATCH));
-        const bool warp_idle = __all_sync(0xffffffffu, s.done || !ok);
-        if (ok && !warp_idle) {
-            const GaussRec *recs = sm.rec[buf];
-            // which of the batch's records reach this warp's pixel block (one ballot per 32 records)
-            uint32_t rows_mask[BATCH / 32];
+        if (!__all_sync(0xffffffffu, ok)) {
+            ++b;
+            break;
+        }
+        const uint32_t cnt = min((uint32_t)BATCH, s1 - (s0 + (uint32_t)b * BATCH));
+        const GaussRec *recs = ring.rec[buf];
+        const uint32_t pos_b = pos0 + (uint32_t)b * BATCH + 1u;
 #pragma unroll
-            for (int w = 0; w < BATCH / 32; ++w) {
-                const uint32_t k = (uint32_t)w * 32u + (uint32_t)lane;
-                bool hit = false;
-                if (k < cnt) {
-                    const uint32_t lo = __float_as_uint(recs[k].r2.z), hi = __float_as_uint(recs[k].r2.w);
-                    hit = (hi >> 16) >= wy0 && (lo >> 16) <= wy1 && (hi & 0xFFFFu) >= wx0 && (lo & 0xFFFFu) <= wx1;
-                }
-                rows_mask[w] = __ballot_sync(0xffffffffu, hit);
+        for (int w = 0; w < BATCH / 32; ++w) {
+            // records of this group of 32 whose rectangle reaches the warp's block
+            const uint32_t kk = (uint32_t)w * 32u + (uint32_t)lane;
+            bool hit = false;
+            if (kk < cnt) {
+                const uint32_t lo = __float_as_uint(recs[kk].r2.z), hi = __float_as_uint(recs[kk].r2.w);
+                hit = (hi >> 16) >= wy0 && (lo >> 16) <= wy1 && (hi & 0xFFFFu) >= wx0 && (lo & 0xFFFFu) <= wx1;
             }
-#pragma unroll
-            for (int w = 0; w < BATCH / 32; ++w) {
-                uint32_t m = s.done ? 0u : rows_mask[w];
-                while (m) {
-                    const uint32_t k = (uint32_t)w * 32u + (uint32_t)(__ffs(m) - 1);
-                    m &= m - 1u;
-                    const float4 r2 = recs[k].r2;
-                    if (!rect_contains(r2, upx, upy)) continue;
-                    const float4 r0 = recs[k].r0;
-                    const float4 r1 = recs[k].r1;
-                    const AlphaEval e = eval_alpha(r0, r1, pxc, pyc);
-                    const float al = e.al;
-                    if (al < kAlphaMin) continue;
-                    const float om = __fsub_rn(1.0f, al);
-                    const float nT = __fmul_rn(s.T, om);
-                    if (nT < kTMin) {
-                        s.done = true;
-                        break;
-                    }
-                    const float wgt = __fmul_rn(al, s.T);
-                    const float col[3] = {r1.w, r2.x, r2.y};
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) s.C[c] = __fmaf_rn(col[c], wgt, s.C[c]);
-                    s.D = __fmaf_rn(r1.z, wgt, s.D);
-                    if (GRAD) {
-                        const float ax = e.capped ? 0.0f : -__fmul_rn(al, e.ex);
-                        const float ay = e.capped ? 0.0f : -__fmul_rn(al, e.ey);
-                        const float wx = __fmaf_rn(s.Tx, al, __fmul_rn(s.T, ax));
-                        const float wy = __fmaf_rn(s.Ty, al, __fmul_rn(s.T, ay));
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            s.Cx[c] = __fmaf_rn(col[c], wx, s.Cx[c]);
-                            s.Cy[c] = __fmaf_rn(col[c], wy, s.Cy[c]);
-                        }
-                        s.Tx = __fmaf_rn(-ax, s.T, __fmul_rn(om, s.Tx));
-                        s.Ty = __fmaf_rn(-ay, s.T, __fmul_rn(om, s.Ty));
-                    }
-                    s.T = nT;
-                    if (STATE) s.last = (uint32_t)b * BATCH + k + 1u;
+            uint32_t m = __ballot_sync(0xffffffffu, hit);
+            if (s.done) m = 0u;
+            while (m) {
+                const uint32_t k = (uint32_t)w * 32u + (uint32_t)(__ffs(m) - 1);
+                m &= m - 1u;
+                const float4 r2 = recs[k].r2;
+                if (!rect_contains(r2, upx, upy)) continue;
+                if (blend<GRAD, STATE>(s, recs[k].r0, recs[k].r1, r2, pxc, pyc, pos_b + k)) {
+                    s.done = true;
+                    s.stopped = true;
+                    break;
                 }
             }
         }
-        if (!ok) s.done = true;
-        if (__syncthreads_and(s.done)) {
+        if (__all_sync(0xffffffffu, s.done)) {
             ++b;
             break;
         }
     }
-    // batches issued ahead of an early exit must land before their buffers are reused or the CTA exits
+    // batches issued ahead of an early exit must land before their slots are reused or the CTA exits
     for (int q = b; q < nbatches && q < b + kStages - 1; ++q) {
-        if (!mbar_wait_bounded(&sm.bar[q % kStages], phase[q % kStages], kWaitTries)) ok = false;
+        if (!mbar_wait_bounded(&ring.bar[q % kStages], phase[q % kStages], kWaitTries)) ok = false;
         phase[q % kStages] ^= 1u;
     }
-    if (inside) {
-        const int64_t HW = (int64_t)a.width * a.height;
-        const int64_t p = (int64_t)py * a.width + px;
-        if (a.rgb)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) a.rgb[c * HW + p] = __fmaf_rn(s.T, a.bg[c], s.C[c]);
-        if (GRAD) {
-            if (a.dcdx)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) a.dcdx[c * HW + p] = __fmaf_rn(a.bg[c], s.Tx, s.Cx[c]);
-            if (a.dcdy)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) a.dcdy[c * HW + p] = __fmaf_rn(a.bg[c], s.Ty, s.Cy[c]);
-        }
-        if (a.depth) a.depth[p] = s.D;
-        if (a.alpha) a.alpha[p] = __fsub_rn(1.0f, s.T);
-        if (STATE) {
-            a.final_T[p] = s.T;
-            a.final_Tx[p] = s.Tx;
-            a.final_Ty[p] = s.Ty;
-            a.n_contrib[p] = s.last;
-        }
-    }
+    __syncwarp();
     return ok;
 }
 
-template <int TILE, int BATCH>
-__device__ __forceinline__ void init_barriers(TileSmem<TILE, BATCH> &sm)
+template <bool GRAD, bool STATE>
+__device__ __forceinline__ void write_final(const CompositeArgs &a, int px, int py, const PixelAcc &s)
 {
-    if (threadIdx.x == 0) {
+    const int64_t HW = (int64_t)a.width * a.height;
+    const int64_t p = (int64_t)py * a.width + px;
+    if (a.rgb)
 #pragma unroll
-        for (int s = 0; s < kStages; ++s) mbar_init(&sm.bar[s], 1);
-        fence_mbar_init();
+        for (int c = 0; c < 3; ++c) a.rgb[c * HW + p] = __fmaf_rn(s.T, a.bg[c], s.C[c]);
+    if (GRAD) {
+        if (a.dcdx)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a.dcdx[c * HW + p] = __fmaf_rn(a.bg[c], s.Tx, s.Cx[c]);
+        if (a.dcdy)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a.dcdy[c * HW + p] = __fmaf_rn(a.bg[c], s.Ty, s.Cy[c]);
     }
-    __syncthreads();
+    if (a.depth) a.depth[p] = s.D;
+    if (a.alpha) a.alpha[p] = __fsub_rn(1.0f, s.T);
+    if (STATE) {
+        a.final_T[p] = s.T;
+        a.final_Tx[p] = s.Tx;
+        a.final_Ty[p] = s.Ty;
+        a.n_contrib[p] = s.last;
+    }
+}
+
+// partial state of one pixel: planar [16][TILE*TILE] per slot, coalesced per value
+template <int TILE>
+__device__ __forceinline__ void write_partial(float *slot, int tid, const PixelAcc &s)
+{
+    constexpr int NT = TILE * TILE;
+    float v[kPartialVals] = {s.C[0], s.C[1], s.C[2], s.Cx[0], s.Cx[1], s.Cx[2], s.Cy[0], s.Cy[1], s.Cy[2],
+                             s.D, s.T, s.Tx, s.Ty, __uint_as_float(s.last), s.stopped ? 1.0f : 0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < kPartialVals; ++k) slot[k * NT + tid] = v[k];
+}
+
+template <int TILE>
+__device__ __forceinline__ void read_partial(const float *slot, int tid, PixelAcc &q)
+{
+    constexpr int NT = TILE * TILE;
+    float v[kPartialVals];
+#pragma unroll
+    for (int k = 0; k < kPartialVals; ++k) v[k] = slot[k * NT + tid];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        q.C[c] = v[c];
+        q.Cx[c] = v[3 + c];
+        q.Cy[c] = v[6 + c];
+    }
+    q.D = v[9];
+    q.T = v[10];
+    q.Tx = v[11];
+    q.Ty = v[12];
+    q.last = __float_as_uint(v[13]);
+    q.stopped = v[14] != 0.0f;
+}
+
+// P <- P then Q (composition of two consecutive segments, product rule)
+template <bool GRAD, bool STATE>
+__device__ __forceinline__ void compose(PixelAcc &P, const PixelAcc &Q)
+{
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        if (GRAD) {
+            P.Cx[ch] = __fmaf_rn(P.T, Q.Cx[ch], __fmaf_rn(P.Tx, Q.C[ch], P.Cx[ch]));
+            P.Cy[ch] = __fmaf_rn(P.T, Q.Cy[ch], __fmaf_rn(P.Ty, Q.C[ch], P.Cy[ch]));
+        }
+        P.C[ch] = __fmaf_rn(P.T, Q.C[ch], P.C[ch]);
+    }
+    P.D = __fmaf_rn(P.T, Q.D, P.D);
+    if (GRAD) {
+        const float tx2 = __fmaf_rn(P.Tx, Q.T, __fmul_rn(P.T, Q.Tx));
+        const float ty2 = __fmaf_rn(P.Ty, Q.T, __fmul_rn(P.T, Q.Ty));
+        P.Tx = tx2;
+        P.Ty = ty2;
+    }
+    P.T = __fmul_rn(P.T, Q.T);
+    if (STATE && Q.last) P.last = Q.last;
 }
 
 template <int TILE, int BATCH, bool GRAD, bool STATE>
 __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
 {
-    __shared__ TileSmem<TILE, BATCH> sm;
-    init_barriers(sm);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t tile, s0, s1, slot = kWholeTile;
+    if (a.items) {
+        if (blockIdx.x >= a.plan_counts[0]) return;
+        const uint4 it = a.items[blockIdx.x];
+        tile = it.x;
+        s0 = it.y;
+        s1 = it.z;
+        slot = it.w;
+    } else {
+        tile = a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x;
+        const uint2 r = a.ranges[tile];
+        s0 = r.x;
+        s1 = r.y > r.x ? r.y : r.x;
+    }
+    WarpRing<BATCH> &ring = reinterpret_cast<WarpRing<BATCH> *>(smem_raw)[threadIdx.x >> 5];
+    ring_init(ring);
     uint32_t phase[kStages] = {};
-    // heaviest tiles first: CTAs are dispatched roughly in blockIdx order
-    const uint32_t t = a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x;
-    const int tx = (int)(t % (uint32_t)a.tiles_x), ty = (int)(t / (uint32_t)a.tiles_x);
-    const bool ok = composite_tile<TILE, BATCH, GRAD, STATE>(a, tx, ty, sm, phase);
-    if (!ok && threadIdx.x == 0) atomicOr(a.err_word, kErrTmaTimeout);
+    const int tx = (int)(tile % (uint32_t)a.tiles_x), ty = (int)(tile / (uint32_t)a.tiles_x);
+    int px, py, bx0, by0;
+    tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);
+    const bool inside = px < a.width && py < a.height;
+    PixelAcc s;
+    acc_init(s, inside);
+    const uint32_t pos0 = s0 - a.ranges[tile].x;
+    const bool ok = warp_span<BATCH, GRAD, STATE>(a, px, py, bx0, by0, s0, s1, pos0, ring, phase, s);
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(a.err_word, kErrTmaTimeout);
+    if (slot == kWholeTile) {
+        if (inside) write_final<GRAD, STATE>(a, px, py, s);
+    } else {
+        write_partial<TILE>(a.partial + (size_t)slot * kPartialVals * TILE * TILE, threadIdx.x, s);
+    }
+}
+
+// Merge of split tiles: fold the chunks' partial states front to back. For
+// each chunk in order, every pixel whose stop does not fall in it folds it;
+// the pixels whose stop does (it stopped locally, or prefix T * chunk T
+// < 1e-4) re-walk that chunk from their exact prefix states through the same
+// staged, masked warp pass as compositing. A pixel that then did not stop
+// (the fold's product and the sequential product differ by rounding) simply
+// continues with the next chunk.
+template <int TILE, int BATCH, bool GRAD, bool STATE>
+__global__ void __launch_bounds__(TILE *TILE) k_merge(const CompositeArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (blockIdx.x >= a.plan_counts[1]) return;
+    const uint32_t tile = a.split_tiles[blockIdx.x], slot0 = a.split_slot0[blockIdx.x];
+    const uint2 r = a.ranges[tile];
+    const uint32_t chunk = (uint32_t)a.chunk;
+    const uint32_t nch = (r.y - r.x + chunk - 1) / chunk;
+    const int tx = (int)(tile % (uint32_t)a.tiles_x), ty = (int)(tile / (uint32_t)a.tiles_x);
+    int px, py, bx0, by0;
+    tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);
+    const bool inside = px < a.width && py < a.height;
+    WarpRing<BATCH> &ring = reinterpret_cast<WarpRing<BATCH> *>(smem_raw)[threadIdx.x >> 5];
+    ring_init(ring);
+    uint32_t phase[kStages] = {};
+    PixelAcc P;
+    acc_init(P, inside);  // P.done: pixel finished (outside, or stopped)
+    bool ok = true;
+    for (uint32_t c = 0; c < nch; ++c) {
+        bool walk = false;
+        if (!P.done) {
+            PixelAcc Q;
+            read_partial<TILE>(a.partial + (size_t)(slot0 + c) * kPartialVals * TILE * TILE, threadIdx.x, Q);
+            walk = Q.stopped || __fmul_rn(P.T, Q.T) < kTMin;
+            if (!walk) compose<GRAD, STATE>(P, Q);
+        }
+        if (!__any_sync(0xffffffffu, walk)) continue;
+        const bool was_done = P.done;
+        P.done = !walk;  // only the walking lanes take part
+        P.stopped = false;
+        const uint32_t k0 = r.x + c * chunk, k1 = min(r.y, k0 + chunk);
+        ok &= warp_span<BATCH, GRAD, STATE>(a, px, py, bx0, by0, k0, k1, k0 - r.x, ring, phase, P);
+        P.done = was_done || (walk && P.stopped);
+    }
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(a.err_word, kErrTmaTimeout);
+    if (inside) write_final<GRAD, STATE>(a, px, py, P);
 }
 
 // Serving: a persistent grid pulls (request, tile) items from a flat work list
 // described by per-request prefixes; every request's outputs and buffers are
 // its own. Items are handed out by an atomic counter (no waiting on anything).
 constexpr int kMaxServeReqs = 256;
+constexpr int kServeBatch = 32;
 
-template <int TILE, int BATCH>
+template <int TILE>
 __global__ void __launch_bounds__(TILE *TILE) k_composite_persistent(const ServeItem *__restrict__ reqs, int n_reqs,
                                                                      uint32_t total_items, uint32_t *work_counter)
 {
-    __shared__ TileSmem<TILE, BATCH> sm;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t s_first[kMaxServeReqs + 1];
     __shared__ uint32_t s_item;
     for (int r = threadIdx.x; r < n_reqs; r += blockDim.x) s_first[r] = reqs[r].first_item;
     if (threadIdx.x == 0) s_first[n_reqs] = total_items;
-    init_barriers(sm);
+    WarpRing<kServeBatch> &ring = reinterpret_cast<WarpRing<kServeBatch> *>(smem_raw)[threadIdx.x >> 5];
+    ring_init(ring);
     uint32_t phase[kStages] = {};
     for (;;) {
+        __syncthreads();
         if (threadIdx.x == 0) s_item = atomicAdd(work_counter, 1u);
         __syncthreads();
         const uint32_t item = s_item;
-        __syncthreads();
         if (item >= total_items) break;
         int lo = 0, hi = n_reqs - 1;  // last request with first_item <= item
         while (lo < hi) {
@@ -244,43 +418,110 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_persistent(const Serve
         uint32_t t = item - s_first[lo];
         if (a.tile_order) t = a.tile_order[t];
         const int tx = (int)(t % (uint32_t)a.tiles_x), ty = (int)(t / (uint32_t)a.tiles_x);
+        int px, py, bx0, by0;
+        tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);
+        const bool inside = px < a.width && py < a.height;
+        const uint2 rg = a.ranges[t];
+        PixelAcc s;
+        acc_init(s, inside);
         bool ok;
-        if (a.dcdx || a.dcdy) ok = composite_tile<TILE, BATCH, true, false>(a, tx, ty, sm, phase);
-        else ok = composite_tile<TILE, BATCH, false, false>(a, tx, ty, sm, phase);
-        if (!ok && threadIdx.x == 0) atomicOr(a.err_word, kErrTmaTimeout);
-        __syncthreads();
+        const bool grad = a.dcdx || a.dcdy;
+        const uint32_t e = rg.y > rg.x ? rg.y : rg.x;
+        if (grad) ok = warp_span<kServeBatch, true, false>(a, px, py, bx0, by0, rg.x, e, 0, ring, phase, s);
+        else ok = warp_span<kServeBatch, false, false>(a, px, py, bx0, by0, rg.x, e, 0, ring, phase, s);
+        if (!ok && (threadIdx.x & 31) == 0) atomicOr(a.err_word, kErrTmaTimeout);
+        if (inside) {
+            if (grad) write_final<true, false>(a, px, py, s);
+            else write_final<false, false>(a, px, py, s);
+        }
     }
 }
 
-template <int TILE, int BATCH>
-cudaError_t launch_tb(const CompositeArgs &a, cudaStream_t s)
+// Dynamic shared memory above 48 KB needs an opt-in per kernel and device;
+// done on the first (never captured) launch. `done` is the kernel's own flags.
+template <class F>
+cudaError_t opt_in_smem(F *kernel, size_t bytes, bool (&done)[64])
 {
-    const dim3 grid(a.tiles_x * a.tiles_y);
-    const bool grad = a.dcdx || a.dcdy;
-    const bool state = a.final_T != nullptr;
-    if (grad && state) k_composite<TILE, BATCH, true, true><<<grid, TILE * TILE, 0, s>>>(a);
-    else if (grad) k_composite<TILE, BATCH, true, false><<<grid, TILE * TILE, 0, s>>>(a);
-    else if (state) k_composite<TILE, BATCH, false, true><<<grid, TILE * TILE, 0, s>>>(a);
-    else k_composite<TILE, BATCH, false, false><<<grid, TILE * TILE, 0, s>>>(a);
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
+
+template <int TILE, int BATCH, bool GRAD, bool STATE>
+cudaError_t launch_one(const CompositeArgs &a, unsigned nb, cudaStream_t s)
+{
+    constexpr size_t smem = smem_bytes<TILE, BATCH>();
+    static bool done[64];
+    cudaError_t e = opt_in_smem(k_composite<TILE, BATCH, GRAD, STATE>, smem, done);
+    if (e != cudaSuccess) return e;
+    k_composite<TILE, BATCH, GRAD, STATE><<<nb, TILE * TILE, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TILE, int BATCH>
+cudaError_t launch_tb(const CompositeArgs &a, int64_t max_items, cudaStream_t s)
+{
+    if constexpr (smem_bytes<TILE, BATCH>() > (size_t)kMaxSmem) {
+        return cudaErrorInvalidValue;
+    } else {
+        const unsigned nb = a.items ? (unsigned)max_items : (unsigned)(a.tiles_x * a.tiles_y);
+        if (nb == 0) return cudaSuccess;
+        const bool grad = a.dcdx || a.dcdy;
+        const bool state = a.final_T != nullptr;
+        if (grad && state) return launch_one<TILE, BATCH, true, true>(a, nb, s);
+        if (grad) return launch_one<TILE, BATCH, true, false>(a, nb, s);
+        if (state) return launch_one<TILE, BATCH, false, true>(a, nb, s);
+        return launch_one<TILE, BATCH, false, false>(a, nb, s);
+    }
+}
+
+template <int TILE>
+cudaError_t launch_t(const CompositeArgs &a, int batch, int64_t max_items, cudaStream_t s)
+{
+    switch (batch) {
+    case 32: return launch_tb<TILE, 32>(a, max_items, s);
+    case 64: return launch_tb<TILE, 64>(a, max_items, s);
+    case 128: return launch_tb<TILE, 128>(a, max_items, s);
+    default: return launch_tb<TILE, 256>(a, max_items, s);
+    }
+}
+
+template <int TILE, bool GRAD, bool STATE>
+cudaError_t launch_merge_one(const CompositeArgs &a, unsigned nb, cudaStream_t s)
+{
+    constexpr size_t smem = smem_bytes<TILE, 32>();
+    static bool done[64];
+    cudaError_t e = opt_in_smem(k_merge<TILE, 32, GRAD, STATE>, smem, done);
+    if (e != cudaSuccess) return e;
+    k_merge<TILE, 32, GRAD, STATE><<<nb, TILE * TILE, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int TILE>
-cudaError_t launch_t(const CompositeArgs &a, int batch, cudaStream_t s)
+cudaError_t launch_merge_t(const CompositeArgs &a, int64_t max_split, cudaStream_t s)
 {
-    switch (batch) {
-    case 32: return launch_tb<TILE, 32>(a, s);
-    case 64: return launch_tb<TILE, 64>(a, s);
-    case 128: return launch_tb<TILE, 128>(a, s);
-    default: return launch_tb<TILE, 256>(a, s);
-    }
+    const bool grad = a.dcdx || a.dcdy;
+    const bool state = a.final_T != nullptr;
+    const unsigned nb = (unsigned)max_split;
+    if (grad && state) return launch_merge_one<TILE, true, true>(a, nb, s);
+    if (grad) return launch_merge_one<TILE, true, false>(a, nb, s);
+    if (state) return launch_merge_one<TILE, false, true>(a, nb, s);
+    return launch_merge_one<TILE, false, false>(a, nb, s);
 }
 
-template <int TILE, int BATCH>
+template <int TILE>
 int persistent_grid()
 {
+    constexpr size_t smem = smem_bytes<TILE, kServeBatch>();
+    static bool done[64];
+    opt_in_smem(k_composite_persistent<TILE>, smem, done);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_persistent<TILE, BATCH>, TILE * TILE, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_persistent<TILE>, TILE * TILE, smem);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -291,25 +532,39 @@ int persistent_grid()
 
 bool composite_supported(int tile, int batch)
 {
-    return (tile == 8 || tile == 16 || tile == 32) && (batch == 32 || batch == 64 || batch == 128 || batch == 256);
+    if (!(tile == 8 || tile == 16 || tile == 32) || !(batch == 32 || batch == 64 || batch == 128 || batch == 256))
+        return false;
+    // each warp holds kStages batches of 48-byte records
+    const size_t bytes = (size_t)(tile * tile / 32) * ((size_t)kStages * batch * sizeof(GaussRec) + 8 * kStages);
+    return bytes <= (size_t)kMaxSmem;
 }
 
-cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, cudaStream_t s)
+cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, int64_t max_items, cudaStream_t s)
 {
     if (a.tiles_x == 0 || a.tiles_y == 0) return cudaSuccess;
     switch (tile) {
-    case 8: return launch_t<8>(a, batch, s);
-    case 16: return launch_t<16>(a, batch, s);
-    default: return launch_t<32>(a, batch, s);
+    case 8: return launch_t<8>(a, batch, max_items, s);
+    case 16: return launch_t<16>(a, batch, max_items, s);
+    default: return launch_t<32>(a, batch, max_items, s);
+    }
+}
+
+cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, cudaStream_t s)
+{
+    if (!a.items || max_split <= 0) return cudaSuccess;
+    switch (tile) {
+    case 8: return launch_merge_t<8>(a, max_split, s);
+    case 16: return launch_merge_t<16>(a, max_split, s);
+    default: return launch_merge_t<32>(a, max_split, s);
     }
 }
 
 int composite_persistent_grid(int tile, int batch)
 {
     (void)batch;
-    if (tile == 8) return persistent_grid<8, 128>();
-    if (tile == 32) return persistent_grid<32, 128>();
-    return persistent_grid<16, 128>();
+    if (tile == 8) return persistent_grid<8>();
+    if (tile == 32) return persistent_grid<32>();
+    return persistent_grid<16>();
 }
 
 cudaError_t launch_composite_persistent(const ServeItem *reqs, int n_reqs, uint32_t total_items, int tile, int batch,
@@ -318,9 +573,14 @@ cudaError_t launch_composite_persistent(const ServeItem *reqs, int n_reqs, uint3
     (void)batch;
     if (n_reqs <= 0 || total_items == 0) return cudaSuccess;
     if (n_reqs > kMaxServeReqs) return cudaErrorInvalidValue;
-    if (tile == 8) k_composite_persistent<8, 128><<<grid, 64, 0, s>>>(reqs, n_reqs, total_items, work_counter);
-    else if (tile == 32) k_composite_persistent<32, 128><<<grid, 1024, 0, s>>>(reqs, n_reqs, total_items, work_counter);
-    else k_composite_persistent<16, 128><<<grid, 256, 0, s>>>(reqs, n_reqs, total_items, work_counter);
+    if (tile == 8)
+        k_composite_persistent<8><<<grid, 64, smem_bytes<8, kServeBatch>(), s>>>(reqs, n_reqs, total_items, work_counter);
+    else if (tile == 32)
+        k_composite_persistent<32><<<grid, 1024, smem_bytes<32, kServeBatch>(), s>>>(reqs, n_reqs, total_items,
+                                                                                     work_counter);
+    else
+        k_composite_persistent<16><<<grid, 256, smem_bytes<16, kServeBatch>(), s>>>(reqs, n_reqs, total_items,
+                                                                                   work_counter);
     return cudaGetLastError();
 }
 

@@ -132,11 +132,26 @@ struct CompositeArgs {
     uint32_t *n_contrib;
     uint32_t *err_word;
     const uint32_t *tile_order;  // tiles by decreasing list length (nullable = row-major)
+    // work plan (nullable: then one CTA per whole tile, in tile_order)
+    const uint4 *items;            // (tile, start, end, slot | kWholeTile)
+    const uint32_t *plan_counts;   // (n_items, n_split, n_slots)
+    const uint32_t *split_tiles;   // split tile ids
+    const uint32_t *split_slot0;   // first slot of each split tile
+    float *partial;                // [slot][16][TILE*TILE] per-pixel partial state of chunks
+    int32_t chunk;                 // records per chunk of a split tile
 };
+constexpr uint32_t kWholeTile = 0xFFFFFFFFu;
+int64_t plan_max_slots(int64_t max_k, int chunk);
+int64_t plan_max_items(int n_tiles, int64_t max_k, int chunk);
+cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, uint4 *items, uint32_t *split_tiles,
+                        uint32_t *split_slot0, uint32_t *counts, cudaStream_t s);
+// merge of split tiles' chunks (after launch_composite with a plan)
+cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, cudaStream_t s);
 // order tiles by decreasing list length (power-of-two buckets)
 cudaError_t launch_tile_order(const uint2 *ranges, int n_tiles, uint32_t *order, cudaStream_t s);
 bool composite_supported(int tile, int batch);
-cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, cudaStream_t s);
+// grid: one CTA per work item (bounded by max_items when a plan is given), else per tile
+cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, int64_t max_items, cudaStream_t s);
 
 // serving: tiles of several requests from one (request, tile) work list
 struct ServeItem {  // one request's compositing description (device copy)

@@ -80,6 +80,9 @@ struct Frame {
     Buf rec, bin, ntiles, bsums, boffs;
     Buf keys[2], vals[2], sort_scr, rec_sorted;
     Buf ranges, order;
+    Buf items, split_tiles, split_slot0, plan_counts, partial;  // compositing work plan
+    int chunk = 2048;
+    int64_t max_items = 0, max_split = 0;
     Buf fT, fTx, fTy, ncontrib;
     Buf counters;
     int64_t n = 0, K = 0, key_cap = 0;
@@ -229,7 +232,10 @@ struct gs_context {
     uint32_t *h_counters = nullptr;  // pinned
     Buf g2d;
     Buf host_planes;
-    std::map<TuneKey, std::pair<int, int>> tune;
+    struct Tuned {
+        int tile, batch, chunk;
+    };
+    std::map<TuneKey, Tuned> tune;
     StageTimer timer;
     int64_t st_frames = 0, st_sum_k = 0, st_sum_v = 0, st_max_k = 0;
     ~gs_context()
@@ -271,31 +277,39 @@ struct gs_graph {
 namespace gsr {
 namespace {
 
-void pick_tile_batch(gs_context *ctx, const gs_scene *s, const gs_camera *c, const gs_render_opts *o, int *tile,
-                     int *batch)
+constexpr int kDefaultTile = 16, kDefaultBatch = 32, kDefaultChunk = 512;
+
+// tile / batch / chunk: explicit options win, then the autotuner's cache for
+// (W, H, N bucket, SH degree), then the defaults.
+void pick_config(gs_context *ctx, const gs_scene *s, const gs_camera *c, const gs_render_opts *o, int *tile,
+                 int *batch, int *chunk)
 {
-    int t = o->tile, b = o->batch;
-    if (t == 0 || b == 0) {
+    int t = o->tile, b = o->batch, k = o->chunk;
+    if (t == 0 || b == 0 || k == 0) {
         const int nb = s->n > 0 ? (int)std::log2((double)s->n) : 0;
         auto it = ctx->tune.find(TuneKey{c->width, c->height, nb, s->sh_degree});
         if (it != ctx->tune.end()) {
-            if (t == 0) t = it->second.first;
-            if (b == 0) b = it->second.second;
+            if (t == 0) t = it->second.tile;
+            if (b == 0) b = it->second.batch;
+            if (k == 0) k = it->second.chunk;
         }
     }
-    *tile = t ? t : 16;
-    *batch = b ? b : 64;
+    *tile = t ? t : kDefaultTile;
+    *batch = b ? b : kDefaultBatch;
+    *chunk = k ? k : kDefaultChunk;
 }
 
 // Per-Gaussian and per-pixel buffers + geometry of a frame.
 gs_status frame_setup(Frame *f, const gs_scene *s, const gs_camera *c, const gs_render_opts *o, int tile, int batch,
-                      bool state)
+                      int chunk, bool state)
 {
     f->n = s->n;
     f->W = c->width;
     f->H = c->height;
     f->tile = tile;
     f->batch = batch;
+    if (chunk < 64 || chunk > (1 << 24)) return fail(GS_ERR_INVALID_ARG, "chunk must be 0 or 64..2^24");
+    f->chunk = chunk;
     f->deg = s->sh_degree;
     for (int k = 0; k < 3; ++k) f->bg[k] = o->bg[k];
     f->cam = make_cam(*c, tile);
@@ -333,6 +347,21 @@ gs_status frame_keys(Frame *f, int64_t cap)
     GSR_CUDA(f->sort_scr.ensure(sort_scratch_bytes(std::max<int64_t>(cap, 1))));
     GSR_CUDA(f->rec_sorted.ensure(sizeof(GaussRec) * (size_t)std::max<int64_t>(cap, 1)));
     f->key_cap = cap;
+    return GS_OK;
+}
+
+// Work-plan buffers for up to `cap` instances at the frame's tile size and
+// tile count: every split tile has > chunk records, so slots <= 2 cap / chunk + 2.
+gs_status frame_plan(Frame *f, int64_t cap)
+{
+    const int64_t slots = plan_max_slots(cap, f->chunk);
+    f->max_items = plan_max_items(f->n_tiles, cap, f->chunk);
+    f->max_split = std::min<int64_t>(f->n_tiles, cap / f->chunk + 1);
+    GSR_CUDA(f->items.ensure(sizeof(uint4) * (size_t)f->max_items));
+    GSR_CUDA(f->split_tiles.ensure(sizeof(uint32_t) * (size_t)f->max_split));
+    GSR_CUDA(f->split_slot0.ensure(sizeof(uint32_t) * (size_t)f->max_split));
+    GSR_CUDA(f->plan_counts.ensure(sizeof(uint32_t) * 4));
+    GSR_CUDA(f->partial.ensure(sizeof(float) * 16 * (size_t)f->tile * f->tile * (size_t)slots));
     return GS_OK;
 }
 
@@ -380,6 +409,12 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
     }
     c.err_word = f->counters.as<uint32_t>() + kCntErr;
     c.tile_order = f->order.as<uint32_t>();
+    c.items = f->items.as<uint4>();
+    c.plan_counts = f->plan_counts.as<uint32_t>();
+    c.split_tiles = f->split_tiles.as<uint32_t>();
+    c.split_slot0 = f->split_slot0.as<uint32_t>();
+    c.partial = f->partial.as<float>();
+    c.chunk = f->chunk;
     return c;
 }
 
@@ -409,10 +444,13 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     GSR_CUDA(mark(ev, 4, st, capture));
     GSR_CUDA(launch_ranges(f->keys[res].as<uint64_t>(), f->vals[res].as<uint32_t>(), cnt, max_k, f->rec.as<GaussRec>(),
                            f->rec_sorted.as<GaussRec>(), f->ranges.as<uint2>(), f->n_tiles, st));
-    GSR_CUDA(launch_tile_order(f->ranges.as<uint2>(), f->n_tiles, f->order.as<uint32_t>(), st));
+    GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->chunk, f->items.as<uint4>(),
+                         f->split_tiles.as<uint32_t>(), f->split_slot0.as<uint32_t>(), f->plan_counts.as<uint32_t>(),
+                         st));
     GSR_CUDA(mark(ev, 5, st, capture));
     const CompositeArgs ca = comp_args(f, out);
-    GSR_CUDA(launch_composite(ca, f->tile, f->batch, st));
+    GSR_CUDA(launch_composite(ca, f->tile, f->batch, f->max_items, st));
+    GSR_CUDA(launch_merge(ca, f->tile, f->max_split, st));
     GSR_CUDA(mark(ev, 6, st, capture));
     return GS_OK;
 }
@@ -429,11 +467,13 @@ gs_status err_status(uint32_t err)
 gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, const gs_render_opts *o,
                         const gs_outputs *out, Frame *f, cudaStream_t st)
 {
-    int tile, batch;
-    pick_tile_batch(ctx, s, c, o, &tile, &batch);
-    if (!composite_supported(tile, batch)) return fail(GS_ERR_INVALID_ARG, "tile must be 8/16/32, batch 32/64/128/256");
+    int tile, batch, chunk;
+    pick_config(ctx, s, c, o, &tile, &batch, &chunk);
+    if (!composite_supported(tile, batch))
+        return fail(GS_ERR_INVALID_ARG, "tile must be 8/16/32 and batch 32/64/128/256 with the warps' staging rings "
+                                        "fitting shared memory");
     const bool state = (o->flags & GS_EMIT_BWD_STATE) != 0;
-    gs_status r = frame_setup(f, s, c, o, tile, batch, state);
+    gs_status r = frame_setup(f, s, c, o, tile, batch, chunk, state);
     if (r != GS_OK) return r;
     uint32_t *cnt = f->counters.as<uint32_t>();
     cudaEvent_t *ev = nullptr;
@@ -461,6 +501,7 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
         r = frame_keys(f, f->K);
         if (r != GS_OK) return r;
     }
+    if ((r = frame_plan(f, f->K)) != GS_OK) return r;
     // counters[kCntEff] was clamped to kMaxInstances; K fits, so it equals K.
     return enqueue_after_scan(f, out, f->K, st, ev, false);
 }
@@ -669,8 +710,8 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
     if (opts->flags & GS_EMIT_BWD_STATE) return fail(GS_ERR_INVALID_ARG, "graphs do not keep backward state");
     GSR_CUDA(cudaSetDevice(ctx->device));
     cudaGetLastError();  // a stale non-sticky error must not be charged to this call's launches
-    int tile, batch;
-    pick_tile_batch(ctx, scene, cam, opts, &tile, &batch);
+    int tile, batch, chunk;
+    pick_config(ctx, scene, cam, opts, &tile, &batch, &chunk);
     if (!composite_supported(tile, batch)) return fail(GS_ERR_INVALID_ARG, "unsupported tile/batch");
     if (capacity <= 0) capacity = std::max<int64_t>(4 * scene->n, 1024);
     if (capacity > kMaxInstances) return fail(GS_ERR_INVALID_ARG, "capacity above 2^30 - 1");
@@ -685,8 +726,9 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
     g->capacity = capacity;
     g->tile = tile;
     Frame *f = g->f;
-    r = frame_setup(f, scene, cam, opts, tile, batch, false);
+    r = frame_setup(f, scene, cam, opts, tile, batch, chunk, false);
     if (r == GS_OK) r = frame_keys(f, capacity);
+    if (r == GS_OK) r = frame_plan(f, capacity);
     if (r == GS_OK) {
         cudaError_t e = cudaMemsetAsync(f->counters.p, 0, sizeof(uint32_t) * kCntSlots, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -864,7 +906,7 @@ gs_status gs_context_stats(gs_context *ctx, gs_stream stream, int reset, gs_fram
 // ---------------------------------------------------------------------------- autotuner
 
 gs_status gs_autotune(gs_context *ctx, const gs_scene *scene, const gs_camera *cam, const gs_outputs *out, int iters,
-                      gs_stream stream, int32_t *best_tile, int32_t *best_batch, float *best_ms)
+                      gs_stream stream, int32_t *best_tile, int32_t *best_batch, int32_t *best_chunk, float *best_ms)
 {
     if (!ctx || !out) return fail(GS_ERR_INVALID_ARG, "NULL argument");
     gs_status r = check_scene(scene);
@@ -875,36 +917,42 @@ gs_status gs_autotune(gs_context *ctx, const gs_scene *scene, const gs_camera *c
     cudaEvent_t e0, e1;
     GSR_CUDA(cudaEventCreate(&e0));
     GSR_CUDA(cudaEventCreate(&e1));
-    const int tiles[3] = {8, 16, 32}, batches[4] = {32, 64, 128, 256};
+    const int tiles[3] = {8, 16, 32}, batches[4] = {32, 64, 128, 256}, chunks[3] = {512, 2048, 8192};
     float best = 1e30f;
-    int bt = 16, bb = 64;
+    int bt = kDefaultTile, bb = kDefaultBatch, bc = kDefaultChunk;
     for (int t : tiles)
-        for (int b : batches) {
-            gs_render_opts o{};
-            o.tile = t;
-            o.batch = b;
-            r = gs_render_forward(ctx, scene, cam, &o, out, nullptr, stream);  // warm-up
-            if (r != GS_OK) break;
-            cudaEventRecord(e0, st);
-            for (int it = 0; it < iters && r == GS_OK; ++it) r = gs_render_forward(ctx, scene, cam, &o, out, nullptr, stream);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= iters;
-            if (r == GS_OK && ms < best) {
-                best = ms;
-                bt = t;
-                bb = b;
+        for (int b : batches)
+            for (int c : chunks) {
+                if (!composite_supported(t, b)) continue;  // the warps' staging rings must fit shared memory
+                gs_render_opts o{};
+                o.tile = t;
+                o.batch = b;
+                o.chunk = c;
+                r = gs_render_forward(ctx, scene, cam, &o, out, nullptr, stream);  // warm-up
+                if (r != GS_OK) break;
+                cudaEventRecord(e0, st);
+                for (int it = 0; it < iters && r == GS_OK; ++it)
+                    r = gs_render_forward(ctx, scene, cam, &o, out, nullptr, stream);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= iters;
+                if (r == GS_OK && ms < best) {
+                    best = ms;
+                    bt = t;
+                    bb = b;
+                    bc = c;
+                }
             }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (r != GS_OK) return r;
     const int nb = scene->n > 0 ? (int)std::log2((double)scene->n) : 0;
-    ctx->tune[TuneKey{cam->width, cam->height, nb, scene->sh_degree}] = {bt, bb};
+    ctx->tune[TuneKey{cam->width, cam->height, nb, scene->sh_degree}] = {bt, bb, bc};
     if (best_tile) *best_tile = bt;
     if (best_batch) *best_batch = bb;
+    if (best_chunk) *best_chunk = bc;
     if (best_ms) *best_ms = best;
     return GS_OK;
 }

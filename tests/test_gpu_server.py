@@ -71,10 +71,15 @@ def test_requests_same_alone_and_in_the_mix(env):
         assert st == 0
         lats.append(lat)
     assert min(lats) > 0
+    # The server composites each tile in one pass; the plain path may split a
+    # long tile list into chunks and merge them exactly, which reassociates fp32
+    # sums: equal up to rounding (well inside the oracle tolerances).
     for (sid, cam), o in zip(reqs, outs):
         ref = ctx.forward(scenes[sid], cam, tile=16, bg=bg)
+        whole = ctx.forward(scenes[sid], cam, tile=16, bg=bg, chunk=1 << 24)
         for k in ref:
-            assert torch.equal(o[k], ref[k]), k
+            assert torch.equal(o[k], whole[k]), k
+            assert (o[k] - ref[k]).abs().max().item() < 2e-5, k
     srv.close()
 
 
