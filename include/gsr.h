@@ -239,6 +239,26 @@ gs_status gs_server_cancel(gs_server *srv, uint64_t req_id);
 gs_status gs_server_drain(gs_server *srv);
 gs_status gs_server_destroy(gs_server *srv);
 
+/* ---------------------------------------------------------------- sorting without allocation
+ * No counterpart in the paper: an entry point for callers that cannot call
+ * cudaMalloc (code inside a CUDA-graph capture, under a framework whose memory
+ * pool owns the device, or in a loop that must not allocate after start-up).
+ * Stable LSD radix sort of n (key, value) pairs by the low `bits` bits of the
+ * key -- the same onesweep kernels that sort the render's (tile, depth) keys.
+ * keys_in/vals_in (device, read only) are sorted into keys_out/vals_out
+ * (device, caller-owned; may alias the inputs). Keys 8-byte and values 4-byte
+ * aligned. Asynchronous on `stream`.
+ * Scratch comes from one static device array of about 14 MB that the library
+ * image holds on every GPU it is loaded on, until the process exits; n is at
+ * most 1,048,576 (GS_ERR_INVALID_ARG beyond). It allocates nothing: the first
+ * call on a device looks up the array's device address once (so make that
+ * first call before any stream capture). Every call reuses the same array:
+ * calls whose work overlaps on the GPU race and must be ordered by the caller.
+ * A bounded lookback wait that gives up leaves the output unsorted without
+ * returning an error from this asynchronous call. */
+gs_status gs_sort_pairs_static(const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out,
+                               uint32_t *vals_out, int64_t n, int32_t bits, gs_stream stream);
+
 /* ---------------------------------------------------------------- misc */
 const char *gs_last_error(void);
 const char *gs_version(void);

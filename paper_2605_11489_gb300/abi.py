@@ -34,7 +34,7 @@ ENTRY_POINTS = (
     "gs_render_backward", "gs_state_view_get", "gs_context_stats", "gs_state_free", "gs_graph_create",
     "gs_graph_render", "gs_graph_check", "gs_graph_stats", "gs_graph_destroy", "gs_autotune", "gs_server_create", "gs_server_load_scene",
     "gs_server_submit", "gs_server_poll", "gs_server_cancel", "gs_server_drain", "gs_server_destroy",
-    "gs_last_error", "gs_version",
+    "gs_sort_pairs_static", "gs_last_error", "gs_version",
 )
 
 
@@ -116,6 +116,7 @@ def _declare(L):
         "gs_server_cancel": [P, U64],
         "gs_server_drain": [P],
         "gs_server_destroy": [P],
+        "gs_sort_pairs_static": [P, P, P, P, I64, I32, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
