@@ -180,6 +180,101 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """--workload serve: the continuous-batching server against the plain
+    one-request-at-a-time renderer on the same mixed-resolution request stream.
+
+    4 resident scenes (0.5M, 1M, 3M, 6M clustered Gaussians, SH degree 3), a
+    seeded stream of requests with random orbit cameras and resolutions uniform
+    over {480x270, 960x540, 1280x720, 1920x1080}, 40 GB sort-buffer budget.
+      plain:    each request rendered by gs_render_forward, one after another
+      server:   all requests submitted at once (throughput), then a Poisson
+                stream at 0.8x the plain renderer's request rate (latency)
+    Prints one JSON line."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2605_11489_gb300 import abi, api, synth
+
+    torch.cuda.set_device(0)
+    n_req = args.requests
+    sizes = tuple(int(s * args.serve_scale) for s in synth.SERVING_SCENE_SIZES)
+    scenes = [api.Scene.from_arrays(synth.serving_scene(n, 10 + i)) for i, n in enumerate(sizes)]
+    reqs = synth.serving_requests(n_req, 5, 100.0, sizes)
+    outs = {}
+    for r in reqs:
+        key = (r.camera.width, r.camera.height)
+        if key not in outs:
+            outs[key] = api.alloc_outputs(*key)
+    px_total = sum(r.camera.width * r.camera.height for r in reqs)
+    ctx = api.Context(0)
+    stream = torch.cuda.Stream()
+    for r in reqs[:8]:  # warm-up
+        ctx.forward(scenes[r.scene], r.camera, out=outs[(r.camera.width, r.camera.height)], tile=16, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        ctx.forward(scenes[r.scene], r.camera, out=outs[(r.camera.width, r.camera.height)], tile=16, stream=stream)
+    stream.synchronize()
+    t_plain = time.perf_counter() - t0
+    plain_rate = n_req / t_plain
+    ctx.close()
+
+    srv = api.Server(sort_budget_bytes=int(args.budget_gb * (1 << 30)), max_inflight=args.inflight)
+    sids = [srv.load_scene(s) for s in scenes]
+
+    def run_stream(arrivals):
+        lat = [None] * n_req
+        ids = [None] * n_req
+        pending = set()
+        start = time.perf_counter()
+        i = 0
+        while i < n_req or pending:
+            now = time.perf_counter() - start
+            while i < n_req and arrivals[i] <= now:
+                r = reqs[i]
+                ids[i] = srv.submit(sids[r.scene], r.camera, outs[(r.camera.width, r.camera.height)])
+                pending.add(i)
+                i += 1
+            for j in list(pending):
+                st, l = srv.poll(ids[j])
+                if st != abi.GS_NOT_READY:
+                    if st != 0:
+                        raise RuntimeError("request %d failed: %d" % (j, st))
+                    lat[j] = l
+                    pending.discard(j)
+            if pending and not (i < n_req and arrivals[i] <= time.perf_counter() - start):
+                time.sleep(0.0002)
+        return time.perf_counter() - start, lat
+
+    for k in range(8):  # warm-up
+        srv.submit(sids[reqs[k].scene], reqs[k].camera, outs[(reqs[k].camera.width, reqs[k].camera.height)])
+    srv.drain()
+    t_burst, lat_burst = run_stream([0.0] * n_req)
+    rate = args.load * plain_rate
+    rng = __import__("numpy").random.default_rng(5)
+    arr = list(__import__("numpy").cumsum(rng.exponential(1.0 / rate, n_req)))
+    t_poisson, lat_p = run_stream(arr)
+    srv.close()
+    lat_p = sorted(lat_p)
+    pct = lambda q: lat_p[min(n_req - 1, int(q * n_req))]
+    line = {"metric": "serving Mpix/s (mixed-resolution stream)", "value": px_total / t_burst / 1e6,
+            "unit": "Mpix/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve", "requests": n_req, "scenes": list(sizes),
+                       "resolutions": ["%dx%d" % r for r in synth.SERVING_RESOLUTIONS],
+                       "sort_budget_gb": args.budget_gb, "max_inflight": args.inflight},
+            "plain_per_request": {"value": px_total / t_plain / 1e6, "unit": "Mpix/s",
+                                  "requests_per_s": plain_rate},
+            "speedup_vs_plain": t_plain / t_burst,
+            "poisson": {"rate_req_per_s": rate, "load_vs_plain": args.load, "p50_ms": pct(0.5),
+                        "p99_ms": pct(0.99), "mean_ms": sum(lat_p) / n_req,
+                        "throughput_mpix_s": px_total / t_poisson / 1e6},
+            "burst_p50_ms": sorted(lat_burst)[n_req // 2]}
+    print(json.dumps(line), flush=True)
+
+
 def algorithmic(stage, w, deg, n, K_avg, V_avg, passes, pixels, pairs):
     """Algorithmic work of one launch of `stage` (bytes, or FP32 ops for compositing)."""
     sh_bytes = 12 * (deg + 1) ** 2
@@ -193,8 +288,37 @@ def algorithmic(stage, w, deg, n, K_avg, V_avg, passes, pixels, pairs):
         return "hbm", 8.0 * K_avg
     if stage == "scan":
         return "hbm", 8.0 * n / 1024
-    # composite: FP32 operations of the per-pair work
-    return "alu", pairs
+    # composite: FP32 FLOP of the per-pair work, FMA = 2 ("K6"): 16 per evaluated
+    # pair (alpha), 38 more per blended pair (Eq. 2-4 updates), on the census' counts
+    p_eval, p_blend = pairs
+    return "alu", FLOP_PER_EVAL * p_eval + FLOP_PER_BLEND * p_blend
+
+
+FLOP_PER_EVAL = 16.0
+FLOP_PER_BLEND = 38.0
+SMS, FP32_LANES = 152, 128
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak: SMs x FP32 lanes x 2 FLOP x clock."""
+    return SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+
+
+def recorded_traffic(stage):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu summary,
+    if it was taken on the current source of that kernel (else None)."""
+    import hashlib
+
+    src = {"composite": "composite.cu", "sort": "sort.cu", "project": "project.cu"}.get(stage)
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not src or not os.path.exists(path):
+        return None
+    sha = hashlib.sha1(open(os.path.join(ROOT, "paper_2605_11489_gb300", "csrc", src), "rb").read()).hexdigest()
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("stage") == stage and f.get("source_sha1") == sha:
+            return float(f["dram_bytes_per_launch"])
+    return None
 
 
 def main():
@@ -203,7 +327,12 @@ def main():
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
+    ap.add_argument("--serve-scale", type=float, default=1.0, help="serve: scale of the scene sizes")
+    ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: sort-buffer budget")
+    ap.add_argument("--inflight", type=int, default=16, help="serve: in-flight request slots")
+    ap.add_argument("--load", type=float, default=0.8, help="serve: Poisson rate / plain renderer's rate")
     ap.add_argument("--tile", type=int, default=0, help="tile side 8/16/32 (0 = autotune)")
     ap.add_argument("--batch", type=int, default=0, help="Gaussians per shared-memory batch (0 = autotune)")
     ap.add_argument("--chunk", type=int, default=0, help="records per chunk of a split tile list (0 = autotune)")
@@ -214,6 +343,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serving(args)
 
     import torch
 
@@ -242,9 +373,12 @@ def main():
     if not (tile and batch and chunk):
         t, b, c, _ = ctx.autotune(scene, cams[0], out, iters=3, stream=stream)
         tile, batch, chunk = tile or t, batch or b, chunk or c
+    # the pair census runs the sequential pass (no list splitting), so its counts are
+    # the method's own: pairs up to each pixel's stop
     for cam in cams:
-        ctx.forward(scene, cam, out=out, tile=tile, batch=batch, chunk=chunk, stream=stream)
+        ctx.forward(scene, cam, out=out, tile=tile, batch=batch, chunk=1 << 24, count=True, stream=stream)
     pre = ctx.stats(reset=True, stream=stream)
+    census = (pre["pairs_evaluated"] / len(cams), pre["pairs_blended"] / len(cams))
     capacity = int(pre["instances_max"] * 1.25) + 4096
     graph = ctx.graph(scene, cams[0], out, capacity=capacity, tile=tile, batch=batch, chunk=chunk, timed=True,
                       stream=stream)
@@ -290,15 +424,26 @@ def main():
     passes = math.ceil((32 + max(1, math.ceil(math.log2(max(n_tiles, 2))))) / 8)
     dom = max(stage_ms, key=lambda k: stage_ms[k])
     hbm_peak, sm_max_mhz, peak_src = measured_peaks()
-    bound, amount = algorithmic(dom, (W, H), sc.deg, sc.n, K_avg, V_avg, passes, W * H, 0.0)
-    if bound == "hbm":
-        achieved = amount / (stage_ms[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": amount, "launch_ms": stage_ms[dom]}
-    else:
-        roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "launch_ms": stage_ms[dom]}
+    def roofline(stage):
+        bound, amount = algorithmic(stage, (W, H), sc.deg, sc.n, K_avg, V_avg, passes, W * H, census)
+        ms_stage = stage_ms[stage]
+        if bound == "hbm":
+            achieved = amount / (ms_stage * 1e-3) / 1e9
+            return {"bound": "hbm", "kernel": stage, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": recorded_traffic(stage),
+                    "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src,
+                    "algorithmic_bytes_per_launch": amount, "launch_ms": ms_stage}
+        peak = fp32_peak_tflops(sm_max_mhz)
+        achieved = amount / (ms_stage * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(stage),
+                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz" % (SMS, FP32_LANES, sm_max_mhz),
+                "algorithmic_flop_per_launch": amount, "launch_ms": ms_stage,
+                "pairs_evaluated_per_frame": census[0], "pairs_blended_per_frame": census[1]}
+
+    roof = roofline(dom)
+    stage_roofline = {k: {kk: v[kk] for kk in ("bound", "achieved", "unit", "frac")}
+                      for k, v in ((s, roofline(s)) for s in ("project", "sort", "composite"))}
 
     # end to end through the public API: camera in from the host, planes out to pinned host memory
     e2e = None
@@ -336,7 +481,8 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "frames_per_s": 1e3 * args.steps * world / ms,
                 "stage_ms": stage_ms, "instances_per_frame": K_avg, "visible_per_frame": V_avg,
-                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+                "roofline": roof, "stage_roofline": stage_roofline, "clocks": clocks, "e2e": e2e,
+                "cpu_baseline": cpu,
                 "gpu_launches": args.steps * (6 + passes)}
         print(json.dumps(line), flush=True)
     graph.close()

@@ -83,7 +83,9 @@ typedef struct {
 
 enum {
     GS_EMIT_BWD_STATE = 1u,       /* keep what gs_render_backward needs */
-    GS_TIME_STAGES = 2u           /* record CUDA events at every stage boundary (see gs_frame_stats) */
+    GS_TIME_STAGES = 2u,          /* record CUDA events at every stage boundary (see gs_frame_stats) */
+    GS_COUNT_PAIRS = 4u           /* diagnostic: count evaluated and blended (pixel, Gaussian) pairs
+                                     (plain forward only; adds a synchronisation; see gs_frame_stats) */
 };
 
 typedef struct {
@@ -142,6 +144,8 @@ typedef struct {
     int64_t instances_max;        /* largest K */
     double stage_ms[6];
     int64_t timed_frames;         /* frames that carried stage events */
+    int64_t pairs_evaluated;      /* GS_COUNT_PAIRS: pixel inside a Gaussian's support rectangle, before the stop */
+    int64_t pairs_blended;        /* GS_COUNT_PAIRS: of those, alpha >= 1/255 and blended */
 } gs_frame_stats;
 
 /* ---------------------------------------------------------------- context */

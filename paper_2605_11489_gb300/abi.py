@@ -23,6 +23,7 @@ GS_ERR_CAPACITY = -5
 GS_ERR_CANCELLED = -6
 GS_EMIT_BWD_STATE = 1
 GS_TIME_STAGES = 2
+GS_COUNT_PAIRS = 4
 STAGES = ("project", "scan", "duplicate", "sort", "ranges", "composite")
 
 STATUS_NAMES = {0: "GS_OK", 1: "GS_NOT_READY", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_OOM", -3: "GS_ERR_CUDA",
@@ -73,7 +74,8 @@ class GsStateView(C.Structure):
 
 class GsFrameStats(C.Structure):
     _fields_ = [("frames", C.c_int64), ("instances_total", C.c_int64), ("visible_total", C.c_int64),
-                ("instances_max", C.c_int64), ("stage_ms", C.c_double * 6), ("timed_frames", C.c_int64)]
+                ("instances_max", C.c_int64), ("stage_ms", C.c_double * 6), ("timed_frames", C.c_int64),
+                ("pairs_evaluated", C.c_int64), ("pairs_blended", C.c_int64)]
 
 
 class GsError(RuntimeError):

@@ -82,18 +82,20 @@ def camera_struct(cam) -> GsCamera:
     return c
 
 
-def opts_struct(tile=0, batch=0, bg=(0.0, 0.0, 0.0), state=False, timed=False, chunk=0) -> GsRenderOpts:
+def opts_struct(tile=0, batch=0, bg=(0.0, 0.0, 0.0), state=False, timed=False, chunk=0, count=False) -> GsRenderOpts:
     o = GsRenderOpts()
     o.tile, o.batch, o.chunk = int(tile), int(batch), int(chunk)
     for k in range(3):
         o.bg[k] = float(bg[k])
-    o.flags = (abi.GS_EMIT_BWD_STATE if state else 0) | (abi.GS_TIME_STAGES if timed else 0)
+    o.flags = (abi.GS_EMIT_BWD_STATE if state else 0) | (abi.GS_TIME_STAGES if timed else 0) | \
+        (abi.GS_COUNT_PAIRS if count else 0)
     return o
 
 
 def _stats_dict(st) -> dict:
     return dict(frames=st.frames, instances_total=st.instances_total, visible_total=st.visible_total,
                 instances_max=st.instances_max, timed_frames=st.timed_frames,
+                pairs_evaluated=st.pairs_evaluated, pairs_blended=st.pairs_blended,
                 stage_ms={k: st.stage_ms[i] for i, k in enumerate(abi.STAGES)})
 
 
@@ -210,12 +212,12 @@ class Context:
             pass
 
     def forward(self, scene: Scene, cam, tile=0, batch=0, bg=(0.0, 0.0, 0.0), keys=OUTPUT_KEYS, out=None,
-                state=False, timed=False, stream=None, chunk=0):
+                state=False, timed=False, stream=None, chunk=0, count=False):
         """Render; returns the output dict (and a State if state=True)."""
         if out is None:
             out = alloc_outputs(cam.width, cam.height, keys)
         sc, cm = scene.struct(), camera_struct(cam)
-        op, ou = opts_struct(tile, batch, bg, state, timed, chunk), outputs_struct(out)
+        op, ou = opts_struct(tile, batch, bg, state, timed, chunk, count), outputs_struct(out)
         hs = C.c_void_p()
         check(abi.lib().gs_render_forward(self.h, C.byref(sc), C.byref(cm), C.byref(op), C.byref(ou),
                                           C.byref(hs) if state else None, _stream_ptr(stream)))

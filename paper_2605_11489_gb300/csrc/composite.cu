@@ -60,6 +60,7 @@ struct PixelAcc {
     float T, Tx, Ty, D;
     float C[3], Cx[3], Cy[3];
     uint32_t last;
+    uint32_t n_eval, n_blend;  // pairs counted in the GS_COUNT_PAIRS instantiation only
     bool done, stopped;
 };
 
@@ -72,6 +73,7 @@ __device__ __forceinline__ void acc_init(PixelAcc &s, bool inside)
     s.last = 0;
     s.done = !inside;
     s.stopped = false;
+    s.n_eval = s.n_blend = 0;
 }
 
 // Pixel of thread `tid`: warps own 8x4 blocks, row-major over the tile.
@@ -88,10 +90,11 @@ __device__ __forceinline__ void tile_pixel(int tid, int tile_x, int tile_y, int 
 
 // One Gaussian record at one pixel (Eq. 2-4). Returns true when the pixel
 // stops (the record would take T below 1e-4; it is not blended).
-template <bool GRAD, bool STATE>
+template <bool GRAD, bool STATE, bool COUNT = false>
 __device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float4 &r1, const float4 &r2, float pxc,
                                       float pyc, uint32_t pos)
 {
+    if (COUNT) ++s.n_eval;
     const AlphaEval e = eval_alpha(r0, r1, pxc, pyc);
     const float al = e.al;
     if (al < kAlphaMin) return false;
@@ -118,6 +121,7 @@ __device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float
     }
     s.T = nT;
     if (STATE) s.last = pos;
+    if (COUNT) ++s.n_blend;
     return false;
 }
 
@@ -141,7 +145,7 @@ __device__ __forceinline__ void ring_init(WarpRing<BATCH> &ring)
 // pixel state. (px, py) is the lane's pixel, (bx0, by0) the warp's 8x4 block,
 // pos0 the list position of s0 within its tile. The warp's ring carries its
 // mbarrier parities in `phase`. Returns false if a bounded wait gave up.
-template <int BATCH, bool GRAD, bool STATE>
+template <int BATCH, bool GRAD, bool STATE, bool COUNT = false>
 __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py, int bx0, int by0, uint32_t s0,
                                           uint32_t s1, uint32_t pos0, WarpRing<BATCH> &ring,
                                           uint32_t (&phase)[kStages], PixelAcc &s)
@@ -199,7 +203,7 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
                 m &= m - 1u;
                 const float4 r2 = recs[k].r2;
                 if (!rect_contains(r2, upx, upy)) continue;
-                if (blend<GRAD, STATE>(s, recs[k].r0, recs[k].r1, r2, pxc, pyc, pos_b + k)) {
+                if (blend<GRAD, STATE, COUNT>(s, recs[k].r0, recs[k].r1, r2, pxc, pyc, pos_b + k)) {
                     s.done = true;
                     s.stopped = true;
                     break;
@@ -301,7 +305,7 @@ __device__ __forceinline__ void compose(PixelAcc &P, const PixelAcc &Q)
     if (STATE && Q.last) P.last = Q.last;
 }
 
-template <int TILE, int BATCH, bool GRAD, bool STATE>
+template <int TILE, int BATCH, bool GRAD, bool STATE, bool COUNT = false>
 __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -329,8 +333,20 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
     PixelAcc s;
     acc_init(s, inside);
     const uint32_t pos0 = s0 - a.ranges[tile].x;
-    const bool ok = warp_span<BATCH, GRAD, STATE>(a, px, py, bx0, by0, s0, s1, pos0, ring, phase, s);
+    const bool ok = warp_span<BATCH, GRAD, STATE, COUNT>(a, px, py, bx0, by0, s0, s1, pos0, ring, phase, s);
     if (!ok && (threadIdx.x & 31) == 0) atomicOr(a.err_word, kErrTmaTimeout);
+    if (COUNT) {  // evaluated (inside a support rectangle) and blended pairs of this warp
+        unsigned long long ne = s.n_eval, nb = s.n_blend;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ne += __shfl_xor_sync(0xffffffffu, ne, o);
+            nb += __shfl_xor_sync(0xffffffffu, nb, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(a.pair_counts, ne);
+            atomicAdd(a.pair_counts + 1, nb);
+        }
+    }
     if (slot == kWholeTile) {
         if (inside) write_final<GRAD, STATE>(a, px, py, s);
     } else {
@@ -452,14 +468,14 @@ cudaError_t opt_in_smem(F *kernel, size_t bytes, bool (&done)[64])
     return e;
 }
 
-template <int TILE, int BATCH, bool GRAD, bool STATE>
+template <int TILE, int BATCH, bool GRAD, bool STATE, bool COUNT = false>
 cudaError_t launch_one(const CompositeArgs &a, unsigned nb, cudaStream_t s)
 {
     constexpr size_t smem = smem_bytes<TILE, BATCH>();
     static bool done[64];
-    cudaError_t e = opt_in_smem(k_composite<TILE, BATCH, GRAD, STATE>, smem, done);
+    cudaError_t e = opt_in_smem(k_composite<TILE, BATCH, GRAD, STATE, COUNT>, smem, done);
     if (e != cudaSuccess) return e;
-    k_composite<TILE, BATCH, GRAD, STATE><<<nb, TILE * TILE, smem, s>>>(a);
+    k_composite<TILE, BATCH, GRAD, STATE, COUNT><<<nb, TILE * TILE, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -473,6 +489,9 @@ cudaError_t launch_tb(const CompositeArgs &a, int64_t max_items, cudaStream_t s)
         if (nb == 0) return cudaSuccess;
         const bool grad = a.dcdx || a.dcdy;
         const bool state = a.final_T != nullptr;
+        if (a.pair_counts && !state)  // diagnostic pair census (GS_COUNT_PAIRS)
+            return grad ? launch_one<TILE, BATCH, true, false, true>(a, nb, s)
+                        : launch_one<TILE, BATCH, false, false, true>(a, nb, s);
         if (grad && state) return launch_one<TILE, BATCH, true, true>(a, nb, s);
         if (grad) return launch_one<TILE, BATCH, true, false>(a, nb, s);
         if (state) return launch_one<TILE, BATCH, false, true>(a, nb, s);

@@ -60,6 +60,7 @@ enum CounterSlot : int {
     kCntSumK = 6,       // u64 (slots 6-7): sum of K over frames since reset
     kCntSumV = 8,       // u64 (slots 8-9): sum of visible Gaussians over frames since reset
     kCntFrames = 10,    // frames since reset
+    kCntPairs = 12,     // u64 x2 (slots 12-15): evaluated and blended pairs (GS_COUNT_PAIRS)
     kCntSlots = 16,
     kCntPerFrame = 4,   // slots 0..3 are cleared at the start of every frame
 };
@@ -139,6 +140,7 @@ struct CompositeArgs {
     const uint32_t *split_slot0;   // first slot of each split tile
     float *partial;                // [slot][16][TILE*TILE] per-pixel partial state of chunks
     int32_t chunk;                 // records per chunk of a split tile
+    unsigned long long *pair_counts;  // (evaluated, blended) pairs: the GS_COUNT_PAIRS census (nullable)
 };
 constexpr uint32_t kWholeTile = 0xFFFFFFFFu;
 int64_t plan_max_slots(int64_t max_k, int chunk);

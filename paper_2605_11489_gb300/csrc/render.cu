@@ -92,6 +92,7 @@ struct Frame {
     float bg[3] = {0, 0, 0};
     CamParams cam{};
     bool has_state = false;
+    bool count_pairs = false;
 };
 
 // Per-stage CUDA-event timer: a ring of event sets, one set of kBounds events
@@ -237,7 +238,7 @@ struct gs_context {
     };
     std::map<TuneKey, Tuned> tune;
     StageTimer timer;
-    int64_t st_frames = 0, st_sum_k = 0, st_sum_v = 0, st_max_k = 0;
+    int64_t st_frames = 0, st_sum_k = 0, st_sum_v = 0, st_max_k = 0, st_pairs_eval = 0, st_pairs_blend = 0;
     ~gs_context()
     {
         for (Frame *f : pool) delete f;
@@ -415,6 +416,7 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
     c.split_slot0 = f->split_slot0.as<uint32_t>();
     c.partial = f->partial.as<float>();
     c.chunk = f->chunk;
+    if (f->count_pairs) c.pair_counts = reinterpret_cast<unsigned long long *>(f->counters.as<uint32_t>() + kCntPairs);
     return c;
 }
 
@@ -474,6 +476,7 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
                                         "fitting shared memory");
     const bool state = (o->flags & GS_EMIT_BWD_STATE) != 0;
     gs_status r = frame_setup(f, s, c, o, tile, batch, chunk, state);
+    f->count_pairs = (o->flags & GS_COUNT_PAIRS) != 0;
     if (r != GS_OK) return r;
     uint32_t *cnt = f->counters.as<uint32_t>();
     cudaEvent_t *ev = nullptr;
@@ -503,7 +506,14 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
     }
     if ((r = frame_plan(f, f->K)) != GS_OK) return r;
     // counters[kCntEff] was clamped to kMaxInstances; K fits, so it equals K.
-    return enqueue_after_scan(f, out, f->K, st, ev, false);
+    r = enqueue_after_scan(f, out, f->K, st, ev, false);
+    if (r != GS_OK || !f->count_pairs) return r;
+    GSR_CUDA(cudaMemcpyAsync(ctx->h_counters, cnt, sizeof(uint32_t) * kCntSlots, cudaMemcpyDeviceToHost, st));
+    GSR_CUDA(cudaStreamSynchronize(st));
+    const uint32_t *h = ctx->h_counters;
+    ctx->st_pairs_eval += (int64_t)((uint64_t)h[kCntPairs] | ((uint64_t)h[kCntPairs + 1] << 32));
+    ctx->st_pairs_blend += (int64_t)((uint64_t)h[kCntPairs + 2] | ((uint64_t)h[kCntPairs + 3] << 32));
+    return GS_OK;
 }
 
 }  // namespace
@@ -896,8 +906,11 @@ gs_status gs_context_stats(gs_context *ctx, gs_stream stream, int reset, gs_fram
     if (!ctx || !stats) return fail(GS_ERR_INVALID_ARG, "NULL argument");
     GSR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     fill_stats(stats, ctx->st_frames, ctx->st_sum_k, ctx->st_sum_v, ctx->st_max_k, ctx->timer);
+    stats->pairs_evaluated = ctx->st_pairs_eval;
+    stats->pairs_blended = ctx->st_pairs_blend;
     if (reset) {
         ctx->st_frames = ctx->st_sum_k = ctx->st_sum_v = ctx->st_max_k = 0;
+        ctx->st_pairs_eval = ctx->st_pairs_blend = 0;
         ctx->timer.reset();
     }
     return GS_OK;
