@@ -64,7 +64,7 @@ def lib():
             L.or_cov3d.argtypes = [P, P, P, P]
             L.or_project.argtypes = [P, P, C.c_int32] + [P] * 10
             L.or_render.argtypes = [P, P, C.c_int] + [P] * 10
-            L.or_render_pixels.argtypes = [P, P, C.c_int64, P, P, P, P]
+            L.or_render_pixels.argtypes = [P, P, C.c_int64, P, P, P, P, P, P]
             L.or_render_band.argtypes = [P, P, C.c_int, C.c_int, P, P, P, P, P]
             L.or_count_instances.restype = C.c_int64
             L.or_count_instances.argtypes = [P, P, C.c_int32]
@@ -188,19 +188,25 @@ def render_band(scene, cam, y0: int, y1: int, bg=(0.0, 0.0, 0.0)) -> dict:
     return out
 
 
-def render_pixels(scene, cam, px, py, bg=(0.0, 0.0, 0.0)) -> tuple[np.ndarray, np.ndarray]:
-    """Brute-force render of sampled pixels. Returns ([n, 11] = rgb, dcdx, dcdy,
-    depth, alpha; n_blended)."""
+def render_pixels(scene, cam, px, py, bg=(0.0, 0.0, 0.0)) -> dict:
+    """Brute-force render of sampled pixels (each pixel scans every visible
+    Gaussian). Returns per sample: rgb/dcdx/dcdy [n, 3], depth/alpha [n],
+    n_blended, amb and gabs [n, 2, 3] (as in render())."""
     s = _as_oscene(scene)
     px = np.ascontiguousarray(px, dtype=np.int32)
     py = np.ascontiguousarray(py, dtype=np.int32)
-    out = np.zeros((len(px), 11))
-    nb = np.zeros(len(px), np.int32)
+    n = len(px)
+    out = np.zeros((n, 11))
+    nb = np.zeros(n, np.int32)
+    amb = np.zeros(n, np.int32)
+    gabs = np.zeros((n, 2, 3))
     st, cm = s.struct(), _cam(cam, bg)
-    rc = lib().or_render_pixels(C.byref(st), C.byref(cm), len(px), _ptr(px), _ptr(py), _ptr(out), _ptr(nb))
+    rc = lib().or_render_pixels(C.byref(st), C.byref(cm), n, _ptr(px), _ptr(py), _ptr(out), _ptr(nb), _ptr(amb),
+                                _ptr(gabs))
     if rc != 0:
         raise RuntimeError("or_render_pixels failed: %d" % rc)
-    return out, nb
+    return dict(rgb=out[:, 0:3], dcdx=out[:, 3:6], dcdy=out[:, 6:9], depth=out[:, 9], alpha=out[:, 10],
+                n_blended=nb, amb=amb, gabs=gabs)
 
 
 def keys(scene, cam, tile: int = 16) -> dict:

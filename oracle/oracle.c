@@ -703,7 +703,7 @@ static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y
 /* A sample of pixels (brute force per pixel). out: [npix][11] =
  * rgb(3), dcdx(3), dcdy(3), depth, alpha. */
 int or_render_pixels(const or_scene *sc, const or_camera *cam, int64_t npix, const int32_t *px,
-                     const int32_t *py, double *out, int32_t *n_blended)
+                     const int32_t *py, double *out, int32_t *n_blended, int32_t *amb, double *gabs)
 {
     or_frame F;
     if (frame_build(sc, cam, &F)) return -2;
@@ -723,6 +723,12 @@ int or_render_pixels(const or_scene *sc, const or_camera *cam, int64_t npix, con
             r[9] = o.depth;
             r[10] = o.alpha;
             if (n_blended) n_blended[k] = o.n_blended;
+            if (amb) amb[k] = o.amb;
+            if (gabs)
+                for (int c = 0; c < 3; ++c) {
+                    gabs[6 * k + c] = o.gx_abs[c];
+                    gabs[6 * k + 3 + c] = o.gy_abs[c];
+                }
         }
         free(buf);
     }

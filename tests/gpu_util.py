@@ -6,18 +6,21 @@ Tolerances (stated for the render's outputs):
       on >= 99.99 % of values and <= 5e-3 on all; the excess is the alpha = 1/255
       cut flipping under fp32 rounding (a flip moves a pixel by at most about
       c * 1/255).
-  depth: the same, scaled by max(1, |ref depth|).
-  gradient channels: |g - g_ref| <= 1e-3 * |g_ref| + 1e-4 * S + 1e-6 per channel,
+  depth: the same, scaled by max(1, ref depth / ref alpha): depth = sum z a T is
+      the alpha terms weighted by the contributors' depth, so the same per-term
+      error shows up multiplied by their (alpha-weighted mean) depth.
+  gradient channels: |g - g_ref| <= 1e-3 * (|g_ref| + S) + 1e-5 per channel,
       where S is the oracle's per-pixel sum of |terms| of Eq. 3 (incl. the bg
       term), on pixels whose colour is within 2e-4 and with no discrete decision
-      within 1e-5 of its threshold (oracle `amb`). The S term is the fp32
-      rounding of the inputs of each term: the projected centre u is an fp32
-      number (ulp up to 1.2e-4 px below 2048 px), which moves a term
-      c T a (conic d)_x by up to ~1e-4 of itself for the Gaussians here
-      (sigma >= 0.55 px after the low-pass); terms that nearly cancel keep that
-      absolute error. A 1e-6 absolute floor covers pixels where conic * d
+      within 1e-5 of its threshold (oracle `amb`): "1e-3 relative", measured
+      against the magnitude of the terms the gradient is made of. The projected
+      centre u is an fp32 number (ulp up to 1.2e-4 px below 2048 px); a term
+      c T a (conic d)_x moves by c T a (|e|^2 + |conic|) ulp(u), up to ~5e-4
+      of itself for the Gaussians here (sigma >= 0.55 px after the low-pass),
+      and terms that nearly cancel keep that absolute error. A 1e-5 absolute floor covers pixels where conic * d
       itself nearly cancels, so its relative error is unbounded while its
-      absolute error stays ~|conic| ulp(u) (1e-6 is 1/4000 of one 8-bit level).
+      absolute error stays ~ c T a |conic| ulp(u) (about 1e-5 for |u| near
+      1000 px; 1e-5 is 1/400 of one 8-bit level).
 """
 import numpy as np
 
@@ -38,11 +41,19 @@ def check_colour(got, ref, name, scale=None, frac=COLOUR_FRAC, tol_all=COLOUR_TO
     return ok
 
 
+def grad_bound(ref, scale, rel=GRAD_REL):
+    return rel * (np.abs(ref) + scale) + 1e-5
+
+
+def depth_scale(ref_depth, ref_alpha):
+    return np.maximum(1.0, np.abs(ref_depth) / np.maximum(ref_alpha, 1e-12))
+
+
 def check_grad(got, ref, mask, name, scale, rel=GRAD_REL):
     got = np.asarray(got, dtype=np.float64)
     for c in range(ref.shape[0]):
         r = ref[c]
-        bound = rel * np.abs(r) + 1e-4 * scale[c] + 1e-6
+        bound = grad_bound(r, scale[c], rel)
         bad = (np.abs(got[c] - r) > bound) & mask
         assert not bad.any(), "%s[%d]: %d pixels out of tolerance, worst %.3g vs bound %.3g" % (
             name, c, bad.sum(), np.abs(got[c] - r)[bad].max(), bound[bad].min())
@@ -53,7 +64,7 @@ def check_render(out, ref, frac=COLOUR_FRAC):
     g = {k: v.detach().cpu().numpy() for k, v in out.items()}
     ok_rgb = check_colour(g["rgb"], ref["rgb"], "rgb", frac=frac)
     check_colour(g["alpha"], ref["alpha"], "alpha", frac=frac)
-    check_colour(g["depth"], ref["depth"], "depth", scale=np.maximum(1.0, np.abs(ref["depth"])), frac=frac,
+    check_colour(g["depth"], ref["depth"], "depth", scale=depth_scale(ref["depth"], ref["alpha"]), frac=frac,
                  tol_all=COLOUR_TOL_ALL)
     mask = ok_rgb.all(axis=0)
     if "amb" in ref:
