@@ -25,16 +25,24 @@
 //
 // Load balance: a tile whose list is longer than `chunk` records is split into
 // depth-contiguous chunks, one work item each, composited from the identity
-// state into per-pixel partial states (C, C_x, C_y, D, T, T_x, T_y). The merge
-// folds them front to back with the exact composition of two segments a, b:
+// state into per-pixel partial states (C, C_x, C_y, D, T, T_x, T_y). Two
+// segments a, b compose exactly as
 //   C = Ca + Ta Cb,  C_x = Cxa + Txa Cb + Ta Cxb,  D = Da + Ta Db,
 //   T = Ta Tb,       T_x = Txa Tb + Ta Txb                     (product rule)
 // which equals the sequential result as long as no Gaussian of the tile was
-// cut off by the T < 1e-4 stop. T only decreases, so the stop falls inside
-// chunk c exactly when c stopped locally or prefix T * chunk T < 1e-4; that
-// chunk is then re-walked from the exact prefix state, so the stop rule is
-// applied exactly as in one sequential pass.
+// cut off by the T < 1e-4 stop. T only decreases, so a pixel's stop falls in
+// chunk c exactly when c stopped locally or (prefix T) * (chunk T) < 1e-4.
+// Finishing a split tile takes two launches:
+//   k_rewalk: one pass per chunk, in parallel over all chunks. The lanes whose
+//     stop falls in this chunk fold the partial states in front of it into
+//     their exact prefix state and walk on from there through the same staged,
+//     masked warp pass, until they stop; they write their pixels.
+//   k_finish: one pass per split tile; every other pixel folds all chunks
+//     front to back and writes its result.
+// Both decide "stop in chunk c" from the same product chain of chunk T's, so
+// every pixel is written exactly once.
 #include "gsr_internal.cuh"
+#include <algorithm>
 
 namespace gsr {
 namespace {
@@ -354,50 +362,113 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
     }
 }
 
-// Merge of split tiles: fold the chunks' partial states front to back. For
-// each chunk in order, every pixel whose stop does not fall in it folds it;
-// the pixels whose stop does (it stopped locally, or prefix T * chunk T
-// < 1e-4) re-walk that chunk from their exact prefix states through the same
-// staged, masked warp pass as compositing. A pixel that then did not stop
-// (the fold's product and the sequential product differ by rounding) simply
-// continues with the next chunk.
+// Pixel `tid` of a split tile: does its stop fall in front of chunk c, in it,
+// or later? Follows the prefix product chain of the chunks' T exactly as the
+// fold in k_rewalk / k_finish does. Loads are issued four chunks at a time.
+template <int TILE>
+__device__ __forceinline__ int stop_chunk_relation(const float *slot0, int tid, uint32_t c)
+{
+    constexpr int NT = TILE * TILE;
+    constexpr size_t kSlot = (size_t)kPartialVals * NT;
+    float T = 1.0f;
+    for (uint32_t j0 = 0; j0 <= c; j0 += 4) {
+        float tj[4], sj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool in = j0 + u <= c;
+            tj[u] = in ? slot0[(j0 + u) * kSlot + 10 * NT + tid] : 1.0f;
+            sj[u] = in ? slot0[(j0 + u) * kSlot + 14 * NT + tid] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (j0 + u > c) break;
+            if (sj[u] != 0.0f || __fmul_rn(T, tj[u]) < kTMin) return j0 + u < c ? -1 : 0;
+            T = __fmul_rn(T, tj[u]);
+        }
+    }
+    return 1;  // -1: stop before c, 0: stop in c, 1: no stop up to and including c
+}
+
+// Split tiles, part 1 (one chunk per warp-item, all chunks in parallel): the
+// lanes whose stop falls in this chunk fold the partial states of the chunks
+// in front of it (exact prefix state), then walk the tile's records from the
+// chunk's start through the staged, masked warp pass until they stop, and
+// write their pixels. A lane whose walk ends the chunk without stopping (the
+// fold's product and the sequential one differ by rounding) walks on into the
+// next chunks, which continues the sequential pass exactly.
 template <int TILE, int BATCH, bool GRAD, bool STATE>
-__global__ void __launch_bounds__(TILE *TILE) k_merge(const CompositeArgs a)
+__global__ void __launch_bounds__(TILE *TILE) k_rewalk(const CompositeArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (blockIdx.x >= a.plan_counts[1]) return;
-    const uint32_t tile = a.split_tiles[blockIdx.x], slot0 = a.split_slot0[blockIdx.x];
-    const uint2 r = a.ranges[tile];
-    const uint32_t chunk = (uint32_t)a.chunk;
-    const uint32_t nch = (r.y - r.x + chunk - 1) / chunk;
-    const int tx = (int)(tile % (uint32_t)a.tiles_x), ty = (int)(tile / (uint32_t)a.tiles_x);
-    int px, py, bx0, by0;
-    tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);
-    const bool inside = px < a.width && py < a.height;
+    constexpr int NT = TILE * TILE;
     WarpRing<BATCH> &ring = reinterpret_cast<WarpRing<BATCH> *>(smem_raw)[threadIdx.x >> 5];
     ring_init(ring);
     uint32_t phase[kStages] = {};
-    PixelAcc P;
-    acc_init(P, inside);  // P.done: pixel finished (outside, or stopped)
     bool ok = true;
-    for (uint32_t c = 0; c < nch; ++c) {
-        bool walk = false;
-        if (!P.done) {
-            PixelAcc Q;
-            read_partial<TILE>(a.partial + (size_t)(slot0 + c) * kPartialVals * TILE * TILE, threadIdx.x, Q);
-            walk = Q.stopped || __fmul_rn(P.T, Q.T) < kTMin;
-            if (!walk) compose<GRAD, STATE>(P, Q);
-        }
+    const uint32_t n_slots = a.plan_counts[2];
+    const uint32_t chunk = (uint32_t)a.chunk;
+    for (uint32_t b = blockIdx.x; b < n_slots; b += gridDim.x) {
+        const uint4 it = a.items[b];  // split chunks occupy items [0, n_slots), slot == index
+        const uint32_t tile = it.x;
+        const uint2 r = a.ranges[tile];
+        const uint32_t c = (it.y - r.x) / chunk;
+        const float *slot0 = a.partial + (size_t)(b - c) * kPartialVals * NT;
+        const int tx = (int)(tile % (uint32_t)a.tiles_x), ty = (int)(tile / (uint32_t)a.tiles_x);
+        int px, py, bx0, by0;
+        tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);
+        const bool inside = px < a.width && py < a.height;
+        const bool walk = inside && stop_chunk_relation<TILE>(slot0, threadIdx.x, c) == 0;
         if (!__any_sync(0xffffffffu, walk)) continue;
-        const bool was_done = P.done;
-        P.done = !walk;  // only the walking lanes take part
-        P.stopped = false;
-        const uint32_t k0 = r.x + c * chunk, k1 = min(r.y, k0 + chunk);
-        ok &= warp_span<BATCH, GRAD, STATE>(a, px, py, bx0, by0, k0, k1, k0 - r.x, ring, phase, P);
-        P.done = was_done || (walk && P.stopped);
+        PixelAcc P;
+        acc_init(P, walk);
+        if (walk && c > 0) {  // exact prefix state; the next chunk's loads overlap this fold
+            PixelAcc Qn;
+            read_partial<TILE>(slot0, threadIdx.x, Qn);
+            for (uint32_t j = 0; j < c; ++j) {
+                const PixelAcc Q = Qn;
+                if (j + 1 < c) read_partial<TILE>(slot0 + (size_t)(j + 1) * kPartialVals * NT, threadIdx.x, Qn);
+                compose<GRAD, STATE>(P, Q);
+            }
+        }
+        ok &= warp_span<BATCH, GRAD, STATE>(a, px, py, bx0, by0, it.y, r.y, it.y - r.x, ring, phase, P);
+        if (walk) write_final<GRAD, STATE>(a, px, py, P);
     }
     if (!ok && (threadIdx.x & 31) == 0) atomicOr(a.err_word, kErrTmaTimeout);
-    if (inside) write_final<GRAD, STATE>(a, px, py, P);
+}
+
+// Split tiles, part 2 (one split tile per CTA): the pixels whose stop falls in
+// no chunk fold all chunks front to back and write their results; the next
+// chunk's partial state is loaded while the current one is folded.
+template <int TILE, bool GRAD, bool STATE>
+__global__ void __launch_bounds__(TILE *TILE) k_finish(const CompositeArgs a)
+{
+    constexpr int NT = TILE * TILE;
+    const uint32_t n_split = a.plan_counts[1];
+    const uint32_t chunk = (uint32_t)a.chunk;
+    for (uint32_t b = blockIdx.x; b < n_split; b += gridDim.x) {
+        const uint32_t tile = a.split_tiles[b];
+        const float *slot0 = a.partial + (size_t)a.split_slot0[b] * kPartialVals * NT;
+        const uint2 r = a.ranges[tile];
+        const uint32_t nch = (r.y - r.x + chunk - 1) / chunk;
+        const int tx = (int)(tile % (uint32_t)a.tiles_x), ty = (int)(tile / (uint32_t)a.tiles_x);
+        int px, py, bx0, by0;
+        tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);
+        if (px >= a.width || py >= a.height) continue;
+        PixelAcc P, Qn;
+        acc_init(P, true);
+        read_partial<TILE>(slot0, threadIdx.x, Qn);
+        bool stopped = false;
+        for (uint32_t c = 0; c < nch; ++c) {
+            const PixelAcc Q = Qn;
+            if (c + 1 < nch) read_partial<TILE>(slot0 + (size_t)(c + 1) * kPartialVals * NT, threadIdx.x, Qn);
+            if (Q.stopped || __fmul_rn(P.T, Q.T) < kTMin) {  // k_rewalk owns this pixel
+                stopped = true;
+                break;
+            }
+            compose<GRAD, STATE>(P, Q);
+        }
+        if (!stopped) write_final<GRAD, STATE>(a, px, py, P);
+    }
 }
 
 // Serving: a persistent grid pulls (request, tile) items from a flat work list
@@ -510,27 +581,33 @@ cudaError_t launch_t(const CompositeArgs &a, int batch, int64_t max_items, cudaS
     }
 }
 
+// Grid of the split-tile passes: enough CTAs to fill the GPU a few times over,
+// each looping over its share of the (device-side counted) work.
+constexpr int64_t kMergeGridMax = 152 * 12;
+
 template <int TILE, bool GRAD, bool STATE>
-cudaError_t launch_merge_one(const CompositeArgs &a, unsigned nb, cudaStream_t s)
+cudaError_t launch_merge_one(const CompositeArgs &a, int64_t max_split, int64_t max_slots, cudaStream_t s)
 {
     constexpr size_t smem = smem_bytes<TILE, 32>();
     static bool done[64];
-    cudaError_t e = opt_in_smem(k_merge<TILE, 32, GRAD, STATE>, smem, done);
+    cudaError_t e = opt_in_smem(k_rewalk<TILE, 32, GRAD, STATE>, smem, done);
     if (e != cudaSuccess) return e;
-    k_merge<TILE, 32, GRAD, STATE><<<nb, TILE * TILE, smem, s>>>(a);
+    k_rewalk<TILE, 32, GRAD, STATE><<<(unsigned)std::min(max_slots, kMergeGridMax), TILE * TILE, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_finish<TILE, GRAD, STATE><<<(unsigned)std::min(max_split, kMergeGridMax), TILE * TILE, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int TILE>
-cudaError_t launch_merge_t(const CompositeArgs &a, int64_t max_split, cudaStream_t s)
+cudaError_t launch_merge_t(const CompositeArgs &a, int64_t max_split, int64_t max_slots, cudaStream_t s)
 {
     const bool grad = a.dcdx || a.dcdy;
     const bool state = a.final_T != nullptr;
-    const unsigned nb = (unsigned)max_split;
-    if (grad && state) return launch_merge_one<TILE, true, true>(a, nb, s);
-    if (grad) return launch_merge_one<TILE, true, false>(a, nb, s);
-    if (state) return launch_merge_one<TILE, false, true>(a, nb, s);
-    return launch_merge_one<TILE, false, false>(a, nb, s);
+    if (grad && state) return launch_merge_one<TILE, true, true>(a, max_split, max_slots, s);
+    if (grad) return launch_merge_one<TILE, true, false>(a, max_split, max_slots, s);
+    if (state) return launch_merge_one<TILE, false, true>(a, max_split, max_slots, s);
+    return launch_merge_one<TILE, false, false>(a, max_split, max_slots, s);
 }
 
 template <int TILE>
@@ -568,13 +645,13 @@ cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, int64_
     }
 }
 
-cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, cudaStream_t s)
+cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, int64_t max_slots, cudaStream_t s)
 {
-    if (!a.items || max_split <= 0) return cudaSuccess;
+    if (!a.items || max_split <= 0 || max_slots <= 0) return cudaSuccess;
     switch (tile) {
-    case 8: return launch_merge_t<8>(a, max_split, s);
-    case 16: return launch_merge_t<16>(a, max_split, s);
-    default: return launch_merge_t<32>(a, max_split, s);
+    case 8: return launch_merge_t<8>(a, max_split, max_slots, s);
+    case 16: return launch_merge_t<16>(a, max_split, max_slots, s);
+    default: return launch_merge_t<32>(a, max_split, max_slots, s);
     }
 }
 

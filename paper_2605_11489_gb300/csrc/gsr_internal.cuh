@@ -148,7 +148,7 @@ int64_t plan_max_items(int n_tiles, int64_t max_k, int chunk);
 cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, uint4 *items, uint32_t *split_tiles,
                         uint32_t *split_slot0, uint32_t *counts, cudaStream_t s);
 // merge of split tiles' chunks (after launch_composite with a plan)
-cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, cudaStream_t s);
+cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, int64_t max_slots, cudaStream_t s);
 // order tiles by decreasing list length (power-of-two buckets)
 cudaError_t launch_tile_order(const uint2 *ranges, int n_tiles, uint32_t *order, cudaStream_t s);
 bool composite_supported(int tile, int batch);

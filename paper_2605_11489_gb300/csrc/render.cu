@@ -82,7 +82,7 @@ struct Frame {
     Buf ranges, order;
     Buf items, split_tiles, split_slot0, plan_counts, partial;  // compositing work plan
     int chunk = 2048;
-    int64_t max_items = 0, max_split = 0;
+    int64_t max_items = 0, max_split = 0, max_slots = 0;
     Buf fT, fTx, fTy, ncontrib;
     Buf counters;
     int64_t n = 0, K = 0, key_cap = 0;
@@ -356,6 +356,7 @@ gs_status frame_keys(Frame *f, int64_t cap)
 gs_status frame_plan(Frame *f, int64_t cap)
 {
     const int64_t slots = plan_max_slots(cap, f->chunk);
+    f->max_slots = slots;
     f->max_items = plan_max_items(f->n_tiles, cap, f->chunk);
     f->max_split = std::min<int64_t>(f->n_tiles, cap / f->chunk + 1);
     GSR_CUDA(f->items.ensure(sizeof(uint4) * (size_t)f->max_items));
@@ -452,7 +453,7 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     GSR_CUDA(mark(ev, 5, st, capture));
     const CompositeArgs ca = comp_args(f, out);
     GSR_CUDA(launch_composite(ca, f->tile, f->batch, f->max_items, st));
-    GSR_CUDA(launch_merge(ca, f->tile, f->max_split, st));
+    GSR_CUDA(launch_merge(ca, f->tile, f->max_split, f->max_slots, st));
     GSR_CUDA(mark(ev, 6, st, capture));
     return GS_OK;
 }

@@ -28,6 +28,7 @@ constexpr uint32_t kFlagPre = 2u << 30;
 constexpr uint32_t kFlagMask = 3u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 constexpr uint32_t kMaxSpins = 1u << 22;
+constexpr int kLook = 8;  // predecessors read per lookback round trip
 constexpr size_t kPassSmem = (size_t)kPart * 8 + (size_t)kPart * 4 + (size_t)kWarps * kRadix * 4;
 
 __device__ __forceinline__ uint32_t ld_vol(const uint32_t *p) { return *reinterpret_cast<const volatile uint32_t *>(p); }
@@ -154,7 +155,9 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(const uint64_t *__restri
     }
     uint32_t cexcl, hexcl;
     block_excl_scan2(cnt, hist[tid], cexcl, hexcl, s_tmp);
-    // decoupled lookback for this digit
+    // decoupled lookback for this digit, kLook predecessors per round trip:
+    // their words are loaded together and summed newest first until an
+    // inclusive prefix is met; a word not yet published is re-read on its own.
     uint32_t *st = status + (size_t)part * kRadix + tid;
     uint32_t excl = 0;
     if (part == 0) {
@@ -163,20 +166,31 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(const uint64_t *__restri
         st_vol(st, kFlagAgg | cnt);
         int p = (int)part - 1;
         uint32_t spins = 0;
-        while (p >= 0) {
-            const uint32_t s = ld_vol(status + (size_t)p * kRadix + tid);
-            const uint32_t f = s & kFlagMask;
-            if (f == 0u) {
-                if (++spins > kMaxSpins) {
-                    atomicOr(err, kErrSortTimeout);
+        bool done = false;
+        while (!done && p >= 0) {
+            uint32_t w[kLook];
+#pragma unroll
+            for (int u = 0; u < kLook; ++u) w[u] = p - u >= 0 ? ld_vol(status + (size_t)(p - u) * kRadix + tid) : 0u;
+#pragma unroll
+            for (int u = 0; u < kLook; ++u) {
+                if (done || p < 0) break;
+                uint32_t s = w[u];
+                while ((s & kFlagMask) == 0u) {
+                    if (++spins > kMaxSpins) {
+                        atomicOr(err, kErrSortTimeout);
+                        break;
+                    }
+                    __nanosleep(32);
+                    s = ld_vol(status + (size_t)p * kRadix + tid);
+                }
+                if ((s & kFlagMask) == 0u) {  // gave up
+                    done = true;
                     break;
                 }
-                __nanosleep(32);
-                continue;
+                excl += s & kValMask;
+                if ((s & kFlagMask) == kFlagPre) done = true;
+                --p;
             }
-            excl += s & kValMask;
-            if (f == kFlagPre) break;
-            --p;
         }
         st_vol(st, kFlagPre | ((excl + cnt) & kValMask));
     }
