@@ -68,15 +68,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const uint32_t *__
 
 // One thread per quad of Gaussians (same partition as the projection); emits
 // key = (tile id << 32) | fp32 bits of depth, val = Gaussian index, for every
-// tile of each Gaussian's support rectangle, in index order.
+// tile of each Gaussian's support rectangle, in index order. With `hist`, it
+// also builds the radix sort's per-pass digit histograms of exactly the keys
+// it writes (8-bit digits, `passes` of them): the four depth digits are shared
+// by all of a Gaussian's keys and counted once per Gaussian, the tile digits
+// once per key; block counts are merged into `hist` with one atomic per bin.
 __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__restrict__ ntiles,
                                                             const uint4 *__restrict__ bin,
                                                             const uint32_t *__restrict__ block_offs, int64_t n,
                                                             int tile_shift, int tiles_x, uint64_t *__restrict__ keys,
                                                             uint32_t *__restrict__ vals, unsigned long long capacity,
-                                                            uint32_t *counters)
+                                                            uint32_t *counters, uint32_t *__restrict__ hist,
+                                                            int passes)
 {
     __shared__ uint32_t s_warp[kProjThreads / 32];
+    __shared__ uint32_t s_hist[8 * 256];
+    if (hist)
+        for (int i = threadIdx.x; i < passes * 256; i += kProjThreads) s_hist[i] = 0;
     const int64_t i0 = ((int64_t)blockIdx.x * kProjThreads + threadIdx.x) * 4;
     uint4 nt = make_uint4(0, 0, 0, 0);
     if (i0 < n) nt = *reinterpret_cast<const uint4 *>(ntiles + i0);
@@ -93,7 +101,6 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
     uint32_t before = 0;
     for (int w = 0; w < warp; ++w) before += s_warp[w];
     unsigned long long off = (unsigned long long)block_offs[blockIdx.x] + before + (v - mine);
-    if (mine == 0) return;
     const uint32_t cnt[4] = {nt.x, nt.y, nt.z, nt.w};
     bool overflow = false;
 #pragma unroll
@@ -103,11 +110,20 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
         const int x0 = (b.y & 0xFFFFu) >> tile_shift, y0 = (b.y >> 16) >> tile_shift;
         const int x1 = (b.z & 0xFFFFu) >> tile_shift, y1 = (b.z >> 16) >> tile_shift;
         const uint32_t idx = (uint32_t)(i0 + g);
+        if (hist) {  // depth digits: every written key of this Gaussian shares them
+            const uint32_t written =
+                off >= capacity ? 0u : (uint32_t)min((unsigned long long)cnt[g], capacity - off);
+            for (int p = 0; p < passes && p < 4; ++p)
+                if (written) atomicAdd(&s_hist[p * 256 + ((b.x >> (8 * p)) & 0xFFu)], written);
+        }
         for (int ty = y0; ty <= y1; ++ty)
             for (int tx = x0; tx <= x1; ++tx) {
+                const uint32_t tile = (uint32_t)(ty * tiles_x + tx);
                 if (off < capacity) {
-                    keys[off] = ((uint64_t)(uint32_t)(ty * tiles_x + tx) << 32) | (uint64_t)b.x;
+                    keys[off] = ((uint64_t)tile << 32) | (uint64_t)b.x;
                     vals[off] = idx;
+                    if (hist)
+                        for (int p = 4; p < passes; ++p) atomicAdd(&s_hist[p * 256 + ((tile >> (8 * (p - 4))) & 0xFFu)], 1u);
                 } else {
                     overflow = true;
                 }
@@ -115,6 +131,11 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
             }
     }
     if (overflow) atomicOr(&counters[kCntErr], kErrCapacity);
+    if (hist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < passes * 256; i += kProjThreads)
+            if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
+    }
 }
 
 // Per-tile [start, end) of the sorted keys and, in the same pass, the records
@@ -285,12 +306,17 @@ cudaError_t launch_scan_blocks(const uint32_t *block_sums, int nblocks, uint32_t
 
 cudaError_t launch_duplicate(const uint32_t *ntiles, const uint4 *bin, const uint32_t *block_offsets, int64_t n,
                              int tile_shift, int tiles_x, uint64_t *keys, uint32_t *vals, int64_t capacity,
-                             uint32_t *counters, cudaStream_t s)
+                             uint32_t *counters, uint32_t *hist, int passes, cudaStream_t s)
 {
+    if (hist) {
+        if (passes < 1 || passes > 8) return cudaErrorInvalidValue;
+        const cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 8 * 256, s);
+        if (e != cudaSuccess) return e;
+    }
     const int nb = project_blocks(n);
     if (nb == 0) return cudaSuccess;
     k_duplicate<<<nb, kProjThreads, 0, s>>>(ntiles, bin, block_offsets, n, tile_shift, tiles_x, keys, vals,
-                                            (unsigned long long)capacity, counters);
+                                            (unsigned long long)capacity, counters, hist, passes);
     return cudaGetLastError();
 }
 

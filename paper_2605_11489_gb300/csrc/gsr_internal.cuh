@@ -100,10 +100,11 @@ cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s);
 // scan of the projection's per-block sums -> per-block offsets and K
 cudaError_t launch_scan_blocks(const uint32_t *block_sums, int nblocks, uint32_t *block_offsets,
                                uint32_t *counters, int64_t capacity, cudaStream_t s);
-// (tile, depth) key duplication
+// (tile, depth) key duplication; with `hist` ([8][256], cleared here) also the
+// radix sort's digit histograms of the written keys, for a sort of `passes` digits
 cudaError_t launch_duplicate(const uint32_t *ntiles, const uint4 *bin, const uint32_t *block_offsets,
                              int64_t n, int tile_shift, int tiles_x, uint64_t *keys, uint32_t *vals,
-                             int64_t capacity, uint32_t *counters, cudaStream_t s);
+                             int64_t capacity, uint32_t *counters, uint32_t *hist, int passes, cudaStream_t s);
 // per-tile [start, end) from sorted keys, plus the records gathered into sorted order
 cudaError_t launch_ranges(const uint64_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
                           const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, cudaStream_t s);
@@ -119,8 +120,11 @@ size_t sort_scratch_bytes(int64_t capacity);
 void sort_scratch_carve(void *base, int64_t capacity, SortScratch *s);
 int sort_passes(int bits);
 // Sorts keys[0]/vals[0] into the buffer pair returned in *result (0 or 1).
+// hist_ready: scr.hist already holds the digit histograms of the keys (built
+// by launch_duplicate), so the histogram pass is skipped.
 cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *counters, uint32_t *err_word,
-                        int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s);
+                        int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s,
+                        bool hist_ready = false);
 
 struct CompositeArgs {
     const GaussRec *rec;  // records in sorted (instance) order: tile t's list is rec[ranges[t].x, ranges[t].y)

@@ -433,16 +433,16 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
                              bool capture = false)
 {
     uint32_t *cnt = f->counters.as<uint32_t>();
-    GSR_CUDA(launch_duplicate(f->ntiles.as<uint32_t>(), f->bin.as<uint4>(), f->boffs.as<uint32_t>(), f->n,
-                              f->cam.tile_shift, f->tiles_x, f->keys[0].as<uint64_t>(), f->vals[0].as<uint32_t>(),
-                              f->key_cap, cnt, st));
-    GSR_CUDA(mark(ev, 3, st, capture));
     SortScratch scr;
     sort_scratch_carve(f->sort_scr.p, f->key_cap, &scr);
+    GSR_CUDA(launch_duplicate(f->ntiles.as<uint32_t>(), f->bin.as<uint4>(), f->boffs.as<uint32_t>(), f->n,
+                              f->cam.tile_shift, f->tiles_x, f->keys[0].as<uint64_t>(), f->vals[0].as<uint32_t>(),
+                              f->key_cap, cnt, scr.hist, sort_passes(f->bits), st));
+    GSR_CUDA(mark(ev, 3, st, capture));
     uint64_t *kk[2] = {f->keys[0].as<uint64_t>(), f->keys[1].as<uint64_t>()};
     uint32_t *vv[2] = {f->vals[0].as<uint32_t>(), f->vals[1].as<uint32_t>()};
     int res = 0;
-    GSR_CUDA(launch_sort(kk, vv, cnt, cnt + kCntErr, max_k, f->bits, scr, &res, st));
+    GSR_CUDA(launch_sort(kk, vv, cnt, cnt + kCntErr, max_k, f->bits, scr, &res, st, true));
     f->sorted = res;
     GSR_CUDA(mark(ev, 4, st, capture));
     GSR_CUDA(launch_ranges(f->keys[res].as<uint64_t>(), f->vals[res].as<uint32_t>(), cnt, max_k, f->rec.as<GaussRec>(),

@@ -306,13 +306,13 @@ gs_status enqueue_sort(gs_server *S, Slot &sl)
     p += up(sizeof(uint32_t) * k1);
     sl.rec_sorted = reinterpret_cast<GaussRec *>(p);
     p += up(sizeof(GaussRec) * k1);
-    GSR_CUDA(launch_duplicate(static_cast<uint32_t *>(sl.ntiles.p), static_cast<uint4 *>(sl.bin.p),
-                              static_cast<uint32_t *>(sl.boffs.p), s.n, sl.cam.tile_shift, sl.cam.tiles_x, sl.keys[0],
-                              sl.vals[0], K, cnt, sl.stream));
     SortScratch scr;
     sort_scratch_carve(p, k1, &scr);
+    GSR_CUDA(launch_duplicate(static_cast<uint32_t *>(sl.ntiles.p), static_cast<uint4 *>(sl.bin.p),
+                              static_cast<uint32_t *>(sl.boffs.p), s.n, sl.cam.tile_shift, sl.cam.tiles_x, sl.keys[0],
+                              sl.vals[0], K, cnt, scr.hist, sort_passes(sl.bits), sl.stream));
     int res = 0;
-    GSR_CUDA(launch_sort(sl.keys, sl.vals, cnt, cnt + kCntErr, K, sl.bits, scr, &res, sl.stream));
+    GSR_CUDA(launch_sort(sl.keys, sl.vals, cnt, cnt + kCntErr, K, sl.bits, scr, &res, sl.stream, true));
     sl.sorted = res;
     GSR_CUDA(launch_ranges(sl.keys[res], sl.vals[res], cnt, K, static_cast<const GaussRec *>(sl.rec.p), sl.rec_sorted,
                            static_cast<uint2 *>(sl.ranges.p), sl.n_tiles, sl.stream));

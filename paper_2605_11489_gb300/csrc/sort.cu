@@ -87,7 +87,7 @@ __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_
     eb = pb + ib - b;
 }
 
-__global__ void __launch_bounds__(kThreads) k_sort_pass(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+__global__ void __launch_bounds__(kThreads, 3) k_sort_pass(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                         uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                         const uint32_t *__restrict__ counters, int shift,
                                                         const uint32_t *__restrict__ hist, uint32_t *status,
@@ -241,7 +241,7 @@ void sort_scratch_carve(void *base, int64_t capacity, SortScratch *s)
 }
 
 cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *counters, uint32_t *err_word,
-                        int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s)
+                        int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready)
 {
     const int passes = sort_passes(bits);
     *result = passes & 1;
@@ -256,15 +256,23 @@ cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *co
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
         e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
         if (e != cudaSuccess) return e;
+        // three partitions per SM need the largest shared-memory carveout
+        e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
-    e = cudaMemsetAsync(scr.hist, 0, sizeof(uint32_t) * (8 * kRadix + 8), s);
+    // histograms (unless ready) and partition tickets, then the lookback words
+    e = hist_ready ? cudaMemsetAsync(scr.part_ctr, 0, sizeof(uint32_t) * 8, s)
+                   : cudaMemsetAsync(scr.hist, 0, sizeof(uint32_t) * (8 * kRadix + 8), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(scr.status, 0, sizeof(uint32_t) * (size_t)passes * parts * kRadix, s);
     if (e != cudaSuccess) return e;
-    const int64_t hist_blocks = std::min<int64_t>((max_k + kThreads * 8 - 1) / (kThreads * 8), 152 * 8);
-    k_sort_hist<<<(unsigned)hist_blocks, kThreads, 0, s>>>(keys[0], counters, passes, scr.hist);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!hist_ready) {
+        const int64_t hist_blocks = std::min<int64_t>((max_k + kThreads * 8 - 1) / (kThreads * 8), 152 * 8);
+        k_sort_hist<<<(unsigned)hist_blocks, kThreads, 0, s>>>(keys[0], counters, passes, scr.hist);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     for (int p = 0; p < passes; ++p) {
         const int src = p & 1, dst = src ^ 1;
         k_sort_pass<<<(unsigned)parts, kThreads, kPassSmem, s>>>(keys[src], vals[src], keys[dst], vals[dst], counters,
