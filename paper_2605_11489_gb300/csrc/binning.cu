@@ -188,17 +188,26 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
     for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(t)], 1u)] = (uint32_t)t;
 }
 
-// Compositing work plan. A tile whose list is longer than `chunk` is split into
-// depth-contiguous chunks of `chunk` records; each chunk is a work item whose
-// per-pixel partial state goes to its own slot, and the split tile is merged
-// front to back afterwards. Items: all chunks first (slot order), then the
-// whole tiles, longest lists first. One CTA; tiles scanned in index order.
+// Compositing work plan. A tile whose list is longer than `head` is split into
+// depth-contiguous chunks: the first of `head` records, the others of `chunk`
+// (chunk_of / chunk_start / chunk_count); each chunk is a work item whose
+// per-pixel partial state goes to its own slot (a split tile's slots are
+// consecutive), and the split tile is finished front to back afterwards.
+// Items come in two waves, composited by two launches:
+//   wave A, items [0, n_tiles): the first chunk of every split tile (in split
+//     order), then the whole tiles, longest lists first;
+//   wave B, items [n_tiles, n_items): the later chunks, in slot order. They
+//     run after wave A, so they can leave out the pixels that already stopped
+//     in their tile's first chunk.
+// One CTA; tiles scanned in index order.
 //   items[i]       = (tile, start, end, slot | kWholeTile)
 //   split_tiles[s] = tile id of the s-th split tile, split_slot0[s] = its first slot
-//   counts         = (n_items, n_split, n_slots)
+//   slot_split[k]  = the split tile (index s) that slot k belongs to
+//   counts         = (n_items, n_split, n_slots, n_tiles = size of wave A)
 __global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges, int n_tiles, uint32_t chunk,
-                                               uint4 *__restrict__ items, uint32_t *__restrict__ split_tiles,
-                                               uint32_t *__restrict__ split_slot0, uint32_t *__restrict__ counts)
+                                               uint32_t head, uint4 *__restrict__ items, uint32_t *__restrict__ split_tiles,
+                                               uint32_t *__restrict__ split_slot0, uint32_t *__restrict__ slot_split,
+                                               uint32_t *__restrict__ counts)
 {
     __shared__ uint32_t s_a[1024], s_b[1024];
     __shared__ uint32_t s_cnt[33];
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges,
     auto nch = [&](int t) {
         const uint2 r = ranges[t];
         const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-        return len > chunk ? (len + chunk - 1) / chunk : 1u;
+        return chunk_count(len, head, chunk);
     };
     uint32_t my_split = 0, my_slots = 0;
     for (int t = t0; t < t1; ++t) {
@@ -243,11 +252,15 @@ __global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges,
         if (c > 1) {
             split_tiles[sp] = (uint32_t)t;
             split_slot0[sp] = slot;
-            ++sp;
+            items[sp] = make_uint4((uint32_t)t, r.x, r.x + head, slot);  // wave A: first chunk
+            const uint32_t later = (uint32_t)n_tiles + (slot - sp);       // wave B: chunks before ours
             for (uint32_t k = 0; k < c; ++k) {
-                const uint32_t s0 = r.x + k * chunk;
-                items[slot + k] = make_uint4((uint32_t)t, s0, min(r.y, s0 + chunk), slot + k);
+                slot_split[slot + k] = sp;
+                if (k == 0) continue;
+                const uint32_t s0 = r.x + chunk_start(k, head, chunk);
+                items[later + k - 1] = make_uint4((uint32_t)t, s0, min(r.y, s0 + chunk), slot + k);
             }
+            ++sp;
             slot += c;
         } else {
             const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
@@ -256,15 +269,16 @@ __global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges,
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t run = n_slots;
+        uint32_t run = n_split;
         for (int b = 0; b < 33; ++b) {
             const uint32_t c = s_cnt[b];
             s_cnt[b] = run;
             run += c;
         }
-        counts[0] = run;
+        counts[0] = (uint32_t)n_tiles + n_slots - n_split;
         counts[1] = n_split;
         counts[2] = n_slots;
+        counts[3] = (uint32_t)n_tiles;
     }
     __syncthreads();
     for (int t = t0; t < t1; ++t) {
@@ -278,14 +292,16 @@ __global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges,
 
 }  // namespace
 
-int64_t plan_max_slots(int64_t max_k, int chunk) { return 2 * (max_k / chunk) + 2; }
+// a split tile has > head >= chunk records and at most 2 + (len - head) / chunk slots
+int64_t plan_max_slots(int64_t max_k, int chunk) { return 3 * (max_k / chunk) + 2; }
 int64_t plan_max_items(int n_tiles, int64_t max_k, int chunk) { return n_tiles + plan_max_slots(max_k, chunk); }
 
-cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, uint4 *items, uint32_t *split_tiles,
-                        uint32_t *split_slot0, uint32_t *counts, cudaStream_t s)
+cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, int head, uint4 *items, uint32_t *split_tiles,
+                        uint32_t *split_slot0, uint32_t *slot_split, uint32_t *counts, cudaStream_t s)
 {
-    if (n_tiles <= 0) return cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 3, s);
-    k_plan<<<1, 1024, 0, s>>>(ranges, n_tiles, (uint32_t)chunk, items, split_tiles, split_slot0, counts);
+    if (n_tiles <= 0) return cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 4, s);
+    k_plan<<<1, 1024, 0, s>>>(ranges, n_tiles, (uint32_t)chunk, (uint32_t)head, items, split_tiles, split_slot0,
+                              slot_split, counts);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,8 @@
 // sorted) records with one TMA bulk copy per batch (cp.async.bulk, completion
 // counted on the warp's mbarrier) while the warp blends the current one; the
 // warp builds, with one ballot per 32 records, the mask of records whose
-// rectangle reaches its block and visits only those, in order. No barrier
+// rectangle reaches its block; from those, each lane keeps the ones whose
+// rectangle holds its own pixel and blends only these, in order. No barrier
 // spans warps: a warp whose pixels are all saturated stops on its own. The
 // tile's list is read once per warp from L2 (DRAM once). Waits are bounded.
 //
@@ -205,13 +206,22 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
                 hit = (hi >> 16) >= wy0 && (lo >> 16) <= wy1 && (hi & 0xFFFFu) >= wx0 && (lo & 0xFFFFu) <= wx1;
             }
             uint32_t m = __ballot_sync(0xffffffffu, hit);
-            if (s.done) m = 0u;
+            // this lane's own list: the hit records whose rectangle holds its
+            // pixel (a warp-uniform pass over the hits, one rect test each),
+            // then only those are blended, each lane at its own pace
+            uint32_t mine = 0u;
             while (m) {
-                const uint32_t k = (uint32_t)w * 32u + (uint32_t)(__ffs(m) - 1);
+                const int j = __ffs(m) - 1;
                 m &= m - 1u;
-                const float4 r2 = recs[k].r2;
-                if (!rect_contains(r2, upx, upy)) continue;
-                if (blend<GRAD, STATE, COUNT>(s, recs[k].r0, recs[k].r1, r2, pxc, pyc, pos_b + k)) {
+                const float4 r2 = recs[w * 32 + j].r2;
+                if (rect_contains(r2, upx, upy)) mine |= 1u << j;
+            }
+            if (s.done) mine = 0u;
+            while (mine) {
+                const uint32_t k = (uint32_t)w * 32u + (uint32_t)(__ffs(mine) - 1);
+                mine &= mine - 1u;
+                const GaussRec &R = recs[k];
+                if (blend<GRAD, STATE, COUNT>(s, R.r0, R.r1, R.r2, pxc, pyc, pos_b + k)) {
                     s.done = true;
                     s.stopped = true;
                     break;
@@ -319,8 +329,11 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t tile, s0, s1, slot = kWholeTile;
     if (a.items) {
-        if (blockIdx.x >= a.plan_counts[0]) return;
-        const uint4 it = a.items[blockIdx.x];
+        uint32_t idx = blockIdx.x;
+        if (a.wave == 1 && idx >= a.plan_counts[3]) return;
+        if (a.wave == 2) idx += a.plan_counts[3];
+        if (idx >= a.plan_counts[0]) return;
+        const uint4 it = a.items[idx];
         tile = it.x;
         s0 = it.y;
         s1 = it.z;
@@ -341,6 +354,14 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
     PixelAcc s;
     acc_init(s, inside);
     const uint32_t pos0 = s0 - a.ranges[tile].x;
+    // a later chunk (wave B) leaves out the pixels that stopped in the tile's
+    // first chunk: their stop is there, so no later partial state of theirs is read
+    bool skip = false;
+    if (slot != kWholeTile && pos0 >= (uint32_t)a.head) {
+        const uint32_t c = chunk_of(pos0, (uint32_t)a.head, (uint32_t)a.chunk);
+        skip = a.partial[(size_t)(slot - c) * kPartialVals * TILE * TILE + 14 * TILE * TILE + threadIdx.x] != 0.0f;
+        if (skip) s.done = true;
+    }
     const bool ok = warp_span<BATCH, GRAD, STATE, COUNT>(a, px, py, bx0, by0, s0, s1, pos0, ring, phase, s);
     if (!ok && (threadIdx.x & 31) == 0) atomicOr(a.err_word, kErrTmaTimeout);
     if (COUNT) {  // evaluated (inside a support rectangle) and blended pairs of this warp
@@ -357,7 +378,7 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
     }
     if (slot == kWholeTile) {
         if (inside) write_final<GRAD, STATE>(a, px, py, s);
-    } else {
+    } else if (!skip) {
         write_partial<TILE>(a.partial + (size_t)slot * kPartialVals * TILE * TILE, threadIdx.x, s);
     }
 }
@@ -408,11 +429,12 @@ __global__ void __launch_bounds__(TILE *TILE) k_rewalk(const CompositeArgs a)
     const uint32_t n_slots = a.plan_counts[2];
     const uint32_t chunk = (uint32_t)a.chunk;
     for (uint32_t b = blockIdx.x; b < n_slots; b += gridDim.x) {
-        const uint4 it = a.items[b];  // split chunks occupy items [0, n_slots), slot == index
-        const uint32_t tile = it.x;
+        const uint32_t sp = a.slot_split[b];
+        const uint32_t tile = a.split_tiles[sp], first = a.split_slot0[sp];
         const uint2 r = a.ranges[tile];
-        const uint32_t c = (it.y - r.x) / chunk;
-        const float *slot0 = a.partial + (size_t)(b - c) * kPartialVals * NT;
+        const uint32_t c = b - first;
+        const uint32_t k0 = r.x + chunk_start(c, (uint32_t)a.head, chunk);
+        const float *slot0 = a.partial + (size_t)first * kPartialVals * NT;
         const int tx = (int)(tile % (uint32_t)a.tiles_x), ty = (int)(tile / (uint32_t)a.tiles_x);
         int px, py, bx0, by0;
         tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);
@@ -421,6 +443,13 @@ __global__ void __launch_bounds__(TILE *TILE) k_rewalk(const CompositeArgs a)
         if (!__any_sync(0xffffffffu, walk)) continue;
         PixelAcc P;
         acc_init(P, walk);
+        if (c == 0) {  // the first chunk started from the identity: its partial state is exact
+            if (walk) {
+                read_partial<TILE>(slot0, threadIdx.x, P);
+                write_final<GRAD, STATE>(a, px, py, P);
+            }
+            continue;
+        }
         if (walk && c > 0) {  // exact prefix state; the next chunk's loads overlap this fold
             PixelAcc Qn;
             read_partial<TILE>(slot0, threadIdx.x, Qn);
@@ -430,7 +459,7 @@ __global__ void __launch_bounds__(TILE *TILE) k_rewalk(const CompositeArgs a)
                 compose<GRAD, STATE>(P, Q);
             }
         }
-        ok &= warp_span<BATCH, GRAD, STATE>(a, px, py, bx0, by0, it.y, r.y, it.y - r.x, ring, phase, P);
+        ok &= warp_span<BATCH, GRAD, STATE>(a, px, py, bx0, by0, k0, r.y, k0 - r.x, ring, phase, P);
         if (walk) write_final<GRAD, STATE>(a, px, py, P);
     }
     if (!ok && (threadIdx.x & 31) == 0) atomicOr(a.err_word, kErrTmaTimeout);
@@ -449,7 +478,7 @@ __global__ void __launch_bounds__(TILE *TILE) k_finish(const CompositeArgs a)
         const uint32_t tile = a.split_tiles[b];
         const float *slot0 = a.partial + (size_t)a.split_slot0[b] * kPartialVals * NT;
         const uint2 r = a.ranges[tile];
-        const uint32_t nch = (r.y - r.x + chunk - 1) / chunk;
+        const uint32_t nch = chunk_count(r.y - r.x, (uint32_t)a.head, chunk);
         const int tx = (int)(tile % (uint32_t)a.tiles_x), ty = (int)(tile / (uint32_t)a.tiles_x);
         int px, py, bx0, by0;
         tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);
@@ -558,6 +587,7 @@ cudaError_t launch_tb(const CompositeArgs &a, int64_t max_items, cudaStream_t s)
     } else {
         const unsigned nb = a.items ? (unsigned)max_items : (unsigned)(a.tiles_x * a.tiles_y);
         if (nb == 0) return cudaSuccess;
+        if (a.items && a.wave == 0) return cudaErrorInvalidValue;  // a plan runs as wave A, then wave B
         const bool grad = a.dcdx || a.dcdy;
         const bool state = a.final_T != nullptr;
         if (a.pair_counts && !state)  // diagnostic pair census (GS_COUNT_PAIRS)
@@ -635,14 +665,24 @@ bool composite_supported(int tile, int batch)
     return bytes <= (size_t)kMaxSmem;
 }
 
-cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, int64_t max_items, cudaStream_t s)
+cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, int64_t max_a, int64_t max_b,
+                             cudaStream_t s)
 {
     if (a.tiles_x == 0 || a.tiles_y == 0) return cudaSuccess;
-    switch (tile) {
-    case 8: return launch_t<8>(a, batch, max_items, s);
-    case 16: return launch_t<16>(a, batch, max_items, s);
-    default: return launch_t<32>(a, batch, max_items, s);
-    }
+    auto one = [&](const CompositeArgs &w, int64_t n) {
+        switch (tile) {
+        case 8: return launch_t<8>(w, batch, n, s);
+        case 16: return launch_t<16>(w, batch, n, s);
+        default: return launch_t<32>(w, batch, n, s);
+        }
+    };
+    if (!a.items) return one(a, 0);
+    CompositeArgs w = a;
+    w.wave = 1;
+    cudaError_t e = one(w, max_a);
+    if (e != cudaSuccess) return e;
+    w.wave = 2;
+    return max_b > 0 ? one(w, max_b) : cudaSuccess;
 }
 
 cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, int64_t max_slots, cudaStream_t s)

@@ -139,25 +139,49 @@ struct CompositeArgs {
     const uint32_t *tile_order;  // tiles by decreasing list length (nullable = row-major)
     // work plan (nullable: then one CTA per whole tile, in tile_order)
     const uint4 *items;            // (tile, start, end, slot | kWholeTile)
-    const uint32_t *plan_counts;   // (n_items, n_split, n_slots)
+    const uint32_t *plan_counts;   // (n_items, n_split, n_slots, size of wave A)
     const uint32_t *split_tiles;   // split tile ids
     const uint32_t *split_slot0;   // first slot of each split tile
+    const uint32_t *slot_split;    // split tile index of each slot
+    int32_t wave;                  // items launched: 0 all, 1 wave A, 2 wave B
     float *partial;                // [slot][16][TILE*TILE] per-pixel partial state of chunks
-    int32_t chunk;                 // records per chunk of a split tile
+    int32_t chunk;                 // records per later chunk of a split tile
+    int32_t head;                  // records in a split tile's first chunk (kHeadChunks * chunk)
     unsigned long long *pair_counts;  // (evaluated, blended) pairs: the GS_COUNT_PAIRS census (nullable)
 };
 constexpr uint32_t kWholeTile = 0xFFFFFFFFu;
+// A tile list longer than head = kHeadChunks * chunk records is split into a
+// first chunk of `head` records and later chunks of `chunk` records. Most
+// pixels that saturate do so within the first records of a long list, so a
+// long first chunk lets the later chunks leave those pixels out.
+constexpr int kHeadChunks = 4;
+// chunk index of list position `pos`, first position of chunk c, chunks of a list of `len`
+__host__ __device__ inline uint32_t chunk_of(uint32_t pos, uint32_t head, uint32_t chunk)
+{
+    return pos < head ? 0u : 1u + (pos - head) / chunk;
+}
+__host__ __device__ inline uint32_t chunk_start(uint32_t c, uint32_t head, uint32_t chunk)
+{
+    return c == 0 ? 0u : head + (c - 1) * chunk;
+}
+__host__ __device__ inline uint32_t chunk_count(uint32_t len, uint32_t head, uint32_t chunk)
+{
+    return len > head ? 1u + (len - head + chunk - 1) / chunk : 1u;
+}
 int64_t plan_max_slots(int64_t max_k, int chunk);
 int64_t plan_max_items(int n_tiles, int64_t max_k, int chunk);
-cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, uint4 *items, uint32_t *split_tiles,
-                        uint32_t *split_slot0, uint32_t *counts, cudaStream_t s);
+cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, int head, uint4 *items, uint32_t *split_tiles,
+                        uint32_t *split_slot0, uint32_t *slot_split, uint32_t *counts, cudaStream_t s);
 // merge of split tiles' chunks (after launch_composite with a plan)
 cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, int64_t max_slots, cudaStream_t s);
 // order tiles by decreasing list length (power-of-two buckets)
 cudaError_t launch_tile_order(const uint2 *ranges, int n_tiles, uint32_t *order, cudaStream_t s);
 bool composite_supported(int tile, int batch);
 // grid: one CTA per work item (bounded by max_items when a plan is given), else per tile
-cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, int64_t max_items, cudaStream_t s);
+// With a work plan (a.items): wave A over up to `max_a` items, then wave B over
+// up to `max_b`; without one: one CTA per tile.
+cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, int64_t max_a, int64_t max_b,
+                             cudaStream_t s);
 
 // serving: tiles of several requests from one (request, tile) work list
 struct ServeItem {  // one request's compositing description (device copy)

@@ -80,7 +80,7 @@ struct Frame {
     Buf rec, bin, ntiles, bsums, boffs;
     Buf keys[2], vals[2], sort_scr, rec_sorted;
     Buf ranges, order;
-    Buf items, split_tiles, split_slot0, plan_counts, partial;  // compositing work plan
+    Buf items, split_tiles, split_slot0, slot_split, plan_counts, partial;  // compositing work plan
     int chunk = 2048;
     int64_t max_items = 0, max_split = 0, max_slots = 0;
     Buf fT, fTx, fTy, ncontrib;
@@ -309,7 +309,7 @@ gs_status frame_setup(Frame *f, const gs_scene *s, const gs_camera *c, const gs_
     f->H = c->height;
     f->tile = tile;
     f->batch = batch;
-    if (chunk < 64 || chunk > (1 << 24)) return fail(GS_ERR_INVALID_ARG, "chunk must be 0 or 64..2^24");
+    if (chunk < 16 || chunk > (1 << 24)) return fail(GS_ERR_INVALID_ARG, "chunk must be 0 or 16..2^24");
     f->chunk = chunk;
     f->deg = s->sh_degree;
     for (int k = 0; k < 3; ++k) f->bg[k] = o->bg[k];
@@ -352,16 +352,17 @@ gs_status frame_keys(Frame *f, int64_t cap)
 }
 
 // Work-plan buffers for up to `cap` instances at the frame's tile size and
-// tile count: every split tile has > chunk records, so slots <= 2 cap / chunk + 2.
+// tile count (see plan_max_slots for the slot bound).
 gs_status frame_plan(Frame *f, int64_t cap)
 {
     const int64_t slots = plan_max_slots(cap, f->chunk);
     f->max_slots = slots;
     f->max_items = plan_max_items(f->n_tiles, cap, f->chunk);
-    f->max_split = std::min<int64_t>(f->n_tiles, cap / f->chunk + 1);
+    f->max_split = std::min<int64_t>(f->n_tiles, cap / ((int64_t)kHeadChunks * f->chunk) + 1);
     GSR_CUDA(f->items.ensure(sizeof(uint4) * (size_t)f->max_items));
     GSR_CUDA(f->split_tiles.ensure(sizeof(uint32_t) * (size_t)f->max_split));
     GSR_CUDA(f->split_slot0.ensure(sizeof(uint32_t) * (size_t)f->max_split));
+    GSR_CUDA(f->slot_split.ensure(sizeof(uint32_t) * (size_t)slots));
     GSR_CUDA(f->plan_counts.ensure(sizeof(uint32_t) * 4));
     GSR_CUDA(f->partial.ensure(sizeof(float) * 16 * (size_t)f->tile * f->tile * (size_t)slots));
     return GS_OK;
@@ -415,8 +416,10 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
     c.plan_counts = f->plan_counts.as<uint32_t>();
     c.split_tiles = f->split_tiles.as<uint32_t>();
     c.split_slot0 = f->split_slot0.as<uint32_t>();
+    c.slot_split = f->slot_split.as<uint32_t>();
     c.partial = f->partial.as<float>();
     c.chunk = f->chunk;
+    c.head = kHeadChunks * f->chunk;
     if (f->count_pairs) c.pair_counts = reinterpret_cast<unsigned long long *>(f->counters.as<uint32_t>() + kCntPairs);
     return c;
 }
@@ -447,12 +450,13 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     GSR_CUDA(mark(ev, 4, st, capture));
     GSR_CUDA(launch_ranges(f->keys[res].as<uint64_t>(), f->vals[res].as<uint32_t>(), cnt, max_k, f->rec.as<GaussRec>(),
                            f->rec_sorted.as<GaussRec>(), f->ranges.as<uint2>(), f->n_tiles, st));
-    GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->chunk, f->items.as<uint4>(),
-                         f->split_tiles.as<uint32_t>(), f->split_slot0.as<uint32_t>(), f->plan_counts.as<uint32_t>(),
+    GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->chunk, kHeadChunks * f->chunk, f->items.as<uint4>(),
+                         f->split_tiles.as<uint32_t>(), f->split_slot0.as<uint32_t>(), f->slot_split.as<uint32_t>(),
+                         f->plan_counts.as<uint32_t>(),
                          st));
     GSR_CUDA(mark(ev, 5, st, capture));
     const CompositeArgs ca = comp_args(f, out);
-    GSR_CUDA(launch_composite(ca, f->tile, f->batch, f->max_items, st));
+    GSR_CUDA(launch_composite(ca, f->tile, f->batch, f->n_tiles, f->max_slots, st));
     GSR_CUDA(launch_merge(ca, f->tile, f->max_split, f->max_slots, st));
     GSR_CUDA(mark(ev, 6, st, capture));
     return GS_OK;
@@ -931,7 +935,7 @@ gs_status gs_autotune(gs_context *ctx, const gs_scene *scene, const gs_camera *c
     cudaEvent_t e0, e1;
     GSR_CUDA(cudaEventCreate(&e0));
     GSR_CUDA(cudaEventCreate(&e1));
-    const int tiles[3] = {8, 16, 32}, batches[4] = {32, 64, 128, 256}, chunks[3] = {512, 2048, 8192};
+    const int tiles[3] = {8, 16, 32}, batches[4] = {32, 64, 128, 256}, chunks[3] = {256, 512, 2048};
     float best = 1e30f;
     int bt = kDefaultTile, bb = kDefaultBatch, bc = kDefaultChunk;
     for (int t : tiles)

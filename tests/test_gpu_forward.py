@@ -144,11 +144,14 @@ def _dense_scene(n, seed, opaque=False):
     return s
 
 
+@pytest.mark.parametrize("chunk", [16, 64])
 @pytest.mark.parametrize("opaque", [False, True])
-def test_split_tiles_exact_merge(env, opaque):
-    """Chunked compositing of long tile lists (chunk = 64 records) against the
-    unsplit pass and the oracle; with opaque Gaussians the T < 1e-4 stop falls
-    inside chunks and those chunks are re-walked from the exact prefix state."""
+def test_split_tiles_exact_merge(env, opaque, chunk):
+    """Chunked compositing of long tile lists (a first chunk of 4 * chunk
+    records, later chunks of `chunk`) against the unsplit pass and the oracle;
+    with opaque Gaussians the T < 1e-4 stop falls inside first and later
+    chunks: later chunks leave out pixels that stopped in the first, and a
+    later chunk holding a stop is re-walked from the exact prefix state."""
     api, O, ctx = env
     sc = _dense_scene(3000, 21 + opaque, opaque)
     cam = synth.tiny_camera(128, 96)
@@ -158,9 +161,9 @@ def test_split_tiles_exact_merge(env, opaque):
         assert (ref["final_T"] < 2e-4).mean() > 0.02  # the stop is reached in many pixels
     for tile in (8, 16):
         whole = _render(api, ctx, sc, cam, bg=bg, tile=tile, chunk=1 << 24)
-        split, st = _render(api, ctx, sc, cam, bg=bg, tile=tile, chunk=64, state=True)
+        split, st = _render(api, ctx, sc, cam, bg=bg, tile=tile, chunk=chunk, state=True)
         v = st.view()
-        assert (v["ranges"][:, 1] - v["ranges"][:, 0]).max() > 4 * 64  # tiles really are split
+        assert (v["ranges"][:, 1] - v["ranges"][:, 0]).max() > 8 * chunk  # tiles really are split
         st.free()
         check_render(whole, ref)
         check_render(split, ref)
@@ -179,14 +182,15 @@ def test_split_tiles_backward_state(env):
     scene = api.Scene.from_arrays(sc)
     gi = {k: torch.from_numpy(v).cuda() for k, v in synth.upstream_grads(96, 64, 2).items()}
     grads = []
-    for chunk in (1 << 24, 64):
+    for chunk in (1 << 24, 64, 16):
         out, st = ctx.forward(scene, cam, state=True, chunk=chunk)
         g = ctx.backward(st, scene, gi)
         st.free()
         grads.append([t.clone() for t in g])
-    for a, b in zip(*grads):
-        scale = a.abs().max().item() + 1e-12
-        assert (a - b).abs().max().item() <= 1e-3 * scale
+    for split in grads[1:]:
+        for a, b in zip(grads[0], split):
+            scale = a.abs().max().item() + 1e-12
+            assert (a - b).abs().max().item() <= 1e-3 * scale
 
 
 def test_single_gaussian_closed_form_on_gpu(env):
