@@ -67,6 +67,23 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), n
 
 
+def slowest_rank(seconds_or_ms, world, device="cpu"):
+    """Max over ranks of a per-rank duration (the job's time); identity at world == 1."""
+    if world <= 1:
+        return float(seconds_or_ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(seconds_or_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(pixels_per_rank, world, duration_s):
+    """Whole-job Mpix/s: the pixels all ranks rendered over the slowest rank's time."""
+    return pixels_per_rank * world / duration_s / 1e6
+
+
 def start_clock_sampler(path, gpu_index):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -280,16 +297,17 @@ def algorithmic(stage, w, deg, n, K_avg, V_avg, passes, pixels, pairs):
     sh_bytes = 12 * (deg + 1) ** 2
     if stage == "project":
         return "hbm", 12.0 * n + (12 + 16 + 4 + sh_bytes + 48) * V_avg
-    if stage == "sort":
-        return "hbm", K_avg * (8 + 24 * passes)
+    if stage == "sort":  # every pass reads and writes each 8-byte key and 4-byte value
+        return "hbm", K_avg * 24 * passes
     if stage == "duplicate":
         return "hbm", 16.0 * V_avg + 12.0 * K_avg + 4.0 * n
-    if stage == "ranges":
-        return "hbm", 8.0 * K_avg
+    if stage == "ranges":  # key + value read, 48-byte record gathered and written, per instance
+        return "hbm", (8.0 + 4.0 + 48.0 + 48.0) * K_avg
     if stage == "scan":
         return "hbm", 8.0 * n / 1024
-    # composite: FP32 FLOP of the per-pair work, FMA = 2 ("K6"): 16 per evaluated
-    # pair (alpha), 38 more per blended pair (Eq. 2-4 updates), on the census' counts
+    # composite: FP32 FLOP of the per-pair work, an FMA counted as 2: 16 per evaluated pair
+    # (alpha: offset, quadratic form, exponent, opacity), 38 more per blended pair (the
+    # Eq. 2-4 updates of colour, depth, T and the x/y gradient terms), on the census' counts
     p_eval, p_blend = pairs
     return "alu", FLOP_PER_EVAL * p_eval + FLOP_PER_BLEND * p_blend
 
@@ -408,12 +426,8 @@ def main():
         smi_f.close()
     clocks = read_clocks(clk_path)
     st = graph.stats(reset=True, stream=stream)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    pixels = W * H * args.steps * world
-    value = pixels / (ms * 1e-3) / 1e6
+    ms = slowest_rank(ms, world, "cuda")
+    value = job_throughput(W * H * args.steps, world, ms * 1e-3)
 
     # per-stage times from events recorded inside the timed replays
     stage_ms = st["stage_ms"]
@@ -458,11 +472,8 @@ def main():
         for i in range(e2e_steps):
             ctx.forward_to_host(scene, cams[i % len(cams)], host, tile=tile, batch=batch, stream=stream)
         dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": W * H * e2e_steps * world / dt / 1e6, "unit": "Mpix/s",
+        dt = slowest_rank(dt, world, "cuda")
+        e2e = {"value": job_throughput(W * H * e2e_steps, world, dt), "unit": "Mpix/s",
                "h2d_bytes_per_step": GS_CAMERA_BYTES, "d2h_bytes_per_step": 11 * W * H * 4,
                "path": "gs_render_forward_to_host (plain forward + D2H of rgb, dC/dx, dC/dy, depth, alpha)"}
 
@@ -483,7 +494,9 @@ def main():
                 "stage_ms": stage_ms, "instances_per_frame": K_avg, "visible_per_frame": V_avg,
                 "roofline": roof, "stage_roofline": stage_roofline, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu,
-                "gpu_launches": args.steps * (6 + passes)}
+                # kernels per frame: projection, block scan, duplication, `passes` sort
+                # passes, ranges, plan, two compositing waves, re-walk, finish
+                "gpu_launches": args.steps * (9 + passes)}
         print(json.dumps(line), flush=True)
     graph.close()
     ctx.close()

@@ -267,6 +267,30 @@ def test_brute_equals_binned_bitwise(oracle_lib):
             assert np.array_equal(a[k], b[k]), k
 
 
+def test_sampled_pixels_and_bands_equal_the_brute_force_image(oracle_lib):
+    """render_pixels (each sample scans every visible Gaussian, used for the
+    full-size samples) and render_band (the timed CPU baseline's unit) give the
+    brute-force image's values at those pixels / rows, bit for bit."""
+    O = oracle_lib
+    sc = synth.tiny_scene(2048, 7)
+    cam = synth.jittered_tiny_cameras(3, 7)[2]
+    bg = (0.1, 0.3, 0.2)
+    full = O.render(sc, cam, bg=bg, mode="brute")
+    rng = np.random.default_rng(1)
+    px = rng.integers(0, cam.width, 300)
+    py = rng.integers(0, cam.height, 300)
+    s = O.render_pixels(sc, cam, px, py, bg=bg)
+    for k in OUT_KEYS:
+        ref = full[k][:, py, px].T if full[k].ndim == 3 else full[k][py, px]
+        assert np.array_equal(s[k], ref), k
+    assert np.array_equal(s["amb"], full["amb"][py, px])
+    y0, y1 = 37, 61
+    band = O.render_band(sc, cam, y0, y1, bg=bg)
+    for k in OUT_KEYS:
+        assert np.array_equal(band[k][..., y0:y1, :], full[k][..., y0:y1, :]), k
+        assert not band[k][..., :y0, :].any() and not band[k][..., y1:, :].any(), k
+
+
 def test_blend_weights_sum_to_alpha(oracle_lib):
     """With every colour 1 and bg 0, Eq. 2 gives I = sum a_i T_i = 1 - T_final."""
     O = oracle_lib
