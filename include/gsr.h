@@ -93,9 +93,12 @@ typedef struct {
     int32_t batch;                /* Gaussians per shared-memory batch: 32/64/128/256; 0 = default */
     float bg[3];                  /* background colour */
     uint32_t flags;               /* GS_EMIT_* */
-    int32_t chunk;                /* a tile list longer than this is split into chunks composited in
-                                     parallel and merged exactly; multiple of 256, 0 = default 2048 */
-    int32_t _reserved;
+    int32_t chunk;                /* records per later chunk of a split tile list: a list longer than
+                                     `head` is composited as a first chunk of `head` records, then
+                                     chunks of `chunk` records, in parallel, and merged exactly
+                                     (product rule of Eq. 2-4, stop rule re-applied where it falls
+                                     inside a chunk); 16..2^24, 0 = autotuned/default 512 */
+    int32_t head;                 /* records in a split list's first chunk, >= chunk; 0 = 4 * chunk */
 } gs_render_opts;
 
 /* Caller-owned device outputs; a NULL plane is not written (and, for dcdx and
@@ -215,7 +218,7 @@ gs_status gs_graph_destroy(gs_graph *graph);
 /* ---------------------------------------------------------------- autotuner
  * Times the forward for every tile in {8, 16, 32}, batch in {32, 64, 128, 256}
  * (pairs whose per-warp staging rings fit shared memory) and chunk in
- * {512, 2048, 8192} (CUDA events, `iters` frames each, after one warm-up) and
+ * {256, 512, 2048} (CUDA events, `iters` frames each, after one warm-up) and
  * records the fastest in the context's cache, keyed by (W, H, N bucket, SH
  * degree); later calls with tile / batch / chunk = 0 use it. Synchronous.
  * Any output pointer may be NULL. */

@@ -52,7 +52,7 @@ class GsCamera(C.Structure):
 
 class GsRenderOpts(C.Structure):
     _fields_ = [("tile", C.c_int32), ("batch", C.c_int32), ("bg", C.c_float * 3), ("flags", C.c_uint32),
-                ("chunk", C.c_int32), ("_reserved", C.c_int32)]
+                ("chunk", C.c_int32), ("head", C.c_int32)]
 
 
 class GsOutputs(C.Structure):

@@ -82,9 +82,10 @@ def camera_struct(cam) -> GsCamera:
     return c
 
 
-def opts_struct(tile=0, batch=0, bg=(0.0, 0.0, 0.0), state=False, timed=False, chunk=0, count=False) -> GsRenderOpts:
+def opts_struct(tile=0, batch=0, bg=(0.0, 0.0, 0.0), state=False, timed=False, chunk=0, count=False,
+                head=0) -> GsRenderOpts:
     o = GsRenderOpts()
-    o.tile, o.batch, o.chunk = int(tile), int(batch), int(chunk)
+    o.tile, o.batch, o.chunk, o.head = int(tile), int(batch), int(chunk), int(head)
     for k in range(3):
         o.bg[k] = float(bg[k])
     o.flags = (abi.GS_EMIT_BWD_STATE if state else 0) | (abi.GS_TIME_STAGES if timed else 0) | \
@@ -212,12 +213,12 @@ class Context:
             pass
 
     def forward(self, scene: Scene, cam, tile=0, batch=0, bg=(0.0, 0.0, 0.0), keys=OUTPUT_KEYS, out=None,
-                state=False, timed=False, stream=None, chunk=0, count=False):
+                state=False, timed=False, stream=None, chunk=0, count=False, head=0):
         """Render; returns the output dict (and a State if state=True)."""
         if out is None:
             out = alloc_outputs(cam.width, cam.height, keys)
         sc, cm = scene.struct(), camera_struct(cam)
-        op, ou = opts_struct(tile, batch, bg, state, timed, chunk, count), outputs_struct(out)
+        op, ou = opts_struct(tile, batch, bg, state, timed, chunk, count, head), outputs_struct(out)
         hs = C.c_void_p()
         check(abi.lib().gs_render_forward(self.h, C.byref(sc), C.byref(cm), C.byref(op), C.byref(ou),
                                           C.byref(hs) if state else None, _stream_ptr(stream)))
@@ -252,8 +253,8 @@ class Context:
         return _stats_dict(st)
 
     def graph(self, scene: Scene, cam, out: dict, capacity=0, tile=0, batch=0, bg=(0.0, 0.0, 0.0), timed=False,
-              stream=None, chunk=0):
-        return Graph(self, scene, cam, out, capacity, tile, batch, bg, stream, timed, chunk)
+              stream=None, chunk=0, head=0):
+        return Graph(self, scene, cam, out, capacity, tile, batch, bg, stream, timed, chunk, head)
 
     def autotune(self, scene: Scene, cam, out: dict, iters=3, stream=None):
         """Returns (tile, batch, chunk, ms) of the fastest configuration, now cached."""
@@ -268,10 +269,10 @@ class Graph:
     """Captured whole-frame forward replayed with a new camera per frame."""
 
     def __init__(self, ctx: Context, scene: Scene, cam, out: dict, capacity, tile, batch, bg, stream, timed=False,
-                 chunk=0):
+                 chunk=0, head=0):
         self.ctx, self.scene, self.out = ctx, scene, out  # keep the buffers alive
         sc, cm = scene.struct(), camera_struct(cam)
-        op, ou = opts_struct(tile, batch, bg, timed=timed, chunk=chunk), outputs_struct(out)
+        op, ou = opts_struct(tile, batch, bg, timed=timed, chunk=chunk, head=head), outputs_struct(out)
         h = C.c_void_p()
         check(abi.lib().gs_graph_create(ctx.h, C.byref(sc), C.byref(cm), C.byref(op), C.byref(ou), int(capacity),
                                         _stream_ptr(stream), C.byref(h)))

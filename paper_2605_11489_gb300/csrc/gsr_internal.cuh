@@ -146,14 +146,14 @@ struct CompositeArgs {
     int32_t wave;                  // items launched: 0 all, 1 wave A, 2 wave B
     float *partial;                // [slot][16][TILE*TILE] per-pixel partial state of chunks
     int32_t chunk;                 // records per later chunk of a split tile
-    int32_t head;                  // records in a split tile's first chunk (kHeadChunks * chunk)
+    int32_t head;                  // records in a split tile's first chunk (>= chunk)
     unsigned long long *pair_counts;  // (evaluated, blended) pairs: the GS_COUNT_PAIRS census (nullable)
 };
 constexpr uint32_t kWholeTile = 0xFFFFFFFFu;
-// A tile list longer than head = kHeadChunks * chunk records is split into a
-// first chunk of `head` records and later chunks of `chunk` records. Most
-// pixels that saturate do so within the first records of a long list, so a
-// long first chunk lets the later chunks leave those pixels out.
+// A tile list longer than `head` records (default kHeadChunks * chunk) is split
+// into a first chunk of `head` records and later chunks of `chunk` records.
+// Most pixels that saturate do so within the first records of a long list, so
+// a long first chunk lets the later chunks leave those pixels out.
 constexpr int kHeadChunks = 4;
 // chunk index of list position `pos`, first position of chunk c, chunks of a list of `len`
 __host__ __device__ inline uint32_t chunk_of(uint32_t pos, uint32_t head, uint32_t chunk)

@@ -82,6 +82,7 @@ struct Frame {
     Buf ranges, order;
     Buf items, split_tiles, split_slot0, slot_split, plan_counts, partial;  // compositing work plan
     int chunk = 2048;
+    int head = 4 * 2048;  // records in a split list's first chunk
     int64_t max_items = 0, max_split = 0, max_slots = 0;
     Buf fT, fTx, fTy, ncontrib;
     Buf counters;
@@ -310,7 +311,10 @@ gs_status frame_setup(Frame *f, const gs_scene *s, const gs_camera *c, const gs_
     f->tile = tile;
     f->batch = batch;
     if (chunk < 16 || chunk > (1 << 24)) return fail(GS_ERR_INVALID_ARG, "chunk must be 0 or 16..2^24");
+    const int64_t head = o->head ? (int64_t)o->head : (int64_t)kHeadChunks * chunk;
+    if (head < chunk || head > (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "head must be 0 or chunk..2^30");
     f->chunk = chunk;
+    f->head = (int)head;
     f->deg = s->sh_degree;
     for (int k = 0; k < 3; ++k) f->bg[k] = o->bg[k];
     f->cam = make_cam(*c, tile);
@@ -358,7 +362,7 @@ gs_status frame_plan(Frame *f, int64_t cap)
     const int64_t slots = plan_max_slots(cap, f->chunk);
     f->max_slots = slots;
     f->max_items = plan_max_items(f->n_tiles, cap, f->chunk);
-    f->max_split = std::min<int64_t>(f->n_tiles, cap / ((int64_t)kHeadChunks * f->chunk) + 1);
+    f->max_split = std::min<int64_t>(f->n_tiles, cap / f->head + 1);
     GSR_CUDA(f->items.ensure(sizeof(uint4) * (size_t)f->max_items));
     GSR_CUDA(f->split_tiles.ensure(sizeof(uint32_t) * (size_t)f->max_split));
     GSR_CUDA(f->split_slot0.ensure(sizeof(uint32_t) * (size_t)f->max_split));
@@ -419,7 +423,7 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
     c.slot_split = f->slot_split.as<uint32_t>();
     c.partial = f->partial.as<float>();
     c.chunk = f->chunk;
-    c.head = kHeadChunks * f->chunk;
+    c.head = f->head;
     if (f->count_pairs) c.pair_counts = reinterpret_cast<unsigned long long *>(f->counters.as<uint32_t>() + kCntPairs);
     return c;
 }
@@ -450,7 +454,7 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     GSR_CUDA(mark(ev, 4, st, capture));
     GSR_CUDA(launch_ranges(f->keys[res].as<uint64_t>(), f->vals[res].as<uint32_t>(), cnt, max_k, f->rec.as<GaussRec>(),
                            f->rec_sorted.as<GaussRec>(), f->ranges.as<uint2>(), f->n_tiles, st));
-    GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->chunk, kHeadChunks * f->chunk, f->items.as<uint4>(),
+    GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->chunk, f->head, f->items.as<uint4>(),
                          f->split_tiles.as<uint32_t>(), f->split_slot0.as<uint32_t>(), f->slot_split.as<uint32_t>(),
                          f->plan_counts.as<uint32_t>(),
                          st));
