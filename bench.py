@@ -494,9 +494,9 @@ def main():
                 "stage_ms": stage_ms, "instances_per_frame": K_avg, "visible_per_frame": V_avg,
                 "roofline": roof, "stage_roofline": stage_roofline, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu,
-                # kernels per frame: projection, block scan, duplication, `passes` sort
+                # kernels per frame: projection, colour, block scan, duplication, `passes` sort
                 # passes, ranges, plan, two compositing waves, re-walk, finish
-                "gpu_launches": args.steps * (9 + passes)}
+                "gpu_launches": args.steps * (10 + passes)}
         print(json.dumps(line), flush=True)
     graph.close()
     ctx.close()

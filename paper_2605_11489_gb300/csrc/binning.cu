@@ -199,81 +199,77 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
 //   wave B, items [n_tiles, n_items): the later chunks, in slot order. They
 //     run after wave A, so they can leave out the pixels that already stopped
 //     in their tile's first chunk.
-// One CTA; tiles scanned in index order.
 //   items[i]       = (tile, start, end, slot | kWholeTile)
 //   split_tiles[s] = tile id of the s-th split tile, split_slot0[s] = its first slot
 //   slot_split[k]  = the split tile (index s) that slot k belongs to
 //   counts         = (n_items, n_split, n_slots, n_tiles = size of wave A)
+// One CTA; each warp takes 32 consecutive tiles at a time. A split tile gets
+// its split index and its slots from one packed counter, (splits << 32) +
+// slots, so that both come in the same order and the later chunks before a
+// tile's own number slot - split index. Whole tiles are bucketed by
+// floor(log2(length)), with one atomic per bucket and warp.
 __global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges, int n_tiles, uint32_t chunk,
-                                               uint32_t head, uint4 *__restrict__ items, uint32_t *__restrict__ split_tiles,
+                                               uint32_t head, uint4 *__restrict__ items,
+                                               uint32_t *__restrict__ split_tiles,
                                                uint32_t *__restrict__ split_slot0, uint32_t *__restrict__ slot_split,
                                                uint32_t *__restrict__ counts)
 {
-    __shared__ uint32_t s_a[1024], s_b[1024];
-    __shared__ uint32_t s_cnt[33];
-    __shared__ uint32_t s_tot[2];
-    const int per = (n_tiles + 1023) / 1024;
-    const int t0 = threadIdx.x * per, t1 = min(n_tiles, t0 + per);
-    auto nch = [&](int t) {
-        const uint2 r = ranges[t];
+    __shared__ unsigned long long s_alloc;  // (split tiles << 32) | slots handed out so far
+    __shared__ uint32_t s_bucket[33];       // whole tiles per bucket, then next free item per bucket
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    if (threadIdx.x == 0) s_alloc = 0ull;
+    if (threadIdx.x < 33) s_bucket[threadIdx.x] = 0u;
+    __syncthreads();
+    auto bucket_of = [](uint32_t len) { return len == 0 ? 32u : (uint32_t)__clz(len); };  // longer -> smaller
+
+    // pass 1: split tiles are placed; whole tiles are counted per bucket
+    for (int base = warp * 32; base < n_tiles; base += 1024) {
+        const int t = base + lane;
+        uint2 r = make_uint2(0u, 0u);
+        if (t < n_tiles) r = ranges[t];
         const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-        return chunk_count(len, head, chunk);
-    };
-    uint32_t my_split = 0, my_slots = 0;
-    for (int t = t0; t < t1; ++t) {
-        const uint32_t c = nch(t);
-        if (c > 1) {
-            ++my_split;
-            my_slots += c;
+        const uint32_t c = t < n_tiles ? chunk_count(len, head, chunk) : 0u;
+        const bool split = c > 1, whole = c == 1;
+        // split: exclusive prefix of slot counts over the warp's split lanes
+        const uint32_t smask = __ballot_sync(0xffffffffu, split);
+        uint32_t inc = split ? c : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
         }
-    }
-    s_a[threadIdx.x] = my_split;
-    s_b[threadIdx.x] = my_slots;
-    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {  // exclusive scans of 1024 per-thread totals
-        uint32_t ra = 0, rb = 0;
-        for (int i = 0; i < 1024; ++i) {
-            const uint32_t a = s_a[i], b = s_b[i];
-            s_a[i] = ra;
-            s_b[i] = rb;
-            ra += a;
-            rb += b;
-        }
-        s_tot[0] = ra;
-        s_tot[1] = rb;
-    }
-    __syncthreads();
-    uint32_t sp = s_a[threadIdx.x], slot = s_b[threadIdx.x];
-    const uint32_t n_split = s_tot[0], n_slots = s_tot[1];
-    for (int t = t0; t < t1; ++t) {
-        const uint2 r = ranges[t];
-        const uint32_t c = nch(t);
-        if (c > 1) {
+        const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        unsigned long long got = 0ull;
+        if (lane == 0 && smask)
+            got = atomicAdd(&s_alloc, ((unsigned long long)__popc(smask) << 32) | (unsigned long long)total);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (split) {
+            const uint32_t sp = (uint32_t)(got >> 32) + (uint32_t)__popc(smask & lt);
+            const uint32_t slot = (uint32_t)(got & 0xffffffffull) + inc - c;
             split_tiles[sp] = (uint32_t)t;
             split_slot0[sp] = slot;
             items[sp] = make_uint4((uint32_t)t, r.x, r.x + head, slot);  // wave A: first chunk
-            const uint32_t later = (uint32_t)n_tiles + (slot - sp);       // wave B: chunks before ours
+            const uint32_t later = (uint32_t)n_tiles + (slot - sp);      // wave B: later chunks before ours
             for (uint32_t k = 0; k < c; ++k) {
                 slot_split[slot + k] = sp;
                 if (k == 0) continue;
                 const uint32_t s0 = r.x + chunk_start(k, head, chunk);
                 items[later + k - 1] = make_uint4((uint32_t)t, s0, min(r.y, s0 + chunk), slot + k);
             }
-            ++sp;
-            slot += c;
-        } else {
-            const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-            atomicAdd(&s_cnt[len == 0 ? 32 : __clz(len)], 1u);
         }
+        const uint32_t b = whole ? bucket_of(len) : 64u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        if (whole && lane == __ffs(peers) - 1) atomicAdd(&s_bucket[b], (uint32_t)__popc(peers));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t run = n_split;
-        for (int b = 0; b < 33; ++b) {
-            const uint32_t c = s_cnt[b];
-            s_cnt[b] = run;
-            run += c;
+        const uint32_t n_split = (uint32_t)(s_alloc >> 32), n_slots = (uint32_t)(s_alloc & 0xffffffffull);
+        uint32_t run = n_split;  // whole tiles follow the first chunks
+        for (int q = 0; q < 33; ++q) {
+            const uint32_t cnt = s_bucket[q];
+            s_bucket[q] = run;
+            run += cnt;
         }
         counts[0] = (uint32_t)n_tiles + n_slots - n_split;
         counts[1] = n_split;
@@ -281,12 +277,20 @@ __global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges,
         counts[3] = (uint32_t)n_tiles;
     }
     __syncthreads();
-    for (int t = t0; t < t1; ++t) {
-        if (nch(t) > 1) continue;
-        const uint2 r = ranges[t];
+    // pass 2: whole tiles into their buckets
+    for (int base = warp * 32; base < n_tiles; base += 1024) {
+        const int t = base + lane;
+        uint2 r = make_uint2(0u, 0u);
+        if (t < n_tiles) r = ranges[t];
         const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-        const uint32_t pos = atomicAdd(&s_cnt[len == 0 ? 32 : __clz(len)], 1u);
-        items[pos] = make_uint4((uint32_t)t, r.x, r.x + len, kWholeTile);
+        const bool whole = t < n_tiles && chunk_count(len, head, chunk) == 1;
+        const uint32_t b = whole ? bucket_of(len) : 64u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t pos = 0;
+        if (whole && lane == leader) pos = atomicAdd(&s_bucket[b], (uint32_t)__popc(peers));
+        pos = __shfl_sync(0xffffffffu, pos, leader) + (uint32_t)__popc(peers & lt);
+        if (whole) items[pos] = make_uint4((uint32_t)t, r.x, r.x + len, kWholeTile);
     }
 }
 

@@ -14,10 +14,12 @@
 // Any other fp32 implementation of the same sequence reproduces them bit for
 // bit.
 //
-// Layout: one thread owns 4 consecutive Gaussians and reads every attribute
-// plane with one 16-byte load per plane (planes are 16-byte aligned, stride a
-// multiple of 4), so a warp moves 512 contiguous bytes per plane. SH planes are
-// read only for quads with at least one surviving Gaussian.
+// Layout: in k_project one thread owns 4 consecutive Gaussians and reads every
+// geometry plane with one 16-byte load per plane (planes are 16-byte aligned,
+// stride a multiple of 4), so a warp moves 512 contiguous bytes per plane; it
+// writes whole records with the colour left at 0. k_colour then streams the SH
+// planes (192 B per Gaussian at degree 3) for the visible Gaussians only, one
+// thread each, and fills in the colour.
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -210,31 +212,48 @@ __device__ __forceinline__ float sh_basis(float x, float y, float z)
 
 template <int K, int NK>
 struct ShAccum {
-    __device__ __forceinline__ static void run(const float *__restrict__ sh, int64_t n_pad, int64_t i0,
-                                               const float (&dx)[4], const float (&dy)[4], const float (&dz)[4],
-                                               float (&col)[4][3])
+    __device__ __forceinline__ static void run(const float *__restrict__ sh, int64_t n_pad, int64_t i, float x,
+                                               float y, float z, float (&col)[3])
     {
+        const float yk = sh_basis<K>(x, y, z);
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            const float4 c4 = __ldg(reinterpret_cast<const float4 *>(sh + (int64_t)(K * 3 + ch) * n_pad + i0));
-#pragma unroll
-            for (int g = 0; g < 4; ++g) col[g][ch] = fmaf(sh_basis<K>(dx[g], dy[g], dz[g]), lane4(c4, g), col[g][ch]);
-        }
-        ShAccum<K + 1, NK>::run(sh, n_pad, i0, dx, dy, dz, col);
+        for (int ch = 0; ch < 3; ++ch) col[ch] = fmaf(yk, __ldg(sh + (int64_t)(K * 3 + ch) * n_pad + i), col[ch]);
+        ShAccum<K + 1, NK>::run(sh, n_pad, i, x, y, z, col);
     }
 };
 template <int NK>
 struct ShAccum<NK, NK> {
-    __device__ __forceinline__ static void run(const float *, int64_t, int64_t, const float (&)[4], const float (&)[4],
-                                               const float (&)[4], float (&)[4][3])
-    {
-    }
+    __device__ __forceinline__ static void run(const float *, int64_t, int64_t, float, float, float, float (&)[3]) {}
 };
 
+// Colour of the visible Gaussians (one thread each, so a warp reads 128
+// contiguous bytes of every SH plane): direction from the camera centre, the
+// SH sum, +0.5, clamped at 0, into the colour fields of the record k_project
+// wrote. Kept apart from the projection so that this stream of SH bytes, the
+// bulk of the step's traffic at degree 3, runs with few registers and many
+// warps in flight (measured faster than 4 Gaussians per thread with 16-byte
+// loads).
 template <int DEG>
-__global__ void __launch_bounds__(kProjThreads) k_project(ProjectArgs a)
+__global__ void __launch_bounds__(256) k_colour(ProjectArgs a)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= a.n || a.ntiles[i] == 0) return;
+    const int64_t np = a.n_pad;
+    const float ex = __ldg(a.means + i) - a.cam.campos[0];
+    const float ey = __ldg(a.means + np + i) - a.cam.campos[1];
+    const float ez = __ldg(a.means + 2 * np + i) - a.cam.campos[2];
+    const float rn = rsqrtf(ex * ex + ey * ey + ez * ez);
+    float col[3] = {0.0f, 0.0f, 0.0f};
+    ShAccum<0, NK>::run(a.sh, np, i, ex * rn, ey * rn, ez * rn, col);
+    float *r = reinterpret_cast<float *>(a.rec + i);
+    r[7] = fmaxf(col[0] + 0.5f, 0.0f);  // r1.w
+    r[8] = fmaxf(col[1] + 0.5f, 0.0f);  // r2.x
+    r[9] = fmaxf(col[2] + 0.5f, 0.0f);  // r2.y
+}
+
+__global__ void __launch_bounds__(kProjThreads) k_project(ProjectArgs a)
+{
     const int64_t q = (int64_t)blockIdx.x * kProjThreads + threadIdx.x;
     const int64_t i0 = q * 4;
     uint32_t my_tiles = 0, my_vis = 0;
@@ -247,42 +266,28 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjectArgs a)
         const float4 l0 = ld4(a.log_scales, 0), l1 = ld4(a.log_scales, 1), l2 = ld4(a.log_scales, 2);
         const float4 qw = ld4(a.quats, 0), qx = ld4(a.quats, 1), qy = ld4(a.quats, 2), qz = ld4(a.quats, 3);
         const float4 lg = ld4(a.logits, 0);
-        Proj P[4];
-        bool any = false;
+        // records of visible Gaussians, colour left 0 for k_colour
+        struct Keep {
+            bool vis;
+            uint32_t nt;
+        } P[4];
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-            if (i0 + g < a.n) {
+            Proj Q;
+            Q.vis = false;
+            Q.nt = 0;
+            if (i0 + g < a.n)
                 project_one(a.cam, lane4(mx, g), lane4(my, g), lane4(mz, g), lane4(l0, g), lane4(l1, g), lane4(l2, g),
-                            lane4(qw, g), lane4(qx, g), lane4(qy, g), lane4(qz, g), lane4(lg, g), P[g]);
-            } else {
-                P[g].vis = false;
-                P[g].nt = 0;
-            }
-            any |= P[g].vis;
-        }
-        if (any) {
-            float dx[4], dy[4], dz[4], col[4][3];
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                const float ex = lane4(mx, g) - a.cam.campos[0], ey = lane4(my, g) - a.cam.campos[1],
-                            ez = lane4(mz, g) - a.cam.campos[2];
-                const float rn = rsqrtf(ex * ex + ey * ey + ez * ez);
-                dx[g] = ex * rn;
-                dy[g] = ey * rn;
-                dz[g] = ez * rn;
-                col[g][0] = col[g][1] = col[g][2] = 0.0f;
-            }
-            ShAccum<0, NK>::run(a.sh, np, i0, dx, dy, dz, col);
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                if (!P[g].vis) continue;
+                            lane4(qw, g), lane4(qx, g), lane4(qy, g), lane4(qz, g), lane4(lg, g), Q);
+            P[g].vis = Q.vis;
+            P[g].nt = Q.nt;
+            if (Q.vis) {
                 GaussRec r;
-                r.r0 = make_float4(P[g].u, P[g].v, P[g].ca, P[g].cb);
-                r.r1 = make_float4(P[g].cc, P[g].o, P[g].z, fmaxf(col[g][0] + 0.5f, 0.0f));
-                r.r2 = make_float4(fmaxf(col[g][1] + 0.5f, 0.0f), fmaxf(col[g][2] + 0.5f, 0.0f),
-                                   __uint_as_float(P[g].rlo), __uint_as_float(P[g].rhi));
+                r.r0 = make_float4(Q.u, Q.v, Q.ca, Q.cb);
+                r.r1 = make_float4(Q.cc, Q.o, Q.z, 0.0f);
+                r.r2 = make_float4(0.0f, 0.0f, __uint_as_float(Q.rlo), __uint_as_float(Q.rhi));
                 a.rec[i0 + g] = r;
-                a.bin[i0 + g] = make_uint4(__float_as_uint(P[g].z), P[g].rlo, P[g].rhi, 0u);
+                a.bin[i0 + g] = make_uint4(__float_as_uint(Q.z), Q.rlo, Q.rhi, 0u);
             }
         }
         *reinterpret_cast<uint4 *>(a.ntiles + i0) = make_uint4(P[0].nt, P[1].nt, P[2].nt, P[3].nt);
@@ -321,26 +326,34 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjectArgs a)
 
 int project_blocks(int64_t n) { return (int)((n + kProjPerBlock - 1) / kProjPerBlock); }
 
-// The projection kernel's entry, to find its node in a captured graph.
-const void *project_kernel_ptr(int deg)
+// The entries of the two kernels that take the camera, to find their nodes
+// in a captured graph: 0 = projection, 1 = colour.
+const void *project_kernel_ptr(int deg, int which)
 {
-    switch (deg) {
-    case 0: return reinterpret_cast<const void *>(k_project<0>);
-    case 1: return reinterpret_cast<const void *>(k_project<1>);
-    case 2: return reinterpret_cast<const void *>(k_project<2>);
-    default: return reinterpret_cast<const void *>(k_project<3>);
+    if (which == 1) {
+        switch (deg) {
+        case 0: return reinterpret_cast<const void *>(k_colour<0>);
+        case 1: return reinterpret_cast<const void *>(k_colour<1>);
+        case 2: return reinterpret_cast<const void *>(k_colour<2>);
+        default: return reinterpret_cast<const void *>(k_colour<3>);
+        }
     }
+    return reinterpret_cast<const void *>(k_project);
 }
 
 cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
 {
     const int nb = project_blocks(a.n);
     if (nb == 0) return cudaSuccess;
+    k_project<<<nb, kProjThreads, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned nc = (unsigned)((a.n + 255) / 256);
     switch (a.deg) {
-    case 0: k_project<0><<<nb, kProjThreads, 0, s>>>(a); break;
-    case 1: k_project<1><<<nb, kProjThreads, 0, s>>>(a); break;
-    case 2: k_project<2><<<nb, kProjThreads, 0, s>>>(a); break;
-    default: k_project<3><<<nb, kProjThreads, 0, s>>>(a); break;
+    case 0: k_colour<0><<<nc, 256, 0, s>>>(a); break;
+    case 1: k_colour<1><<<nc, 256, 0, s>>>(a); break;
+    case 2: k_colour<2><<<nc, 256, 0, s>>>(a); break;
+    default: k_colour<3><<<nc, 256, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }

@@ -42,7 +42,7 @@ gs_status cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
 }
 
-const void *project_kernel_ptr(int deg);  // project.cu
+const void *project_kernel_ptr(int deg, int which);  // project.cu: 0 projection, 1 colour
 
 namespace {
 
@@ -266,7 +266,7 @@ struct gs_graph {
     Frame *f = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t proj_node = nullptr;
+    cudaGraphNode_t proj_node = nullptr, colour_node = nullptr;  // the camera-dependent kernels
     ProjectArgs proj_args{};
     int64_t capacity = 0;
     int tile = 16;
@@ -803,15 +803,17 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
             cudaGraphGetNodes(g->graph, nullptr, &nn);
             std::vector<cudaGraphNode_t> nodes(nn);
             cudaGraphGetNodes(g->graph, nodes.data(), &nn);
-            const void *fp = project_kernel_ptr(scene->sh_degree);
+            const void *fp = project_kernel_ptr(scene->sh_degree, 0), *fc = project_kernel_ptr(scene->sh_degree, 1);
             for (auto nd : nodes) {
                 cudaGraphNodeType ty;
                 cudaGraphNodeGetType(nd, &ty);
                 if (ty != cudaGraphNodeTypeKernel) continue;
                 cudaKernelNodeParams kp;
-                if (cudaGraphKernelNodeGetParams(nd, &kp) == cudaSuccess && kp.func == fp) g->proj_node = nd;
+                if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+                if (kp.func == fp) g->proj_node = nd;
+                if (kp.func == fc) g->colour_node = nd;
             }
-            if (!g->proj_node) r = fail(GS_ERR_CUDA, "projection node not found in captured graph");
+            if (!g->proj_node || !g->colour_node) r = fail(GS_ERR_CUDA, "projection node not found in captured graph");
             if (g->timed) {
                 for (auto nd : nodes) {
                     cudaGraphNodeType ty;
@@ -843,12 +845,14 @@ gs_status gs_graph_render(gs_graph *g, const gs_camera *cam, gs_stream stream)
     gs_status r = check_cam(cam);
     if (r != GS_OK) return r;
     g->proj_args.cam = make_cam(*cam, g->tile);
-    cudaKernelNodeParams kp;
-    GSR_CUDA(cudaGraphKernelNodeGetParams(g->proj_node, &kp));
-    void *args[1] = {&g->proj_args};
-    kp.kernelParams = args;
-    kp.extra = nullptr;
-    GSR_CUDA(cudaGraphExecKernelNodeSetParams(g->exec, g->proj_node, &kp));
+    for (cudaGraphNode_t nd : {g->proj_node, g->colour_node}) {
+        cudaKernelNodeParams kp;
+        GSR_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
+        void *args[1] = {&g->proj_args};
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        GSR_CUDA(cudaGraphExecKernelNodeSetParams(g->exec, nd, &kp));
+    }
     if (g->timed) {
         cudaEvent_t *ev = g->timer.next();
         for (int k = 0; k < StageTimer::kBounds; ++k) GSR_CUDA(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_node[k], ev[k]));
