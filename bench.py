@@ -292,19 +292,23 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
-def algorithmic(stage, w, deg, n, K_avg, V_avg, passes, pixels, pairs):
+def algorithmic(stage, w, deg, n, K_avg, V_avg, tile_passes, pixels, pairs):
     """Algorithmic work of one launch of `stage` (bytes, or FP32 ops for compositing)."""
     sh_bytes = 12 * (deg + 1) ** 2
-    if stage == "project":
+    if stage == "project":  # means of all; scales, quaternion, opacity, SH of the visible; 48-byte record out
         return "hbm", 12.0 * n + (12 + 16 + 4 + sh_bytes + 48) * V_avg
-    if stage == "sort":  # every pass reads and writes each 8-byte key and 4-byte value
-        return "hbm", K_avg * 24 * passes
-    if stage == "duplicate":
-        return "hbm", 16.0 * V_avg + 12.0 * K_avg + 4.0 * n
-    if stage == "ranges":  # key + value read, 48-byte record gathered and written, per instance
-        return "hbm", (8.0 + 4.0 + 48.0 + 48.0) * K_avg
     if stage == "scan":
         return "hbm", 8.0 * n / 1024
+    if stage == "compact":  # tile count of all, depth of the visible; 4-byte key + 4-byte index out
+        return "hbm", 4.0 * n + (4.0 + 8.0) * V_avg
+    if stage == "depth_sort":  # 4 passes, each reads and writes a 4-byte key and a 4-byte value
+        return "hbm", V_avg * 16 * 4
+    if stage == "duplicate":  # index, tile count and rectangle per visible Gaussian; key + index per instance
+        return "hbm", (4.0 + 4.0 + 12.0) * V_avg + 8.0 * K_avg
+    if stage == "tile_sort":
+        return "hbm", K_avg * 16 * tile_passes
+    if stage == "ranges":  # key + value read, 48-byte record gathered and written, per instance
+        return "hbm", (4.0 + 4.0 + 48.0 + 48.0) * K_avg
     # composite: FP32 FLOP of the per-pair work, an FMA counted as 2: 16 per evaluated pair
     # (alpha: offset, quadratic form, exponent, opacity), 38 more per blended pair (the
     # Eq. 2-4 updates of colour, depth, T and the x/y gradient terms), on the census' counts
@@ -327,7 +331,8 @@ def recorded_traffic(stage):
     if it was taken on the current source of that kernel (else None)."""
     import hashlib
 
-    src = {"composite": "composite.cu", "sort": "sort.cu", "project": "project.cu"}.get(stage)
+    src = {"composite": "composite.cu", "depth_sort": "sort.cu", "tile_sort": "sort.cu",
+           "project": "project.cu"}.get(stage)
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not src or not os.path.exists(path):
         return None
@@ -435,11 +440,11 @@ def main():
     K_avg = st["instances_total"] / frames
     V_avg = st["visible_total"] / frames
     n_tiles = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
-    passes = math.ceil((32 + max(1, math.ceil(math.log2(max(n_tiles, 2))))) / 8)
+    tile_passes = math.ceil(max(1, math.ceil(math.log2(max(n_tiles, 2)))) / 8)
     dom = max(stage_ms, key=lambda k: stage_ms[k])
     hbm_peak, sm_max_mhz, peak_src = measured_peaks()
     def roofline(stage):
-        bound, amount = algorithmic(stage, (W, H), sc.deg, sc.n, K_avg, V_avg, passes, W * H, census)
+        bound, amount = algorithmic(stage, (W, H), sc.deg, sc.n, K_avg, V_avg, tile_passes, W * H, census)
         ms_stage = stage_ms[stage]
         if bound == "hbm":
             achieved = amount / (ms_stage * 1e-3) / 1e9
@@ -457,7 +462,7 @@ def main():
 
     roof = roofline(dom)
     stage_roofline = {k: {kk: v[kk] for kk in ("bound", "achieved", "unit", "frac")}
-                      for k, v in ((s, roofline(s)) for s in ("project", "sort", "composite"))}
+                      for k, v in ((s, roofline(s)) for s in abi.STAGES)}
 
     # end to end through the public API: camera in from the host, planes out to pinned host memory
     e2e = None
@@ -494,9 +499,10 @@ def main():
                 "stage_ms": stage_ms, "instances_per_frame": K_avg, "visible_per_frame": V_avg,
                 "roofline": roof, "stage_roofline": stage_roofline, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu,
-                # kernels per frame: projection, colour, block scan, duplication, `passes` sort
+                # kernels per frame: projection, colour, block scan, compaction, 4 depth-sort
+                # passes, tile-count sums, their scan, duplication, `tile_passes` tile-sort
                 # passes, ranges, plan, two compositing waves, re-walk, finish
-                "gpu_launches": args.steps * (10 + passes)}
+                "gpu_launches": args.steps * (17 + tile_passes)}
         print(json.dumps(line), flush=True)
     graph.close()
     ctx.close()

@@ -137,15 +137,15 @@ typedef struct {
 
 /* Counters of the frames rendered since the last reset, and (with
  * GS_TIME_STAGES) the mean per-frame device time of each stage, from CUDA
- * events recorded on the launch stream at the stage boundaries:
- * [0] projection + SH (K1), [1] scan (K2), [2] key duplication (K3),
- * [3] radix sort (K4), [4] tile ranges (K5), [5] compositing + gradients (K6). */
+ * events recorded on the launch stream at the stage boundaries (see stage_ms). */
 typedef struct {
     int64_t frames;               /* frames since the last reset */
     int64_t instances_total;      /* sum over those frames of K, the (Gaussian, tile) instances */
     int64_t visible_total;        /* sum of Gaussians that survived culling */
     int64_t instances_max;        /* largest K */
-    double stage_ms[6];
+    double stage_ms[8];           /* mean device ms per frame of: projection (+ colour), block scan,
+                                     visible compaction, depth sort, tile-key duplication, tile sort,
+                                     tile ranges (+ work plan), compositing (all of its launches) */
     int64_t timed_frames;         /* frames that carried stage events */
     int64_t pairs_evaluated;      /* GS_COUNT_PAIRS: pixel inside a Gaussian's support rectangle, before the stop */
     int64_t pairs_blended;        /* GS_COUNT_PAIRS: of those, alpha >= 1/255 and blended */

@@ -24,7 +24,7 @@ GS_ERR_CANCELLED = -6
 GS_EMIT_BWD_STATE = 1
 GS_TIME_STAGES = 2
 GS_COUNT_PAIRS = 4
-STAGES = ("project", "scan", "duplicate", "sort", "ranges", "composite")
+STAGES = ("project", "scan", "compact", "depth_sort", "duplicate", "tile_sort", "ranges", "composite")
 
 STATUS_NAMES = {0: "GS_OK", 1: "GS_NOT_READY", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_OOM", -3: "GS_ERR_CUDA",
                 -4: "GS_ERR_TIMEOUT", -5: "GS_ERR_CAPACITY", -6: "GS_ERR_CANCELLED"}
@@ -74,7 +74,7 @@ class GsStateView(C.Structure):
 
 class GsFrameStats(C.Structure):
     _fields_ = [("frames", C.c_int64), ("instances_total", C.c_int64), ("visible_total", C.c_int64),
-                ("instances_max", C.c_int64), ("stage_ms", C.c_double * 6), ("timed_frames", C.c_int64),
+                ("instances_max", C.c_int64), ("stage_ms", C.c_double * len(STAGES)), ("timed_frames", C.c_int64),
                 ("pairs_evaluated", C.c_int64), ("pairs_blended", C.c_int64)]
 
 

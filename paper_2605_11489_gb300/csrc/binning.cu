@@ -1,13 +1,21 @@
-// Tile binning: instance offsets (K2), (tile, depth) key duplication (K3) and
-// per-tile ranges of the sorted keys (K5). The depth sort itself (paper Sec. 3:
-// "the resulting 2D Gaussians are depth-sorted") is a radix sort over these
-// keys (sort.cu); binning by tile lets compositing walk only the Gaussians
-// whose support reaches each tile.
-//
-// The scan is split to avoid a separate pass over the per-Gaussian counts: the
-// projection kernel already reduced tiles-touched per block of 1024 Gaussians;
-// K2 scans those block sums in one CTA; K3 re-reads the counts it needs anyway
-// and finishes the scan inside each block.
+// Tile binning and the depth order (paper Sec. 3: the projected Gaussians are
+// depth-sorted; binning by tile lets compositing walk only the Gaussians whose
+// support reaches each tile). The order wanted is (tile, depth, index), the
+// order of a stable sort of (tile << 32 | fp32 depth bits) keys. It is built
+// depth first, which moves far fewer bytes than sorting the 12-byte
+// (key, value) pairs of every instance on all 45 bits:
+//   K2  scan of the projection's per-block tile and visible counts: K, and the
+//       compacted position of each block's visible Gaussians;
+//   K3a the visible Gaussians' 32-bit depth keys and indices, compacted in
+//       index order, with the depth sort's digit histograms;
+//   K4a stable radix sort of those V pairs by depth (sort.cu, 4 passes);
+//   K3b per 1,024 depth-sorted Gaussians the sum of their tile counts, a scan
+//       of those sums, then every Gaussian's tile keys (32-bit tile id) and
+//       index, emitted in depth order, with the tile sort's digit histograms;
+//   K4b stable radix sort of the K instances by tile id (1 or 2 passes);
+//   K5  per-tile ranges, with the records gathered into sorted order.
+// Equal (tile, depth) keep index order because K3a emits in index order and
+// both sorts are stable.
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -15,19 +23,16 @@ namespace {
 
 constexpr int kScanThreads = 1024;
 
-// Exclusive scan of per-block tile counts; writes offsets, K = total, and the
-// capacity-clamped K used downstream (with an overflow bit if clamped).
-__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const uint32_t *__restrict__ sums, int nb,
-                                                              uint32_t *__restrict__ offs, uint32_t *counters,
-                                                              unsigned long long capacity)
+// Exclusive scan over 1,024 threads of per-block counts `sums[0, nb)` into
+// `offs`; returns the total in every thread.
+__device__ unsigned long long block_scan_counts(const uint32_t *__restrict__ sums, int nb, uint32_t *__restrict__ offs,
+                                                unsigned long long *s_warp)
 {
-    __shared__ unsigned long long s_warp[kScanThreads / 32];
     const int per = (nb + kScanThreads - 1) / kScanThreads;
     const int b0 = threadIdx.x * per;
     unsigned long long local = 0;
     for (int k = 0; k < per; ++k)
         if (b0 + k < nb) local += sums[b0 + k];
-    // inclusive warp scan
     unsigned long long v = local;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -35,6 +40,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const uint32_t *__
         unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += t;
     }
+    __syncthreads();  // s_warp may still be read by an earlier call
     if (lane == 31) s_warp[warp] = v;
     __syncthreads();
     if (warp == 0) {
@@ -53,8 +59,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const uint32_t *__
             offs[b0 + k] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
             run += sums[b0 + k];
         }
+    return s_warp[31];
+}
+
+// K2: exclusive scans of the per-block tile counts (-> K, the capacity-clamped
+// K used downstream, with an overflow bit if clamped) and of the per-block
+// visible counts (-> where each block's visible Gaussians go when compacted).
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const uint32_t *__restrict__ sums,
+                                                              const uint32_t *__restrict__ vis_sums, int nb,
+                                                              uint32_t *__restrict__ offs,
+                                                              uint32_t *__restrict__ vis_offs, uint32_t *counters,
+                                                              unsigned long long capacity)
+{
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    const unsigned long long total = block_scan_counts(sums, nb, offs, s_warp);
+    if (vis_sums) block_scan_counts(vis_sums, nb, vis_offs, s_warp);
     if (threadIdx.x == kScanThreads - 1) {
-        const unsigned long long total = run;
         counters[kCntTotal] = (uint32_t)(total & 0xffffffffull);
         counters[kCntTotalHi] = (uint32_t)(total >> 32);
         const unsigned long long eff = total < capacity ? total : capacity;
@@ -66,64 +86,137 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const uint32_t *__
     }
 }
 
-// One thread per quad of Gaussians (same partition as the projection); emits
-// key = (tile id << 32) | fp32 bits of depth, val = Gaussian index, for every
-// tile of each Gaussian's support rectangle, in index order. With `hist`, it
-// also builds the radix sort's per-pass digit histograms of exactly the keys
-// it writes (8-bit digits, `passes` of them): the four depth digits are shared
-// by all of a Gaussian's keys and counted once per Gaussian, the tile digits
-// once per key; block counts are merged into `hist` with one atomic per bin.
-__global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__restrict__ ntiles,
-                                                            const uint4 *__restrict__ bin,
-                                                            const uint32_t *__restrict__ block_offs, int64_t n,
-                                                            int tile_shift, int tiles_x, uint64_t *__restrict__ keys,
-                                                            uint32_t *__restrict__ vals, unsigned long long capacity,
-                                                            uint32_t *counters, uint32_t *__restrict__ hist,
-                                                            int passes)
+// Plain exclusive scan of per-block sums (K3b's counts in depth order).
+__global__ void __launch_bounds__(kScanThreads) k_scan_plain(const uint32_t *__restrict__ sums, int nb,
+                                                             uint32_t *__restrict__ offs)
 {
-    __shared__ uint32_t s_warp[kProjThreads / 32];
-    __shared__ uint32_t s_hist[8 * 256];
-    if (hist)
-        for (int i = threadIdx.x; i < passes * 256; i += kProjThreads) s_hist[i] = 0;
-    const int64_t i0 = ((int64_t)blockIdx.x * kProjThreads + threadIdx.x) * 4;
-    uint4 nt = make_uint4(0, 0, 0, 0);
-    if (i0 < n) nt = *reinterpret_cast<const uint4 *>(ntiles + i0);
-    const uint32_t mine = nt.x + nt.y + nt.z + nt.w;
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    block_scan_counts(sums, nb, offs, s_warp);
+}
+
+// Block-wide exclusive prefix of one value per thread (256 threads) and the
+// block total.
+__device__ __forceinline__ uint32_t block_excl(uint32_t mine, uint32_t *s_warp, uint32_t &total)
+{
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t v = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += t;
     }
     if (lane == 31) s_warp[warp] = v;
     __syncthreads();
     uint32_t before = 0;
-    for (int w = 0; w < warp; ++w) before += s_warp[w];
-    unsigned long long off = (unsigned long long)block_offs[blockIdx.x] + before + (v - mine);
-    const uint32_t cnt[4] = {nt.x, nt.y, nt.z, nt.w};
+    total = 0;
+#pragma unroll
+    for (int w = 0; w < kProjThreads / 32; ++w) {
+        const uint32_t x = s_warp[w];
+        if (w < warp) before += x;
+        total += x;
+    }
+    return before + v - mine;
+}
+
+// Adds a block's digit histograms (shared, `n` bins) into the global ones.
+__device__ __forceinline__ void flush_hist(const uint32_t *s_hist, uint32_t *hist, int n)
+{
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kProjThreads)
+        if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
+}
+
+// K3a: one thread per quad of Gaussians (the projection's partition). Writes
+// the visible ones' depth keys (fp32 bits) and indices at their compacted
+// positions, in index order, and counts the 4 depth digits.
+__global__ void __launch_bounds__(kProjThreads) k_compact(const uint32_t *__restrict__ ntiles,
+                                                          const uint4 *__restrict__ bin,
+                                                          const uint32_t *__restrict__ vis_offs, int64_t n,
+                                                          uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals,
+                                                          uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t s_warp[kProjThreads / 32];
+    __shared__ uint32_t s_hist[4 * 256];
+    for (int i = threadIdx.x; i < 4 * 256; i += kProjThreads) s_hist[i] = 0;
+    const int64_t i0 = ((int64_t)blockIdx.x * kProjThreads + threadIdx.x) * 4;
+    uint4 nt = make_uint4(0, 0, 0, 0);
+    if (i0 < n) nt = *reinterpret_cast<const uint4 *>(ntiles + i0);
+    const uint32_t vis[4] = {nt.x != 0u, nt.y != 0u, nt.z != 0u, nt.w != 0u};
+    uint32_t total;
+    uint32_t off = vis_offs[blockIdx.x] + block_excl(vis[0] + vis[1] + vis[2] + vis[3], s_warp, total);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        if (!vis[g]) continue;
+        const uint32_t z = bin[i0 + g].x;
+        dkeys[off] = z;
+        dvals[off] = (uint32_t)(i0 + g);
+        ++off;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p * 256 + ((z >> (8 * p)) & 0xFFu)], 1u);
+    }
+    flush_hist(s_hist, hist, 4 * 256);
+}
+
+// K3b, first half: per 1,024 depth-sorted Gaussians (256 threads x 4), the
+// sum of their tile counts.
+__global__ void __launch_bounds__(kProjThreads) k_sorted_counts(const uint32_t *__restrict__ dvals,
+                                                                const uint32_t *__restrict__ vcount,
+                                                                const uint32_t *__restrict__ ntiles,
+                                                                uint32_t *__restrict__ sums)
+{
+    __shared__ uint32_t s_warp[kProjThreads / 32];
+    const uint32_t V = *vcount;
+    const uint32_t i0 = (blockIdx.x * kProjThreads + threadIdx.x) * 4;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+        if (i0 + g < V) mine += ntiles[dvals[i0 + g]];
+    uint32_t total;
+    block_excl(mine, s_warp, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// K3b, second half: every depth-sorted Gaussian's keys, key = tile id (32-bit)
+// and value = Gaussian index, for every tile of its support rectangle, at
+// offsets continuing the scan of K3b's block sums; counts the tile digits.
+// Keys past `capacity` are not written (the overflow bit is set).
+__global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__restrict__ dvals,
+                                                            const uint32_t *__restrict__ vcount,
+                                                            const uint32_t *__restrict__ ntiles,
+                                                            const uint4 *__restrict__ bin,
+                                                            const uint32_t *__restrict__ block_offs, int tile_shift,
+                                                            int tiles_x, uint32_t *__restrict__ keys,
+                                                            uint32_t *__restrict__ vals, unsigned long long capacity,
+                                                            uint32_t *counters, uint32_t *__restrict__ hist, int passes)
+{
+    __shared__ uint32_t s_warp[kProjThreads / 32];
+    __shared__ uint32_t s_hist[2 * 256];
+    for (int i = threadIdx.x; i < 2 * 256; i += kProjThreads) s_hist[i] = 0;
+    const uint32_t V = *vcount;
+    const uint32_t i0 = (blockIdx.x * kProjThreads + threadIdx.x) * 4;
+    uint32_t idx[4], cnt[4], mine = 0;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        idx[g] = i0 + g < V ? dvals[i0 + g] : 0u;
+        cnt[g] = i0 + g < V ? ntiles[idx[g]] : 0u;
+        mine += cnt[g];
+    }
+    uint32_t total;
+    unsigned long long off = (unsigned long long)block_offs[blockIdx.x] + block_excl(mine, s_warp, total);
     bool overflow = false;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         if (cnt[g] == 0) continue;
-        const uint4 b = bin[i0 + g];
+        const uint4 b = bin[idx[g]];
         const int x0 = (b.y & 0xFFFFu) >> tile_shift, y0 = (b.y >> 16) >> tile_shift;
         const int x1 = (b.z & 0xFFFFu) >> tile_shift, y1 = (b.z >> 16) >> tile_shift;
-        const uint32_t idx = (uint32_t)(i0 + g);
-        if (hist) {  // depth digits: every written key of this Gaussian shares them
-            const uint32_t written =
-                off >= capacity ? 0u : (uint32_t)min((unsigned long long)cnt[g], capacity - off);
-            for (int p = 0; p < passes && p < 4; ++p)
-                if (written) atomicAdd(&s_hist[p * 256 + ((b.x >> (8 * p)) & 0xFFu)], written);
-        }
         for (int ty = y0; ty <= y1; ++ty)
             for (int tx = x0; tx <= x1; ++tx) {
                 const uint32_t tile = (uint32_t)(ty * tiles_x + tx);
                 if (off < capacity) {
-                    keys[off] = ((uint64_t)tile << 32) | (uint64_t)b.x;
-                    vals[off] = idx;
-                    if (hist)
-                        for (int p = 4; p < passes; ++p) atomicAdd(&s_hist[p * 256 + ((tile >> (8 * (p - 4))) & 0xFFu)], 1u);
+                    keys[off] = tile;
+                    vals[off] = idx[g];
+                    for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + ((tile >> (8 * p)) & 0xFFu)], 1u);
                 } else {
                     overflow = true;
                 }
@@ -131,34 +224,34 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
             }
     }
     if (overflow) atomicOr(&counters[kCntErr], kErrCapacity);
-    if (hist) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < passes * 256; i += kProjThreads)
-            if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
-    }
+    flush_hist(s_hist, hist, passes * 256);
 }
 
-// Per-tile [start, end) of the sorted keys and, in the same pass, the records
-// gathered into sorted (instance) order, so compositing stages each batch of a
-// tile's list with one contiguous bulk copy.
-__global__ void k_ranges(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+// K5: per-tile [start, end) of the sorted tile keys and, in the same pass, the
+// records gathered into sorted (instance) order, so compositing stages each
+// batch of a tile's list with one contiguous bulk copy. With `keys64` it also
+// writes each instance's (tile << 32) | depth-bits key (the state view's).
+__global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                          const uint32_t *__restrict__ counters, const GaussRec *__restrict__ rec,
-                         GaussRec *__restrict__ rec_sorted, uint2 *ranges)
+                         GaussRec *__restrict__ rec_sorted, uint2 *ranges, const uint4 *__restrict__ bin,
+                         uint64_t *__restrict__ keys64)
 {
     const uint32_t K = counters[kCntEff];
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= K) return;
-    const uint32_t t = (uint32_t)(keys[i] >> 32);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = i;
-    if (i == K - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = i + 1;
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
+    if (i == K - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
+    const uint32_t g = vals[i];
     if (rec_sorted) {
-        const GaussRec *src = rec + vals[i];
+        const GaussRec *src = rec + g;
         GaussRec r;
         r.r0 = __ldg(&src->r0);
         r.r1 = __ldg(&src->r1);
         r.r2 = __ldg(&src->r2);
         rec_sorted[i] = r;
     }
+    if (keys64) keys64[i] = ((uint64_t)t << 32) | (uint64_t)bin[g].x;
 }
 
 // Tiles ordered by decreasing list length, bucketed by floor(log2(length)), so
@@ -316,39 +409,55 @@ cudaError_t launch_tile_order(const uint2 *ranges, int n_tiles, uint32_t *order,
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_blocks(const uint32_t *block_sums, int nblocks, uint32_t *block_offsets, uint32_t *counters,
-                               int64_t capacity, cudaStream_t s)
+cudaError_t launch_scan_blocks(const uint32_t *block_sums, const uint32_t *vis_sums, int nblocks,
+                               uint32_t *block_offsets, uint32_t *vis_offsets, uint32_t *counters, int64_t capacity,
+                               cudaStream_t s)
 {
-    k_scan_blocks<<<1, kScanThreads, 0, s>>>(block_sums, nblocks, block_offsets, counters,
+    k_scan_blocks<<<1, kScanThreads, 0, s>>>(block_sums, vis_sums, nblocks, block_offsets, vis_offsets, counters,
                                               (unsigned long long)capacity);
     return cudaGetLastError();
 }
 
-cudaError_t launch_duplicate(const uint32_t *ntiles, const uint4 *bin, const uint32_t *block_offsets, int64_t n,
-                             int tile_shift, int tiles_x, uint64_t *keys, uint32_t *vals, int64_t capacity,
-                             uint32_t *counters, uint32_t *hist, int passes, cudaStream_t s)
+cudaError_t launch_compact(const uint32_t *ntiles, const uint4 *bin, const uint32_t *vis_offsets, int64_t n,
+                           uint32_t *dkeys, uint32_t *dvals, uint32_t *hist, cudaStream_t s)
 {
-    if (hist) {
-        if (passes < 1 || passes > 8) return cudaErrorInvalidValue;
-        const cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 8 * 256, s);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 8 * 256, s);
+    if (e != cudaSuccess) return e;
     const int nb = project_blocks(n);
     if (nb == 0) return cudaSuccess;
-    k_duplicate<<<nb, kProjThreads, 0, s>>>(ntiles, bin, block_offsets, n, tile_shift, tiles_x, keys, vals,
+    k_compact<<<nb, kProjThreads, 0, s>>>(ntiles, bin, vis_offsets, n, dkeys, dvals, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int64_t max_v, const uint32_t *ntiles,
+                             const uint4 *bin, uint32_t *bsums, uint32_t *boffs, int tile_shift, int tiles_x,
+                             uint32_t *keys, uint32_t *vals, int64_t capacity, uint32_t *counters, uint32_t *hist,
+                             int passes, cudaStream_t s)
+{
+    if (passes < 0 || passes > 2) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 8 * 256, s);
+    if (e != cudaSuccess) return e;
+    const int nb = project_blocks(max_v);
+    if (nb == 0) return cudaSuccess;
+    k_sorted_counts<<<nb, kProjThreads, 0, s>>>(dvals, vcount, ntiles, bsums);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_scan_plain<<<1, kScanThreads, 0, s>>>(bsums, nb, boffs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_duplicate<<<nb, kProjThreads, 0, s>>>(dvals, vcount, ntiles, bin, boffs, tile_shift, tiles_x, keys, vals,
                                             (unsigned long long)capacity, counters, hist, passes);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const uint64_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
-                          const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, cudaStream_t s)
+cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
+                          const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, const uint4 *bin,
+                          uint64_t *keys64, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess) return e;
     if (max_k <= 0) return cudaSuccess;
     const int threads = 256;
     const int64_t nb = (max_k + threads - 1) / threads;
-    k_ranges<<<(unsigned)nb, threads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges);
+    k_ranges<<<(unsigned)nb, threads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges, bin, keys64);
     return cudaGetLastError();
 }
 

@@ -91,23 +91,38 @@ struct ProjectArgs {
     GaussRec *rec;
     uint4 *bin;
     uint32_t *ntiles;
-    uint32_t *block_sums;
-    uint32_t *counters;  // visible count accumulates into kCntVisible / kCntSumV
+    uint32_t *block_sums;  // per block of 1,024 Gaussians: tiles touched
+    uint32_t *block_vis;   // per block of 1,024 Gaussians: visible Gaussians
+    uint32_t *counters;    // visible count accumulates into kCntVisible / kCntSumV
 };
 int project_blocks(int64_t n);
+// geometry (records without colour, bin, tile counts, block sums), then the SH
+// colour of the visible Gaussians; launch_project runs both on one stream
+cudaError_t launch_project_geometry(const ProjectArgs &a, cudaStream_t s);
+cudaError_t launch_colour(const ProjectArgs &a, cudaStream_t s);
 cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s);
 
-// scan of the projection's per-block sums -> per-block offsets and K
-cudaError_t launch_scan_blocks(const uint32_t *block_sums, int nblocks, uint32_t *block_offsets,
-                               uint32_t *counters, int64_t capacity, cudaStream_t s);
-// (tile, depth) key duplication; with `hist` ([8][256], cleared here) also the
-// radix sort's digit histograms of the written keys, for a sort of `passes` digits
-cudaError_t launch_duplicate(const uint32_t *ntiles, const uint4 *bin, const uint32_t *block_offsets,
-                             int64_t n, int tile_shift, int tiles_x, uint64_t *keys, uint32_t *vals,
-                             int64_t capacity, uint32_t *counters, uint32_t *hist, int passes, cudaStream_t s);
-// per-tile [start, end) from sorted keys, plus the records gathered into sorted order
-cudaError_t launch_ranges(const uint64_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
-                          const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, cudaStream_t s);
+// K2: scans of the projection's per-block tile counts (-> K in counters) and,
+// when vis_sums is given, of its per-block visible counts
+cudaError_t launch_scan_blocks(const uint32_t *block_sums, const uint32_t *vis_sums, int nblocks,
+                               uint32_t *block_offsets, uint32_t *vis_offsets, uint32_t *counters, int64_t capacity,
+                               cudaStream_t s);
+// K3a: depth keys + indices of the visible Gaussians, compacted; `hist`
+// ([8][256], cleared here) gets the depth sort's 4 digit histograms
+cudaError_t launch_compact(const uint32_t *ntiles, const uint4 *bin, const uint32_t *vis_offsets, int64_t n,
+                           uint32_t *dkeys, uint32_t *dvals, uint32_t *hist, cudaStream_t s);
+// K3b: tile keys (u32) + indices of the depth-sorted Gaussians dvals[0, *vcount),
+// in that order; `hist` (cleared here) gets the tile sort's `passes` (<= 2)
+// digit histograms. bsums/boffs: per 1,024 sorted Gaussians, >= project_blocks(max_v).
+cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int64_t max_v, const uint32_t *ntiles,
+                             const uint4 *bin, uint32_t *bsums, uint32_t *boffs, int tile_shift, int tiles_x,
+                             uint32_t *keys, uint32_t *vals, int64_t capacity, uint32_t *counters, uint32_t *hist,
+                             int passes, cudaStream_t s);
+// K5: per-tile [start, end) from the sorted tile keys, the records gathered into
+// sorted order, and (keys64 != NULL) each instance's (tile << 32 | depth bits)
+cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
+                          const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, const uint4 *bin,
+                          uint64_t *keys64, cudaStream_t s);
 
 // onesweep LSD radix sort of (keys, vals) on the low `bits` bits, K from counters[kCntEff]
 struct SortScratch {
@@ -125,6 +140,10 @@ int sort_passes(int bits);
 cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *counters, uint32_t *err_word,
                         int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s,
                         bool hist_ready = false);
+// The same over 32-bit keys; the element count is the device word *count.
+cudaError_t launch_sort32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *count, uint32_t *err_word,
+                          int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s,
+                          bool hist_ready);
 
 struct CompositeArgs {
     const GaussRec *rec;  // records in sorted (instance) order: tile t's list is rec[ranges[t].x, ranges[t].y)

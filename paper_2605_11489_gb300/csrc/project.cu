@@ -21,6 +21,7 @@
 // planes (192 B per Gaussian at degree 3) for the visible Gaussians only, one
 // thread each, and fills in the colour.
 #include "gsr_internal.cuh"
+#include <algorithm>
 
 namespace gsr {
 namespace {
@@ -315,6 +316,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjectArgs a)
             cv += s_warp[1][w];
         }
         a.block_sums[blockIdx.x] = t;
+        if (a.block_vis) a.block_vis[blockIdx.x] = cv;
         if (cv) {
             atomicAdd(&a.counters[kCntVisible], cv);
             atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kCntSumV), (unsigned long long)cv);
@@ -341,13 +343,17 @@ const void *project_kernel_ptr(int deg, int which)
     return reinterpret_cast<const void *>(k_project);
 }
 
-cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
+cudaError_t launch_project_geometry(const ProjectArgs &a, cudaStream_t s)
 {
     const int nb = project_blocks(a.n);
     if (nb == 0) return cudaSuccess;
     k_project<<<nb, kProjThreads, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colour(const ProjectArgs &a, cudaStream_t s)
+{
+    if (a.n <= 0) return cudaSuccess;
     const unsigned nc = (unsigned)((a.n + 255) / 256);
     switch (a.deg) {
     case 0: k_colour<0><<<nc, 256, 0, s>>>(a); break;
@@ -356,6 +362,12 @@ cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
     default: k_colour<3><<<nc, 256, 0, s>>>(a); break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s)
+{
+    cudaError_t e = launch_project_geometry(a, s);
+    return e != cudaSuccess ? e : launch_colour(a, s);
 }
 
 }  // namespace gsr

@@ -78,7 +78,9 @@ struct Buf {
 // All per-frame device buffers. Owned by a context (pooled), a state or a graph.
 struct Frame {
     Buf rec, bin, ntiles, bsums, boffs;
-    Buf keys[2], vals[2], sort_scr, rec_sorted;
+    Buf keys[2], vals[2], sort_scr, rec_sorted;     // tile keys (u32) and Gaussian indices, per instance
+    Buf dkeys[2], dvals[2], vsums, voffs, bsums2, boffs2;  // depth order of the visible Gaussians
+    Buf keys64;                                     // (tile << 32 | depth bits) per instance, for a state view
     Buf ranges, order;
     Buf items, split_tiles, split_slot0, slot_split, plan_counts, partial;  // compositing work plan
     int chunk = 2048;
@@ -100,12 +102,12 @@ struct Frame {
 // per frame, recorded at the stage boundaries on the launch stream (plain
 // path) or retargeted into a graph's event-record nodes before each replay.
 struct StageTimer {
-    static constexpr int kBounds = 7;  // before K1 | K1 | K2 | K3 | K4 | K5 | K6
+    static constexpr int kBounds = 9;  // before K1 | K1 | K2 | K3a | K4a | K3b | K4b | K5+plan | K6
     static constexpr int kRing = 512;
     std::vector<cudaEvent_t> ev;
     int head = 0;
     int64_t in_ring = 0;  // recorded slots not yet folded
-    double sum_ms[kBounds - 1] = {0, 0, 0, 0, 0, 0};
+    double sum_ms[kBounds - 1] = {};
     int64_t folded = 0;
     ~StageTimer()
     {
@@ -329,6 +331,14 @@ gs_status frame_setup(Frame *f, const gs_scene *s, const gs_camera *c, const gs_
     GSR_CUDA(f->ntiles.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(n4, 4)));
     GSR_CUDA(f->bsums.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
     GSR_CUDA(f->boffs.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
+    for (int k = 0; k < 2; ++k) {
+        GSR_CUDA(f->dkeys[k].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(s->n, 1)));
+        GSR_CUDA(f->dvals[k].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(s->n, 1)));
+    }
+    GSR_CUDA(f->vsums.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
+    GSR_CUDA(f->voffs.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
+    GSR_CUDA(f->bsums2.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
+    GSR_CUDA(f->boffs2.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
     GSR_CUDA(f->ranges.ensure(sizeof(uint2) * (size_t)f->n_tiles));
     GSR_CUDA(f->order.ensure(sizeof(uint32_t) * (size_t)f->n_tiles));
     GSR_CUDA(f->counters.ensure(sizeof(uint32_t) * kCntSlots));
@@ -345,11 +355,11 @@ gs_status frame_setup(Frame *f, const gs_scene *s, const gs_camera *c, const gs_
 
 gs_status frame_keys(Frame *f, int64_t cap)
 {
-    GSR_CUDA(f->keys[0].ensure(sizeof(uint64_t) * (size_t)std::max<int64_t>(cap, 1)));
-    GSR_CUDA(f->keys[1].ensure(sizeof(uint64_t) * (size_t)std::max<int64_t>(cap, 1)));
+    GSR_CUDA(f->keys[0].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(cap, 1)));
+    GSR_CUDA(f->keys[1].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(cap, 1)));
     GSR_CUDA(f->vals[0].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(cap, 1)));
     GSR_CUDA(f->vals[1].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(cap, 1)));
-    GSR_CUDA(f->sort_scr.ensure(sort_scratch_bytes(std::max<int64_t>(cap, 1))));
+
     GSR_CUDA(f->rec_sorted.ensure(sizeof(GaussRec) * (size_t)std::max<int64_t>(cap, 1)));
     f->key_cap = cap;
     return GS_OK;
@@ -368,6 +378,10 @@ gs_status frame_plan(Frame *f, int64_t cap)
     GSR_CUDA(f->split_slot0.ensure(sizeof(uint32_t) * (size_t)f->max_split));
     GSR_CUDA(f->slot_split.ensure(sizeof(uint32_t) * (size_t)slots));
     GSR_CUDA(f->plan_counts.ensure(sizeof(uint32_t) * 4));
+    if (f->has_state) GSR_CUDA(f->keys64.ensure(sizeof(uint64_t) * (size_t)std::max<int64_t>(cap, 1)));
+    // one scratch serves both sorts (they run one after the other): sized for
+    // the larger of the instance capacity and the Gaussian count
+    GSR_CUDA(f->sort_scr.ensure(sort_scratch_bytes(std::max<int64_t>(std::max<int64_t>(cap, f->n), 1))));
     GSR_CUDA(f->partial.ensure(sizeof(float) * 16 * (size_t)f->tile * f->tile * (size_t)slots));
     return GS_OK;
 }
@@ -388,6 +402,7 @@ ProjectArgs proj_args(Frame *f, const gs_scene *s)
     a.bin = f->bin.as<uint4>();
     a.ntiles = f->ntiles.as<uint32_t>();
     a.block_sums = f->bsums.as<uint32_t>();
+    a.block_vis = f->vsums.as<uint32_t>();
     a.counters = f->counters.as<uint32_t>();
     return a;
 }
@@ -441,28 +456,40 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
 {
     uint32_t *cnt = f->counters.as<uint32_t>();
     SortScratch scr;
-    sort_scratch_carve(f->sort_scr.p, f->key_cap, &scr);
-    GSR_CUDA(launch_duplicate(f->ntiles.as<uint32_t>(), f->bin.as<uint4>(), f->boffs.as<uint32_t>(), f->n,
-                              f->cam.tile_shift, f->tiles_x, f->keys[0].as<uint64_t>(), f->vals[0].as<uint32_t>(),
-                              f->key_cap, cnt, scr.hist, sort_passes(f->bits), st));
+    sort_scratch_carve(f->sort_scr.p, std::max<int64_t>(f->key_cap, f->n), &scr);
+    // K3a, K4a: the visible Gaussians in depth order
+    GSR_CUDA(launch_compact(f->ntiles.as<uint32_t>(), f->bin.as<uint4>(), f->voffs.as<uint32_t>(), f->n,
+                            f->dkeys[0].as<uint32_t>(), f->dvals[0].as<uint32_t>(), scr.hist, st));
     GSR_CUDA(mark(ev, 3, st, capture));
-    uint64_t *kk[2] = {f->keys[0].as<uint64_t>(), f->keys[1].as<uint64_t>()};
+    uint32_t *dk[2] = {f->dkeys[0].as<uint32_t>(), f->dkeys[1].as<uint32_t>()};
+    uint32_t *dv[2] = {f->dvals[0].as<uint32_t>(), f->dvals[1].as<uint32_t>()};
+    int dres = 0;
+    GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, cnt + kCntErr, f->n, 32, scr, &dres, st, true));
+    GSR_CUDA(mark(ev, 4, st, capture));
+    // K3b, K4b: tile keys in depth order, then stable by tile
+    const int tbits = f->bits - 32;
+    GSR_CUDA(launch_duplicate(dv[dres], cnt + kCntVisible, f->n, f->ntiles.as<uint32_t>(), f->bin.as<uint4>(),
+                              f->bsums2.as<uint32_t>(), f->boffs2.as<uint32_t>(), f->cam.tile_shift, f->tiles_x,
+                              f->keys[0].as<uint32_t>(), f->vals[0].as<uint32_t>(), f->key_cap, cnt, scr.hist,
+                              sort_passes(tbits), st));
+    GSR_CUDA(mark(ev, 5, st, capture));
+    uint32_t *kk[2] = {f->keys[0].as<uint32_t>(), f->keys[1].as<uint32_t>()};
     uint32_t *vv[2] = {f->vals[0].as<uint32_t>(), f->vals[1].as<uint32_t>()};
     int res = 0;
-    GSR_CUDA(launch_sort(kk, vv, cnt, cnt + kCntErr, max_k, f->bits, scr, &res, st, true));
+    GSR_CUDA(launch_sort32(kk, vv, cnt + kCntEff, cnt + kCntErr, max_k, tbits, scr, &res, st, true));
     f->sorted = res;
-    GSR_CUDA(mark(ev, 4, st, capture));
-    GSR_CUDA(launch_ranges(f->keys[res].as<uint64_t>(), f->vals[res].as<uint32_t>(), cnt, max_k, f->rec.as<GaussRec>(),
-                           f->rec_sorted.as<GaussRec>(), f->ranges.as<uint2>(), f->n_tiles, st));
+    GSR_CUDA(mark(ev, 6, st, capture));
+    GSR_CUDA(launch_ranges(kk[res], vv[res], cnt, max_k, f->rec.as<GaussRec>(), f->rec_sorted.as<GaussRec>(),
+                           f->ranges.as<uint2>(), f->n_tiles, f->bin.as<uint4>(),
+                           f->has_state ? f->keys64.as<uint64_t>() : nullptr, st));
     GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->chunk, f->head, f->items.as<uint4>(),
                          f->split_tiles.as<uint32_t>(), f->split_slot0.as<uint32_t>(), f->slot_split.as<uint32_t>(),
-                         f->plan_counts.as<uint32_t>(),
-                         st));
-    GSR_CUDA(mark(ev, 5, st, capture));
+                         f->plan_counts.as<uint32_t>(), st));
+    GSR_CUDA(mark(ev, 7, st, capture));
     const CompositeArgs ca = comp_args(f, out);
     GSR_CUDA(launch_composite(ca, f->tile, f->batch, f->n_tiles, f->max_slots, st));
     GSR_CUDA(launch_merge(ca, f->tile, f->max_split, f->max_slots, st));
-    GSR_CUDA(mark(ev, 6, st, capture));
+    GSR_CUDA(mark(ev, 8, st, capture));
     return GS_OK;
 }
 
@@ -498,7 +525,8 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
     const ProjectArgs pa = proj_args(f, s);
     GSR_CUDA(launch_project(pa, st));
     GSR_CUDA(mark(ev, 1, st, false));
-    GSR_CUDA(launch_scan_blocks(pa.block_sums, project_blocks(s->n), f->boffs.as<uint32_t>(), cnt, kMaxInstances, st));
+    GSR_CUDA(launch_scan_blocks(pa.block_sums, pa.block_vis, project_blocks(s->n), f->boffs.as<uint32_t>(),
+                                f->voffs.as<uint32_t>(), cnt, kMaxInstances, st));
     GSR_CUDA(mark(ev, 2, st, false));
     GSR_CUDA(cudaMemcpyAsync(ctx->h_counters, cnt, sizeof(uint32_t) * kCntSlots, cudaMemcpyDeviceToHost, st));
     GSR_CUDA(cudaStreamSynchronize(st));
@@ -696,7 +724,7 @@ gs_status gs_state_view_get(const gs_fwd_state *state, gs_state_view *v)
     v->tiles_x = f->tiles_x;
     v->tiles_y = f->tiles_y;
     v->tile = f->tile;
-    v->keys = f->keys[f->sorted].as<uint64_t>();
+    v->keys = f->has_state ? f->keys64.as<uint64_t>() : nullptr;
     v->vals = f->vals[f->sorted].as<uint32_t>();
     v->ranges = f->ranges.as<uint32_t>();
     v->ntiles = f->ntiles.as<uint32_t>();
@@ -770,8 +798,8 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
             g->proj_args = proj_args(f, scene);
             GSR_CUDA(launch_project(g->proj_args, s2));
             GSR_CUDA(mark(evs, 1, s2, capture));
-            GSR_CUDA(launch_scan_blocks(g->proj_args.block_sums, project_blocks(scene->n), f->boffs.as<uint32_t>(),
-                                        cnt, capacity, s2));
+            GSR_CUDA(launch_scan_blocks(g->proj_args.block_sums, g->proj_args.block_vis, project_blocks(scene->n),
+                                        f->boffs.as<uint32_t>(), f->voffs.as<uint32_t>(), cnt, capacity, s2));
             GSR_CUDA(mark(evs, 2, s2, capture));
             return enqueue_after_scan(f, out, capacity, s2, evs, capture);
         };

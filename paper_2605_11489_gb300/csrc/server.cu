@@ -5,8 +5,9 @@
 // through three stages:
 //   1. admit   - a free in-flight slot takes it; projection + scan (K1, K2) run
 //                on the slot's own stream and the instance count K is copied back.
-//   2. sort    - once K is known the request's sort buffers (keys, values, both
-//                ping-pong halves, sort scratch: about 25 B per instance) are
+//   2. sort    - once K is known the request's sort buffers (tile keys and
+//                values, both ping-pong halves, sorted records, sort scratch:
+//                about 66 B per instance) are
 //                taken from a fixed byte budget; if the budget is short the
 //                request waits, in arrival order. K3-K5 run on the slot stream.
 //   3. compose - whenever the compositing stream is idle, every sorted request
@@ -156,6 +157,7 @@ struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_scan = nullptr, ev_sorted = nullptr;
     DevBuf rec, bin, ntiles, bsums, boffs, ranges, order, counters;
+    DevBuf vsums, voffs, bsums2, boffs2, dkeys[2], dvals[2], dscr;  // depth order (per Gaussian)
     GaussRec *rec_sorted = nullptr;  // in the sort memory
     uint32_t *h_counters = nullptr;  // pinned
     void *sort_mem = nullptr;        // from the arena
@@ -164,7 +166,7 @@ struct Slot {
     int n_tiles = 0, bits = 32;
     int64_t K = 0;
     int sorted = 0;
-    uint64_t *keys[2] = {nullptr, nullptr};
+    uint32_t *keys[2] = {nullptr, nullptr};  // tile keys, in the sort memory
     uint32_t *vals[2] = {nullptr, nullptr};
 };
 
@@ -234,8 +236,7 @@ size_t sort_bytes(int64_t K)
 {
     const int64_t k = std::max<int64_t>(K, 1);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return 2 * up(sizeof(uint64_t) * k) + 2 * up(sizeof(uint32_t) * k) + up(sizeof(GaussRec) * k) +
-           up(sort_scratch_bytes(k));
+    return 4 * up(sizeof(uint32_t) * k) + up(sizeof(GaussRec) * k) + up(sort_scratch_bytes(k));
 }
 
 // Stage 1: projection + scan on the slot's stream; K copied back.
@@ -256,6 +257,15 @@ gs_status admit(gs_server *S, int si, Request *r)
     GSR_CUDA(sl.ntiles.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(n4, 4)));
     GSR_CUDA(sl.bsums.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
     GSR_CUDA(sl.boffs.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
+    GSR_CUDA(sl.vsums.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
+    GSR_CUDA(sl.voffs.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
+    GSR_CUDA(sl.bsums2.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
+    GSR_CUDA(sl.boffs2.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
+    for (int k = 0; k < 2; ++k) {
+        GSR_CUDA(sl.dkeys[k].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(s.n, 1)));
+        GSR_CUDA(sl.dvals[k].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(s.n, 1)));
+    }
+    GSR_CUDA(sl.dscr.ensure(sort_scratch_bytes(std::max<int64_t>(s.n, 1))));
     GSR_CUDA(sl.ranges.ensure(sizeof(uint2) * (size_t)sl.n_tiles));
     GSR_CUDA(sl.order.ensure(sizeof(uint32_t) * (size_t)sl.n_tiles));
     GSR_CUDA(sl.counters.ensure(sizeof(uint32_t) * kCntSlots));
@@ -275,9 +285,11 @@ gs_status admit(gs_server *S, int si, Request *r)
     a.bin = static_cast<uint4 *>(sl.bin.p);
     a.ntiles = static_cast<uint32_t *>(sl.ntiles.p);
     a.block_sums = static_cast<uint32_t *>(sl.bsums.p);
+    a.block_vis = static_cast<uint32_t *>(sl.vsums.p);
     a.counters = cnt;
     GSR_CUDA(launch_project(a, sl.stream));
-    GSR_CUDA(launch_scan_blocks(a.block_sums, nb, static_cast<uint32_t *>(sl.boffs.p), cnt, (1ll << 30) - 1, sl.stream));
+    GSR_CUDA(launch_scan_blocks(a.block_sums, a.block_vis, nb, static_cast<uint32_t *>(sl.boffs.p),
+                                static_cast<uint32_t *>(sl.voffs.p), cnt, (1ll << 30) - 1, sl.stream));
     GSR_CUDA(cudaMemcpyAsync(sl.h_counters, cnt, sizeof(uint32_t) * kCntSlots, cudaMemcpyDeviceToHost, sl.stream));
     GSR_CUDA(cudaEventRecord(sl.ev_scan, sl.stream));
     sl.req = r;
@@ -296,26 +308,37 @@ gs_status enqueue_sort(gs_server *S, Slot &sl)
     const int64_t k1 = std::max<int64_t>(K, 1);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     char *p = static_cast<char *>(sl.sort_mem);
-    sl.keys[0] = reinterpret_cast<uint64_t *>(p);
-    p += up(sizeof(uint64_t) * k1);
-    sl.keys[1] = reinterpret_cast<uint64_t *>(p);
-    p += up(sizeof(uint64_t) * k1);
+    sl.keys[0] = reinterpret_cast<uint32_t *>(p);
+    p += up(sizeof(uint32_t) * k1);
+    sl.keys[1] = reinterpret_cast<uint32_t *>(p);
+    p += up(sizeof(uint32_t) * k1);
     sl.vals[0] = reinterpret_cast<uint32_t *>(p);
     p += up(sizeof(uint32_t) * k1);
     sl.vals[1] = reinterpret_cast<uint32_t *>(p);
     p += up(sizeof(uint32_t) * k1);
     sl.rec_sorted = reinterpret_cast<GaussRec *>(p);
     p += up(sizeof(GaussRec) * k1);
-    SortScratch scr;
+    SortScratch scr, dscr;
     sort_scratch_carve(p, k1, &scr);
-    GSR_CUDA(launch_duplicate(static_cast<uint32_t *>(sl.ntiles.p), static_cast<uint4 *>(sl.bin.p),
-                              static_cast<uint32_t *>(sl.boffs.p), s.n, sl.cam.tile_shift, sl.cam.tiles_x, sl.keys[0],
-                              sl.vals[0], K, cnt, scr.hist, sort_passes(sl.bits), sl.stream));
+    sort_scratch_carve(sl.dscr.p, std::max<int64_t>(s.n, 1), &dscr);
+    // the visible Gaussians in depth order, then their tile keys in that order, stable by tile
+    uint32_t *dk[2] = {static_cast<uint32_t *>(sl.dkeys[0].p), static_cast<uint32_t *>(sl.dkeys[1].p)};
+    uint32_t *dv[2] = {static_cast<uint32_t *>(sl.dvals[0].p), static_cast<uint32_t *>(sl.dvals[1].p)};
+    GSR_CUDA(launch_compact(static_cast<uint32_t *>(sl.ntiles.p), static_cast<uint4 *>(sl.bin.p),
+                            static_cast<uint32_t *>(sl.voffs.p), s.n, dk[0], dv[0], dscr.hist, sl.stream));
+    int dres = 0;
+    GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, cnt + kCntErr, s.n, 32, dscr, &dres, sl.stream, true));
+    const int tbits = sl.bits - 32;
+    GSR_CUDA(launch_duplicate(dv[dres], cnt + kCntVisible, s.n, static_cast<uint32_t *>(sl.ntiles.p),
+                              static_cast<uint4 *>(sl.bin.p), static_cast<uint32_t *>(sl.bsums2.p),
+                              static_cast<uint32_t *>(sl.boffs2.p), sl.cam.tile_shift, sl.cam.tiles_x, sl.keys[0],
+                              sl.vals[0], K, cnt, scr.hist, sort_passes(tbits), sl.stream));
     int res = 0;
-    GSR_CUDA(launch_sort(sl.keys, sl.vals, cnt, cnt + kCntErr, K, sl.bits, scr, &res, sl.stream, true));
+    GSR_CUDA(launch_sort32(sl.keys, sl.vals, cnt + kCntEff, cnt + kCntErr, K, tbits, scr, &res, sl.stream, true));
     sl.sorted = res;
     GSR_CUDA(launch_ranges(sl.keys[res], sl.vals[res], cnt, K, static_cast<const GaussRec *>(sl.rec.p), sl.rec_sorted,
-                           static_cast<uint2 *>(sl.ranges.p), sl.n_tiles, sl.stream));
+                           static_cast<uint2 *>(sl.ranges.p), sl.n_tiles, static_cast<const uint4 *>(sl.bin.p),
+                           nullptr, sl.stream));
     GSR_CUDA(launch_tile_order(static_cast<const uint2 *>(sl.ranges.p), sl.n_tiles, static_cast<uint32_t *>(sl.order.p),
                                sl.stream));
     GSR_CUDA(cudaEventRecord(sl.ev_sorted, sl.stream));

@@ -1,12 +1,16 @@
-// K4: stable LSD radix sort of the (tile, depth) keys with their Gaussian
-// indices, "onesweep" style (Adinets & Merrill, 2022): one pass over the keys
-// builds every digit's global histogram, then each 8-bit digit is sorted in a
-// single pass over the data, with partitions publishing their per-digit counts
-// and resolving their global offsets by decoupled lookback.
+// K4: stable LSD radix sort of keys (32- or 64-bit) with 32-bit values,
+// "onesweep" style (Adinets & Merrill, 2022): every digit's global histogram
+// is known before the first pass (built by the kernel that wrote the keys, or
+// by one pass over them), then each 8-bit digit is sorted in a single pass
+// over the data, with partitions publishing their per-digit counts and
+// resolving their global offsets by decoupled lookback.
 //
-// Only the low `bits` bits are sorted: 32 bits of fp32 depth (positive, so its
-// bit pattern orders like the value) plus ceil(log2(n_tiles)) tile bits.
-// Stability (equal keys keep index order) gives the (depth, index) tie-break.
+// The render sorts twice: the visible Gaussians by their 32-bit depth key
+// (fp32 depth is positive, so its bit pattern orders like the value), then,
+// after the keys are duplicated per tile in that order, the instances by tile
+// id alone. Both are stable, so the result is ordered by (tile, depth, index),
+// the order of a stable sort of (tile << 32 | depth) keys. Only the low `bits`
+// bits are sorted.
 //
 // Partition ids are taken from an atomic ticket, so a partition only ever waits
 // for partitions that are already running. Every wait is still bounded: a
@@ -29,26 +33,31 @@ constexpr uint32_t kFlagMask = 3u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 constexpr uint32_t kMaxSpins = 1u << 22;
 constexpr int kLook = 8;  // predecessors read per lookback round trip
-constexpr size_t kPassSmem = (size_t)kPart * 8 + (size_t)kPart * 4 + (size_t)kWarps * kRadix * 4;
+template <typename KeyT>
+constexpr size_t pass_smem()
+{
+    return (size_t)kPart * sizeof(KeyT) + (size_t)kPart * 4 + (size_t)kWarps * kRadix * 4;
+}
 
 __device__ __forceinline__ uint32_t ld_vol(const uint32_t *p) { return *reinterpret_cast<const volatile uint32_t *>(p); }
 __device__ __forceinline__ void st_vol(uint32_t *p, uint32_t v) { *reinterpret_cast<volatile uint32_t *>(p) = v; }
 
-__global__ void __launch_bounds__(kThreads) k_sort_hist(const uint64_t *__restrict__ keys,
-                                                        const uint32_t *__restrict__ counters, int passes,
+template <typename KeyT>
+__global__ void __launch_bounds__(kThreads) k_sort_hist(const KeyT *__restrict__ keys,
+                                                        const uint32_t *__restrict__ count, int passes,
                                                         uint32_t *__restrict__ hist)
 {
     __shared__ uint32_t sh[8 * kRadix];
     for (int i = threadIdx.x; i < 8 * kRadix; i += kThreads) sh[i] = 0;
     __syncthreads();
-    const uint32_t K = counters[kCntEff];
+    const uint32_t K = *count;
     const int lane = threadIdx.x & 31;
     const uint32_t warp_global = (blockIdx.x * kThreads + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
     for (uint32_t base = warp_global * 32; base < K; base += nwarps * 32) {
         const uint32_t idx = base + lane;
         const bool valid = idx < K;
-        const uint64_t key = valid ? keys[idx] : 0ull;
+        const uint64_t key = valid ? (uint64_t)keys[idx] : 0ull;
         for (int p = 0; p < passes; ++p) {
             const uint32_t d = valid ? (uint32_t)(key >> (8 * p)) & 0xFFu : 0x100u;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -87,23 +96,25 @@ __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_
     eb = pb + ib - b;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_sort_pass(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                                                        uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                        const uint32_t *__restrict__ counters, int shift,
-                                                        const uint32_t *__restrict__ hist, uint32_t *status,
-                                                        uint32_t *part_ctr, uint32_t *err)
+// 64-bit keys: 80 registers and the largest carveout fit three partitions per
+// SM; 32-bit keys fit four.
+template <typename KeyT>
+__global__ void __launch_bounds__(kThreads, sizeof(KeyT) == 8 ? 3 : 4)
+    k_sort_pass(const KeyT *__restrict__ kin, const uint32_t *__restrict__ vin, KeyT *__restrict__ kout,
+                uint32_t *__restrict__ vout, const uint32_t *__restrict__ count, int shift,
+                const uint32_t *__restrict__ hist, uint32_t *status, uint32_t *part_ctr, uint32_t *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *s_vals = reinterpret_cast<uint32_t *>(smem + (size_t)kPart * 8);
-    uint32_t *s_whist = reinterpret_cast<uint32_t *>(smem + (size_t)kPart * 12);
+    KeyT *s_keys = reinterpret_cast<KeyT *>(smem);
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(smem + (size_t)kPart * sizeof(KeyT));
+    uint32_t *s_whist = reinterpret_cast<uint32_t *>(smem + (size_t)kPart * (sizeof(KeyT) + 4));
     __shared__ uint32_t s_base[kRadix];
     __shared__ uint32_t s_start[kRadix];
     __shared__ uint32_t s_tmp[2 * kWarps];
     __shared__ uint32_t s_part;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t K = counters[kCntEff];
+    const uint32_t K = *count;
     const uint32_t nparts = (K + kPart - 1) / kPart;
     if (tid == 0) s_part = atomicAdd(part_ctr, 1u);
     for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
@@ -112,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(const uint64_t *__res
     if (part >= nparts) return;
     const uint32_t base = part * kPart;
 
-    uint64_t k[kItems];
+    KeyT k[kItems];
     uint32_t v[kItems], rk[kItems];
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
@@ -121,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(const uint64_t *__res
             k[j] = kin[idx];
             v[j] = vin[idx];
         } else {
-            k[j] = ~0ull;
+            k[j] = ~KeyT(0);
             v[j] = 0u;
         }
     }
@@ -211,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sort_pass(const uint64_t *__res
     __syncthreads();
     const uint32_t nval = min((uint32_t)kPart, K - base);
     for (uint32_t i = tid; i < nval; i += kThreads) {
-        const uint64_t key = s_keys[i];
+        const KeyT key = s_keys[i];
         const uint32_t d = (uint32_t)(key >> shift) & 0xFFu;
         const uint32_t g = s_base[d] + (i - s_start[d]);
         kout[g] = key;
@@ -240,24 +251,28 @@ void sort_scratch_carve(void *base, int64_t capacity, SortScratch *s)
     s->max_parts = parts_for(capacity) + 1;
 }
 
-cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *counters, uint32_t *err_word,
-                        int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready)
+namespace {
+
+template <typename KeyT>
+cudaError_t sort_impl(KeyT *keys[2], uint32_t *vals[2], const uint32_t *count, uint32_t *err_word, int64_t max_k,
+                      int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready)
 {
     const int passes = sort_passes(bits);
     *result = passes & 1;
     if (max_k <= 0) return cudaSuccess;
     const int64_t parts = parts_for(max_k);
-    if (parts > scr.max_parts || passes > 8) return cudaErrorInvalidValue;
+    if (parts > scr.max_parts || passes > (int)sizeof(KeyT)) return cudaErrorInvalidValue;
+    constexpr size_t smem = pass_smem<KeyT>();
     // once per device, outside any stream capture (the first sort on a device is never captured)
     static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
+        e = cudaFuncSetAttribute(k_sort_pass<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        // three partitions per SM need the largest shared-memory carveout
-        e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributePreferredSharedMemoryCarveout,
+        // several partitions per SM need the largest shared-memory carveout
+        e = cudaFuncSetAttribute(k_sort_pass<KeyT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
@@ -270,18 +285,32 @@ cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *co
     if (e != cudaSuccess) return e;
     if (!hist_ready) {
         const int64_t hist_blocks = std::min<int64_t>((max_k + kThreads * 8 - 1) / (kThreads * 8), 152 * 8);
-        k_sort_hist<<<(unsigned)hist_blocks, kThreads, 0, s>>>(keys[0], counters, passes, scr.hist);
+        k_sort_hist<KeyT><<<(unsigned)hist_blocks, kThreads, 0, s>>>(keys[0], count, passes, scr.hist);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     for (int p = 0; p < passes; ++p) {
         const int src = p & 1, dst = src ^ 1;
-        k_sort_pass<<<(unsigned)parts, kThreads, kPassSmem, s>>>(keys[src], vals[src], keys[dst], vals[dst], counters,
-                                                                 8 * p, scr.hist + p * kRadix,
-                                                                 scr.status + (size_t)p * parts * kRadix,
-                                                                 scr.part_ctr + p, err_word);
+        k_sort_pass<KeyT><<<(unsigned)parts, kThreads, smem, s>>>(keys[src], vals[src], keys[dst], vals[dst], count,
+                                                                  8 * p, scr.hist + p * kRadix,
+                                                                  scr.status + (size_t)p * parts * kRadix,
+                                                                  scr.part_ctr + p, err_word);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *counters, uint32_t *err_word,
+                        int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready)
+{
+    return sort_impl<uint64_t>(keys, vals, counters + kCntEff, err_word, max_k, bits, scr, result, s, hist_ready);
+}
+
+cudaError_t launch_sort32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *count, uint32_t *err_word,
+                          int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready)
+{
+    return sort_impl<uint32_t>(keys, vals, count, err_word, max_k, bits, scr, result, s, hist_ready);
 }
 
 }  // namespace gsr
