@@ -84,8 +84,10 @@ typedef struct {
 enum {
     GS_EMIT_BWD_STATE = 1u,       /* keep what gs_render_backward needs */
     GS_TIME_STAGES = 2u,          /* record CUDA events at every stage boundary (see gs_frame_stats) */
-    GS_COUNT_PAIRS = 4u           /* diagnostic: count evaluated and blended (pixel, Gaussian) pairs
+    GS_COUNT_PAIRS = 4u,          /* diagnostic: count evaluated and blended (pixel, Gaussian) pairs
                                      (plain forward only; adds a synchronisation; see gs_frame_stats) */
+    GS_TIME_COMPOSITE = 8u        /* record CUDA events around the compositing stage only (stage_ms[7]):
+                                     two events per frame instead of nine (ignored with GS_TIME_STAGES) */
 };
 
 typedef struct {

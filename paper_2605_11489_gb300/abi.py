@@ -23,6 +23,7 @@ GS_ERR_CAPACITY = -5
 GS_ERR_CANCELLED = -6
 GS_EMIT_BWD_STATE = 1
 GS_TIME_STAGES = 2
+GS_TIME_COMPOSITE = 8
 GS_COUNT_PAIRS = 4
 STAGES = ("project", "scan", "compact", "depth_sort", "duplicate", "tile_sort", "ranges", "composite")
 

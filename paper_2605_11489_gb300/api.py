@@ -88,8 +88,9 @@ def opts_struct(tile=0, batch=0, bg=(0.0, 0.0, 0.0), state=False, timed=False, c
     o.tile, o.batch, o.chunk, o.head = int(tile), int(batch), int(chunk), int(head)
     for k in range(3):
         o.bg[k] = float(bg[k])
-    o.flags = (abi.GS_EMIT_BWD_STATE if state else 0) | (abi.GS_TIME_STAGES if timed else 0) | \
-        (abi.GS_COUNT_PAIRS if count else 0)
+    # timed: True = events at every stage boundary, "composite" = around compositing only
+    tflag = abi.GS_TIME_COMPOSITE if timed == "composite" else (abi.GS_TIME_STAGES if timed else 0)
+    o.flags = (abi.GS_EMIT_BWD_STATE if state else 0) | tflag | (abi.GS_COUNT_PAIRS if count else 0)
     return o
 
 

@@ -103,8 +103,11 @@ struct Frame {
 // path) or retargeted into a graph's event-record nodes before each replay.
 struct StageTimer {
     static constexpr int kBounds = 9;  // before K1 | K1 | K2 | K3a | K4a | K3b | K4b | K5+plan | K6
+    static constexpr uint32_t kAll = (1u << kBounds) - 1u;
+    static constexpr uint32_t kCompositeOnly = (1u << 7) | (1u << 8);  // around K6 only: two events
     static constexpr int kRing = 512;
     std::vector<cudaEvent_t> ev;
+    std::vector<uint32_t> slot_mask;  // which bounds each slot's frame recorded
     int head = 0;
     int64_t in_ring = 0;  // recorded slots not yet folded
     double sum_ms[kBounds - 1] = {};
@@ -117,6 +120,7 @@ struct StageTimer {
     {
         if (!ev.empty()) return cudaSuccess;
         ev.resize((size_t)kRing * kBounds, nullptr);
+        slot_mask.assign(kRing, 0u);
         for (auto &e : ev) {
             cudaError_t r = cudaEventCreate(&e);
             if (r != cudaSuccess) return r;
@@ -126,10 +130,13 @@ struct StageTimer {
     void fold(int slot)
     {
         cudaEvent_t *e = &ev[(size_t)slot * kBounds];
-        cudaEventSynchronize(e[kBounds - 1]);
+        const uint32_t m = slot_mask[slot];
+        if (!m) return;
+        cudaEventSynchronize(e[31 - __builtin_clz(m)]);
         bool ok = true;
-        float ms[kBounds - 1];
-        for (int k = 0; k < kBounds - 1 && ok; ++k) ok = cudaEventElapsedTime(&ms[k], e[k], e[k + 1]) == cudaSuccess;
+        float ms[kBounds - 1] = {};
+        for (int k = 0; k < kBounds - 1 && ok; ++k)
+            if ((m >> k & 1u) && (m >> (k + 1) & 1u)) ok = cudaEventElapsedTime(&ms[k], e[k], e[k + 1]) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();  // do not leave the failure for the next launch check
             return;
@@ -137,14 +144,16 @@ struct StageTimer {
         for (int k = 0; k < kBounds - 1; ++k) sum_ms[k] += ms[k];
         ++folded;
     }
-    // events of the next frame slot (the slot's previous frame is folded first)
-    cudaEvent_t *next()
+    // events of the next frame slot, recording the bounds in `mask` (the
+    // slot's previous frame is folded first)
+    cudaEvent_t *next(uint32_t mask = kAll)
     {
         if (in_ring == kRing) {
             fold(head);
             --in_ring;
         }
         cudaEvent_t *e = &ev[(size_t)head * kBounds];
+        slot_mask[head] = mask;
         head = (head + 1) % kRing;
         ++in_ring;
         return e;
@@ -164,6 +173,21 @@ struct StageTimer {
         for (double &v : sum_ms) v = 0;
     }
 };
+
+// Stage-boundary events of one frame: `ev` (nullptr = untimed), the bounds
+// recorded, and whether the stream is being captured (external event nodes).
+struct Marks {
+    cudaEvent_t *ev = nullptr;
+    uint32_t mask = 0;
+    bool capture = false;
+};
+
+uint32_t timing_mask(uint32_t flags)
+{
+    if (flags & GS_TIME_STAGES) return StageTimer::kAll;
+    if (flags & GS_TIME_COMPOSITE) return StageTimer::kCompositeOnly;
+    return 0u;
+}
 
 }  // namespace
 
@@ -276,6 +300,7 @@ struct gs_graph {
     bool timed = false;
     StageTimer timer;
     cudaGraphNode_t ev_node[StageTimer::kBounds] = {};
+    uint32_t mark_mask = 0;  // stage bounds the graph records
 };
 
 namespace gsr {
@@ -444,15 +469,14 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
 }
 
 // K3..K6 given capacity `cap` (graph path) or the exact count (plain path).
-// Boundary event k (nullptr = untimed); graph capture records external nodes.
-cudaError_t mark(cudaEvent_t *ev, int k, cudaStream_t st, bool capture)
+// Boundary event k, if timed and in the mask; graph capture records external nodes.
+cudaError_t mark(const Marks &m, int k, cudaStream_t st)
 {
-    if (!ev) return cudaSuccess;
-    return capture ? cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal) : cudaEventRecord(ev[k], st);
+    if (!m.ev || !(m.mask >> k & 1u)) return cudaSuccess;
+    return m.capture ? cudaEventRecordWithFlags(m.ev[k], st, cudaEventRecordExternal) : cudaEventRecord(m.ev[k], st);
 }
 
-gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cudaStream_t st, cudaEvent_t *ev = nullptr,
-                             bool capture = false)
+gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cudaStream_t st, const Marks &mk = Marks{})
 {
     uint32_t *cnt = f->counters.as<uint32_t>();
     SortScratch scr;
@@ -460,36 +484,36 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     // K3a, K4a: the visible Gaussians in depth order
     GSR_CUDA(launch_compact(f->ntiles.as<uint32_t>(), f->bin.as<uint4>(), f->voffs.as<uint32_t>(), f->n,
                             f->dkeys[0].as<uint32_t>(), f->dvals[0].as<uint32_t>(), scr.hist, st));
-    GSR_CUDA(mark(ev, 3, st, capture));
+    GSR_CUDA(mark(mk, 3, st));
     uint32_t *dk[2] = {f->dkeys[0].as<uint32_t>(), f->dkeys[1].as<uint32_t>()};
     uint32_t *dv[2] = {f->dvals[0].as<uint32_t>(), f->dvals[1].as<uint32_t>()};
     int dres = 0;
     GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, cnt + kCntErr, f->n, 32, scr, &dres, st, true));
-    GSR_CUDA(mark(ev, 4, st, capture));
+    GSR_CUDA(mark(mk, 4, st));
     // K3b, K4b: tile keys in depth order, then stable by tile
     const int tbits = f->bits - 32;
     GSR_CUDA(launch_duplicate(dv[dres], cnt + kCntVisible, f->n, f->ntiles.as<uint32_t>(), f->bin.as<uint4>(),
                               f->bsums2.as<uint32_t>(), f->boffs2.as<uint32_t>(), f->cam.tile_shift, f->tiles_x,
                               f->keys[0].as<uint32_t>(), f->vals[0].as<uint32_t>(), f->key_cap, cnt, scr.hist,
                               sort_passes(tbits), st));
-    GSR_CUDA(mark(ev, 5, st, capture));
+    GSR_CUDA(mark(mk, 5, st));
     uint32_t *kk[2] = {f->keys[0].as<uint32_t>(), f->keys[1].as<uint32_t>()};
     uint32_t *vv[2] = {f->vals[0].as<uint32_t>(), f->vals[1].as<uint32_t>()};
     int res = 0;
     GSR_CUDA(launch_sort32(kk, vv, cnt + kCntEff, cnt + kCntErr, max_k, tbits, scr, &res, st, true));
     f->sorted = res;
-    GSR_CUDA(mark(ev, 6, st, capture));
+    GSR_CUDA(mark(mk, 6, st));
     GSR_CUDA(launch_ranges(kk[res], vv[res], cnt, max_k, f->rec.as<GaussRec>(), f->rec_sorted.as<GaussRec>(),
                            f->ranges.as<uint2>(), f->n_tiles, f->bin.as<uint4>(),
                            f->has_state ? f->keys64.as<uint64_t>() : nullptr, st));
     GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->chunk, f->head, f->items.as<uint4>(),
                          f->split_tiles.as<uint32_t>(), f->split_slot0.as<uint32_t>(), f->slot_split.as<uint32_t>(),
                          f->plan_counts.as<uint32_t>(), st));
-    GSR_CUDA(mark(ev, 7, st, capture));
+    GSR_CUDA(mark(mk, 7, st));
     const CompositeArgs ca = comp_args(f, out);
     GSR_CUDA(launch_composite(ca, f->tile, f->batch, f->n_tiles, f->max_slots, st));
     GSR_CUDA(launch_merge(ca, f->tile, f->max_split, f->max_slots, st));
-    GSR_CUDA(mark(ev, 8, st, capture));
+    GSR_CUDA(mark(mk, 8, st));
     return GS_OK;
 }
 
@@ -515,19 +539,20 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
     f->count_pairs = (o->flags & GS_COUNT_PAIRS) != 0;
     if (r != GS_OK) return r;
     uint32_t *cnt = f->counters.as<uint32_t>();
-    cudaEvent_t *ev = nullptr;
-    if (o->flags & GS_TIME_STAGES) {
+    Marks mk;
+    mk.mask = timing_mask(o->flags);
+    if (mk.mask) {
         GSR_CUDA(ctx->timer.init());
-        ev = ctx->timer.next();
+        mk.ev = ctx->timer.next(mk.mask);
     }
     GSR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * kCntSlots, st));
-    GSR_CUDA(mark(ev, 0, st, false));
+    GSR_CUDA(mark(mk, 0, st));
     const ProjectArgs pa = proj_args(f, s);
     GSR_CUDA(launch_project(pa, st));
-    GSR_CUDA(mark(ev, 1, st, false));
+    GSR_CUDA(mark(mk, 1, st));
     GSR_CUDA(launch_scan_blocks(pa.block_sums, pa.block_vis, project_blocks(s->n), f->boffs.as<uint32_t>(),
                                 f->voffs.as<uint32_t>(), cnt, kMaxInstances, st));
-    GSR_CUDA(mark(ev, 2, st, false));
+    GSR_CUDA(mark(mk, 2, st));
     GSR_CUDA(cudaMemcpyAsync(ctx->h_counters, cnt, sizeof(uint32_t) * kCntSlots, cudaMemcpyDeviceToHost, st));
     GSR_CUDA(cudaStreamSynchronize(st));
     const uint64_t K = (uint64_t)ctx->h_counters[kCntTotal] | ((uint64_t)ctx->h_counters[kCntTotalHi] << 32);
@@ -543,7 +568,7 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
     }
     if ((r = frame_plan(f, f->K)) != GS_OK) return r;
     // counters[kCntEff] was clamped to kMaxInstances; K fits, so it equals K.
-    r = enqueue_after_scan(f, out, f->K, st, ev, false);
+    r = enqueue_after_scan(f, out, f->K, st, mk);
     if (r != GS_OK || !f->count_pairs) return r;
     GSR_CUDA(cudaMemcpyAsync(ctx->h_counters, cnt, sizeof(uint32_t) * kCntSlots, cudaMemcpyDeviceToHost, st));
     GSR_CUDA(cudaStreamSynchronize(st));
@@ -784,24 +809,28 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
     // warm-up (sets kernel attributes outside capture), then capture
     if (r == GS_OK) {
         uint32_t *cnt = f->counters.as<uint32_t>();
-        g->timed = (opts->flags & GS_TIME_STAGES) != 0;
+        g->mark_mask = timing_mask(opts->flags);
+        g->timed = g->mark_mask != 0u;
         cudaEvent_t *cap_ev = nullptr;
         if (g->timed) {
             cudaError_t e = g->timer.init();
             if (e != cudaSuccess) r = cuda_fail(e, "stage timer");
-            else cap_ev = g->timer.next();
+            else cap_ev = g->timer.next(g->mark_mask);
         }
         auto enqueue = [&](cudaStream_t s2, bool capture) -> gs_status {
-            cudaEvent_t *evs = capture ? cap_ev : nullptr;
+            Marks evs;
+            evs.ev = capture ? cap_ev : nullptr;
+            evs.mask = g->mark_mask;
+            evs.capture = capture;
             GSR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * kCntPerFrame, s2));
-            GSR_CUDA(mark(evs, 0, s2, capture));
+            GSR_CUDA(mark(evs, 0, s2));
             g->proj_args = proj_args(f, scene);
             GSR_CUDA(launch_project(g->proj_args, s2));
-            GSR_CUDA(mark(evs, 1, s2, capture));
+            GSR_CUDA(mark(evs, 1, s2));
             GSR_CUDA(launch_scan_blocks(g->proj_args.block_sums, g->proj_args.block_vis, project_blocks(scene->n),
                                         f->boffs.as<uint32_t>(), f->voffs.as<uint32_t>(), cnt, capacity, s2));
-            GSR_CUDA(mark(evs, 2, s2, capture));
-            return enqueue_after_scan(f, out, capacity, s2, evs, capture);
+            GSR_CUDA(mark(evs, 2, s2));
+            return enqueue_after_scan(f, out, capacity, s2, evs);
         };
         if (r == GS_OK) r = enqueue(st, false);
         if (r == GS_OK) {
@@ -850,10 +879,11 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
                     cudaEvent_t e = nullptr;
                     cudaGraphEventRecordNodeGetEvent(nd, &e);
                     for (int k = 0; k < StageTimer::kBounds; ++k)
-                        if (cap_ev[k] == e) g->ev_node[k] = nd;
+                        if ((g->mark_mask >> k & 1u) && cap_ev[k] == e) g->ev_node[k] = nd;
                 }
                 for (int k = 0; k < StageTimer::kBounds; ++k)
-                    if (!g->ev_node[k]) r = fail(GS_ERR_CUDA, "stage event node not found in captured graph");
+                    if ((g->mark_mask >> k & 1u) && !g->ev_node[k])
+                        r = fail(GS_ERR_CUDA, "stage event node not found in captured graph");
                 g->timer.reset();  // the capture-time event set was never recorded
             }
         }
@@ -882,8 +912,9 @@ gs_status gs_graph_render(gs_graph *g, const gs_camera *cam, gs_stream stream)
         GSR_CUDA(cudaGraphExecKernelNodeSetParams(g->exec, nd, &kp));
     }
     if (g->timed) {
-        cudaEvent_t *ev = g->timer.next();
-        for (int k = 0; k < StageTimer::kBounds; ++k) GSR_CUDA(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_node[k], ev[k]));
+        cudaEvent_t *ev = g->timer.next(g->mark_mask);
+        for (int k = 0; k < StageTimer::kBounds; ++k)
+            if (g->mark_mask >> k & 1u) GSR_CUDA(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_node[k], ev[k]));
     }
     GSR_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
     return GS_OK;
