@@ -200,31 +200,54 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
         for (int w = 0; w < BATCH / 32; ++w) {
             // records of this group of 32 whose rectangle reaches the warp's block
             const uint32_t kk = (uint32_t)w * 32u + (uint32_t)lane;
-            bool hit = false;
+            uint32_t lo = 0xFFFFFFFFu, hi = 0u;  // an empty rectangle past the batch's end
             if (kk < cnt) {
-                const uint32_t lo = __float_as_uint(recs[kk].r2.z), hi = __float_as_uint(recs[kk].r2.w);
-                hit = (hi >> 16) >= wy0 && (lo >> 16) <= wy1 && (hi & 0xFFFFu) >= wx0 && (lo & 0xFFFFu) <= wx1;
+                lo = __float_as_uint(recs[kk].r2.z);
+                hi = __float_as_uint(recs[kk].r2.w);
             }
+            const bool hit = (hi >> 16) >= wy0 && (lo >> 16) <= wy1 && (hi & 0xFFFFu) >= wx0 && (lo & 0xFFFFu) <= wx1;
             uint32_t m = __ballot_sync(0xffffffffu, hit);
             // this lane's own list: the hit records whose rectangle holds its
-            // pixel (a warp-uniform pass over the hits, one rect test each),
-            // then only those are blended, each lane at its own pace
+            // pixel. A warp-uniform pass over the hits, four at a time, with
+            // each rectangle taken from the lane that loaded it; then only
+            // those records are blended, each lane at its own pace.
             uint32_t mine = 0u;
+            auto holds = [&](int j) {
+                const uint32_t l = __shfl_sync(0xffffffffu, lo, j), h = __shfl_sync(0xffffffffu, hi, j);
+                return upx >= (l & 0xFFFFu) && upx <= (h & 0xFFFFu) && upy >= (l >> 16) && upy <= (h >> 16);
+            };
             while (m) {
-                const int j = __ffs(m) - 1;
+                const int j0 = __ffs(m) - 1;
                 m &= m - 1u;
-                const float4 r2 = recs[w * 32 + j].r2;
-                if (rect_contains(r2, upx, upy)) mine |= 1u << j;
+                const int j1 = m ? __ffs(m) - 1 : j0;
+                m &= m - 1u;
+                const int j2 = m ? __ffs(m) - 1 : j0;
+                m &= m - 1u;
+                const int j3 = m ? __ffs(m) - 1 : j0;
+                m &= m - 1u;
+                const bool h0 = holds(j0), h1 = holds(j1), h2 = holds(j2), h3 = holds(j3);
+                mine |= (h0 ? 1u << j0 : 0u) | (h1 ? 1u << j1 : 0u) | (h2 ? 1u << j2 : 0u) | (h3 ? 1u << j3 : 0u);
             }
             if (s.done) mine = 0u;
-            while (mine) {
-                const uint32_t k = (uint32_t)w * 32u + (uint32_t)(__ffs(mine) - 1);
+            if (mine) {  // the next record's loads are issued before the current one is blended
+                uint32_t k = (uint32_t)w * 32u + (uint32_t)(__ffs(mine) - 1);
                 mine &= mine - 1u;
-                const GaussRec &R = recs[k];
-                if (blend<GRAD, STATE, COUNT>(s, R.r0, R.r1, R.r2, pxc, pyc, pos_b + k)) {
-                    s.done = true;
-                    s.stopped = true;
-                    break;
+                float4 a0 = recs[k].r0, a1 = recs[k].r1, a2 = recs[k].r2;
+                for (;;) {
+                    const bool more = mine != 0u;
+                    const uint32_t kn = more ? (uint32_t)w * 32u + (uint32_t)(__ffs(mine) - 1) : k;
+                    mine &= mine - 1u;
+                    const float4 b0 = recs[kn].r0, b1 = recs[kn].r1, b2 = recs[kn].r2;
+                    if (blend<GRAD, STATE, COUNT>(s, a0, a1, a2, pxc, pyc, pos_b + k)) {
+                        s.done = true;
+                        s.stopped = true;
+                        break;
+                    }
+                    if (!more) break;
+                    k = kn;
+                    a0 = b0;
+                    a1 = b1;
+                    a2 = b2;
                 }
             }
         }
