@@ -177,9 +177,13 @@ __global__ void __launch_bounds__(kProjThreads) k_sorted_counts(const uint32_t *
 }
 
 // K3b, second half: every depth-sorted Gaussian's keys, key = tile id (32-bit)
-// and value = Gaussian index, for every tile of its support rectangle, at
-// offsets continuing the scan of K3b's block sums; counts the tile digits.
-// Keys past `capacity` are not written (the overflow bit is set).
+// and value = Gaussian index, for every tile of its support rectangle (rows,
+// then columns), at offsets continuing the scan of K3b's block sums; counts
+// the tile digits. Keys past `capacity` are not written (the overflow bit is
+// set). Each warp owns 128 consecutive sorted Gaussians and deals their keys
+// out to consecutive lanes, so that the stores are coalesced: lane l emits the
+// warp's keys l, l + 32, ..., finding each key's Gaussian by a binary search
+// over the warp's prefix of tile counts.
 __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__restrict__ dvals,
                                                             const uint32_t *__restrict__ vcount,
                                                             const uint32_t *__restrict__ ntiles,
@@ -189,39 +193,69 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
                                                             uint32_t *__restrict__ vals, unsigned long long capacity,
                                                             uint32_t *counters, uint32_t *__restrict__ hist, int passes)
 {
-    __shared__ uint32_t s_warp[kProjThreads / 32];
+    constexpr int kWarps = kProjThreads / 32, kPerWarp = 128;
+    __shared__ uint32_t s_warp[kWarps];
     __shared__ uint32_t s_hist[2 * 256];
+    __shared__ uint32_t s_pre[kWarps][kPerWarp + 1];  // exclusive prefix of tile counts, then the warp's total
+    __shared__ uint32_t s_idx[kWarps][kPerWarp];      // Gaussian index
+    __shared__ uint32_t s_org[kWarps][kPerWarp];      // first tile of its rectangle: tx | ty << 16
+    __shared__ uint32_t s_wid[kWarps][kPerWarp];      // width of its rectangle in tiles
     for (int i = threadIdx.x; i < 2 * 256; i += kProjThreads) s_hist[i] = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t V = *vcount;
     const uint32_t i0 = (blockIdx.x * kProjThreads + threadIdx.x) * 4;
-    uint32_t idx[4], cnt[4], mine = 0;
+    uint32_t cnt[4], mine = 0;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        idx[g] = i0 + g < V ? dvals[i0 + g] : 0u;
-        cnt[g] = i0 + g < V ? ntiles[idx[g]] : 0u;
+        const uint32_t idx = i0 + g < V ? dvals[i0 + g] : 0u;
+        cnt[g] = i0 + g < V ? ntiles[idx] : 0u;
+        uint32_t org = 0, wid = 1;
+        if (cnt[g]) {
+            const uint4 b = bin[idx];
+            const uint32_t x0 = (b.y & 0xFFFFu) >> tile_shift, y0 = (b.y >> 16) >> tile_shift;
+            const uint32_t x1 = (b.z & 0xFFFFu) >> tile_shift;
+            org = x0 | (y0 << 16);
+            wid = x1 - x0 + 1;
+        }
+        s_idx[warp][lane * 4 + g] = idx;
+        s_org[warp][lane * 4 + g] = org;
+        s_wid[warp][lane * 4 + g] = wid;
         mine += cnt[g];
     }
     uint32_t total;
-    unsigned long long off = (unsigned long long)block_offs[blockIdx.x] + block_excl(mine, s_warp, total);
-    bool overflow = false;
+    const uint32_t excl = block_excl(mine, s_warp, total);  // (block-wide; includes a barrier)
+    // the warp's offsets: prefix within the warp, the warp's first key's global offset
+    const uint32_t warp_first = __shfl_sync(0xffffffffu, excl, 0);
+    uint32_t run = excl - warp_first;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        if (cnt[g] == 0) continue;
-        const uint4 b = bin[idx[g]];
-        const int x0 = (b.y & 0xFFFFu) >> tile_shift, y0 = (b.y >> 16) >> tile_shift;
-        const int x1 = (b.z & 0xFFFFu) >> tile_shift, y1 = (b.z >> 16) >> tile_shift;
-        for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1; ++tx) {
-                const uint32_t tile = (uint32_t)(ty * tiles_x + tx);
-                if (off < capacity) {
-                    keys[off] = tile;
-                    vals[off] = idx[g];
-                    for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + ((tile >> (8 * p)) & 0xFFu)], 1u);
-                } else {
-                    overflow = true;
-                }
-                ++off;
-            }
+        s_pre[warp][lane * 4 + g] = run;
+        run += cnt[g];
+    }
+    if (lane == 31) s_pre[warp][kPerWarp] = run;
+    __syncwarp();
+    const uint32_t T = s_pre[warp][kPerWarp];
+    const unsigned long long base = (unsigned long long)block_offs[blockIdx.x] + warp_first;
+    bool overflow = false;
+    for (uint32_t e = (uint32_t)lane; e < T; e += 32) {
+        int lo = 0, hi = kPerWarp;  // last j with s_pre[j] <= e (it has a nonzero count)
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_pre[warp][mid] <= e) lo = mid + 1;
+            else hi = mid;
+        }
+        const int j = lo - 1;
+        const uint32_t li = e - s_pre[warp][j], w = s_wid[warp][j], org = s_org[warp][j];
+        const uint32_t q = li / w;
+        const uint32_t tile = ((org >> 16) + q) * (uint32_t)tiles_x + (org & 0xFFFFu) + (li - q * w);
+        const unsigned long long off = base + e;
+        if (off < capacity) {
+            keys[off] = tile;
+            vals[off] = s_idx[warp][j];
+            for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + ((tile >> (8 * p)) & 0xFFu)], 1u);
+        } else {
+            overflow = true;
+        }
     }
     if (overflow) atomicOr(&counters[kCntErr], kErrCapacity);
     flush_hist(s_hist, hist, passes * 256);
