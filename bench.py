@@ -364,6 +364,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="records per chunk of a split tile list (0 = autotune)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-backward", action="store_true", help="skip the forward+backward timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -500,6 +501,38 @@ def main():
                "h2d_bytes_per_step": GS_CAMERA_BYTES, "d2h_bytes_per_step": 11 * W * H * 4,
                "path": "gs_render_forward_to_host (plain forward + D2H of rgb, dC/dx, dC/dy, depth, alpha)"}
 
+    # the backward workload: forward keeping the state, then the backward of
+    # N(0,1) upstream gradients on rgb, dC/dx and dC/dy (CUDA events, plain calls)
+    bwd = None
+    if not args.no_backward:
+        ups = synth.upstream_grads(W, H, 3)
+        g_in = {k: torch.from_numpy(v).to("cuda") for k, v in ups.items()}
+        grads = scene.zeros_like_grads()
+        torch.cuda.synchronize()  # inputs made on the default stream, used on `stream`
+        for i in range(2):
+            o, state = ctx.forward(scene, cams[i], out=out, tile=tile, batch=batch, chunk=chunk, state=True,
+                                   stream=stream)
+            ctx.backward(state, scene, g_in, grads=grads, stream=stream)
+            state.free()
+        n_b = min(args.steps, 20)
+        ef, eb, ee = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        f_ms = b_ms = 0.0
+        for i in range(n_b):
+            ef.record(stream)
+            o, state = ctx.forward(scene, cams[i % len(cams)], out=out, tile=tile, batch=batch, chunk=chunk,
+                                   state=True, stream=stream)
+            eb.record(stream)
+            ctx.backward(state, scene, g_in, grads=grads, stream=stream)
+            ee.record(stream)
+            ee.synchronize()
+            f_ms += ef.elapsed_time(eb)
+            b_ms += eb.elapsed_time(ee)
+            state.free()
+        bwd = {"frames": n_b, "forward_with_state_ms": f_ms / n_b, "backward_ms": b_ms / n_b,
+               "fwd_bwd_mpix_s": W * H / ((f_ms + b_ms) / n_b * 1e-3) / 1e6,
+               "path": "gs_render_forward (GS_EMIT_BWD_STATE, plain) + gs_render_backward; upstream N(0,1) on "
+                       "rgb, dC/dx, dC/dy; grads of means, log-scales, quaternions, opacity logits, SH"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc, cams, args.workload)
@@ -514,6 +547,7 @@ def main():
                            "l2": "inputs larger than L2 (scene %.0f MB)" % (sc.nbytes() / 1e6),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "frames_per_s": 1e3 * args.steps * world / ms,
+                "backward": bwd,
                 "stage_ms": stage_ms,
                 "stage_ms_source": "composite: CUDA events inside the timed replays; the other stages: a "
                                    "second replay of the camera path with events at every stage boundary",
