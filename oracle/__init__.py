@@ -7,8 +7,10 @@ and the two share no code: the only common module is the seeded input generator
 
 The C source (``oracle.c``) is a plain, per-pixel, untiled reference renderer:
 FP64 continuous math, plus an fp32 round-to-nearest sequence for the discrete
-decisions (depth key, support rectangle). Every function here is a thin ctypes
-wrapper around it.
+decisions (depth key, support rectangle). It also holds the frame-interpolation
+geometry of Sec. 4.2 (camera motion vectors, the depth-tested forward warp and the
+warped gradient), with the target pixel and the depth test decided by an fp32
+sequence in the same way. Every function here is a thin ctypes wrapper around it.
 """
 from __future__ import annotations
 
@@ -70,6 +72,8 @@ def lib():
             L.or_count_instances.argtypes = [P, P, C.c_int32]
             L.or_keys.argtypes = [P, P, C.c_int32, C.c_int64, P, P, P]
             L.or_backward.argtypes = [P, P] + [P] * 11
+            L.or_warp.argtypes = [P, P, P, P, C.c_double, C.c_int32, P, C.c_int32] + [P] * 9
+            L.or_warp.restype = C.c_int
             L.or_max_threads.restype = C.c_int
             L.or_set_threads.argtypes = [C.c_int]
             _lib = L
@@ -243,6 +247,36 @@ def backward(scene, cam, g_rgb=None, g_dcdx=None, g_dcdy=None, g_depth=None, g_a
     if rc != 0:
         raise RuntimeError("or_backward failed: %d" % rc)
     return out
+
+
+def warp(src_cam, dst_cam, depth, alpha=None, alpha_min=0.0, planes=None, dcdx=None, dcdy=None) -> dict:
+    """Frame-interpolation geometry of Sec. 4.2 for one source frame (oracle.c, or_warp).
+
+    depth, alpha: [H, W] of the source frame (alpha None: depth is a point depth).
+    planes: [C, H, W] carried by the forward warp; dcdx, dcdy: [G, H, W] source image
+    gradients. Returns motion [2, H, W] (fp32 spec, NaN where a pixel does not move),
+    motion64 (the same map in FP64), index [Ht, Wt] (winning source pixel, -1 = hole),
+    z [Ht, Wt] (winner's target-camera z, fp32 spec), out [C, Ht, Wt], out_dcdx/out_dcdy
+    [G, Ht, Wt] (the warped gradient w(G, V) . dx/dy)."""
+    W, H, Wt, Ht = src_cam.width, src_cam.height, dst_cam.width, dst_cam.height
+    f64 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    depth, alpha = f64(depth), f64(alpha)
+    assert depth.shape == (H, W) and (alpha is None or alpha.shape == (H, W))
+    planes = f64(planes) if planes is not None else np.zeros((0, H, W))
+    C_ = planes.shape[0]
+    G = 0 if dcdx is None else int(np.shape(dcdx)[0])
+    dcdx = f64(dcdx) if G else None
+    dcdy = f64(dcdy) if G else None
+    res = dict(motion=np.zeros((2, H, W), np.float32), motion64=np.zeros((2, H, W)),
+               index=np.zeros((Ht, Wt), np.int32), z=np.zeros((Ht, Wt), np.float32),
+               out=np.zeros((C_, Ht, Wt)), out_dcdx=np.zeros((G, Ht, Wt)), out_dcdy=np.zeros((G, Ht, Wt)))
+    sc, dc = _cam(src_cam), _cam(dst_cam)
+    rc = lib().or_warp(C.byref(sc), C.byref(dc), _ptr(depth), _ptr(alpha), float(alpha_min), C_, _ptr(planes), G,
+                       _ptr(dcdx), _ptr(dcdy), *[_ptr(res[k]) for k in
+                       ("motion", "motion64", "index", "z", "out", "out_dcdx", "out_dcdy")])
+    if rc != 0:
+        raise MemoryError("or_warp: allocation failed")
+    return res
 
 
 def max_threads() -> int:

@@ -1065,3 +1065,207 @@ void or_set_threads(int n)
     (void)n;
 #endif
 }
+
+/* ===================================================================== frame-interpolation geometry
+ * The geometric half of the paper's frame interpolation (Sec. 4.2, "Forward-Backward
+ * Warping"): camera motion vectors, the warp operator w(., V) and the warped gradient.
+ *
+ *   V[x]        = Proj(UnProj(x, D[x], P_src), P_dst) - x
+ *   w(F, V)     : forward warp. Every source pixel that moves lands on the target pixel
+ *                 containing x + V[x]; of the pixels landing on one target pixel, the one
+ *                 nearest to the target camera wins (target-camera z, then the smaller
+ *                 source index); a target pixel nobody lands on is a hole (0, index -1).
+ *   G_dst       = w(G_src, V) . dx/dy : the gradient of a warped image by the chain rule,
+ *                 dx/dy = (dy/dx)^-1 with dy/dx = I + dV/dx the spatial derivative of the
+ *                 motion map, taken by central differences over the source pixel grid.
+ *
+ * Readings (the paper is silent on them): D is the render's depth channel normalised by
+ * its alpha (a convex combination of the blended Gaussians' camera z) and a pixel moves
+ * only where alpha > alpha_min; UnProj lifts pixel centre (i + 0.5, j + 0.5) to camera z
+ * = D; the warp is nearest-pixel with a depth test; a one-sided difference replaces the
+ * central one where a neighbour does not move, the identity where neither does; a
+ * non-positive Jacobian determinant (a fold) gives a zero warped gradient.
+ *
+ * The discrete decisions (which target pixel, which source wins) follow the fp32
+ * round-to-nearest sequence of warp_pos32 so that an fp32 implementation can reproduce
+ * them bit for bit; motion vectors are reported from the same sequence. The determinant,
+ * inverse and gradient products are FP64. warp_pos64 evaluates the same map in FP64
+ * (pins compare it with closed forms and bound the fp32 sequence's rounding).
+ */
+
+/* fp32 spec: target position (u, v) and target-camera z of source pixel (i, j).
+ * Returns 1 when the pixel moves: alpha > alpha_min (or depth > 0 without alpha) and
+ * the lifted point lies beyond the target camera's near plane. */
+static int warp_pos32(const or_camera *s, const or_camera *t, const double *depth, const double *alpha,
+                      double alpha_min, int W, int i, int j, float *u, float *v, float *z)
+{
+    const int64_t p = (int64_t)j * W + i;
+    float d;
+    if (alpha) {
+        const float a = (float)alpha[p];
+        if (!(a > (float)alpha_min)) return 0;
+        d = (float)depth[p] / a;
+    } else {
+        d = (float)depth[p];
+        if (!(d > 0.0f)) return 0;
+    }
+    /* UnProj: camera-space point of the pixel centre at camera z = d, then world. */
+    const float xn = (((float)i + 0.5f) - (float)s->cx) / (float)s->fx;
+    const float yn = (((float)j + 0.5f) - (float)s->cy) / (float)s->fy;
+    const float xc = xn * d, yc = yn * d, zc = d;
+    float R[12], Q[12];
+    for (int k = 0; k < 12; ++k) {
+        R[k] = (float)s->viewmat[k];
+        Q[k] = (float)t->viewmat[k];
+    }
+    const float a0 = xc - R[3], a1 = yc - R[7], a2 = zc - R[11];
+    /* world = R^T (camera - t) */
+    const float xw = (R[0] * a0 + R[4] * a1) + R[8] * a2;
+    const float yw = (R[1] * a0 + R[5] * a1) + R[9] * a2;
+    const float zw = (R[2] * a0 + R[6] * a1) + R[10] * a2;
+    /* Proj into the target camera. */
+    const float X = ((Q[0] * xw + Q[1] * yw) + Q[2] * zw) + Q[3];
+    const float Y = ((Q[4] * xw + Q[5] * yw) + Q[6] * zw) + Q[7];
+    const float Z = ((Q[8] * xw + Q[9] * yw) + Q[10] * zw) + Q[11];
+    if (!(Z > (float)t->near_plane)) return 0;
+    *u = ((float)t->fx * X) / Z + (float)t->cx;
+    *v = ((float)t->fy * Y) / Z + (float)t->cy;
+    *z = Z;
+    return 1;
+}
+
+/* The same map in FP64 (same moving-pixel rule, decided in fp32 as above). */
+static int warp_pos64(const or_camera *s, const or_camera *t, const double *depth, const double *alpha,
+                      double alpha_min, int W, int i, int j, double *u, double *v, double *z)
+{
+    const int64_t p = (int64_t)j * W + i;
+    double d;
+    if (alpha) {
+        if (!((float)alpha[p] > (float)alpha_min)) return 0;
+        d = depth[p] / alpha[p];
+    } else {
+        if (!((float)depth[p] > 0.0f)) return 0;
+        d = depth[p];
+    }
+    const double *R = s->viewmat, *Q = t->viewmat;
+    const double cam[3] = {(i + 0.5 - s->cx) / s->fx * d, (j + 0.5 - s->cy) / s->fy * d, d};
+    double w[3];
+    for (int r = 0; r < 3; ++r)
+        w[r] = R[0 * 4 + r] * (cam[0] - R[3]) + R[1 * 4 + r] * (cam[1] - R[7]) + R[2 * 4 + r] * (cam[2] - R[11]);
+    double c[3];
+    for (int r = 0; r < 3; ++r) c[r] = Q[r * 4 + 0] * w[0] + Q[r * 4 + 1] * w[1] + Q[r * 4 + 2] * w[2] + Q[r * 4 + 3];
+    if (!(c[2] > t->near_plane)) return 0;
+    *u = t->fx * c[0] / c[2] + t->cx;
+    *v = t->fy * c[1] / c[2] + t->cy;
+    *z = c[2];
+    return 1;
+}
+
+/* Motion vectors, forward warp and warped gradients of one source frame.
+ *   depth, alpha      [H][W] (alpha may be NULL: depth is then a point depth)
+ *   planes            [channels][H][W], carried to the target by the warp
+ *   dcdx, dcdy        [gch][H][W] source image gradients (NULL when gch == 0)
+ * Outputs (any may be NULL):
+ *   motion            [2][H][W] fp32 spec V, NaN where the pixel does not move
+ *   motion64          [2][H][W] FP64 V, NaN where the pixel does not move
+ *   index             [Ht][Wt]  winning source pixel j*W+i, -1 for a hole
+ *   zdst              [Ht][Wt]  the winner's target-camera z (fp32 spec), 0 for a hole
+ *   out               [channels][Ht][Wt]
+ *   out_dcdx/out_dcdy [gch][Ht][Wt] */
+int or_warp(const or_camera *src, const or_camera *dst, const double *depth, const double *alpha,
+            double alpha_min, int32_t channels, const double *planes, int32_t gch, const double *dcdx,
+            const double *dcdy, float *motion, double *motion64, int32_t *index, float *zdst, double *out,
+            double *out_dcdx, double *out_dcdy)
+{
+    const int W = src->width, H = src->height, Wt = dst->width, Ht = dst->height;
+    const int64_t n = (int64_t)W * H, nt = (int64_t)Wt * Ht;
+    float *pu = malloc(sizeof(float) * (size_t)(n ? n : 1));
+    float *pv = malloc(sizeof(float) * (size_t)(n ? n : 1));
+    float *pz = malloc(sizeof(float) * (size_t)(n ? n : 1));
+    unsigned char *mv = malloc((size_t)(n ? n : 1));
+    uint64_t *best = malloc(sizeof(uint64_t) * (size_t)(nt ? nt : 1));
+    if (!pu || !pv || !pz || !mv || !best) {
+        free(pu); free(pv); free(pz); free(mv); free(best);
+        return -1;
+    }
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            const int64_t p = (int64_t)j * W + i;
+            mv[p] = (unsigned char)warp_pos32(src, dst, depth, alpha, alpha_min, W, i, j, &pu[p], &pv[p], &pz[p]);
+            if (motion) {
+                motion[p] = mv[p] ? pu[p] - ((float)i + 0.5f) : NAN;
+                motion[n + p] = mv[p] ? pv[p] - ((float)j + 0.5f) : NAN;
+            }
+            if (motion64) {
+                double u, v, z;
+                if (warp_pos64(src, dst, depth, alpha, alpha_min, W, i, j, &u, &v, &z)) {
+                    motion64[p] = u - (i + 0.5);
+                    motion64[n + p] = v - (j + 0.5);
+                } else {
+                    motion64[p] = motion64[n + p] = NAN;
+                }
+            }
+        }
+    /* The depth test: scatter every moving pixel into its target pixel. */
+    for (int64_t q = 0; q < nt; ++q) best[q] = UINT64_MAX;
+    for (int64_t p = 0; p < n; ++p) {
+        if (!mv[p]) continue;
+        if (!(pu[p] >= 0.0f && pu[p] < (float)Wt && pv[p] >= 0.0f && pv[p] < (float)Ht)) continue;
+        const int64_t q = (int64_t)floorf(pv[p]) * Wt + (int64_t)floorf(pu[p]);
+        uint32_t zb;
+        memcpy(&zb, &pz[p], 4);
+        const uint64_t key = ((uint64_t)zb << 32) | (uint64_t)p;
+        if (key < best[q]) best[q] = key;
+    }
+    for (int64_t q = 0; q < nt; ++q) {
+        const int hole = best[q] == UINT64_MAX;
+        const int64_t p = hole ? -1 : (int64_t)(best[q] & 0xFFFFFFFFu);
+        if (index) index[q] = (int32_t)p;
+        if (zdst) zdst[q] = hole ? 0.0f : pz[p];
+        if (out)
+            for (int c = 0; c < channels; ++c) out[c * nt + q] = hole ? 0.0 : planes[c * n + p];
+        if (gch <= 0 || !out_dcdx || !out_dcdy) continue;
+        double J[4] = {1.0, 0.0, 0.0, 1.0}, det = 1.0;  /* J = [[du/dx, du/dy], [dv/dx, dv/dy]] */
+        if (!hole) {
+            const int i = (int)(p % W), j = (int)(p / W);
+            /* d(position)/dx: neighbours left/right in the source row */
+            const int L = i > 0 && mv[p - 1], Rn = i < W - 1 && mv[p + 1];
+            if (L && Rn) {
+                J[0] = ((double)pu[p + 1] - (double)pu[p - 1]) * 0.5;
+                J[2] = ((double)pv[p + 1] - (double)pv[p - 1]) * 0.5;
+            } else if (Rn) {
+                J[0] = (double)pu[p + 1] - (double)pu[p];
+                J[2] = (double)pv[p + 1] - (double)pv[p];
+            } else if (L) {
+                J[0] = (double)pu[p] - (double)pu[p - 1];
+                J[2] = (double)pv[p] - (double)pv[p - 1];
+            }
+            /* d(position)/dy: neighbours above/below */
+            const int U = j > 0 && mv[p - W], D = j < H - 1 && mv[p + W];
+            if (U && D) {
+                J[1] = ((double)pu[p + W] - (double)pu[p - W]) * 0.5;
+                J[3] = ((double)pv[p + W] - (double)pv[p - W]) * 0.5;
+            } else if (D) {
+                J[1] = (double)pu[p + W] - (double)pu[p];
+                J[3] = (double)pv[p + W] - (double)pv[p];
+            } else if (U) {
+                J[1] = (double)pu[p] - (double)pu[p - W];
+                J[3] = (double)pv[p] - (double)pv[p - W];
+            }
+            det = J[0] * J[3] - J[1] * J[2];
+        }
+        for (int c = 0; c < gch; ++c) {
+            double gx = 0.0, gy = 0.0;
+            if (!hole && det > 0.0) {
+                const double g0 = dcdx[c * n + p], g1 = dcdy[c * n + p];
+                /* (g0, g1) . J^-1, J^-1 = [[J3, -J1], [-J2, J0]] / det */
+                gx = (g0 * J[3] - g1 * J[2]) / det;
+                gy = (g1 * J[0] - g0 * J[1]) / det;
+            }
+            out_dcdx[c * nt + q] = gx;
+            out_dcdy[c * nt + q] = gy;
+        }
+    }
+    free(pu); free(pv); free(pz); free(mv); free(best);
+    return 0;
+}

@@ -93,6 +93,12 @@ class Camera:
         return Camera(self.viewmat.copy(), self.fx, self.fy, self.cx + dcx, self.cy + dcy,
                       self.width, self.height, self.near, self.eye)
 
+    def scaled(self, factor: int) -> "Camera":
+        """Same pose at ``factor`` times the resolution (the high-resolution frame of a
+        super-sampling factor S = factor)."""
+        return Camera(self.viewmat.copy(), self.fx * factor, self.fy * factor, self.cx * factor,
+                      self.cy * factor, self.width * factor, self.height * factor, self.near, self.eye)
+
 
 # ----------------------------------------------------------------------------- scenes
 
@@ -278,3 +284,44 @@ def upstream_grads(width: int, height: int, seed: int = 3) -> dict:
     rng = np.random.default_rng(seed)
     return {k: rng.standard_normal((3, height, width), dtype=np.float32)
             for k in ("rgb", "dcdx", "dcdy")}
+
+
+# ----------------------------------------------------------------------------- frame interpolation inputs
+
+def interpolation_cameras(width: int = 960, height: int = 540, frames: int = 60, k: int = 0):
+    """(P0, P0.5, P1): frames k and k + 1 of the ``frames``-frame orbit of the large
+    scene and the pose half-way between them (the same orbit sampled twice as densely)."""
+    dense = orbit_cameras(2 * frames, width, height)
+    return dense[2 * k], dense[2 * k + 1], dense[2 * k + 2]
+
+
+def warp_frame(width: int, height: int, seed: int, depth_range=(40.0, 130.0), occluders: int = 24,
+               holes: int = 6, channels: int = 3, grad_channels: int = 3) -> dict:
+    """A synthetic rendered frame as the frame-interpolation warp sees it: a smooth
+    tilted-surface depth with nearer rectangular occluders (depth discontinuities),
+    empty regions (alpha 0) and soft alpha at their edges, smooth colour planes and
+    N(0, 1) gradient planes. ``depth`` is unnormalised like the render's depth channel
+    (point depth x alpha). All planes fp32, [H, W] or [C, H, W]."""
+    rng = np.random.default_rng(seed)
+    ys, xs = np.mgrid[0:height, 0:width].astype(np.float64)
+    u, v = (xs + 0.5) / width, (ys + 0.5) / height
+    d0, d1 = depth_range
+    base = d0 + (d1 - d0) * (0.35 + 0.4 * v + 0.15 * u + 0.05 * np.sin(7.0 * u + 3.0 * v))
+    point = base.copy()
+    for _ in range(occluders):
+        w, h = rng.uniform(0.03, 0.2) * width, rng.uniform(0.03, 0.2) * height
+        x0, y0 = rng.uniform(-0.1, 1.0) * width, rng.uniform(-0.1, 1.0) * height
+        m = (xs >= x0) & (xs < x0 + w) & (ys >= y0) & (ys < y0 + h)
+        point[m] = np.minimum(point[m], rng.uniform(0.4, 0.9) * base[m])
+    alpha = np.ones((height, width))
+    for _ in range(holes):
+        cx, cy = rng.uniform(0, width), rng.uniform(0, height)
+        r = rng.uniform(0.02, 0.1) * max(width, height)
+        dist = np.hypot(xs - cx, ys - cy)
+        alpha = np.minimum(alpha, np.clip((dist - r) / (0.25 * r + 1.0), 0.0, 1.0))
+    planes = np.stack([0.5 + 0.5 * np.sin(rng.uniform(2, 12) * u + rng.uniform(2, 12) * v + rng.uniform(0, 6))
+                       for _ in range(channels)]) if channels else np.zeros((0, height, width))
+    return dict(depth=(point * alpha).astype(np.float32), alpha=alpha.astype(np.float32),
+                planes=planes.astype(np.float32),
+                dcdx=rng.standard_normal((grad_channels, height, width)).astype(np.float32),
+                dcdy=rng.standard_normal((grad_channels, height, width)).astype(np.float32))
