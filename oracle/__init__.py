@@ -72,7 +72,7 @@ def lib():
             L.or_count_instances.argtypes = [P, P, C.c_int32]
             L.or_keys.argtypes = [P, P, C.c_int32, C.c_int64, P, P, P]
             L.or_backward.argtypes = [P, P] + [P] * 11
-            L.or_warp.argtypes = [P, P, P, P, C.c_double, C.c_int32, P, C.c_int32] + [P] * 9
+            L.or_warp.argtypes = [P, P, P, P, C.c_double, C.c_int32, P, C.c_int32] + [P] * 10
             L.or_warp.restype = C.c_int
             L.or_max_threads.restype = C.c_int
             L.or_set_threads.argtypes = [C.c_int]
@@ -257,7 +257,9 @@ def warp(src_cam, dst_cam, depth, alpha=None, alpha_min=0.0, planes=None, dcdx=N
     gradients. Returns motion [2, H, W] (fp32 spec, NaN where a pixel does not move),
     motion64 (the same map in FP64), index [Ht, Wt] (winning source pixel, -1 = hole),
     z [Ht, Wt] (winner's target-camera z, fp32 spec), out [C, Ht, Wt], out_dcdx/out_dcdy
-    [G, Ht, Wt] (the warped gradient w(G, V) . dx/dy)."""
+    [G, Ht, Wt] (the warped gradient w(G, V) . dx/dy), jac [4, Ht, Wt] (the Jacobian
+    J = [[du/dx, du/dy], [dv/dx, dv/dy]] of the landing map used at each target pixel,
+    row-major entries; the identity at holes)."""
     W, H, Wt, Ht = src_cam.width, src_cam.height, dst_cam.width, dst_cam.height
     f64 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
     depth, alpha = f64(depth), f64(alpha)
@@ -269,11 +271,12 @@ def warp(src_cam, dst_cam, depth, alpha=None, alpha_min=0.0, planes=None, dcdx=N
     dcdy = f64(dcdy) if G else None
     res = dict(motion=np.zeros((2, H, W), np.float32), motion64=np.zeros((2, H, W)),
                index=np.zeros((Ht, Wt), np.int32), z=np.zeros((Ht, Wt), np.float32),
-               out=np.zeros((C_, Ht, Wt)), out_dcdx=np.zeros((G, Ht, Wt)), out_dcdy=np.zeros((G, Ht, Wt)))
+               out=np.zeros((C_, Ht, Wt)), out_dcdx=np.zeros((G, Ht, Wt)), out_dcdy=np.zeros((G, Ht, Wt)),
+               jac=np.zeros((4, Ht, Wt)))
     sc, dc = _cam(src_cam), _cam(dst_cam)
     rc = lib().or_warp(C.byref(sc), C.byref(dc), _ptr(depth), _ptr(alpha), float(alpha_min), C_, _ptr(planes), G,
                        _ptr(dcdx), _ptr(dcdy), *[_ptr(res[k]) for k in
-                       ("motion", "motion64", "index", "z", "out", "out_dcdx", "out_dcdy")])
+                       ("motion", "motion64", "index", "z", "out", "out_dcdx", "out_dcdy", "jac")])
     if rc != 0:
         raise MemoryError("or_warp: allocation failed")
     return res

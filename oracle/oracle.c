@@ -1171,11 +1171,13 @@ static int warp_pos64(const or_camera *s, const or_camera *t, const double *dept
  *   index             [Ht][Wt]  winning source pixel j*W+i, -1 for a hole
  *   zdst              [Ht][Wt]  the winner's target-camera z (fp32 spec), 0 for a hole
  *   out               [channels][Ht][Wt]
- *   out_dcdx/out_dcdy [gch][Ht][Wt] */
+ *   out_dcdx/out_dcdy [gch][Ht][Wt]
+ *   jac               [4][Ht][Wt]  the Jacobian J used at each target pixel (J00, J01, J10, J11;
+ *                                  the identity at holes), computed whether or not gch > 0 */
 int or_warp(const or_camera *src, const or_camera *dst, const double *depth, const double *alpha,
             double alpha_min, int32_t channels, const double *planes, int32_t gch, const double *dcdx,
             const double *dcdy, float *motion, double *motion64, int32_t *index, float *zdst, double *out,
-            double *out_dcdx, double *out_dcdy)
+            double *out_dcdx, double *out_dcdy, double *jac)
 {
     const int W = src->width, H = src->height, Wt = dst->width, Ht = dst->height;
     const int64_t n = (int64_t)W * H, nt = (int64_t)Wt * Ht;
@@ -1224,7 +1226,7 @@ int or_warp(const or_camera *src, const or_camera *dst, const double *depth, con
         if (zdst) zdst[q] = hole ? 0.0f : pz[p];
         if (out)
             for (int c = 0; c < channels; ++c) out[c * nt + q] = hole ? 0.0 : planes[c * n + p];
-        if (gch <= 0 || !out_dcdx || !out_dcdy) continue;
+        if ((gch <= 0 || !out_dcdx || !out_dcdy) && !jac) continue;
         double J[4] = {1.0, 0.0, 0.0, 1.0}, det = 1.0;  /* J = [[du/dx, du/dy], [dv/dx, dv/dy]] */
         if (!hole) {
             const int i = (int)(p % W), j = (int)(p / W);
@@ -1254,6 +1256,9 @@ int or_warp(const or_camera *src, const or_camera *dst, const double *depth, con
             }
             det = J[0] * J[3] - J[1] * J[2];
         }
+        if (jac)
+            for (int k = 0; k < 4; ++k) jac[k * nt + q] = J[k];
+        if (gch <= 0 || !out_dcdx || !out_dcdy) continue;
         for (int c = 0; c < gch; ++c) {
             double gx = 0.0, gy = 0.0;
             if (!hole && det > 0.0) {

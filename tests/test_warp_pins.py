@@ -122,6 +122,10 @@ def test_dolly_scales_about_the_principal_point(dz):
     for key, gkey in (("out_dcdx", "dcdx"), ("out_dcdy", "dcdy")):
         want = f[gkey].reshape(2, -1)[:, p[inner]] / s
         np.testing.assert_allclose(r[key][:, hit][:, inner], want, rtol=2e-4, atol=1e-5)
+    # The Jacobian the oracle reports is s I there, and the identity at holes.
+    jac = r["jac"][:, hit][:, inner]
+    np.testing.assert_allclose(jac, np.array([s, 0.0, 0.0, s])[:, None] * np.ones_like(jac), atol=2e-4 * s)
+    assert np.array_equal(r["jac"][:, ~hit], np.array([1.0, 0.0, 0.0, 1.0])[:, None] * np.ones((4, (~hit).sum())))
     if s > 1:
         assert (~hit).sum() > 0  # magnification opens holes between the source pixels
     else:
@@ -156,6 +160,7 @@ def test_roll_about_the_optical_axis_rotates_the_gradient(theta):
     si, sj = p % cam.width, p // cam.width
     inner = (si > 0) & (si < cam.width - 1) & (sj > 0) & (sj < cam.height - 1)
     g = np.stack([f["dcdx"].reshape(2, -1)[:, p[inner]], f["dcdy"].reshape(2, -1)[:, p[inner]]], axis=-1)
+    np.testing.assert_allclose(r["jac"][:, hit][:, inner], J.reshape(4, 1) * np.ones((4, inner.sum())), atol=2e-4)
     want = g @ np.linalg.inv(J)  # row vector times dx/dy
     np.testing.assert_allclose(r["out_dcdx"][:, hit][:, inner], want[..., 0], rtol=2e-4, atol=2e-5)
     np.testing.assert_allclose(r["out_dcdy"][:, hit][:, inner], want[..., 1], rtol=2e-4, atol=2e-5)
