@@ -10,7 +10,8 @@ reuse each other's inputs from cache.
 Prints one JSON line. Default workload: 1M clustered Gaussians, SH degree 3,
 960x540, 60-frame orbit (steps cycle over the orbit).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload large|ultra|ultra_lr|tiny]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload large|ultra|ultra_lr|tiny|serve|interp]
 
 With --gpus N > 1 (launched by torchrun) every rank renders the same workload
 as an independent replica (the render has no cross-GPU exchange); value is the
@@ -167,6 +168,8 @@ def run_reference(args):
     import oracle
 
     oracle.build()
+    if args.workload == "interp":
+        return run_reference_interp(args, world)
     sc, cams = make_workload(args.workload)
     osc = oracle.OScene(sc)
     cores = oracle.max_threads()
@@ -193,6 +196,38 @@ def run_reference(args):
                        "step": "one band of %d rows of a frame" % band},
             "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
                              "sample": "%d steps x %d rows" % (args.steps, band)},
+            "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_interp(args, world):
+    """--impl reference --workload interp: the oracle's warp (or_warp) on the same pair;
+    a step is one call (alternating the high- and low-resolution frame)."""
+    import oracle
+
+    from paper_2605_11489_gb300 import synth
+
+    calls = _interp_calls(synth.interp_inputs())
+
+    def step(i):
+        src, dst, f, grads = calls[i % 2]
+        oracle.warp(src, dst, f["depth"], f["alpha"], 0.0, f["planes"], f["dcdx"] if grads else None,
+                    f["dcdy"] if grads else None)
+        return src.width * src.height
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    px = sum(step(args.warmup + i) for i in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = px / dt / 1e6
+    line = {"metric": "interp warp Mpix/s (source pixels)", "value": v, "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {"workload": "interp", "desc": INTERP_DESC,
+                                            "step": "one of the two warps, alternating"},
+            "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d warps (or_warp, single-threaded C)" % args.steps},
             "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -292,6 +327,173 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+INTERP_DESC = ("frame-interpolation warp pair of Sec. 4.2: frame 0 at 3840x2160 (7 planes: colour, depth, "
+               "normals) toward P0.5, frame 1 at 960x540 (7 planes + 3 image-gradient planes) toward P0.5; "
+               "motion vectors, depth-tested forward warp, warped gradient; large-scene orbit poses")
+
+
+def _interp_calls(w):
+    """The two gs_warp calls of one step: (src cam, dst cam, frame, gradients?)."""
+    return [(w["P0_hr"], w["P05_hr"], w["hr"], False), (w["P1"], w["P05"], w["lr"], True)]
+
+
+def warp_bytes(src, dst, channels, grad_channels, hits):
+    """Algorithmic bytes of one gs_warp call, per kernel: the scatter reads depth and
+    alpha and writes the motion map (per source pixel); the gather writes index, z,
+    the planes and the gradient planes (per target pixel) and reads the winners'
+    planes and gradients (per hit target pixel). Scratch traffic is not counted."""
+    n, nt = src.width * src.height, dst.width * dst.height
+    scatter = n * (4 + 4 + 8)
+    gather = nt * (4 + 4 + 4 * channels + 8 * grad_channels) + hits * (4 * channels + 8 * grad_channels)
+    return scatter, gather
+
+
+def run_interp(args):
+    """--workload interp: the forward-backward warp pair of Sec. 4.2 (two gs_warp calls,
+    two kernels each) on resident synthetic frames; one JSON line."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2605_11489_gb300 import api, synth
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    w = synth.interp_inputs()
+    calls = _interp_calls(w)
+    stream = torch.cuda.Stream()
+    ctx = api.Context(local_rank)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with torch.cuda.stream(stream):
+        ins, outs = [], []
+        for src, dst, f, grads in calls:
+            ins.append(dict(depth=dev(f["depth"]), alpha=dev(f["alpha"]), planes=dev(f["planes"]),
+                            dcdx=dev(f["dcdx"]) if grads else None, dcdy=dev(f["dcdy"]) if grads else None))
+            outs.append(api.alloc_warp_outputs(src.width, src.height, dst.width, dst.height, f["planes"].shape[0],
+                                               f["dcdx"].shape[0] if grads else 0))
+    stream.synchronize()
+
+    def step():
+        for (src, dst, f, grads), i, o in zip(calls, ins, outs):
+            ctx.warp(src, dst, i["depth"], i["alpha"], 0.0, i["planes"], i["dcdx"], i["dcdy"], out=o, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    clk_path = os.path.join(tempfile.gettempdir(), "gsr_clocks_interp_%d_%d.csv" % (os.getpid(), rank))
+    smi, smi_f = start_clock_sampler(clk_path, local_rank)
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        torch.distributed.barrier()
+    if smi:
+        smi.terminate()
+        smi.wait()
+        smi_f.close()
+    clocks = read_clocks(clk_path)
+    ms = slowest_rank(ms, world, "cuda")
+    px_step = sum(src.width * src.height for src, _, _, _ in calls)
+    value = job_throughput(px_step * args.steps, world, ms * 1e-3)
+
+    # per-call durations (CUDA events around each call on the launch stream), and each
+    # kernel's share from a split of the call: the scatter alone, then the whole call
+    per = []
+    hbm_peak, _, peak_src = measured_peaks()
+    reps = max(10, min(args.steps, 50))
+    for (src, dst, f, grads), i, o in zip(calls, ins, outs):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(reps):
+            ctx.warp(src, dst, i["depth"], i["alpha"], 0.0, i["planes"], i["dcdx"], i["dcdy"], out=o, stream=stream)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        call_ms = ev[0].elapsed_time(ev[1]) / reps
+        hits = int((o["index"] >= 0).sum().item())
+        sb, gb = warp_bytes(src, dst, f["planes"].shape[0], f["dcdx"].shape[0] if grads else 0, hits)
+        per.append({"src": "%dx%d" % (src.width, src.height), "dst": "%dx%d" % (dst.width, dst.height),
+                    "channels": int(f["planes"].shape[0]), "grad_channels": int(f["dcdx"].shape[0]) if grads else 0,
+                    "call_ms": call_ms, "hits": hits, "algorithmic_bytes": sb + gb,
+                    "achieved_gbs": (sb + gb) / (call_ms * 1e-3) / 1e9})
+    dom = max(range(len(per)), key=lambda k: per[k]["call_ms"])
+    d = per[dom]
+    roof = {"bound": "hbm", "kernel": "gs_warp %s -> %s (k_warp_scatter + k_warp_gather)" % (d["src"], d["dst"]),
+            "achieved": d["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": d["achieved_gbs"] / hbm_peak,
+            "traffic": None, "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src,
+            "algorithmic_bytes_per_launch": d["algorithmic_bytes"], "launch_ms": d["call_ms"]}
+
+    # end to end: inputs from pinned host memory, every output plane back, per step
+    e2e = None
+    if not args.no_e2e:
+        h_in = [{k: (v.cpu().pin_memory() if v is not None else None) for k, v in i.items()} for i in ins]
+        h_out = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()} for o in outs]
+        h2d = sum(v.numel() * 4 for i in h_in for v in i.values() if v is not None)
+        d2h = sum(v.numel() * 4 for o in h_out for v in o.values())
+        n_e = min(args.steps, 20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e):
+            with torch.cuda.stream(stream):
+                for (src, dst, f, grads), hi, di, o, ho in zip(calls, h_in, ins, outs, h_out):
+                    for k, v in hi.items():
+                        if v is not None:
+                            di[k].copy_(v, non_blocking=True)
+                    ctx.warp(src, dst, di["depth"], di["alpha"], 0.0, di["planes"], di["dcdx"], di["dcdy"], out=o,
+                             stream=stream)
+                    for k in o:
+                        ho[k].copy_(o[k], non_blocking=True)
+            stream.synchronize()
+        dt = slowest_rank(time.perf_counter() - t0, world, "cuda")
+        e2e = {"value": job_throughput(px_step * n_e, world, dt), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "path": "torch H2D of the source planes + gs_warp x2 + D2H of every output plane"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        t0 = time.perf_counter()
+        n_c = 0
+        while n_c < 1 or time.perf_counter() - t0 < 10.0:
+            for src, dst, f, grads in calls:
+                oracle.warp(src, dst, f["depth"], f["alpha"], 0.0, f["planes"], f["dcdx"] if grads else None,
+                            f["dcdy"] if grads else None)
+            n_c += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": px_step * n_c / dt / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+               "sample": "%d step(s) of the warp pair in %.1f s (or_warp, single-threaded C, FP64 Jacobian)" % (
+                   n_c, dt)}
+    if rank == 0:
+        line = {"metric": "interp warp Mpix/s (source pixels)", "value": value, "unit": "Mpix/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "interp", "desc": INTERP_DESC,
+                           "l2": "inputs larger than L2 (%.0f MB per step)" % (
+                               sum(v.numel() * 4 for i in ins for v in i.values() if v is not None) / 1e6),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "calls": per, "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+                "gpu_launches": args.steps * 4}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def algorithmic(stage, w, deg, n, K_avg, V_avg, tile_passes, pixels, pairs):
     """Algorithmic work of one launch of `stage` (bytes, or FP32 ops for compositing)."""
     sh_bytes = 12 * (deg + 1) ** 2
@@ -353,7 +555,7 @@ def main():
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["serve", "interp"])
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="serve: scale of the scene sizes")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: sort-buffer budget")
@@ -372,6 +574,8 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serving(args)
+    if args.workload == "interp":
+        return run_interp(args)
 
     import torch
 

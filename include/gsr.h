@@ -268,6 +268,61 @@ gs_status gs_server_destroy(gs_server *srv);
 gs_status gs_sort_pairs_static(const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out,
                                uint32_t *vals_out, int64_t n, int32_t bits, gs_stream stream);
 
+/* ---------------------------------------------------------------- frame-interpolation warp
+ * The geometric half of the paper's frame interpolation (Sec. 4.2, "Forward-
+ * Backward Warping"), applied to one rendered source frame toward one target
+ * camera (the forward-backward scheme calls it twice: frame 0 and frame 1,
+ * each toward the intermediate pose):
+ *   motion  V[x] = Proj(UnProj(x, D[x], P_src), P_dst) - x               (Sec. 4.2)
+ *   warp    w(F, V): every moving source pixel lands on the target pixel that
+ *           contains x + V[x]; among several, the one nearest the target camera
+ *           wins (target-camera z, ties to the smaller source index j*W+i); a
+ *           target pixel nobody reaches is a hole (index -1, planes 0)
+ *   warped gradient  G_dst = w(G_src, V) . (I + dV/dx)^-1                (Sec. 4.2)
+ *           (the row vector of source image gradients times the inverse of
+ *           the landing map's Jacobian, taken by central differences over the
+ *           source pixel grid, one-sided where a neighbour does not move, the
+ *           identity where neither does; 0 where the determinant is <= 0)
+ * UnProj lifts pixel centre (i + 0.5, j + 0.5) to source-camera z = D, where
+ * D = depth / alpha (the render's depth channel is alpha-weighted) and a pixel
+ * moves only where alpha > alpha_min and its target-camera z exceeds the target
+ * camera's near_plane. With alpha == NULL, depth is a point depth and a pixel
+ * moves where it is > 0. The landing position, the depth test and the motion
+ * map follow one fixed fp32 round-to-nearest operation sequence (exactly
+ * reproducible); the Jacobian and the gradient product are fp32 with
+ * compensated 2x2 determinants. Depth must be finite.
+ * Layouts: source planes [c][H][W], target planes [c][Ht][Wt], fp32, device,
+ * caller-owned, 4-byte aligned; (W, H) and (Wt, Ht) are the cameras' sizes. */
+typedef struct {
+    const float *depth;           /* [H][W] alpha-weighted depth (or point depth when alpha is NULL) */
+    const float *alpha;           /* [H][W] nullable */
+    float alpha_min;              /* a pixel moves only where alpha > alpha_min */
+    int32_t channels;             /* planes carried by the warp (colour, depth, normals ...), 0..64 */
+    const float *planes;          /* [channels][H][W] */
+    int32_t grad_channels;        /* image-gradient channels, 0..64 */
+    const float *dcdx, *dcdy;     /* [grad_channels][H][W] dI/dx, dI/dy of the source frame */
+} gs_warp_input;
+
+typedef struct {                  /* every plane nullable (NULL = not written) */
+    float *motion;                /* [2][H][W]   V (x then y), NaN where the pixel does not move */
+    int32_t *index;               /* [Ht][Wt]    winning source pixel j*W+i, -1 for a hole */
+    float *z;                     /* [Ht][Wt]    the winner's target-camera z, 0 for a hole */
+    float *planes;                /* [channels][Ht][Wt] */
+    float *dcdx, *dcdy;           /* [grad_channels][Ht][Wt] warped gradient */
+} gs_warp_output;
+
+/* Motion vectors, depth-tested forward warp and warped gradient of one source
+ * frame (above). Two kernel launches on `stream`, asynchronous. The context
+ * owns the scratch (a 64-bit depth-test slot per target pixel, kept all ones
+ * between calls, and a landing position per source pixel), grown with
+ * cudaMalloc on demand; calls on one context must be ordered on the GPU.
+ * Errors: GS_ERR_INVALID_ARG (NULL context/cameras/input/output/depth, camera
+ * sizes outside 1..65535, negative target near_plane, channel counts outside
+ * 0..64, gradients asked for without both input and output planes, misaligned
+ * planes), GS_ERR_OOM, GS_ERR_CUDA. */
+gs_status gs_warp(gs_context *ctx, const gs_camera *src, const gs_camera *dst, const gs_warp_input *in,
+                  const gs_warp_output *out, gs_stream stream);
+
 /* ---------------------------------------------------------------- misc */
 const char *gs_last_error(void);
 const char *gs_version(void);

@@ -36,7 +36,7 @@ ENTRY_POINTS = (
     "gs_render_backward", "gs_state_view_get", "gs_context_stats", "gs_state_free", "gs_graph_create",
     "gs_graph_render", "gs_graph_check", "gs_graph_stats", "gs_graph_destroy", "gs_autotune", "gs_server_create", "gs_server_load_scene",
     "gs_server_submit", "gs_server_poll", "gs_server_cancel", "gs_server_drain", "gs_server_destroy",
-    "gs_sort_pairs_static", "gs_last_error", "gs_version",
+    "gs_sort_pairs_static", "gs_warp", "gs_last_error", "gs_version",
 )
 
 
@@ -77,6 +77,16 @@ class GsFrameStats(C.Structure):
     _fields_ = [("frames", C.c_int64), ("instances_total", C.c_int64), ("visible_total", C.c_int64),
                 ("instances_max", C.c_int64), ("stage_ms", C.c_double * len(STAGES)), ("timed_frames", C.c_int64),
                 ("pairs_evaluated", C.c_int64), ("pairs_blended", C.c_int64)]
+
+
+class GsWarpInput(C.Structure):
+    _fields_ = [("depth", C.c_void_p), ("alpha", C.c_void_p), ("alpha_min", C.c_float), ("channels", C.c_int32),
+                ("planes", C.c_void_p), ("grad_channels", C.c_int32), ("dcdx", C.c_void_p), ("dcdy", C.c_void_p)]
+
+
+class GsWarpOutput(C.Structure):
+    _fields_ = [("motion", C.c_void_p), ("index", C.c_void_p), ("z", C.c_void_p), ("planes", C.c_void_p),
+                ("dcdx", C.c_void_p), ("dcdy", C.c_void_p)]
 
 
 class GsError(RuntimeError):
@@ -120,6 +130,8 @@ def _declare(L):
         "gs_server_drain": [P],
         "gs_server_destroy": [P],
         "gs_sort_pairs_static": [P, P, P, P, I64, I32, P],
+        "gs_warp": [P, C.POINTER(GsCamera), C.POINTER(GsCamera), C.POINTER(GsWarpInput), C.POINTER(GsWarpOutput),
+                    P],
     }
     for name, args in sig.items():
         f = getattr(L, name)

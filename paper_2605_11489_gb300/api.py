@@ -107,6 +107,19 @@ def alloc_outputs(width, height, keys=OUTPUT_KEYS, device="cuda") -> dict:
     return {k: torch.empty(shp[k], dtype=torch.float32, device=device) for k in keys}
 
 
+WARP_KEYS = ("motion", "index", "z", "planes", "dcdx", "dcdy")
+
+
+def alloc_warp_outputs(width, height, width_t, height_t, channels, grad_channels, keys=WARP_KEYS,
+                       device="cuda") -> dict:
+    """Target planes of gs_warp (and the source-sized motion map)."""
+    shp = {"motion": ((2, height, width), torch.float32), "index": ((height_t, width_t), torch.int32),
+           "z": ((height_t, width_t), torch.float32), "planes": ((channels, height_t, width_t), torch.float32),
+           "dcdx": ((grad_channels, height_t, width_t), torch.float32),
+           "dcdy": ((grad_channels, height_t, width_t), torch.float32)}
+    return {k: torch.empty(shp[k][0], dtype=shp[k][1], device=device) for k in keys}
+
+
 def outputs_struct(out: dict) -> GsOutputs:
     return GsOutputs(*[_ptr(out.get(k)) for k in OUTPUT_KEYS])
 
@@ -247,6 +260,26 @@ class Context:
         check(abi.lib().gs_render_backward(self.h, state.handle, C.byref(sc), C.byref(gi), C.byref(go),
                                            _stream_ptr(stream)))
         return grads
+
+    def warp(self, src_cam, dst_cam, depth, alpha=None, alpha_min=0.0, planes=None, dcdx=None, dcdy=None,
+             out=None, keys=WARP_KEYS, stream=None) -> dict:
+        """Frame-interpolation warp of one source frame toward ``dst_cam`` (gs_warp):
+        motion vectors, the depth-tested forward warp of ``planes`` and the warped
+        gradient of (dcdx, dcdy). Inputs are device tensors [H, W] / [C, H, W]; returns
+        (or fills) the dict of target planes named in ``keys``."""
+        H, W, Ht, Wt = src_cam.height, src_cam.width, dst_cam.height, dst_cam.width
+        C_ = 0 if planes is None else int(planes.shape[0])
+        G = 0 if dcdx is None else int(dcdx.shape[0])
+        for t in (depth, alpha, planes, dcdx, dcdy):
+            if t is not None and not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError("warp inputs must be contiguous fp32 CUDA tensors")
+        if out is None:
+            out = alloc_warp_outputs(W, H, Wt, Ht, C_, G, keys)
+        gi = abi.GsWarpInput(_ptr(depth), _ptr(alpha), float(alpha_min), C_, _ptr(planes), G, _ptr(dcdx), _ptr(dcdy))
+        go = abi.GsWarpOutput(*[_ptr(out.get(k)) for k in WARP_KEYS])
+        sc, dc = camera_struct(src_cam), camera_struct(dst_cam)
+        check(abi.lib().gs_warp(self.h, C.byref(sc), C.byref(dc), C.byref(gi), C.byref(go), _stream_ptr(stream)))
+        return out
 
     def stats(self, reset=False, stream=None) -> dict:
         st = abi.GsFrameStats()

@@ -238,6 +238,21 @@ struct ProjectBwdArgs {
 };
 cudaError_t launch_project_backward(const ProjectBwdArgs &a, cudaStream_t s);
 
+// frame-interpolation warp (warp.cu): scatter + gather launches, and the
+// context-owned scratch it runs on (render.cu)
+gs_status check_warp_args(const gs_camera *src, const gs_camera *dst, const gs_warp_input *in,
+                          const gs_warp_output *out);
+bool warp_needs_positions(const gs_warp_input &in, const gs_warp_output &out);
+cudaError_t launch_warp(const gs_camera &src, const gs_camera &dst, const gs_warp_input &in, const gs_warp_output &out,
+                        float2 *pos, unsigned long long *best, cudaStream_t s);
+// Device of the context, and its warp scratch for n_src source and n_dst target
+// pixels; `best` is all ones on return (filled on (re)allocation or after a
+// failed call). A call that fails after launching must call warp_scratch_dirty.
+int context_device(const gs_context *ctx);
+gs_status context_warp_scratch(gs_context *ctx, size_t n_src, size_t n_dst, cudaStream_t st, float2 **pos,
+                               unsigned long long **best);
+void warp_scratch_dirty(gs_context *ctx);
+
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {

@@ -260,6 +260,8 @@ struct gs_context {
     uint32_t *h_counters = nullptr;  // pinned
     Buf g2d;
     Buf host_planes;
+    Buf warp_pos, warp_best;    // frame-interpolation warp: landing positions, depth-test slots
+    bool warp_best_clean = false;  // warp_best holds all ones (every slot empty)
     struct Tuned {
         int tile, batch, chunk;
     };
@@ -579,6 +581,30 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
 }
 
 }  // namespace
+}  // namespace gsr
+
+namespace gsr {
+
+int context_device(const gs_context *ctx) { return ctx->device; }
+
+gs_status context_warp_scratch(gs_context *ctx, size_t n_src, size_t n_dst, cudaStream_t st, float2 **pos,
+                               unsigned long long **best)
+{
+    GSR_CUDA(ctx->warp_pos.ensure(sizeof(float2) * std::max<size_t>(n_src, 1)));
+    void *old = ctx->warp_best.p;
+    GSR_CUDA(ctx->warp_best.ensure(sizeof(unsigned long long) * std::max<size_t>(n_dst, 1)));
+    if (ctx->warp_best.p != old || !ctx->warp_best_clean) {
+        // every slot starts empty; the gather kernel leaves it so after each call
+        GSR_CUDA(cudaMemsetAsync(ctx->warp_best.p, 0xFF, ctx->warp_best.bytes, st));
+        ctx->warp_best_clean = true;
+    }
+    *pos = ctx->warp_pos.as<float2>();
+    *best = ctx->warp_best.as<unsigned long long>();
+    return GS_OK;
+}
+
+void warp_scratch_dirty(gs_context *ctx) { ctx->warp_best_clean = false; }
+
 }  // namespace gsr
 
 // ============================================================================ C ABI

@@ -325,3 +325,17 @@ def warp_frame(width: int, height: int, seed: int, depth_range=(40.0, 130.0), oc
                 planes=planes.astype(np.float32),
                 dcdx=rng.standard_normal((grad_channels, height, width)).astype(np.float32),
                 dcdy=rng.standard_normal((grad_channels, height, width)).astype(np.float32))
+
+
+def interp_inputs(width: int = 960, height: int = 540, scale: int = 4, k: int = 0, seed: int = 11,
+                  channels: int = 7, grad_channels: int = 3) -> dict:
+    """The frame-interpolation warp workload of Sec. 4.2 for frames k, k + 1 of the large
+    scene's orbit: P0, P0.5, P1 at the low resolution; the high-resolution frame 0
+    (``scale`` x the size: colour, depth and normal planes, ``channels`` in all) that is
+    warped toward P0.5 at high resolution, and the low-resolution frame 1 (the same
+    planes plus ``grad_channels`` image-gradient planes) warped toward P0.5 at low
+    resolution."""
+    P0, P05, P1 = interpolation_cameras(width, height, k=k)
+    hr = warp_frame(width * scale, height * scale, seed, channels=channels, grad_channels=0)
+    lr = warp_frame(width, height, seed + 1, channels=channels, grad_channels=grad_channels)
+    return dict(P0=P0, P05=P05, P1=P1, P0_hr=P0.scaled(scale), P05_hr=P05.scaled(scale), hr=hr, lr=lr)
