@@ -265,27 +265,49 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
 // records gathered into sorted (instance) order, so compositing stages each
 // batch of a tile's list with one contiguous bulk copy. With `keys64` it also
 // writes each instance's (tile << 32) | depth-bits key (the state view's).
-__global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                         const uint32_t *__restrict__ counters, const GaussRec *__restrict__ rec,
-                         GaussRec *__restrict__ rec_sorted, uint2 *ranges, const uint4 *__restrict__ bin,
-                         uint64_t *__restrict__ keys64)
+// Four instances per thread, a block apart (every access coalesced), so that
+// the twelve 16-byte loads of their records are in flight together.
+constexpr int kRangeThreads = 256, kRangePer = 4;
+
+__global__ void __launch_bounds__(kRangeThreads)
+    k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+             const uint32_t *__restrict__ counters, const GaussRec *__restrict__ rec,
+             GaussRec *__restrict__ rec_sorted, uint2 *ranges, const uint4 *__restrict__ bin,
+             uint64_t *__restrict__ keys64)
 {
     const uint32_t K = counters[kCntEff];
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= K) return;
-    const uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-    if (i == K - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
-    const uint32_t g = vals[i];
-    if (rec_sorted) {
-        const GaussRec *src = rec + g;
-        GaussRec r;
-        r.r0 = __ldg(&src->r0);
-        r.r1 = __ldg(&src->r1);
-        r.r2 = __ldg(&src->r2);
-        rec_sorted[i] = r;
+    const uint32_t i0 = blockIdx.x * (kRangeThreads * kRangePer) + threadIdx.x;
+    uint32_t g[kRangePer];
+#pragma unroll
+    for (int k = 0; k < kRangePer; ++k) {
+        const uint32_t i = i0 + (uint32_t)k * kRangeThreads;
+        g[k] = i < K ? vals[i] : 0u;
     }
-    if (keys64) keys64[i] = ((uint64_t)t << 32) | (uint64_t)bin[g].x;
+    if (rec_sorted) {
+        GaussRec r[kRangePer];
+#pragma unroll
+        for (int k = 0; k < kRangePer; ++k) {
+            if (i0 + (uint32_t)k * kRangeThreads >= K) continue;
+            const GaussRec *src = rec + g[k];
+            r[k].r0 = __ldg(&src->r0);
+            r[k].r1 = __ldg(&src->r1);
+            r[k].r2 = __ldg(&src->r2);
+        }
+#pragma unroll
+        for (int k = 0; k < kRangePer; ++k) {
+            const uint32_t i = i0 + (uint32_t)k * kRangeThreads;
+            if (i < K) rec_sorted[i] = r[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kRangePer; ++k) {
+        const uint32_t i = i0 + (uint32_t)k * kRangeThreads;
+        if (i >= K) continue;
+        const uint32_t t = keys[i];
+        if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
+        if (i == K - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
+        if (keys64) keys64[i] = ((uint64_t)t << 32) | (uint64_t)bin[g[k]].x;
+    }
 }
 
 // Tiles ordered by decreasing list length, bucketed by floor(log2(length)), so
@@ -489,9 +511,9 @@ cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess) return e;
     if (max_k <= 0) return cudaSuccess;
-    const int threads = 256;
-    const int64_t nb = (max_k + threads - 1) / threads;
-    k_ranges<<<(unsigned)nb, threads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges, bin, keys64);
+    const int64_t per_block = (int64_t)kRangeThreads * kRangePer;
+    const int64_t nb = (max_k + per_block - 1) / per_block;
+    k_ranges<<<(unsigned)nb, kRangeThreads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges, bin, keys64);
     return cudaGetLastError();
 }
 

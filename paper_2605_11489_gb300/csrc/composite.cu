@@ -17,10 +17,11 @@
 // with its own shared-memory ring of kStages batches of BATCH records and its
 // own mbarriers. Lane 0 stages the next batches of the tile's (contiguous,
 // sorted) records with one TMA bulk copy per batch (cp.async.bulk, completion
-// counted on the warp's mbarrier) while the warp blends the current one; the
-// warp builds, with one ballot per 32 records, the mask of records whose
-// rectangle reaches its block; from those, each lane keeps the ones whose
-// rectangle holds its own pixel and blends only these, in order. No barrier
+// counted on the warp's mbarrier) while the warp blends the current one; per
+// group of 32 records, each lane forms the mask of block pixels inside one
+// record's rectangle, and a warp-wide bit transpose of those masks gives each
+// lane the records whose rectangle holds its own pixel; it blends only these,
+// in order. No barrier
 // spans warps: a warp whose pixels are all saturated stops on its own. The
 // tile's list is read once per warp from L2 (DRAM once). Waits are bounded.
 //
@@ -139,6 +140,22 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// 32x32 bit-matrix transpose across a warp: lane j holds row j (bit L = column
+// L); returns column `lane` (bit j = row j's bit `lane`). Five butterfly stages,
+// each swapping the off-diagonal blocks of the next-smaller block size.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
+{
+    const uint32_t keep[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int sh = 16 >> k;
+        const uint32_t m = keep[k];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sh);
+        x = (lane & sh) ? ((x & ~m) | ((y >> sh) & m)) : ((x & m) | ((y & m) << sh));
+    }
+    return x;
+}
+
 template <int BATCH>
 __device__ __forceinline__ void ring_init(WarpRing<BATCH> &ring)
 {
@@ -178,8 +195,6 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
     };
 
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-    const uint32_t upx = (uint32_t)px, upy = (uint32_t)py;
-    const uint32_t wx0 = (uint32_t)bx0, wx1 = (uint32_t)(bx0 + 7), wy0 = (uint32_t)by0, wy1 = (uint32_t)(by0 + 3);
     bool ok = true;
 
     for (int b = 0; b < kStages - 1 && b < nbatches; ++b) issue(b);
@@ -198,36 +213,26 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
         const uint32_t pos_b = pos0 + (uint32_t)b * BATCH + 1u;
 #pragma unroll
         for (int w = 0; w < BATCH / 32; ++w) {
-            // records of this group of 32 whose rectangle reaches the warp's block
+            // Each lane takes record w*32 + lane of the batch and forms the mask of
+            // the warp's 8x4 block pixels (bit 8*row + column = the lane owning that
+            // pixel) inside its support rectangle; a transpose of these 32 masks
+            // across the warp gives every lane its own list: the records of the
+            // group whose rectangle holds its pixel, in list order. Each lane then
+            // blends only these, at its own pace.
             const uint32_t kk = (uint32_t)w * 32u + (uint32_t)lane;
-            uint32_t lo = 0xFFFFFFFFu, hi = 0u;  // an empty rectangle past the batch's end
+            uint32_t cover = 0u;
             if (kk < cnt) {
-                lo = __float_as_uint(recs[kk].r2.z);
-                hi = __float_as_uint(recs[kk].r2.w);
+                const uint32_t lo = __float_as_uint(recs[kk].r2.z), hi = __float_as_uint(recs[kk].r2.w);
+                const int x0 = max((int)(lo & 0xFFFFu) - bx0, 0), x1 = min((int)(hi & 0xFFFFu) - bx0, 7);
+                const int y0 = max((int)(lo >> 16) - by0, 0), y1 = min((int)(hi >> 16) - by0, 3);
+                if (x0 <= x1 && y0 <= y1) {
+                    const uint32_t xm = (0xFFu >> (7 - x1)) & (0xFFu << x0);
+                    const uint32_t rows = (0xFu >> (3 - y1)) & (0xFu << y0);
+                    cover = xm * ((rows & 1u) | ((rows & 2u) << 7) | ((rows & 4u) << 14) | ((rows & 8u) << 21));
+                }
             }
-            const bool hit = (hi >> 16) >= wy0 && (lo >> 16) <= wy1 && (hi & 0xFFFFu) >= wx0 && (lo & 0xFFFFu) <= wx1;
-            uint32_t m = __ballot_sync(0xffffffffu, hit);
-            // this lane's own list: the hit records whose rectangle holds its
-            // pixel. A warp-uniform pass over the hits, four at a time, with
-            // each rectangle taken from the lane that loaded it; then only
-            // those records are blended, each lane at its own pace.
-            uint32_t mine = 0u;
-            auto holds = [&](int j) {
-                const uint32_t l = __shfl_sync(0xffffffffu, lo, j), h = __shfl_sync(0xffffffffu, hi, j);
-                return upx >= (l & 0xFFFFu) && upx <= (h & 0xFFFFu) && upy >= (l >> 16) && upy <= (h >> 16);
-            };
-            while (m) {
-                const int j0 = __ffs(m) - 1;
-                m &= m - 1u;
-                const int j1 = m ? __ffs(m) - 1 : j0;
-                m &= m - 1u;
-                const int j2 = m ? __ffs(m) - 1 : j0;
-                m &= m - 1u;
-                const int j3 = m ? __ffs(m) - 1 : j0;
-                m &= m - 1u;
-                const bool h0 = holds(j0), h1 = holds(j1), h2 = holds(j2), h3 = holds(j3);
-                mine |= (h0 ? 1u << j0 : 0u) | (h1 ? 1u << j1 : 0u) | (h2 ? 1u << j2 : 0u) | (h3 ? 1u << j3 : 0u);
-            }
+            if (!__any_sync(0xffffffffu, cover != 0u)) continue;
+            uint32_t mine = warp_transpose32(cover, lane);
             if (s.done) mine = 0u;
             if (mine) {  // the next record's loads are issued before the current one is blended
                 uint32_t k = (uint32_t)w * 32u + (uint32_t)(__ffs(mine) - 1);

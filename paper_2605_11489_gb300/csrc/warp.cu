@@ -19,15 +19,17 @@
 // determinant (a fold) gives a zero warped gradient.
 //
 // Two launches:
-//   k_warp_scatter (one thread per source pixel): the landing position, fixed
-//     to one fp32 round-to-nearest operation sequence (no contraction), written
-//     to a position scratch and (optionally) as the motion map; an atomicMin of
-//     the 64-bit key (z bits << 32 | source index) into the target pixel's slot.
-//     z > near >= 0, so the bit pattern of z orders like its value.
-//   k_warp_gather (one thread per target pixel): reads and resets its slot (so
-//     the slot array is all ones again for the next call), copies the winner's
-//     planes, and forms the warped gradient from the winner's neighbours'
-//     positions.
+//   k_warp_scatter (one thread per source column over 4 rows): the landing
+//     position, fixed to one fp32 round-to-nearest operation sequence (no
+//     contraction), written to a position scratch (only when the warped
+//     gradient is asked for) and as the motion map; an atomicMin of the 64-bit
+//     key (z bits << 32 | source index) into the target pixel's slot. z > near
+//     >= 0, so the bit pattern of z orders like its value.
+//   k_warp_gather (four target pixels per thread, a block apart): reads and
+//     resets the slots (so the slot array is all ones again for the next
+//     call), copies the winners' planes with every load of four channels in
+//     flight at once, and forms the warped gradient from each winner's
+//     neighbours' positions.
 #include <cuda_runtime.h>
 
 #include "gsr_internal.cuh"
@@ -45,12 +47,18 @@ struct WarpCams {
     int32_t W, H, Wt, Ht;
 };
 
-// Landing position (u, v) and target-camera z of source pixel (i, j) at lifted
-// depth d: every operation rounded to nearest, in this order.
-__device__ __forceinline__ bool land(const WarpCams &c, int i, int j, float d, float &u, float &v, float &z)
+// Normalised ray offset of pixel-centre coordinate k for focal f and principal
+// point c: ((k + 0.5) - c) / f, rounded to nearest at each step.
+__device__ __forceinline__ float ray_offset(int k, float cpp, float f)
 {
-    const float xn = __fdiv_rn(__fsub_rn(__fadd_rn((float)i, 0.5f), c.scx), c.sfx);
-    const float yn = __fdiv_rn(__fsub_rn(__fadd_rn((float)j, 0.5f), c.scy), c.sfy);
+    return __fdiv_rn(__fsub_rn(__fadd_rn((float)k, 0.5f), cpp), f);
+}
+
+// Landing position (u, v) and target-camera z of the source pixel whose ray
+// offsets are (xn, yn), at lifted depth d: every operation rounded to nearest,
+// in this order.
+__device__ __forceinline__ bool land(const WarpCams &c, float xn, float yn, float d, float &u, float &v, float &z)
+{
     const float a0 = __fsub_rn(__fmul_rn(xn, d), c.sv[3]);
     const float a1 = __fsub_rn(__fmul_rn(yn, d), c.sv[7]);
     const float a2 = __fsub_rn(d, c.sv[11]);
@@ -71,37 +79,52 @@ __device__ __forceinline__ bool land(const WarpCams &c, int i, int j, float d, f
     return true;
 }
 
+// One thread per source column over kScatterRows rows: the column's ray offset
+// is computed once and the rows' offsets once per block (the same values a
+// per-pixel evaluation gives).
+constexpr int kScatterRows = 4;
+
 template <bool kAlpha>
 __global__ void __launch_bounds__(kWarpThreadsX) k_warp_scatter(WarpCams c, const float *__restrict__ depth,
                                                                 const float *__restrict__ alpha, float alpha_min,
                                                                 float2 *__restrict__ pos, float *__restrict__ motion,
                                                                 unsigned long long *__restrict__ best)
 {
-    const int i = blockIdx.x * kWarpThreadsX + threadIdx.x, j = blockIdx.y;
+    __shared__ float s_yn[kScatterRows];
+    const int i = blockIdx.x * kWarpThreadsX + threadIdx.x, j0 = blockIdx.y * kScatterRows;
+    if (threadIdx.x < kScatterRows) s_yn[threadIdx.x] = ray_offset(j0 + (int)threadIdx.x, c.scy, c.sfy);
+    __syncthreads();
     if (i >= c.W) return;
-    const size_t p = (size_t)j * c.W + i;
+    const float xn = ray_offset(i, c.scx, c.sfx);
     const size_t n = (size_t)c.W * c.H;
-    float d;
-    bool moves;
-    if (kAlpha) {
-        const float a = alpha[p];
-        moves = a > alpha_min;
-        d = moves ? __fdiv_rn(depth[p], a) : 0.f;
-    } else {
-        d = depth[p];
-        moves = d > 0.f;
-    }
-    float u = __int_as_float(0x7fc00000), v = u, z = 0.f;
-    if (moves) moves = land(c, i, j, d, u, v, z);
-    if (!moves) u = v = __int_as_float(0x7fc00000);
-    if (pos) pos[p] = make_float2(u, v);  // only the warped gradient needs the neighbours' positions
-    if (motion) {
-        motion[p] = moves ? __fsub_rn(u, __fadd_rn((float)i, 0.5f)) : u;
-        motion[n + p] = moves ? __fsub_rn(v, __fadd_rn((float)j, 0.5f)) : v;
-    }
-    if (moves && u >= 0.f && u < (float)c.Wt && v >= 0.f && v < (float)c.Ht) {
-        const size_t q = (size_t)floorf(v) * c.Wt + (size_t)floorf(u);
-        atomicMin(best + q, ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)p);
+    const float qnan = __int_as_float(0x7fc00000);
+#pragma unroll
+    for (int r = 0; r < kScatterRows; ++r) {
+        const int j = j0 + r;
+        if (j >= c.H) break;
+        const size_t p = (size_t)j * c.W + i;
+        float d;
+        bool moves;
+        if (kAlpha) {
+            const float a = alpha[p];
+            moves = a > alpha_min;
+            d = moves ? __fdiv_rn(depth[p], a) : 0.f;
+        } else {
+            d = depth[p];
+            moves = d > 0.f;
+        }
+        float u = qnan, v = qnan, z = 0.f;
+        if (moves) moves = land(c, xn, s_yn[r], d, u, v, z);
+        if (!moves) u = v = qnan;
+        if (pos) pos[p] = make_float2(u, v);  // only the warped gradient needs the neighbours' positions
+        if (motion) {
+            motion[p] = moves ? __fsub_rn(u, __fadd_rn((float)i, 0.5f)) : u;
+            motion[n + p] = moves ? __fsub_rn(v, __fadd_rn((float)j, 0.5f)) : v;
+        }
+        if (moves && u >= 0.f && u < (float)c.Wt && v >= 0.f && v < (float)c.Ht) {
+            const size_t q = (size_t)floorf(v) * c.Wt + (size_t)floorf(u);
+            atomicMin(best + q, ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)p);
+        }
     }
 }
 
@@ -277,7 +300,7 @@ cudaError_t launch_warp(const gs_camera &src, const gs_camera &dst, const gs_war
     const WarpCams c = warp_cams(src, dst);
     if (!warp_needs_positions(in, out)) pos = nullptr;
     const dim3 blk(kWarpThreadsX);
-    const dim3 gs((src.width + kWarpThreadsX - 1) / kWarpThreadsX, src.height);
+    const dim3 gs((src.width + kWarpThreadsX - 1) / kWarpThreadsX, (src.height + kScatterRows - 1) / kScatterRows);
     const size_t nt = (size_t)dst.width * dst.height;
     const unsigned gt = (unsigned)((nt + kGatherThreads * kGatherPx - 1) / (kGatherThreads * kGatherPx));
     if (in.alpha)
