@@ -265,8 +265,13 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
 // records gathered into sorted (instance) order, so compositing stages each
 // batch of a tile's list with one contiguous bulk copy. With `keys64` it also
 // writes each instance's (tile << 32) | depth-bits key (the state view's).
-// Four instances per thread, a block apart (every access coalesced), so that
-// the twelve 16-byte loads of their records are in flight together.
+// The sorted records are gathered one 16-byte piece per thread: piece e of the
+// output is piece e % 3 of record vals[e / 3], so three consecutive lanes read
+// one record's 48 contiguous bytes and a warp's stores are 512 contiguous bytes
+// (with a thread per record, every lane's load and store touched its own line
+// and the L1 request path bound the kernel). Each thread takes four pieces, a
+// block apart, so their loads are in flight together. The pieces with e % 3 == 0
+// also write the tile ranges and (keys64 != NULL) the 64-bit keys.
 constexpr int kRangeThreads = 256, kRangePer = 4;
 
 __global__ void __launch_bounds__(kRangeThreads)
@@ -276,33 +281,34 @@ __global__ void __launch_bounds__(kRangeThreads)
              uint64_t *__restrict__ keys64)
 {
     const uint32_t K = counters[kCntEff];
-    const uint32_t i0 = blockIdx.x * (kRangeThreads * kRangePer) + threadIdx.x;
+    const uint32_t P = 3u * K;  // 16-byte pieces (K < 2^30)
+    const uint32_t e0 = blockIdx.x * (kRangeThreads * kRangePer) + threadIdx.x;
+    const float4 *src = reinterpret_cast<const float4 *>(rec);
+    float4 *dst = reinterpret_cast<float4 *>(rec_sorted);
+    float4 v[kRangePer];
     uint32_t g[kRangePer];
 #pragma unroll
     for (int k = 0; k < kRangePer; ++k) {
-        const uint32_t i = i0 + (uint32_t)k * kRangeThreads;
-        g[k] = i < K ? vals[i] : 0u;
+        const uint32_t e = e0 + (uint32_t)k * kRangeThreads;
+        g[k] = e < P ? vals[e / 3u] : 0u;
     }
     if (rec_sorted) {
-        GaussRec r[kRangePer];
 #pragma unroll
         for (int k = 0; k < kRangePer; ++k) {
-            if (i0 + (uint32_t)k * kRangeThreads >= K) continue;
-            const GaussRec *src = rec + g[k];
-            r[k].r0 = __ldg(&src->r0);
-            r[k].r1 = __ldg(&src->r1);
-            r[k].r2 = __ldg(&src->r2);
+            const uint32_t e = e0 + (uint32_t)k * kRangeThreads;
+            if (e < P) v[k] = __ldg(src + 3ull * g[k] + e % 3u);
         }
 #pragma unroll
         for (int k = 0; k < kRangePer; ++k) {
-            const uint32_t i = i0 + (uint32_t)k * kRangeThreads;
-            if (i < K) rec_sorted[i] = r[k];
+            const uint32_t e = e0 + (uint32_t)k * kRangeThreads;
+            if (e < P) dst[e] = v[k];
         }
     }
 #pragma unroll
     for (int k = 0; k < kRangePer; ++k) {
-        const uint32_t i = i0 + (uint32_t)k * kRangeThreads;
-        if (i >= K) continue;
+        const uint32_t e = e0 + (uint32_t)k * kRangeThreads;
+        if (e >= P || e % 3u != 0u) continue;
+        const uint32_t i = e / 3u;
         const uint32_t t = keys[i];
         if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
         if (i == K - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
@@ -512,7 +518,7 @@ cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint
     if (e != cudaSuccess) return e;
     if (max_k <= 0) return cudaSuccess;
     const int64_t per_block = (int64_t)kRangeThreads * kRangePer;
-    const int64_t nb = (max_k + per_block - 1) / per_block;
+    const int64_t nb = (3 * max_k + per_block - 1) / per_block;
     k_ranges<<<(unsigned)nb, kRangeThreads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges, bin, keys64);
     return cudaGetLastError();
 }

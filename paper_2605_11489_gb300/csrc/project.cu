@@ -14,10 +14,9 @@
 // Any other fp32 implementation of the same sequence reproduces them bit for
 // bit.
 //
-// Layout: in k_project one thread owns 4 consecutive Gaussians and reads every
-// geometry plane with one 16-byte load per plane (planes are 16-byte aligned,
-// stride a multiple of 4), so a warp moves 512 contiguous bytes per plane; it
-// writes whole records with the colour left at 0. k_colour then streams the SH
+// Layout: in k_project one thread owns one Gaussian, so a warp reads 128
+// contiguous bytes of every geometry plane; it writes whole records with the
+// colour left at 0. k_colour then streams the SH
 // planes (192 B per Gaussian at degree 3) for the visible Gaussians only, one
 // thread each, and fills in the colour.
 #include "gsr_internal.cuh"
@@ -174,10 +173,6 @@ __device__ __forceinline__ void project_one(const CamParams &c, float mx, float 
     P.nt = (uint32_t)(((x1 >> sh) - (x0 >> sh) + 1) * ((y1 >> sh) - (y0 >> sh) + 1));
 }
 
-__device__ __forceinline__ float lane4(const float4 &v, int g)
-{
-    return g == 0 ? v.x : g == 1 ? v.y : g == 2 ? v.z : v.w;
-}
 
 // Real SH basis value k (l-major, m = -l..l, Condon-Shortley phase) at unit (x, y, z).
 template <int K>
@@ -253,50 +248,42 @@ __global__ void __launch_bounds__(256) k_colour(ProjectArgs a)
     r[9] = fmaxf(col[2] + 0.5f, 0.0f);  // r2.y
 }
 
-__global__ void __launch_bounds__(kProjThreads) k_project(ProjectArgs a)
+// One Gaussian per thread, kProjPerBlock (1,024) per block -- the unit of the
+// per-block tile and visibility sums the scan reads. A warp reads 128
+// contiguous bytes of every plane. (Four Gaussians per thread with 16-byte
+// loads needed 80 registers and left the SMs at ~36 % warp occupancy.)
+constexpr int kGeomThreads = kProjPerBlock;
+
+__global__ void __launch_bounds__(kGeomThreads, 1) k_project(ProjectArgs a)
 {
-    const int64_t q = (int64_t)blockIdx.x * kProjThreads + threadIdx.x;
-    const int64_t i0 = q * 4;
+    const int64_t i = (int64_t)blockIdx.x * kGeomThreads + threadIdx.x;
+    const int64_t n4 = (a.n + 3) & ~(int64_t)3;  // ntiles is read 4 at a time: its padding is written 0
     uint32_t my_tiles = 0, my_vis = 0;
-    if (i0 < a.n) {
-        const int64_t np = a.n_pad;
-        auto ld4 = [&](const float *base, int row) {
-            return __ldg(reinterpret_cast<const float4 *>(base + (int64_t)row * np + i0));
-        };
-        const float4 mx = ld4(a.means, 0), my = ld4(a.means, 1), mz = ld4(a.means, 2);
-        const float4 l0 = ld4(a.log_scales, 0), l1 = ld4(a.log_scales, 1), l2 = ld4(a.log_scales, 2);
-        const float4 qw = ld4(a.quats, 0), qx = ld4(a.quats, 1), qy = ld4(a.quats, 2), qz = ld4(a.quats, 3);
-        const float4 lg = ld4(a.logits, 0);
-        // records of visible Gaussians, colour left 0 for k_colour
-        struct Keep {
-            bool vis;
-            uint32_t nt;
-        } P[4];
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            Proj Q;
-            Q.vis = false;
-            Q.nt = 0;
-            if (i0 + g < a.n)
-                project_one(a.cam, lane4(mx, g), lane4(my, g), lane4(mz, g), lane4(l0, g), lane4(l1, g), lane4(l2, g),
-                            lane4(qw, g), lane4(qx, g), lane4(qy, g), lane4(qz, g), lane4(lg, g), Q);
-            P[g].vis = Q.vis;
-            P[g].nt = Q.nt;
-            if (Q.vis) {
-                GaussRec r;
-                r.r0 = make_float4(Q.u, Q.v, Q.ca, Q.cb);
-                r.r1 = make_float4(Q.cc, Q.o, Q.z, 0.0f);
-                r.r2 = make_float4(0.0f, 0.0f, __uint_as_float(Q.rlo), __uint_as_float(Q.rhi));
-                a.rec[i0 + g] = r;
-                a.bin[i0 + g] = make_uint4(__float_as_uint(Q.z), Q.rlo, Q.rhi, 0u);
-            }
+    if (i < n4) {
+        Proj Q;
+        Q.vis = false;
+        Q.nt = 0;
+        if (i < a.n) {
+            const int64_t np = a.n_pad;
+            auto ld = [&](const float *base, int row) { return __ldg(base + (int64_t)row * np + i); };
+            project_one(a.cam, ld(a.means, 0), ld(a.means, 1), ld(a.means, 2), ld(a.log_scales, 0),
+                        ld(a.log_scales, 1), ld(a.log_scales, 2), ld(a.quats, 0), ld(a.quats, 1), ld(a.quats, 2),
+                        ld(a.quats, 3), ld(a.logits, 0), Q);
         }
-        *reinterpret_cast<uint4 *>(a.ntiles + i0) = make_uint4(P[0].nt, P[1].nt, P[2].nt, P[3].nt);
-        my_tiles = P[0].nt + P[1].nt + P[2].nt + P[3].nt;
-        my_vis = (uint32_t)P[0].vis + (uint32_t)P[1].vis + (uint32_t)P[2].vis + (uint32_t)P[3].vis;
+        if (Q.vis) {  // colour left 0 for k_colour
+            GaussRec r;
+            r.r0 = make_float4(Q.u, Q.v, Q.ca, Q.cb);
+            r.r1 = make_float4(Q.cc, Q.o, Q.z, 0.0f);
+            r.r2 = make_float4(0.0f, 0.0f, __uint_as_float(Q.rlo), __uint_as_float(Q.rhi));
+            a.rec[i] = r;
+            a.bin[i] = make_uint4(__float_as_uint(Q.z), Q.rlo, Q.rhi, 0u);
+        }
+        a.ntiles[i] = Q.nt;
+        my_tiles = Q.nt;
+        my_vis = Q.vis ? 1u : 0u;
     }
     // block sum of tiles touched -> per-block sums for the instance-offset scan
-    __shared__ uint32_t s_warp[2][kProjThreads / 32];
+    __shared__ uint32_t s_warp[2][kGeomThreads / 32];
     uint32_t v = my_tiles, c = my_vis;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -311,7 +298,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjectArgs a)
     if (threadIdx.x == 0) {
         uint32_t t = 0, cv = 0;
 #pragma unroll
-        for (int w = 0; w < kProjThreads / 32; ++w) {
+        for (int w = 0; w < kGeomThreads / 32; ++w) {
             t += s_warp[0][w];
             cv += s_warp[1][w];
         }
@@ -347,7 +334,7 @@ cudaError_t launch_project_geometry(const ProjectArgs &a, cudaStream_t s)
 {
     const int nb = project_blocks(a.n);
     if (nb == 0) return cudaSuccess;
-    k_project<<<nb, kProjThreads, 0, s>>>(a);
+    k_project<<<nb, kGeomThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
