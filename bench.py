@@ -11,7 +11,7 @@ Prints one JSON line. Default workload: 1M clustered Gaussians, SH degree 3,
 960x540, 60-frame orbit (steps cycle over the orbit).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload large|ultra|ultra_lr|tiny|serve|interp]
+                  [--workload large|ultra|ultra_lr|tiny|serve|interp|gass]
 
 With --gpus N > 1 (launched by torchrun) every rank renders the same workload
 as an independent replica (the render has no cross-GPU exchange); value is the
@@ -170,6 +170,8 @@ def run_reference(args):
     oracle.build()
     if args.workload == "interp":
         return run_reference_interp(args, world)
+    if args.workload == "gass":
+        return run_reference_gass(args, world)
     sc, cams = make_workload(args.workload)
     osc = oracle.OScene(sc)
     cores = oracle.max_threads()
@@ -228,6 +230,43 @@ def run_reference_interp(args, world):
                                             "step": "one of the two warps, alternating"},
             "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                              "sample": "%d warps (or_warp, single-threaded C)" % args.steps},
+            "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_gass(args, world):
+    """--impl reference --workload gass: the oracle's gradient-aware interpolation (NumPy
+    FP64, Conv -> TConv) of the same 4x upsampling; a step is one band of 32 rows of the
+    oracle's own 960x540 render (colour and gradients)."""
+    import oracle
+    from oracle import gai as og
+
+    from paper_2605_11489_gb300 import synth
+
+    sc, cams = make_workload("large")
+    r = oracle.render(oracle.OScene(sc), cams[0])
+    S, wc, bc, wt, bt = synth.gai_weights(4, 32)
+    H, W = r["rgb"].shape[1:]
+    band = 32
+
+    def step(i):
+        y0 = (i * band) % H
+        sl = slice(y0, min(H, y0 + band))
+        og.gai(r["rgb"][:, sl], r["dcdx"][:, sl], r["dcdy"][:, sl], wc, bc, wt, bt, S)
+        return S * S * W * (sl.stop - sl.start)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    px = sum(step(args.warmup + i) for i in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = px / dt / 1e6
+    line = {"metric": "gass interpolation Mpix/s (4x output pixels)", "value": v, "unit": "Mpix/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {"workload": "gass", "desc": GASS_DESC, "step": "a band of 32 rows"},
+            "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d bands of %d rows (oracle.gai, NumPy FP64)" % (args.steps, band)},
             "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -494,6 +533,127 @@ def run_interp(args):
         torch.distributed.destroy_process_group()
 
 
+GASS_DESC = ("gradient-aware interpolation of Sec. 4.1 (Eq. 7-8): the 960x540 render of the large scene "
+             "(rgb, dC/dx, dC/dy of frame 0) super-sampled x4 to 3840x2160; seeded Conv3x3 (27 -> 32) and 4x4 "
+             "TConv weights")
+
+
+def run_gass(args):
+    """--workload gass: gs_gai_upsample of a rendered frame (resident) by 4; one JSON line."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2605_11489_gb300 import api, synth
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    sc, cams = make_workload("large")
+    W, H = cams[0].width, cams[0].height
+    weights = synth.gai_weights(4, 32)
+    S = weights[0]
+    stream = torch.cuda.Stream()
+    ctx = api.Context(local_rank)
+    with torch.cuda.stream(stream):
+        scene = api.Scene.from_arrays(sc)
+        frame = ctx.forward(scene, cams[0], keys=("rgb", "dcdx", "dcdy"), stream=stream)
+        out = torch.empty((3, S * H, S * W), dtype=torch.float32, device="cuda")
+    stream.synchronize()
+    del scene
+    step = lambda: api.gai_upsample(weights, frame["rgb"], frame["dcdx"], frame["dcdy"], out=out, stream=stream)
+    for _ in range(args.warmup):
+        step()
+    clk_path = os.path.join(tempfile.gettempdir(), "gsr_clocks_gass_%d_%d.csv" % (os.getpid(), rank))
+    smi, smi_f = start_clock_sampler(clk_path, local_rank)
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        torch.distributed.barrier()
+    if smi:
+        smi.terminate()
+        smi.wait()
+        smi_f.close()
+    clocks = read_clocks(clk_path)
+    ms = slowest_rank(ms, world, "cuda")
+    hr_px = S * S * W * H
+    value = job_throughput(hr_px * args.steps, world, ms * 1e-3)
+    hbm_peak, sm_max_mhz, peak_src = measured_peaks()
+    # algorithmic bytes of one launch: the three input planes once (3 channels x 4 B each)
+    # and the S*S outputs (3 channels x 4 B each) per low-resolution pixel
+    bytes_launch = W * H * (3 * 3 * 4 + 3 * S * S * 4)
+    launch_ms = ms / args.steps
+    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+    fma = 3 * W * H * S * S * 27
+    roof = {"bound": "hbm", "kernel": "k_gai<4>", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": None,
+            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src,
+            "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": launch_ms,
+            "fp32_frac": 2 * fma / (launch_ms * 1e-3) / 1e12 / fp32_peak_tflops(sm_max_mhz)}
+    e2e = None
+    if not args.no_e2e:
+        h_in = {k: v.cpu().pin_memory() for k, v in frame.items()}
+        h_out = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+        d_in = {k: torch.empty_like(v) for k, v in frame.items()}
+        n_e = min(args.steps, 30)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e):
+            with torch.cuda.stream(stream):
+                for k in d_in:
+                    d_in[k].copy_(h_in[k], non_blocking=True)
+                api.gai_upsample(weights, d_in["rgb"], d_in["dcdx"], d_in["dcdy"], out=out, stream=stream)
+                h_out.copy_(out, non_blocking=True)
+            stream.synchronize()
+        dt = slowest_rank(time.perf_counter() - t0, world, "cuda")
+        e2e = {"value": job_throughput(hr_px * n_e, world, dt), "unit": "Mpix/s",
+               "h2d_bytes_per_step": 9 * W * H * 4, "d2h_bytes_per_step": 3 * hr_px * 4,
+               "path": "torch H2D of rgb, dC/dx, dC/dy + gs_gai_upsample + D2H of the 4x image"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import gai as og
+
+        f = {k: v.cpu().numpy().astype(np.float64) for k, v in frame.items()}
+        rows = 0
+        t0 = time.perf_counter()
+        while rows < H and (rows == 0 or time.perf_counter() - t0 < 10.0):
+            band = slice(rows, min(H, rows + 64))
+            og.gai(f["rgb"][:, band], f["dcdx"][:, band], f["dcdy"][:, band], *weights[1:], S)
+            rows = band.stop
+        dt = time.perf_counter() - t0
+        cpu = {"value": S * S * W * rows / dt / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+               "sample": "%d of %d low-resolution rows in bands of 64 (oracle.gai, NumPy FP64, Conv -> TConv) "
+                         "in %.1f s" % (rows, H, dt)}
+    if rank == 0:
+        line = {"metric": "gass interpolation Mpix/s (4x output pixels)", "value": value, "unit": "Mpix/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": launch_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "gass", "desc": GASS_DESC, "scale": S, "features": int(weights[1].shape[0]),
+                           "l2": "output larger than L2 (%.0f MB per step)" % (3 * hr_px * 4 / 1e6),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+                "gpu_launches": args.steps}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def algorithmic(stage, w, deg, n, K_avg, V_avg, tile_passes, pixels, pairs):
     """Algorithmic work of one launch of `stage` (bytes, or FP32 ops for compositing)."""
     sh_bytes = 12 * (deg + 1) ** 2
@@ -555,7 +715,7 @@ def main():
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["serve", "interp"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["serve", "interp", "gass"])
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="serve: scale of the scene sizes")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: sort-buffer budget")
@@ -576,6 +736,8 @@ def main():
         return run_serving(args)
     if args.workload == "interp":
         return run_interp(args)
+    if args.workload == "gass":
+        return run_gass(args)
 
     import torch
 

@@ -323,6 +323,38 @@ typedef struct {                  /* every plane nullable (NULL = not written) *
 gs_status gs_warp(gs_context *ctx, const gs_camera *src, const gs_camera *dst, const gs_warp_input *in,
                   const gs_warp_output *out, gs_stream stream);
 
+/* ---------------------------------------------------------------- gradient-aware interpolation
+ * The interpolation step of the paper's super-sampling (Sec. 4.1, "Gradient-Aware
+ * Interpolation", Eq. 5-8), applied to the render's outputs: each low-resolution pixel's
+ * S x S high-resolution block is a linear map of its 3x3 neighbourhood's colour and
+ * analytic gradients (Eq. 7),
+ *   Vec(I_SxS) = M [Vec(I_3x3); Vec(dI/dx_3x3); Vec(dI/dy_3x3)] + b.
+ * Vec is column-wise: input 9 q + 3 (i + 1) + (j + 1) is plane q (0 colour, 1 dI/dx,
+ * 2 dI/dy) at node (x0 + i, y0 + j), and output u S + v is the high-resolution pixel
+ * (S x0 + u, S y0 + v). Nodes outside the image read 0.
+ * The weights come as the paper's two layers (Eq. 8): a 3x3 convolution to `features`
+ * channels (wc, bc) and an SxS stride-S transposed convolution (wt, bt). The call folds
+ * them, in double, into M = wt wc and b = wt bc + bt, and evaluates M x + b in fp32. The
+ * same weights serve every colour channel. The paper's refinement network (GTRR) is not
+ * part of this call. */
+typedef struct {
+    int32_t scale;                /* S: 2, 3 or 4 */
+    int32_t features;             /* C, the feature channels between the layers: 1..1024 */
+    const float *wc;              /* [C][27] host, row-major (convolution weights) */
+    const float *bc;              /* [C] host, nullable = 0 */
+    const float *wt;              /* [S*S][C] host, row-major (transposed-convolution weights) */
+    const float *bt;              /* [S*S] host, nullable = 0 */
+} gs_gai_weights;
+
+/* Super-samples `channels` planes of W x H (rgb, dcdx, dcdy: device, [channels][H][W]
+ * fp32, caller-owned, 4-byte aligned) into out ([channels][S H][S W] fp32, device,
+ * caller-owned, 16-byte aligned). One kernel launch on `stream` (current CUDA device),
+ * asynchronous; the weights are read on the host during the call. Allocates nothing.
+ * Errors: GS_ERR_INVALID_ARG (NULL weights or planes, scale not 2..4, features not
+ * 1..1024, channels not 1..64, sizes outside 1..65535, misaligned planes), GS_ERR_CUDA. */
+gs_status gs_gai_upsample(const gs_gai_weights *w, const float *rgb, const float *dcdx, const float *dcdy,
+                          int32_t channels, int32_t width, int32_t height, float *out, gs_stream stream);
+
 /* ---------------------------------------------------------------- misc */
 const char *gs_last_error(void);
 const char *gs_version(void);

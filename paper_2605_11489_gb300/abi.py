@@ -36,7 +36,7 @@ ENTRY_POINTS = (
     "gs_render_backward", "gs_state_view_get", "gs_context_stats", "gs_state_free", "gs_graph_create",
     "gs_graph_render", "gs_graph_check", "gs_graph_stats", "gs_graph_destroy", "gs_autotune", "gs_server_create", "gs_server_load_scene",
     "gs_server_submit", "gs_server_poll", "gs_server_cancel", "gs_server_drain", "gs_server_destroy",
-    "gs_sort_pairs_static", "gs_warp", "gs_last_error", "gs_version",
+    "gs_sort_pairs_static", "gs_warp", "gs_gai_upsample", "gs_last_error", "gs_version",
 )
 
 
@@ -89,6 +89,11 @@ class GsWarpOutput(C.Structure):
                 ("dcdx", C.c_void_p), ("dcdy", C.c_void_p)]
 
 
+class GsGaiWeights(C.Structure):
+    _fields_ = [("scale", C.c_int32), ("features", C.c_int32), ("wc", C.c_void_p), ("bc", C.c_void_p),
+                ("wt", C.c_void_p), ("bt", C.c_void_p)]
+
+
 class GsError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
@@ -132,6 +137,7 @@ def _declare(L):
         "gs_sort_pairs_static": [P, P, P, P, I64, I32, P],
         "gs_warp": [P, C.POINTER(GsCamera), C.POINTER(GsCamera), C.POINTER(GsWarpInput), C.POINTER(GsWarpOutput),
                     P],
+        "gs_gai_upsample": [C.POINTER(GsGaiWeights), P, P, P, I32, I32, I32, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -388,6 +388,32 @@ class Server:
             pass
 
 
+# ----------------------------------------------------------------------------- gradient-aware interpolation
+def gai_upsample(weights, rgb, dcdx, dcdy, out=None, stream=None):
+    """Super-sampling by the gradient-aware interpolation of Sec. 4.1 (gs_gai_upsample).
+
+    weights: (scale, wc [C, 27], bc [C] or None, wt [S*S, C], bt [S*S] or None), host
+    arrays of the Conv3x3 -> SxS TConv of Eq. 8. rgb, dcdx, dcdy: device [channels, H, W]
+    fp32. Returns (or fills) out [channels, S H, S W]."""
+    S, wc, bc, wt, bt = weights
+    f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+    wc, bc, wt, bt = f32(wc), f32(bc), f32(wt), f32(bt)
+    Cf = wc.shape[0]
+    if wc.shape != (Cf, 27) or wt.shape != (S * S, Cf):
+        raise ValueError("weights must be wc [C, 27] and wt [S*S, C]")
+    for t in (rgb, dcdx, dcdy):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.shape == rgb.shape):
+            raise ValueError("rgb, dcdx, dcdy must be contiguous fp32 CUDA tensors of one shape")
+    ch, H, W = rgb.shape
+    if out is None:
+        out = torch.empty((ch, S * H, S * W), dtype=torch.float32, device=rgb.device)
+    hp = lambda a: None if a is None else a.ctypes.data
+    w = abi.GsGaiWeights(int(S), int(Cf), hp(wc), hp(bc), hp(wt), hp(bt))
+    check(abi.lib().gs_gai_upsample(C.byref(w), _ptr(rgb), _ptr(dcdx), _ptr(dcdy), int(ch), int(W), int(H),
+                                    _ptr(out), _stream_ptr(stream)))
+    return out
+
+
 # ----------------------------------------------------------------------------- autograd
 class _RenderFn(torch.autograd.Function):
     @staticmethod

@@ -339,3 +339,18 @@ def interp_inputs(width: int = 960, height: int = 540, scale: int = 4, k: int = 
     hr = warp_frame(width * scale, height * scale, seed, channels=channels, grad_channels=0)
     lr = warp_frame(width, height, seed + 1, channels=channels, grad_channels=grad_channels)
     return dict(P0=P0, P05=P05, P1=P1, P0_hr=P0.scaled(scale), P05_hr=P05.scaled(scale), hr=hr, lr=lr)
+
+
+# ----------------------------------------------------------------------------- super-sampling weights
+
+def gai_weights(scale: int = 4, features: int = 32, seed: int = 21):
+    """Seeded stand-in weights of the gradient-aware interpolation's two layers (Sec. 4.1,
+    Eq. 8; the trained ones are not available): (scale, wc [C, 27], bc [C], wt [S*S, C],
+    bt [S*S]), fp32, N(0, 1/27) and N(0, 1/C) entries, small biases."""
+    rng = np.random.default_rng(seed)
+    S, Cf = scale, features
+    wc = (rng.standard_normal((Cf, 27)) / np.sqrt(27.0)).astype(np.float32)
+    bc = (0.01 * rng.standard_normal(Cf)).astype(np.float32)
+    wt = (rng.standard_normal((S * S, Cf)) / np.sqrt(Cf)).astype(np.float32)
+    bt = (0.01 * rng.standard_normal(S * S)).astype(np.float32)
+    return S, wc, bc, wt, bt
