@@ -11,7 +11,7 @@ Prints one JSON line. Default workload: 1M clustered Gaussians, SH degree 3,
 960x540, 60-frame orbit (steps cycle over the orbit).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload large|ultra|ultra_lr|tiny|serve|interp|gass]
+                  [--workload large|ultra|ultra_lr|tiny|serve|interp|gass|pipeline]
 
 With --gpus N > 1 (launched by torchrun) every rank renders the same workload
 as an independent replica (the render has no cross-GPU exchange); value is the
@@ -172,6 +172,11 @@ def run_reference(args):
         return run_reference_interp(args, world)
     if args.workload == "gass":
         return run_reference_gass(args, world)
+    if args.workload == "pipeline":
+        print(json.dumps({"impl": "reference", "workload": "pipeline",
+                          "unavailable": "a scheduling pattern of the GPU path; its CPU counterparts are the "
+                                         "large, gass and interp reference arms"}), flush=True)
+        return
     sc, cams = make_workload(args.workload)
     osc = oracle.OScene(sc)
     cores = oracle.max_threads()
@@ -654,6 +659,93 @@ def run_gass(args):
         torch.distributed.destroy_process_group()
 
 
+PIPE_DESC = ("post-rendering chain of Sec. 4 on two streams: 960x540 render of the large scene (1M, SH 3) per "
+             "frame of the 60-frame orbit || x4 gradient-aware interpolation of colour, depth and alpha + forward "
+             "warp of the previous 3840x2160 frame + backward warp of the current 960x540 frame toward the mid "
+             "pose; serial = the same calls on one stream")
+
+
+def run_pipeline(args):
+    """--workload pipeline: api.FramePipeline overlapped against its one-stream form."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2605_11489_gb300 import api, synth
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    sc = synth.large_scene(1_000_000, 1)
+    dense = synth.orbit_cameras(120, 960, 540)
+    frames, mids = dense[0::2], dense[1::2]
+    W, H = frames[0].width, frames[0].height
+    weights = synth.gai_weights(4, 32)
+    ctx = api.Context(local_rank)
+    scene = api.Scene.from_arrays(sc)
+    out = api.alloc_outputs(W, H)
+    stream = torch.cuda.Stream()
+    tile, batch, chunk, _ = ctx.autotune(scene, frames[0], out, iters=3, stream=stream)
+    for cam in frames:
+        ctx.forward(scene, cam, out=out, tile=tile, batch=batch, chunk=chunk, stream=stream)
+    capacity = int(ctx.stats(reset=True, stream=stream)["instances_max"] * 1.25) + 4096
+    del out
+
+    def timed(overlap):
+        pipe = api.FramePipeline(ctx, scene, frames[0], weights, capacity, tile, batch, chunk, overlap=overlap)
+        for t in range(args.warmup):
+            pipe.step(frames[t % len(frames)], mids[(t - 1) % len(mids)])
+        pipe.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0, e1, done = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(pipe.rs)
+        for i in range(args.steps):
+            t = args.warmup + i
+            pipe.step(frames[t % len(frames)], mids[(t - 1) % len(mids)])
+        done.record(pipe.ps)
+        pipe.rs.wait_event(done)
+        e1.record(pipe.rs)
+        e1.synchronize()
+        ms = slowest_rank(e0.elapsed_time(e1), world, "cuda")
+        for g in pipe.graphs:
+            g.check(stream=pipe.rs)  # raises if a frame overflowed the instance capacity
+        pipe.close()
+        return ms
+
+    ms_serial = timed(False)
+    clk_path = os.path.join(tempfile.gettempdir(), "gsr_clocks_pipe_%d_%d.csv" % (os.getpid(), rank))
+    smi, smi_f = start_clock_sampler(clk_path, local_rank)
+    time.sleep(0.3)
+    ms = timed(True)
+    if smi:
+        smi.terminate()
+        smi.wait()
+        smi_f.close()
+    clocks = read_clocks(clk_path)
+    fps = 1e3 * args.steps * world / ms
+    if rank == 0:
+        line = {"metric": "pipeline frames/s (render + x4 interpolation + warp pair)", "value": fps,
+                "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "pipeline", "desc": PIPE_DESC, "tile": tile, "batch": batch, "chunk": chunk,
+                           "parallelism": "replicas" if world > 1 else "single GPU, two streams"},
+                "hr_mpix_s": 16 * W * H * fps / 1e6,
+                "serial": {"frames_per_s": 1e3 * args.steps * world / ms_serial, "ms_per_step": ms_serial / args.steps},
+                "speedup_vs_serial": ms_serial / ms, "clocks": clocks,
+                # per frame: the render graph's kernels (17 + tile-sort passes), 2 interpolations, 2 warps x 2
+                "gpu_launches": args.steps * (17 + 2 + 2 + 4)}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def algorithmic(stage, w, deg, n, K_avg, V_avg, tile_passes, pixels, pairs):
     """Algorithmic work of one launch of `stage` (bytes, or FP32 ops for compositing)."""
     sh_bytes = 12 * (deg + 1) ** 2
@@ -715,7 +807,7 @@ def main():
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["serve", "interp", "gass"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["serve", "interp", "gass", "pipeline"])
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="serve: scale of the scene sizes")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: sort-buffer budget")
@@ -738,6 +830,8 @@ def main():
         return run_interp(args)
     if args.workload == "gass":
         return run_gass(args)
+    if args.workload == "pipeline":
+        return run_pipeline(args)
 
     import torch
 

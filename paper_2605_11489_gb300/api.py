@@ -414,6 +414,93 @@ def gai_upsample(weights, rgb, dcdx, dcdy, out=None, stream=None):
     return out
 
 
+# ----------------------------------------------------------------------------- pipeline
+class FramePipeline:
+    """The post-rendering chain of Sec. 4, with the low-resolution render of the next frame
+    overlapping the super-sampling and interpolation inputs of the current one (Sec. 5.1:
+    super sampling and frame interpolation run in parallel; the pipeline-parallel deployment
+    of Sec. 5.3).
+
+    Per frame t (camera cams[t]; mid = the pose between frames t - 1 and t):
+      render stream:  frame t's colour, gradients, depth and alpha at low resolution
+                      (a captured graph per output buffer; two buffers, alternating)
+      post stream:    x S gradient-aware interpolation of the colour (Sec. 4.1) and of depth
+                      and alpha (no gradients: a linear filter of the values);
+                      forward warp of the x S frame t - 1 toward the mid pose (Sec. 4.2);
+                      backward warp of the low-resolution frame t, with its gradients,
+                      toward the mid pose.
+    Events order the two streams: the post chain of frame t waits for its render, and the
+    render of frame t + 2 waits until the chain of frame t has read their shared buffer.
+    overlap=False runs both on one stream (the serial baseline). Every computation runs in
+    libgsr.so; this class only orders the calls."""
+
+    # an interpolated pixel moves in the forward warp only where its interpolated alpha
+    # exceeds this (the interpolation can leave tiny nonzero values next to empty pixels)
+    HR_ALPHA_MIN = 0.01
+
+    def __init__(self, ctx: "Context", scene: "Scene", cam0, gai_weights, capacity: int, tile=0, batch=0,
+                 chunk=0, overlap=True):
+        S = int(gai_weights[0])
+        W, H = cam0.width, cam0.height
+        self.ctx, self.scene, self.weights, self.S = ctx, scene, gai_weights, S
+        self.rs = torch.cuda.Stream()
+        self.ps = torch.cuda.Stream() if overlap else self.rs
+        self.lr, self.da = [], []
+        for _ in range(2):
+            da = torch.empty((2, H, W), dtype=torch.float32, device="cuda")  # depth, alpha
+            out = alloc_outputs(W, H, keys=("rgb", "dcdx", "dcdy"))
+            out["depth"], out["alpha"] = da[0], da[1]
+            self.lr.append(out)
+            self.da.append(da)
+        self.zero_g = torch.zeros((2, H, W), dtype=torch.float32, device="cuda")
+        self.graphs = [ctx.graph(scene, cam0, self.lr[k], capacity=capacity, tile=tile, batch=batch, chunk=chunk,
+                                 stream=self.rs) for k in range(2)]
+        self.hr_rgb = [torch.empty((3, S * H, S * W), dtype=torch.float32, device="cuda") for _ in range(2)]
+        self.hr_da = [torch.empty((2, S * H, S * W), dtype=torch.float32, device="cuda") for _ in range(2)]
+        self.wctx = Context(ctx.device)  # the warps' scratch, used on the post stream only
+        self.fwd = alloc_warp_outputs(S * W, S * H, S * W, S * H, 3, 0, keys=("motion", "index", "z", "planes"))
+        self.bwd = alloc_warp_outputs(W, H, W, H, 3, 3)
+        self.rendered = [torch.cuda.Event() for _ in range(2)]
+        self.consumed = [torch.cuda.Event() for _ in range(2)]
+        self.used = [False, False]
+        self.prev_cam = None
+        torch.cuda.synchronize()
+
+    def step(self, cam, mid):
+        """Frame `cam` through the chain; `mid` is the pose between the previous frame and it.
+        Asynchronous: after it, the post stream holds this frame's interpolated colour
+        (hr_rgb[k]), depth and alpha (hr_da[k]) and the two warps' outputs (fwd, bwd)."""
+        k = 0 if self.prev_cam is None else 1 - self._k
+        if self.used[k]:
+            self.rs.wait_event(self.consumed[k])
+        self.graphs[k].render(cam, stream=self.rs)
+        self.rendered[k].record(self.rs)
+        self.ps.wait_event(self.rendered[k])
+        lr, S = self.lr[k], self.S
+        gai_upsample(self.weights, lr["rgb"], lr["dcdx"], lr["dcdy"], out=self.hr_rgb[k], stream=self.ps)
+        gai_upsample(self.weights, self.da[k], self.zero_g, self.zero_g, out=self.hr_da[k], stream=self.ps)
+        if self.prev_cam is not None:
+            j = 1 - k
+            self.wctx.warp(self.prev_cam.scaled(S), mid.scaled(S), self.hr_da[j][0], self.hr_da[j][1],
+                           self.HR_ALPHA_MIN, self.hr_rgb[j], out=self.fwd, stream=self.ps)
+        self.wctx.warp(cam, mid, lr["depth"], lr["alpha"], 0.0, lr["rgb"], lr["dcdx"], lr["dcdy"], out=self.bwd,
+                       stream=self.ps)
+        self.consumed[k].record(self.ps)
+        self.used[k] = True
+        self._k, self.prev_cam = k, cam
+        return k
+
+    def synchronize(self):
+        self.rs.synchronize()
+        self.ps.synchronize()
+
+    def close(self):
+        self.synchronize()
+        for g in self.graphs:
+            g.close()
+        self.wctx.close()
+
+
 # ----------------------------------------------------------------------------- autograd
 class _RenderFn(torch.autograd.Function):
     @staticmethod
