@@ -443,8 +443,10 @@ class FramePipeline:
         S = int(gai_weights[0])
         W, H = cam0.width, cam0.height
         self.ctx, self.scene, self.weights, self.S = ctx, scene, gai_weights, S
-        self.rs = torch.cuda.Stream()
-        self.ps = torch.cuda.Stream() if overlap else self.rs
+        # the render stream has the higher priority: the post chain's large grids fill the SMs
+        # the render leaves idle instead of delaying it
+        self.rs = torch.cuda.Stream(priority=-1) if overlap else torch.cuda.Stream()
+        self.ps = torch.cuda.Stream(priority=0) if overlap else self.rs
         self.lr, self.da = [], []
         for _ in range(2):
             da = torch.empty((2, H, W), dtype=torch.float32, device="cuda")  # depth, alpha
