@@ -419,7 +419,7 @@ class FramePipeline:
     """The post-rendering chain of Sec. 4, with the low-resolution render of the next frame
     overlapping the super-sampling and interpolation inputs of the current one (Sec. 5.1:
     super sampling and frame interpolation run in parallel; the pipeline-parallel deployment
-    of Sec. 5.3).
+    of Sec. 5.4).
 
     Per frame t (camera cams[t]; mid = the pose between frames t - 1 and t):
       render stream:  frame t's colour, gradients, depth and alpha at low resolution
