@@ -943,23 +943,41 @@ def main():
     stage_roofline = {k: {kk: v[kk] for kk in ("bound", "achieved", "unit", "frac")}
                       for k, v in ((s, roofline(s)) for s in abi.STAGES)}
 
-    # end to end through the public API: camera in from the host, planes out to pinned host memory
+    # end to end through the public API: each frame's camera from the host, all five output
+    # planes back to pinned host memory, every step (api.HostFrameStream: graph replay with
+    # the copies of one frame overlapping the next frame's render); plus, for context, the
+    # one-frame synchronous call gs_render_forward_to_host
     e2e = None
     if not args.no_e2e:
-        host = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in out.items()}
-        e2e_steps = min(args.steps, 30)
-        for i in range(2):
-            ctx.forward_to_host(scene, cams[i], host, tile=tile, batch=batch, stream=stream)
+        hosts = [{k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in out.items()}
+                 for _ in range(2)]
+        fs = api.HostFrameStream(ctx, scene, cams[0], capacity, tile, batch, chunk)
+        for i in range(3):
+            fs.render(cams[i % len(cams)], hosts[i % 2])
+        fs.synchronize()
+        e2e_steps = min(args.steps, 60)
         if world > 1:
             torch.distributed.barrier()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
+            fs.render(cams[i % len(cams)], hosts[i % 2])
+        fs.synchronize()
+        dt = slowest_rank(time.perf_counter() - t0, world, "cuda")
+        fs.close()
+        host = hosts[0]
+        for i in range(2):
+            ctx.forward_to_host(scene, cams[i], host, tile=tile, batch=batch, stream=stream)
+        n_sync = min(args.steps, 30)
+        t0 = time.perf_counter()
+        for i in range(n_sync):
             ctx.forward_to_host(scene, cams[i % len(cams)], host, tile=tile, batch=batch, stream=stream)
-        dt = time.perf_counter() - t0
-        dt = slowest_rank(dt, world, "cuda")
+        dt_sync = slowest_rank(time.perf_counter() - t0, world, "cuda")
         e2e = {"value": job_throughput(W * H * e2e_steps, world, dt), "unit": "Mpix/s",
                "h2d_bytes_per_step": GS_CAMERA_BYTES, "d2h_bytes_per_step": 11 * W * H * 4,
-               "path": "gs_render_forward_to_host (plain forward + D2H of rgb, dC/dx, dC/dy, depth, alpha)"}
+               "path": "api.HostFrameStream: graph replay per frame with the camera from the host, D2H of rgb, "
+                       "dC/dx, dC/dy, depth, alpha into pinned host memory, copies overlapping the next render",
+               "sync_call": {"value": job_throughput(W * H * n_sync, world, dt_sync), "unit": "Mpix/s",
+                             "path": "gs_render_forward_to_host per frame (plain forward + D2H, synchronous)"}}
 
     # the backward workload: forward keeping the state, then the backward of
     # N(0,1) upstream gradients on rgb, dC/dx and dC/dy (CUDA events, plain calls)

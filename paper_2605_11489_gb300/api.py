@@ -414,6 +414,65 @@ def gai_upsample(weights, rgb, dcdx, dcdy, out=None, stream=None):
     return out
 
 
+# ----------------------------------------------------------------------------- frames to the host
+class HostFrameStream:
+    """Renders a camera sequence into HOST planes (pinned memory), with each frame's
+    device-to-host copies overlapping the next frame's render.
+    - Frames render on a high-priority stream by graph replay (two captured graphs, writing
+      to two device output buffers in turn).
+    - A copy stream moves a finished frame's planes to the caller's host buffers while the
+      next frame renders.
+    - Events order the two streams. A device buffer is rendered into again only after its
+      previous copy has completed.
+    The caller owns the host buffers and must not touch a frame's buffers until
+    `synchronize()` (or until two later frames have been submitted and synchronised). Every
+    computation runs in libgsr.so; the copies are cudaMemcpyAsync."""
+
+    def __init__(self, ctx: "Context", scene: "Scene", cam0, capacity: int, tile=0, batch=0, chunk=0,
+                 keys=OUTPUT_KEYS):
+        W, H = cam0.width, cam0.height
+        self.keys = tuple(keys)
+        self.rs = torch.cuda.Stream(priority=-1)
+        self.cs = torch.cuda.Stream()
+        self.outs = [alloc_outputs(W, H, self.keys) for _ in range(2)]
+        self.graphs = [ctx.graph(scene, cam0, self.outs[k], capacity=capacity, tile=tile, batch=batch,
+                                 chunk=chunk, stream=self.rs) for k in range(2)]
+        self.rendered = [torch.cuda.Event() for _ in range(2)]
+        self.copied = [torch.cuda.Event() for _ in range(2)]
+        self.used = [False, False]
+        self.t = 0
+        torch.cuda.synchronize()
+
+    def render(self, cam, host_out: dict):
+        """Enqueue frame `cam`; its planes land in `host_out` (pinned fp32 CPU tensors of
+        the output shapes, keyed like the device outputs)."""
+        k = self.t % 2
+        if self.used[k]:
+            self.rs.wait_event(self.copied[k])
+        self.graphs[k].render(cam, stream=self.rs)
+        self.rendered[k].record(self.rs)
+        self.cs.wait_event(self.rendered[k])
+        with torch.cuda.stream(self.cs):
+            for key in self.keys:
+                host_out[key].copy_(self.outs[k][key], non_blocking=True)
+        self.copied[k].record(self.cs)
+        self.used[k] = True
+        self.t += 1
+
+    def synchronize(self):
+        """Waits for every submitted frame's copies; raises if a frame overflowed the
+        graphs' instance capacity."""
+        self.rs.synchronize()
+        self.cs.synchronize()
+        for g in self.graphs:
+            g.check(stream=self.rs)
+
+    def close(self):
+        self.synchronize()
+        for g in self.graphs:
+            g.close()
+
+
 # ----------------------------------------------------------------------------- pipeline
 class FramePipeline:
     """The post-rendering chain of Sec. 4, with the low-resolution render of the next frame

@@ -122,3 +122,28 @@ def test_autotune_picks_a_supported_config_and_caches_it(env):
     o2 = ctx.forward(scene, cam, tile=t, batch=b, chunk=k)
     for k in o1:
         assert torch.equal(o1[k], o2[k])
+
+
+def test_host_frame_stream_equals_plain_forward(env):
+    """api.HostFrameStream: frames rendered by graph replay into two device buffers in turn,
+    each frame's planes copied to its host buffers while the next one renders. Every host
+    plane equals the plain forward of its camera bit for bit."""
+    api, ctx = env
+    import torch
+
+    sc = synth.tiny_scene(4096, 0)
+    cams = synth.jittered_tiny_cameras(7, 13)
+    scene = api.Scene.from_arrays(sc)
+    W, H = cams[0].width, cams[0].height
+    shapes = {k: v.shape for k, v in api.alloc_outputs(W, H).items()}
+    hosts = [{k: torch.empty(s, dtype=torch.float32).pin_memory() for k, s in shapes.items()} for _ in cams]
+    fs = api.HostFrameStream(ctx, scene, cams[0], capacity=200_000, tile=16, batch=64)
+    for cam, h in zip(cams, hosts):
+        fs.render(cam, h)
+    fs.synchronize()
+    fs.close()
+    for cam, h in zip(cams, hosts):
+        ref = ctx.forward(scene, cam, tile=16, batch=64)
+        torch.cuda.synchronize()
+        for k in ref:
+            assert torch.equal(h[k], ref[k].cpu()), k
