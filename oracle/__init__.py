@@ -68,6 +68,7 @@ def lib():
             L.or_render.argtypes = [P, P, C.c_int] + [P] * 10
             L.or_render_pixels.argtypes = [P, P, C.c_int64, P, P, P, P, P, P]
             L.or_render_band.argtypes = [P, P, C.c_int, C.c_int, P, P, P, P, P]
+            L.or_render_normals.argtypes = [P, P, P, P, P, P, P]
             L.or_count_instances.restype = C.c_int64
             L.or_count_instances.argtypes = [P, P, C.c_int32]
             L.or_keys.argtypes = [P, P, C.c_int32, C.c_int64, P, P, P]
@@ -175,6 +176,30 @@ def render(scene, cam, bg=(0.0, 0.0, 0.0), mode: str = "binned") -> dict:
                                                   "n_blended", "sig", "amb", "gabs")])
     if rc != 0:
         raise RuntimeError("or_render failed: %d" % rc)
+    return out
+
+
+def render_normals(scene, cam) -> dict:
+    """The normal channel and the normal-view map (binned FP64 render).
+    - normal [3, H, W]: the camera-space normals of the blended Gaussians, weighted like the
+      colour (sum n_i a_i T_i). n_i is the axis of the Gaussian's smallest scale, turned to face
+      the camera: the normal RaDe-GS renders, which the paper uses for its depth and normal
+      maps (Sec. 5.1).
+    - nv [H, W]: -normal . (unit ray of the pixel centre), the normal-view inner product map
+      of Sec. 4.1.
+    - alpha [H, W].
+    - nrm_amb [H, W]: 1 where a blended Gaussian's axis is within 1e-5 of perpendicular to its
+      view direction, so that rounding may turn its normal either way.
+    - amb [H, W]: the render's decision flag."""
+    s = _as_oscene(scene)
+    H, W = cam.height, cam.width
+    out = dict(normal=np.zeros((3, H, W)), nv=np.zeros((H, W)), alpha=np.zeros((H, W)),
+               nrm_amb=np.zeros((H, W), np.int32), amb=np.zeros((H, W), np.int32))
+    st, cm = s.struct(), _cam(cam, (0.0, 0.0, 0.0))
+    rc = lib().or_render_normals(C.byref(st), C.byref(cm),
+                                 *[_ptr(out[k]) for k in ("normal", "nv", "alpha", "nrm_amb", "amb")])
+    if rc != 0:
+        raise RuntimeError("or_render_normals failed: %d" % rc)
     return out
 
 

@@ -293,6 +293,8 @@ typedef struct {
     double dir[3], dn, d[3];
     double rgb[3];
     int rgb_clamped[3];
+    double nrm[3];  /* camera-space normal: the shortest axis, facing the camera (RaDe-GS, Sec. 5.1) */
+    int nrm_amb;    /* the axis is within 1e-5 of perpendicular to the view direction: orientation open */
 } or_cont;
 
 /* Sigma = R S S^T R^T (Sec. 3) for scale s and quaternion q (w, x, y, z), any norm. */
@@ -367,6 +369,18 @@ static void cont_project(const or_scene *sc, const or_camera *cam, int64_t i, or
     for (int k = 0; k < 3; ++k) P->dir[k] = m[k] - cpos[k];
     P->dn = sqrt(P->dir[0] * P->dir[0] + P->dir[1] * P->dir[1] + P->dir[2] * P->dir[2]);
     for (int k = 0; k < 3; ++k) P->d[k] = P->dir[k] / P->dn;
+    /* Normal (the normal channel of RaDe-GS, which the paper renders with, Sec. 5.1): the axis
+     * of the smallest scale -- chosen on the fp32 log-scale inputs, the first of equal ones --
+     * turned to face the camera (n . (mu - C) < 0), in camera coordinates. */
+    int kmin = 0;
+    for (int k = 1; k < 3; ++k)
+        if ((float)sc->log_scales[k * S + i] < (float)sc->log_scales[kmin * S + i]) kmin = k;
+    double nw[3] = {P->R[kmin], P->R[3 + kmin], P->R[6 + kmin]};
+    const double facing = nw[0] * P->dir[0] + nw[1] * P->dir[1] + nw[2] * P->dir[2];
+    P->nrm_amb = fabs(facing) <= 1e-5 * P->dn;
+    if (facing > 0.0)
+        for (int k = 0; k < 3; ++k) nw[k] = -nw[k];
+    for (int r = 0; r < 3; ++r) P->nrm[r] = W[4 * r] * nw[0] + W[4 * r + 1] * nw[1] + W[4 * r + 2] * nw[2];
     double Y[16];
     or_sh_basis(sc->deg, P->d, Y, NULL);
     const int K = (sc->deg + 1) * (sc->deg + 1);
@@ -434,6 +448,8 @@ typedef struct {
 
 typedef struct {
     double rgb[3], gx[3], gy[3], depth, alpha, T, Tx, Ty;
+    double normal[3];  /* sum of n_i a_i T_i (camera space) */
+    int32_t nrm_amb;   /* a blended Gaussian's normal orientation is open (or_cont.nrm_amb) */
     double gx_abs[3], gy_abs[3]; /* sum of |terms| of Eq. 3 (incl. the bg term): the scale of dI/dx, dI/dy */
     int32_t n_blended;
     uint32_t sig;
@@ -449,7 +465,8 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
     const double X = px + 0.5, Yp = py + 0.5;
     double T = 1.0, Tx = 0.0, Ty = 0.0, D = 0.0;
     double C[3] = {0, 0, 0}, Cx[3] = {0, 0, 0}, Cy[3] = {0, 0, 0}, Ax[3] = {0, 0, 0}, Ay[3] = {0, 0, 0};
-    int32_t nb = 0, amb = 0;
+    double N[3] = {0, 0, 0};
+    int32_t nb = 0, amb = 0, namb = 0;
     uint32_t sig = 2166136261u;
     int64_t nt = 0;
     for (int64_t k = 0; k < len; ++k) {
@@ -480,6 +497,8 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
             Ay[c] += fabs(g->rgb[c] * Ty * a) + fabs(g->rgb[c] * T * ay);
         }
         D += g->z * a * T;
+        for (int c = 0; c < 3; ++c) N[c] += g->nrm[c] * a * T;  /* blended like the colour */
+        namb |= g->nrm_amb;
         Tx = -ax * T + (1.0 - a) * Tx;                 /* Eq. 4 */
         Ty = -ay * T + (1.0 - a) * Ty;
         T = T * (1.0 - a);
@@ -495,6 +514,8 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
     }
     out->depth = D;
     out->alpha = 1.0 - T;
+    for (int c = 0; c < 3; ++c) out->normal[c] = N[c];
+    out->nrm_amb = namb;
     out->T = T; out->Tx = Tx; out->Ty = Ty;
     out->n_blended = nb;
     out->sig = sig;
@@ -631,12 +652,14 @@ static int64_t max_bucket(const or_buckets *B)
  * rgb/dcdx/dcdy [3][H][W], depth/alpha/final_T [H][W]; any may be NULL. */
 static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y0, int y1, double *rgb,
                        double *dcdx, double *dcdy, double *depth, double *alpha, double *final_T,
-                       int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs);
+                       int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs, double *normal, double *nv,
+                       int32_t *nrm_amb);
 
 int or_render(const or_scene *sc, const or_camera *cam, int mode, double *rgb, double *dcdx, double *dcdy,
               double *depth, double *alpha, double *final_T, int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs)
 {
-    return render_rows(sc, cam, mode, 0, cam->height, rgb, dcdx, dcdy, depth, alpha, final_T, n_blended, sig, amb, gabs);
+    return render_rows(sc, cam, mode, 0, cam->height, rgb, dcdx, dcdy, depth, alpha, final_T, n_blended, sig, amb, gabs,
+                       NULL, NULL, NULL);
 }
 
 /* Rows [y0, y1) of the frame (binned mode), written into full-size planes. */
@@ -645,12 +668,23 @@ int or_render_band(const or_scene *sc, const or_camera *cam, int y0, int y1, dou
 {
     if (y0 < 0) y0 = 0;
     if (y1 > cam->height) y1 = cam->height;
-    return render_rows(sc, cam, 1, y0, y1, rgb, dcdx, dcdy, depth, alpha, NULL, NULL, NULL, NULL, NULL);
+    return render_rows(sc, cam, 1, y0, y1, rgb, dcdx, dcdy, depth, alpha, NULL, NULL, NULL, NULL, NULL, NULL, NULL,
+                       NULL);
+}
+
+/* The normal channel and the normal-view map (binned mode) with the colour's weights,
+ * plus alpha and the orientation-ambiguity flag per pixel. */
+int or_render_normals(const or_scene *sc, const or_camera *cam, double *normal, double *nv, double *alpha,
+                      int32_t *nrm_amb, int32_t *amb)
+{
+    return render_rows(sc, cam, 1, 0, cam->height, NULL, NULL, NULL, NULL, alpha, NULL, NULL, NULL, amb, NULL, normal,
+                       nv, nrm_amb);
 }
 
 static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y0, int y1, double *rgb,
                        double *dcdx, double *dcdy, double *depth, double *alpha, double *final_T,
-                       int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs)
+                       int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs, double *normal, double *nv,
+                       int32_t *nrm_amb)
 {
     const int W = cam->width, H = cam->height;
     const int64_t HW = (int64_t)W * H;
@@ -691,6 +725,15 @@ static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y
                         gabs[c * HW + p] = o.gx_abs[c];
                         gabs[(3 + c) * HW + p] = o.gy_abs[c];
                     }
+                if (normal)
+                    for (int c = 0; c < 3; ++c) normal[c * HW + p] = o.normal[c];
+                if (nv) {
+                    /* Nv = -N . (unit ray of the pixel centre): 1 x alpha for a surface facing the camera */
+                    const double r[3] = {(px + 0.5 - cam->cx) / cam->fx, (py + 0.5 - cam->cy) / cam->fy, 1.0};
+                    const double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                    nv[p] = -(o.normal[0] * r[0] + o.normal[1] * r[1] + o.normal[2] * r[2]) / rn;
+                }
+                if (nrm_amb) nrm_amb[p] = o.nrm_amb;
             }
         }
         free(buf);
