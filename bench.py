@@ -819,6 +819,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-backward", action="store_true", help="skip the forward+backward timing")
+    ap.add_argument("--no-normals", action="store_true", help="skip the normal-channel timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1011,6 +1012,29 @@ def main():
                "path": "gs_render_forward (GS_EMIT_BWD_STATE, plain) + gs_render_backward; upstream N(0,1) on "
                        "rgb, dC/dx, dC/dy; grads of means, log-scales, quaternions, opacity logits, SH"}
 
+    # the normal channel (plain forward, whole tile lists) against the same plain forward
+    # without it, CUDA events, after two warm-up frames each
+    nrm = None
+    if not args.no_normals:
+        def plain_ms(keys, chunk_):
+            o = api.alloc_outputs(W, H, keys)
+            for i in range(2):
+                ctx.forward(scene, cams[i], out=o, tile=tile, batch=batch, chunk=chunk_, stream=stream)
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n_f = min(args.steps, 20)
+            ea.record(stream)
+            for i in range(n_f):
+                ctx.forward(scene, cams[i % len(cams)], out=o, tile=tile, batch=batch, chunk=chunk_, stream=stream)
+            eb.record(stream)
+            eb.synchronize()
+            return ea.elapsed_time(eb) / n_f
+
+        nrm = {"forward_ms": plain_ms(api.OUTPUT_KEYS, chunk),
+               "forward_unsplit_ms": plain_ms(api.OUTPUT_KEYS, 1 << 24),
+               "forward_with_normals_ms": plain_ms(api.OUTPUT_KEYS + api.NORMAL_KEYS, chunk),
+               "path": "gs_render_forward (plain, one host sync per frame); the normal channel composites "
+                       "whole tile lists, so forward_unsplit_ms is its like-for-like reference"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc, cams, args.workload)
@@ -1026,6 +1050,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "frames_per_s": 1e3 * args.steps * world / ms,
                 "backward": bwd,
+                "normals": nrm,
                 "stage_ms": stage_ms,
                 "stage_ms_source": "composite: CUDA events inside the timed replays; the other stages: a "
                                    "second replay of the camera path with events at every stage boundary",

@@ -104,13 +104,22 @@ typedef struct {
 } gs_render_opts;
 
 /* Caller-owned device outputs; a NULL plane is not written (and, for dcdx and
- * dcdy both NULL, the gradient recursion is not evaluated). */
+ * dcdy both NULL, the gradient recursion is not evaluated).
+ * normal / nv: the normal channel the paper renders with RaDe-GS (Sec. 5.1) and the
+ * normal-view inner product map its super-sampling takes (Sec. 4.1). Each Gaussian's
+ * normal is its shortest axis (the smallest of the fp32 log-scales, the first of equal
+ * ones), turned to face the camera (n . (mean - camera centre) < 0), in camera
+ * coordinates; normal = sum n_i a_i T_i, nv = -normal . (unit ray of the pixel centre).
+ * Only gs_render_forward renders them, without splitting long tile lists; graphs, the
+ * server, host outputs and GS_EMIT_BWD_STATE / GS_COUNT_PAIRS reject them. */
 typedef struct {
     float *rgb;    /* [3][H][W] */
     float *dcdx;   /* [3][H][W]  dI/dx, Eq. 3 */
     float *dcdy;   /* [3][H][W]  dI/dy */
     float *depth;  /* [H][W]     sum z_i a_i T_i */
     float *alpha;  /* [H][W]     1 - T_final */
+    float *normal; /* [3][H][W]  sum n_i a_i T_i, camera coordinates */
+    float *nv;     /* [H][W]     -normal . ray */
 } gs_outputs;
 
 /* Per-parameter gradients, same layout and stride as gs_scene (caller-owned,

@@ -23,6 +23,7 @@ from . import abi
 from .abi import GsCamera, GsOutputs, GsRenderOpts, GsScene, GsSceneGrads, GsStateView, check
 
 OUTPUT_KEYS = ("rgb", "dcdx", "dcdy", "depth", "alpha")
+NORMAL_KEYS = ("normal", "nv")  # the normal channel and the normal-view map (plain forward only)
 
 
 def _stream_ptr(stream) -> int:
@@ -103,7 +104,7 @@ def _stats_dict(st) -> dict:
 
 def alloc_outputs(width, height, keys=OUTPUT_KEYS, device="cuda") -> dict:
     shp = {"rgb": (3, height, width), "dcdx": (3, height, width), "dcdy": (3, height, width),
-           "depth": (height, width), "alpha": (height, width)}
+           "depth": (height, width), "alpha": (height, width), "normal": (3, height, width), "nv": (height, width)}
     return {k: torch.empty(shp[k], dtype=torch.float32, device=device) for k in keys}
 
 
@@ -121,7 +122,7 @@ def alloc_warp_outputs(width, height, width_t, height_t, channels, grad_channels
 
 
 def outputs_struct(out: dict) -> GsOutputs:
-    return GsOutputs(*[_ptr(out.get(k)) for k in OUTPUT_KEYS])
+    return GsOutputs(*[_ptr(out.get(k)) for k in OUTPUT_KEYS + NORMAL_KEYS])
 
 
 # ----------------------------------------------------------------------------- raw device copies (inspection)

@@ -271,14 +271,15 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
 // (with a thread per record, every lane's load and store touched its own line
 // and the L1 request path bound the kernel). Each thread takes four pieces, a
 // block apart, so their loads are in flight together. The pieces with e % 3 == 0
-// also write the tile ranges and (keys64 != NULL) the 64-bit keys.
+// also write the tile ranges, (keys64 != NULL) the 64-bit keys and (nrm_sorted !=
+// NULL) the instance's normal.
 constexpr int kRangeThreads = 256, kRangePer = 4;
 
 __global__ void __launch_bounds__(kRangeThreads)
     k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
              const uint32_t *__restrict__ counters, const GaussRec *__restrict__ rec,
              GaussRec *__restrict__ rec_sorted, uint2 *ranges, const uint4 *__restrict__ bin,
-             uint64_t *__restrict__ keys64)
+             uint64_t *__restrict__ keys64, const float4 *__restrict__ nrm, float4 *__restrict__ nrm_sorted)
 {
     const uint32_t K = counters[kCntEff];
     const uint32_t P = 3u * K;  // 16-byte pieces (K < 2^30)
@@ -313,6 +314,7 @@ __global__ void __launch_bounds__(kRangeThreads)
         if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
         if (i == K - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
         if (keys64) keys64[i] = ((uint64_t)t << 32) | (uint64_t)bin[g[k]].x;
+        if (nrm_sorted) nrm_sorted[i] = __ldg(nrm + g[k]);
     }
 }
 
@@ -512,14 +514,15 @@ cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int6
 
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
                           const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, const uint4 *bin,
-                          uint64_t *keys64, cudaStream_t s)
+                          uint64_t *keys64, cudaStream_t s, const float4 *nrm, float4 *nrm_sorted)
 {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess) return e;
     if (max_k <= 0) return cudaSuccess;
     const int64_t per_block = (int64_t)kRangeThreads * kRangePer;
     const int64_t nb = (3 * max_k + per_block - 1) / per_block;
-    k_ranges<<<(unsigned)nb, kRangeThreads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges, bin, keys64);
+    k_ranges<<<(unsigned)nb, kRangeThreads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges, bin, keys64,
+                                                    nrm, nrm_sorted);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,7 @@ constexpr size_t smem_bytes()
 struct PixelAcc {
     float T, Tx, Ty, D;
     float C[3], Cx[3], Cy[3];
+    float N[3];  // normal channel (the NRM instantiations only)
     uint32_t last;
     uint32_t n_eval, n_blend;  // pairs counted in the GS_COUNT_PAIRS instantiation only
     bool done, stopped;
@@ -79,7 +80,7 @@ __device__ __forceinline__ void acc_init(PixelAcc &s, bool inside)
     s.T = 1.0f;
     s.Tx = s.Ty = s.D = 0.0f;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) s.C[c] = s.Cx[c] = s.Cy[c] = 0.0f;
+    for (int c = 0; c < 3; ++c) s.C[c] = s.Cx[c] = s.Cy[c] = s.N[c] = 0.0f;
     s.last = 0;
     s.done = !inside;
     s.stopped = false;
@@ -100,9 +101,9 @@ __device__ __forceinline__ void tile_pixel(int tid, int tile_x, int tile_y, int 
 
 // One Gaussian record at one pixel (Eq. 2-4). Returns true when the pixel
 // stops (the record would take T below 1e-4; it is not blended).
-template <bool GRAD, bool STATE, bool COUNT = false>
+template <bool GRAD, bool STATE, bool COUNT = false, bool NRM = false>
 __device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float4 &r1, const float4 &r2, float pxc,
-                                      float pyc, uint32_t pos)
+                                      float pyc, uint32_t pos, const float4 *nrm = nullptr)
 {
     if (COUNT) ++s.n_eval;
     const AlphaEval e = eval_alpha(r0, r1, pxc, pyc);
@@ -116,6 +117,12 @@ __device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float
 #pragma unroll
     for (int c = 0; c < 3; ++c) s.C[c] = __fmaf_rn(col[c], wgt, s.C[c]);
     s.D = __fmaf_rn(r1.z, wgt, s.D);
+    if (NRM) {  // the record's normal, blended like the colour
+        const float4 n = __ldg(nrm);
+        s.N[0] = __fmaf_rn(n.x, wgt, s.N[0]);
+        s.N[1] = __fmaf_rn(n.y, wgt, s.N[1]);
+        s.N[2] = __fmaf_rn(n.z, wgt, s.N[2]);
+    }
     if (GRAD) {
         const float ax = e.capped ? 0.0f : -__fmul_rn(al, e.ex);
         const float ay = e.capped ? 0.0f : -__fmul_rn(al, e.ey);
@@ -171,7 +178,7 @@ __device__ __forceinline__ void ring_init(WarpRing<BATCH> &ring)
 // pixel state. (px, py) is the lane's pixel, (bx0, by0) the warp's 8x4 block,
 // pos0 the list position of s0 within its tile. The warp's ring carries its
 // mbarrier parities in `phase`. Returns false if a bounded wait gave up.
-template <int BATCH, bool GRAD, bool STATE, bool COUNT = false>
+template <int BATCH, bool GRAD, bool STATE, bool COUNT = false, bool NRM = false>
 __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py, int bx0, int by0, uint32_t s0,
                                           uint32_t s1, uint32_t pos0, WarpRing<BATCH> &ring,
                                           uint32_t (&phase)[kStages], PixelAcc &s)
@@ -243,7 +250,9 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
                     const uint32_t kn = more ? (uint32_t)w * 32u + (uint32_t)(__ffs(mine) - 1) : k;
                     mine &= mine - 1u;
                     const float4 b0 = recs[kn].r0, b1 = recs[kn].r1, b2 = recs[kn].r2;
-                    if (blend<GRAD, STATE, COUNT>(s, a0, a1, a2, pxc, pyc, pos_b + k)) {
+                    if (blend<GRAD, STATE, COUNT, NRM>(
+                            s, a0, a1, a2, pxc, pyc, pos_b + k,
+                            NRM ? a.nrm_sorted + (s0 + (uint32_t)b * BATCH + k) : nullptr)) {
                         s.done = true;
                         s.stopped = true;
                         break;
@@ -270,7 +279,7 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
     return ok;
 }
 
-template <bool GRAD, bool STATE>
+template <bool GRAD, bool STATE, bool NRM = false>
 __device__ __forceinline__ void write_final(const CompositeArgs &a, int px, int py, const PixelAcc &s)
 {
     const int64_t HW = (int64_t)a.width * a.height;
@@ -288,6 +297,16 @@ __device__ __forceinline__ void write_final(const CompositeArgs &a, int px, int 
     }
     if (a.depth) a.depth[p] = s.D;
     if (a.alpha) a.alpha[p] = __fsub_rn(1.0f, s.T);
+    if (NRM) {
+        if (a.normal)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a.normal[c * HW + p] = s.N[c];
+        if (a.nv) {  // -normal . (unit ray of the pixel centre)
+            const float rx = ((float)px + 0.5f - a.cx) / a.fx, ry = ((float)py + 0.5f - a.cy) / a.fy;
+            const float inv = rsqrtf(rx * rx + ry * ry + 1.0f);
+            a.nv[p] = -(s.N[0] * rx + s.N[1] * ry + s.N[2]) * inv;
+        }
+    }
     if (STATE) {
         a.final_T[p] = s.T;
         a.final_Tx[p] = s.Tx;
@@ -351,7 +370,7 @@ __device__ __forceinline__ void compose(PixelAcc &P, const PixelAcc &Q)
     if (STATE && Q.last) P.last = Q.last;
 }
 
-template <int TILE, int BATCH, bool GRAD, bool STATE, bool COUNT = false>
+template <int TILE, int BATCH, bool GRAD, bool STATE, bool COUNT = false, bool NRM = false>
 __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -390,7 +409,7 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
         skip = a.partial[(size_t)(slot - c) * kPartialVals * TILE * TILE + 14 * TILE * TILE + threadIdx.x] != 0.0f;
         if (skip) s.done = true;
     }
-    const bool ok = warp_span<BATCH, GRAD, STATE, COUNT>(a, px, py, bx0, by0, s0, s1, pos0, ring, phase, s);
+    const bool ok = warp_span<BATCH, GRAD, STATE, COUNT, NRM>(a, px, py, bx0, by0, s0, s1, pos0, ring, phase, s);
     if (!ok && (threadIdx.x & 31) == 0) atomicOr(a.err_word, kErrTmaTimeout);
     if (COUNT) {  // evaluated (inside a support rectangle) and blended pairs of this warp
         unsigned long long ne = s.n_eval, nb = s.n_blend;
@@ -405,7 +424,7 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
         }
     }
     if (slot == kWholeTile) {
-        if (inside) write_final<GRAD, STATE>(a, px, py, s);
+        if (inside) write_final<GRAD, STATE, NRM>(a, px, py, s);
     } else if (!skip) {
         write_partial<TILE>(a.partial + (size_t)slot * kPartialVals * TILE * TILE, threadIdx.x, s);
     }
@@ -596,14 +615,14 @@ cudaError_t opt_in_smem(F *kernel, size_t bytes, bool (&done)[64])
     return e;
 }
 
-template <int TILE, int BATCH, bool GRAD, bool STATE, bool COUNT = false>
+template <int TILE, int BATCH, bool GRAD, bool STATE, bool COUNT = false, bool NRM = false>
 cudaError_t launch_one(const CompositeArgs &a, unsigned nb, cudaStream_t s)
 {
     constexpr size_t smem = smem_bytes<TILE, BATCH>();
     static bool done[64];
-    cudaError_t e = opt_in_smem(k_composite<TILE, BATCH, GRAD, STATE, COUNT>, smem, done);
+    cudaError_t e = opt_in_smem(k_composite<TILE, BATCH, GRAD, STATE, COUNT, NRM>, smem, done);
     if (e != cudaSuccess) return e;
-    k_composite<TILE, BATCH, GRAD, STATE, COUNT><<<nb, TILE * TILE, smem, s>>>(a);
+    k_composite<TILE, BATCH, GRAD, STATE, COUNT, NRM><<<nb, TILE * TILE, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -618,6 +637,11 @@ cudaError_t launch_tb(const CompositeArgs &a, int64_t max_items, cudaStream_t s)
         if (a.items && a.wave == 0) return cudaErrorInvalidValue;  // a plan runs as wave A, then wave B
         const bool grad = a.dcdx || a.dcdy;
         const bool state = a.final_T != nullptr;
+        if (a.nrm_sorted) {  // the normal channel: no backward state, no census, whole tiles
+            if (state || a.pair_counts) return cudaErrorInvalidValue;
+            return grad ? launch_one<TILE, BATCH, true, false, false, true>(a, nb, s)
+                        : launch_one<TILE, BATCH, false, false, false, true>(a, nb, s);
+        }
         if (a.pair_counts && !state)  // diagnostic pair census (GS_COUNT_PAIRS)
             return grad ? launch_one<TILE, BATCH, true, false, true>(a, nb, s)
                         : launch_one<TILE, BATCH, false, false, true>(a, nb, s);

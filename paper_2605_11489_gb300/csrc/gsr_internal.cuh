@@ -94,6 +94,7 @@ struct ProjectArgs {
     uint32_t *block_sums;  // per block of 1,024 Gaussians: tiles touched
     uint32_t *block_vis;   // per block of 1,024 Gaussians: visible Gaussians
     uint32_t *counters;    // visible count accumulates into kCntVisible / kCntSumV
+    float4 *nrm;           // per Gaussian: camera-space normal (x, y, z, 0) of the visible ones (nullable)
 };
 int project_blocks(int64_t n);
 // geometry (records without colour, bin, tile counts, block sums), then the SH
@@ -122,7 +123,8 @@ cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int6
 // sorted order, and (keys64 != NULL) each instance's (tile << 32 | depth bits)
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
                           const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, const uint4 *bin,
-                          uint64_t *keys64, cudaStream_t s);
+                          uint64_t *keys64, cudaStream_t s, const float4 *nrm = nullptr,
+                          float4 *nrm_sorted = nullptr);
 
 // onesweep LSD radix sort of (keys, vals) on the low `bits` bits, K from counters[kCntEff]
 struct SortScratch {
@@ -167,6 +169,10 @@ struct CompositeArgs {
     int32_t chunk;                 // records per later chunk of a split tile
     int32_t head;                  // records in a split tile's first chunk (>= chunk)
     unsigned long long *pair_counts;  // (evaluated, blended) pairs: the GS_COUNT_PAIRS census (nullable)
+    // normal channel (nullable: the normal variant runs only when nrm_sorted is set, whole tiles only)
+    const float4 *nrm_sorted;      // normals in sorted (instance) order, like rec
+    float *normal, *nv;
+    float fx, fy, cx, cy;          // intrinsics: nv's pixel rays
 };
 constexpr uint32_t kWholeTile = 0xFFFFFFFFu;
 // A tile list longer than `head` records (default kHeadChunks * chunk) is split

@@ -79,8 +79,10 @@ struct Proj {
     bool vis;
     float u, v, ca, cb, cc, o, z;
     uint32_t rlo, rhi, nt;
+    float n[3];  // camera-space normal (with NRM only)
 };
 
+template <bool NRM = false>
 __device__ __forceinline__ void project_one(const CamParams &c, float mx, float my, float mz, float ls0, float ls1,
                                             float ls2, float qw, float qx, float qy, float qz, float logit,
                                             Proj &P)
@@ -171,6 +173,22 @@ __device__ __forceinline__ void project_one(const CamParams &c, float mx, float 
     P.rhi = (uint32_t)x1 | ((uint32_t)y1 << 16);
     const int sh = c.tile_shift;
     P.nt = (uint32_t)(((x1 >> sh) - (x0 >> sh) + 1) * ((y1 >> sh) - (y0 >> sh) + 1));
+    if (NRM) {
+        // normal (RaDe-GS, Sec. 5.1): the axis of the smallest scale (the first of equal
+        // log-scales), turned to face the camera, in camera coordinates
+        const int k = ls1 < ls0 ? (ls2 < ls1 ? 2 : 1) : (ls2 < ls0 ? 2 : 0);
+        float nw0 = k == 0 ? R[0] : (k == 1 ? R[1] : R[2]);
+        float nw1 = k == 0 ? R[3] : (k == 1 ? R[4] : R[5]);
+        float nw2 = k == 0 ? R[6] : (k == 1 ? R[7] : R[8]);
+        const float facing = (mx - c.campos[0]) * nw0 + (my - c.campos[1]) * nw1 + (mz - c.campos[2]) * nw2;
+        if (facing > 0.0f) {
+            nw0 = -nw0;
+            nw1 = -nw1;
+            nw2 = -nw2;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) P.n[r] = vm[4 * r] * nw0 + vm[4 * r + 1] * nw1 + vm[4 * r + 2] * nw2;
+    }
 }
 
 
@@ -254,6 +272,7 @@ __global__ void __launch_bounds__(256) k_colour(ProjectArgs a)
 // loads needed 80 registers and left the SMs at ~36 % warp occupancy.)
 constexpr int kGeomThreads = kProjPerBlock;
 
+template <bool NRM>
 __global__ void __launch_bounds__(kGeomThreads, 1) k_project(ProjectArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * kGeomThreads + threadIdx.x;
@@ -266,7 +285,7 @@ __global__ void __launch_bounds__(kGeomThreads, 1) k_project(ProjectArgs a)
         if (i < a.n) {
             const int64_t np = a.n_pad;
             auto ld = [&](const float *base, int row) { return __ldg(base + (int64_t)row * np + i); };
-            project_one(a.cam, ld(a.means, 0), ld(a.means, 1), ld(a.means, 2), ld(a.log_scales, 0),
+            project_one<NRM>(a.cam, ld(a.means, 0), ld(a.means, 1), ld(a.means, 2), ld(a.log_scales, 0),
                         ld(a.log_scales, 1), ld(a.log_scales, 2), ld(a.quats, 0), ld(a.quats, 1), ld(a.quats, 2),
                         ld(a.quats, 3), ld(a.logits, 0), Q);
         }
@@ -277,6 +296,7 @@ __global__ void __launch_bounds__(kGeomThreads, 1) k_project(ProjectArgs a)
             r.r2 = make_float4(0.0f, 0.0f, __uint_as_float(Q.rlo), __uint_as_float(Q.rhi));
             a.rec[i] = r;
             a.bin[i] = make_uint4(__float_as_uint(Q.z), Q.rlo, Q.rhi, 0u);
+            if (NRM) a.nrm[i] = make_float4(Q.n[0], Q.n[1], Q.n[2], 0.0f);
         }
         a.ntiles[i] = Q.nt;
         my_tiles = Q.nt;
@@ -327,14 +347,17 @@ const void *project_kernel_ptr(int deg, int which)
         default: return reinterpret_cast<const void *>(k_colour<3>);
         }
     }
-    return reinterpret_cast<const void *>(k_project);
+    return reinterpret_cast<const void *>(k_project<false>);
 }
 
 cudaError_t launch_project_geometry(const ProjectArgs &a, cudaStream_t s)
 {
     const int nb = project_blocks(a.n);
     if (nb == 0) return cudaSuccess;
-    k_project<<<nb, kGeomThreads, 0, s>>>(a);
+    if (a.nrm)
+        k_project<true><<<nb, kGeomThreads, 0, s>>>(a);
+    else
+        k_project<false><<<nb, kGeomThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -87,6 +87,8 @@ struct Frame {
     int head = 4 * 2048;  // records in a split list's first chunk
     int64_t max_items = 0, max_split = 0, max_slots = 0;
     Buf fT, fTx, fTy, ncontrib;
+    Buf nrm, nrm_sorted;  // the normal channel: per Gaussian, then in sorted (instance) order
+    bool want_nrm = false;
     Buf counters;
     int64_t n = 0, K = 0, key_cap = 0;
     int sorted = 0;
@@ -344,6 +346,7 @@ gs_status frame_setup(Frame *f, const gs_scene *s, const gs_camera *c, const gs_
     if (head < chunk || head > (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "head must be 0 or chunk..2^30");
     f->chunk = chunk;
     f->head = (int)head;
+    f->want_nrm = false;
     f->deg = s->sh_degree;
     for (int k = 0; k < 3; ++k) f->bg[k] = o->bg[k];
     f->cam = make_cam(*c, tile);
@@ -431,6 +434,7 @@ ProjectArgs proj_args(Frame *f, const gs_scene *s)
     a.block_sums = f->bsums.as<uint32_t>();
     a.block_vis = f->vsums.as<uint32_t>();
     a.counters = f->counters.as<uint32_t>();
+    if (f->want_nrm) a.nrm = f->nrm.as<float4>();
     return a;
 }
 
@@ -467,6 +471,15 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
     c.chunk = f->chunk;
     c.head = f->head;
     if (f->count_pairs) c.pair_counts = reinterpret_cast<unsigned long long *>(f->counters.as<uint32_t>() + kCntPairs);
+    if (f->want_nrm) {
+        c.nrm_sorted = f->nrm_sorted.as<float4>();
+        c.normal = out->normal;
+        c.nv = out->nv;
+        c.fx = f->cam.fx;
+        c.fy = f->cam.fy;
+        c.cx = f->cam.cx;
+        c.cy = f->cam.cy;
+    }
     return c;
 }
 
@@ -507,7 +520,9 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     GSR_CUDA(mark(mk, 6, st));
     GSR_CUDA(launch_ranges(kk[res], vv[res], cnt, max_k, f->rec.as<GaussRec>(), f->rec_sorted.as<GaussRec>(),
                            f->ranges.as<uint2>(), f->n_tiles, f->bin.as<uint4>(),
-                           f->has_state ? f->keys64.as<uint64_t>() : nullptr, st));
+                           f->has_state ? f->keys64.as<uint64_t>() : nullptr, st,
+                           f->want_nrm ? f->nrm.as<float4>() : nullptr,
+                           f->want_nrm ? f->nrm_sorted.as<float4>() : nullptr));
     GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->chunk, f->head, f->items.as<uint4>(),
                          f->split_tiles.as<uint32_t>(), f->split_slot0.as<uint32_t>(), f->slot_split.as<uint32_t>(),
                          f->plan_counts.as<uint32_t>(), st));
@@ -537,9 +552,21 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
         return fail(GS_ERR_INVALID_ARG, "tile must be 8/16/32 and batch 32/64/128/256 with the warps' staging rings "
                                         "fitting shared memory");
     const bool state = (o->flags & GS_EMIT_BWD_STATE) != 0;
-    gs_status r = frame_setup(f, s, c, o, tile, batch, chunk, state);
+    // the normal channel composites whole tile lists: its partial states would not fit the
+    // split-tile slots, so no list is split (first chunk 2^30 records)
+    const bool nrm = out->normal || out->nv;
+    if (nrm && (o->flags & (GS_EMIT_BWD_STATE | GS_COUNT_PAIRS)))
+        return fail(GS_ERR_INVALID_ARG, "the normal channel is rendered without GS_EMIT_BWD_STATE and GS_COUNT_PAIRS");
+    gs_render_opts on = *o;
+    if (nrm) {
+        chunk = 1 << 24;
+        on.head = 1 << 30;
+    }
+    gs_status r = frame_setup(f, s, c, &on, tile, batch, chunk, state);
     f->count_pairs = (o->flags & GS_COUNT_PAIRS) != 0;
     if (r != GS_OK) return r;
+    f->want_nrm = nrm;
+    if (nrm) GSR_CUDA(f->nrm.ensure(sizeof(float4) * (size_t)std::max<int64_t>(s->n, 1)));
     uint32_t *cnt = f->counters.as<uint32_t>();
     Marks mk;
     mk.mask = timing_mask(o->flags);
@@ -569,6 +596,7 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
         if (r != GS_OK) return r;
     }
     if ((r = frame_plan(f, f->K)) != GS_OK) return r;
+    if (nrm) GSR_CUDA(f->nrm_sorted.ensure(sizeof(float4) * (size_t)std::max<int64_t>(f->K, 1)));
     // counters[kCntEff] was clamped to kMaxInstances; K fits, so it equals K.
     r = enqueue_after_scan(f, out, f->K, st, mk);
     if (r != GS_OK || !f->count_pairs) return r;
@@ -680,6 +708,8 @@ gs_status gs_render_forward_to_host(gs_context *ctx, const gs_scene *scene, cons
                                     const gs_render_opts *opts, const gs_outputs *host_out, gs_stream stream)
 {
     if (!ctx || !host_out || !cam || !opts) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    if (host_out->normal || host_out->nv)
+        return fail(GS_ERR_INVALID_ARG, "host outputs carry no normal channel (render it with gs_render_forward)");
     gs_status r = check_cam(cam);
     if (r != GS_OK) return r;
     GSR_CUDA(cudaSetDevice(ctx->device));
@@ -802,6 +832,7 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
     if (!graph) return fail(GS_ERR_INVALID_ARG, "graph is NULL");
     *graph = nullptr;
     if (!ctx || !opts || !out) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    if (out->normal || out->nv) return fail(GS_ERR_INVALID_ARG, "graphs do not render the normal channel");
     gs_status r = check_scene(scene);
     if (r != GS_OK) return r;
     if ((r = check_cam(cam)) != GS_OK) return r;
