@@ -31,6 +31,31 @@ namespace {
 
 constexpr int kBwdBatch = 64;
 
+// Sums 10 per-lane values over the warp with 16 shuffles instead of 50: at each step
+// (offsets 16, 8, 4, 2) a lane keeps half of its values, sends the other half to its
+// partner and adds the partner's copy of the half it kept; a last butterfly step
+// (offset 1) completes the sum. Returns, in v[0], the warp total of value
+// ((lane>>4)&1)*8 + ((lane>>3)&1)*4 + ((lane>>2)&1)*2 + ((lane>>1)&1) (values 10..15
+// are zeros), and that index.
+__device__ __forceinline__ int warp_reduce_scatter10(float (&v)[10], int lane)
+{
+    float w[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w[i] = i < 10 ? v[i] : 0.0f;
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {  // offset 2h: keep w[0, h) or w[h, 2h)
+        const bool hi = (lane & (2 * h)) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = hi ? w[i] : w[h + i];
+            const float keep = hi ? w[h + i] : w[i];
+            w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
+        }
+    }
+    v[0] = w[0] + __shfl_xor_sync(0xffffffffu, w[0], 1);
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
 template <int TILE>
 __global__ void __launch_bounds__(TILE *TILE) k_composite_bwd(const BackwardArgs a)
 {
@@ -137,19 +162,12 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_bwd(const BackwardArgs
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int j = 0; j < 10; ++j) {
-                    float v = g10[j];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    g10[j] = v;
-                }
-                if (lane == 0) {
-                    float *dst = a.g2d + (size_t)s_idx[k] * 10;
-#pragma unroll
-                    for (int j = 0; j < 10; ++j)
-                        if (g10[j] != 0.0f) atomicAdd(dst + j, g10[j]);
-                }
+                // warp sums of the 10 adjoints by reduce-scatter: lane l ends with the
+                // total of value ((l>>4)&1)*8 + ((l>>3)&1)*4 + ((l>>2)&1)*2 + ((l>>1)&1),
+                // so up to 10 lanes add their totals in one atomic instruction
+                const int j = warp_reduce_scatter10(g10, lane);
+                if ((lane & 1) == 0 && j < 10 && g10[0] != 0.0f)
+                    atomicAdd(a.g2d + (size_t)s_idx[k] * 10 + j, g10[0]);
             }
         }
     }
