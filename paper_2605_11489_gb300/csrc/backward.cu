@@ -101,10 +101,10 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_bwd(const BackwardArgs
         const int64_t beg = end - kBwdBatch > 0 ? end - kBwdBatch : 0;
         const int cnt = (int)(end - beg);
         __syncthreads();
-        for (int t = tid; t < cnt; t += NT) {
+        for (int t = tid; t < cnt; t += NT) {  // contiguous records when the sorted copy is there
             const uint32_t idx = a.vals[range.x + beg + t];
             s_idx[t] = idx;
-            s_rec[t] = a.rec[idx];
+            s_rec[t] = a.rec_sorted ? a.rec_sorted[range.x + beg + t] : a.rec[idx];
         }
         __syncthreads();
         for (int k = cnt - 1; k >= 0; --k) {

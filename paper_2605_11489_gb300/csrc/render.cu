@@ -755,6 +755,7 @@ gs_status gs_render_backward(gs_context *ctx, const gs_fwd_state *state, const g
     GSR_CUDA(cudaMemsetAsync(ctx->g2d.p, 0, sizeof(float) * 10 * (size_t)f->n, st));
     BackwardArgs b{};
     b.rec = f->rec.as<GaussRec>();
+    b.rec_sorted = f->rec_sorted.as<GaussRec>();
     b.vals = f->vals[f->sorted].as<uint32_t>();
     b.ranges = f->ranges.as<uint2>();
     b.width = f->W;
