@@ -210,8 +210,9 @@ __device__ __forceinline__ void sh_eval_grad(int deg, float x, float y, float z,
     gX[15] = -c3a * (3.f * x * x - 3.f * y * y); gY[15] = 6.f * c3a * x * y;
 }
 
-// K8: one thread per Gaussian; recompute the forward quantities and chain
-// (u, v, conic, opacity, depth, rgb) adjoints to the 3D parameters.
+// K8: one thread per Gaussian; recompute the forward quantities and chain the
+// (u, v, conic, opacity, depth) adjoints to the 3D parameters. The colour's
+// adjoint goes through SH in k_colour_bwd, launched after it.
 __global__ void __launch_bounds__(256) k_project_bwd(const ProjectBwdArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -219,7 +220,6 @@ __global__ void __launch_bounds__(256) k_project_bwd(const ProjectBwdArgs a)
     const int64_t S = a.n_pad;
     const float *g2 = a.g2d + 10 * i;
     float gu = g2[0], gv = g2[1], gca = g2[2], gcb = g2[3], gcc = g2[4], go = g2[5], gz = g2[6];
-    const float grgb[3] = {g2[7], g2[8], g2[9]};
     const CamParams &c = a.cam;
     const float *W = c.vm;
     const float m[3] = {a.means[i], a.means[S + i], a.means[2 * S + i]};
@@ -329,31 +329,56 @@ __global__ void __launch_bounds__(256) k_project_bwd(const ProjectBwdArgs a)
     if (a.d_quats)
         for (int k = 0; k < 4; ++k) a.d_quats[k * S + i] += (qb[k] - qh[k] * dot) / qn;
     if (a.d_logits) a.d_logits[i] += d_logit;
-    // colour through SH and the view direction
+    if (a.d_means)
+        for (int k = 0; k < 3; ++k) a.d_means[k * S + i] += mb[k];
+}
+
+// K8, colour part: the rgb adjoint through SH and the view direction, one thread
+// per Gaussian, added to the SH coefficients' and the mean's gradients. Like the
+// forward's colour kernel it streams the SH planes with few registers: one pass
+// forms the raw colour (whose sign says whether the clamp at 0 let the gradient
+// through), a second re-reads the coefficients (L2-resident by then) to update
+// d_sh and the direction's adjoint. The SH degree is a template argument, so the
+// basis and its gradient are registers.
+template <int DEG>
+__global__ void __launch_bounds__(256) k_colour_bwd(const ProjectBwdArgs a)
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n || a.ntiles[i] == 0) return;
+    const int64_t S = a.n_pad;
+    const float *__restrict__ sh = a.sh + i;
+    float *__restrict__ dsh = a.d_sh ? a.d_sh + i : nullptr;
+    const float *g2 = a.g2d + 10 * i;
+    const float grgb[3] = {g2[7], g2[8], g2[9]};
+    const CamParams &c = a.cam;
+    const float m[3] = {__ldg(a.means + i), __ldg(a.means + S + i), __ldg(a.means + 2 * S + i)};
     const float dir[3] = {m[0] - c.campos[0], m[1] - c.campos[1], m[2] - c.campos[2]};
     const float dn = sqrtf(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
     const float d[3] = {dir[0] / dn, dir[1] / dn, dir[2] / dn};
     float Y[16], gX[16], gY[16], gZ[16];
-    sh_eval_grad(a.deg, d[0], d[1], d[2], Y, gX, gY, gZ);
-    const int NK = (a.deg + 1) * (a.deg + 1);
+    sh_eval_grad(DEG, d[0], d[1], d[2], Y, gX, gY, gZ);
+    float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) raw[ch] += Y[k] * __ldg(sh + (int64_t)(k * 3 + ch) * S);
     float db[3] = {0.f, 0.f, 0.f};
-    for (int ch = 0; ch < 3; ++ch) {
-        float raw = 0.5f;
-        for (int k = 0; k < NK; ++k) raw += Y[k] * a.sh[(int64_t)(k * 3 + ch) * S + i];
-        if (raw < 0.0f) continue;
-        const float gc = grgb[ch];
-        for (int k = 0; k < NK; ++k) {
-            const float shv = a.sh[(int64_t)(k * 3 + ch) * S + i];
-            if (a.d_sh) a.d_sh[(int64_t)(k * 3 + ch) * S + i] += gc * Y[k];
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            if (raw[ch] < 0.0f) continue;  // the colour was clamped to 0: no gradient
+            const float gc = grgb[ch], shv = __ldg(sh + (int64_t)(k * 3 + ch) * S);
+            if (dsh) dsh[(int64_t)(k * 3 + ch) * S] += gc * Y[k];
             db[0] += gc * shv * gX[k];
             db[1] += gc * shv * gY[k];
             db[2] += gc * shv * gZ[k];
         }
-    }
     const float dd = db[0] * d[0] + db[1] * d[1] + db[2] * d[2];
-    for (int k = 0; k < 3; ++k) mb[k] += (db[k] - d[k] * dd) / dn;
     if (a.d_means)
-        for (int k = 0; k < 3; ++k) a.d_means[k * S + i] += mb[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.d_means[k * S + i] += (db[k] - d[k] * dd) / dn;
 }
 
 }  // namespace
@@ -375,6 +400,15 @@ cudaError_t launch_project_backward(const ProjectBwdArgs &a, cudaStream_t s)
     if (a.n == 0) return cudaSuccess;
     const int64_t nb = (a.n + 255) / 256;
     k_project_bwd<<<(unsigned)nb, 256, 0, s>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nc = (a.n + 255) / 256;
+    switch (a.deg) {
+    case 0: k_colour_bwd<0><<<(unsigned)nc, 256, 0, s>>>(a); break;
+    case 1: k_colour_bwd<1><<<(unsigned)nc, 256, 0, s>>>(a); break;
+    case 2: k_colour_bwd<2><<<(unsigned)nc, 256, 0, s>>>(a); break;
+    default: k_colour_bwd<3><<<(unsigned)nc, 256, 0, s>>>(a); break;
+    }
     return cudaGetLastError();
 }
 

@@ -35,15 +35,16 @@ def env():
     return api, oracle, api.Context(0)
 
 
-def _deg3_scene(n, seed):
+def _deg3_scene(n, seed, deg=3):
     rng = np.random.default_rng(seed)
-    s = synth.empty_scene(n, 3)
+    s = synth.empty_scene(n, deg)
+    nk = (deg + 1) ** 2
     s.means[:, :n] = rng.uniform(-1, 1, (3, n))
     s.log_scales[:, :n] = rng.normal(-3.3, 0.5, (3, n))
     s.quats[:, :n] = rng.normal(size=(4, n))
     s.logits[:n] = rng.normal(0.3, 1.5, n)
     s.sh[0, :, :n] = rng.uniform(-1.7, 1.7, (3, n))
-    s.sh[1:, :, :n] = rng.normal(0, 0.2, (15, 3, n))
+    s.sh[1:, :, :n] = rng.normal(0, 0.2, (nk - 1, 3, n))
     return s
 
 
@@ -105,6 +106,19 @@ def test_backward_deg3_with_depth_and_alpha(env, tile):
     got = _gpu_grads(api, ctx, sc, cam, ups, bg, tile=tile)
     ref = O.backward(sc, cam, ups["rgb"], ups["dcdx"], ups["dcdy"], ups["depth"], ups["alpha"], bg=bg)
     _compare(got, ref, sc.n, " tile %d" % tile)
+
+
+@pytest.mark.parametrize("deg", [1, 2])
+def test_backward_sh_degrees_1_and_2(env, deg):
+    """The chain through SH is compiled per degree: degrees 1 and 2 against the oracle."""
+    api, O, ctx = env
+    sc = _deg3_scene(500, 20 + deg, deg)
+    cam = synth.jittered_tiny_cameras(2, 9, 144, 80)[0]
+    bg = (0.1, 0.2, 0.3)
+    ups = _upstream(O, sc, cam, bg)
+    got = _gpu_grads(api, ctx, sc, cam, ups, bg, tile=8)
+    ref = O.backward(sc, cam, ups["rgb"], ups["dcdx"], ups["dcdy"], bg=bg)
+    _compare(got, ref, sc.n, " deg %d" % deg)
 
 
 def test_backward_against_fp32_finite_differences(env):
