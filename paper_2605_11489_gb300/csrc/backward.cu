@@ -213,11 +213,21 @@ __device__ __forceinline__ void sh_eval_grad(int deg, float x, float y, float z,
 // K8: one thread per Gaussian; recompute the forward quantities and chain the
 // (u, v, conic, opacity, depth) adjoints to the 3D parameters. The colour's
 // adjoint goes through SH in k_colour_bwd, launched after it.
-__global__ void __launch_bounds__(256) k_project_bwd(const ProjectBwdArgs a)
+__global__ void __launch_bounds__(256, 3) k_project_bwd(const ProjectBwdArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n || a.ntiles[i] == 0) return;
     const int64_t S = a.n_pad;
+    // the gradients this thread adds to, read up front so that their loads overlap
+    // the arithmetic (the colour kernel adds to d_means only after this one)
+    float acc_ls[3] = {0.f, 0.f, 0.f}, acc_q[4] = {0.f, 0.f, 0.f, 0.f}, acc_lg = 0.f, acc_m[3] = {0.f, 0.f, 0.f};
+    if (a.d_log_scales)
+        for (int k = 0; k < 3; ++k) acc_ls[k] = a.d_log_scales[k * S + i];
+    if (a.d_quats)
+        for (int k = 0; k < 4; ++k) acc_q[k] = a.d_quats[k * S + i];
+    if (a.d_logits) acc_lg = a.d_logits[i];
+    if (a.d_means)
+        for (int k = 0; k < 3; ++k) acc_m[k] = a.d_means[k * S + i];
     const float *g2 = a.g2d + 10 * i;
     float gu = g2[0], gv = g2[1], gca = g2[2], gcb = g2[3], gcc = g2[4], go = g2[5], gz = g2[6];
     const CamParams &c = a.cam;
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const ProjectBwdArgs a)
             Rb[3 * r + q] = acc * s[q];
         }
     if (a.d_log_scales)
-        for (int k = 0; k < 3; ++k) a.d_log_scales[k * S + i] += sb[k] * s[k];
+        for (int k = 0; k < 3; ++k) a.d_log_scales[k * S + i] = acc_ls[k] + sb[k] * s[k];
     float qb[4];
     qb[0] = 2.f * (-z * Rb[1] + y * Rb[2] + z * Rb[3] - x * Rb[5] - y * Rb[6] + x * Rb[7]);
     qb[1] = 2.f * (y * Rb[1] + z * Rb[2] + y * Rb[3] - 2.f * x * Rb[4] - w * Rb[5] + z * Rb[6] + w * Rb[7] - 2.f * x * Rb[8]);
@@ -327,21 +337,21 @@ __global__ void __launch_bounds__(256) k_project_bwd(const ProjectBwdArgs a)
     const float qh[4] = {w, x, y, z};
     const float dot = w * qb[0] + x * qb[1] + y * qb[2] + z * qb[3];
     if (a.d_quats)
-        for (int k = 0; k < 4; ++k) a.d_quats[k * S + i] += (qb[k] - qh[k] * dot) / qn;
-    if (a.d_logits) a.d_logits[i] += d_logit;
+        for (int k = 0; k < 4; ++k) a.d_quats[k * S + i] = acc_q[k] + (qb[k] - qh[k] * dot) / qn;
+    if (a.d_logits) a.d_logits[i] = acc_lg + d_logit;
     if (a.d_means)
-        for (int k = 0; k < 3; ++k) a.d_means[k * S + i] += mb[k];
+        for (int k = 0; k < 3; ++k) a.d_means[k * S + i] = acc_m[k] + mb[k];
 }
 
 // K8, colour part: the rgb adjoint through SH and the view direction, one thread
 // per Gaussian, added to the SH coefficients' and the mean's gradients. Like the
 // forward's colour kernel it streams the SH planes with few registers: one pass
 // forms the raw colour (whose sign says whether the clamp at 0 let the gradient
-// through), a second re-reads the coefficients (L2-resident by then) to update
-// d_sh and the direction's adjoint. The SH degree is a template argument, so the
+// through) and reads d_sh, a second re-reads the coefficients (L2-resident by
+// then) to update d_sh and the direction's adjoint. The SH degree is a template argument, so the
 // basis and its gradient are registers.
 template <int DEG>
-__global__ void __launch_bounds__(256) k_colour_bwd(const ProjectBwdArgs a)
+__global__ void __launch_bounds__(256, 2) k_colour_bwd(const ProjectBwdArgs a)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,11 +368,16 @@ __global__ void __launch_bounds__(256) k_colour_bwd(const ProjectBwdArgs a)
     const float d[3] = {dir[0] / dn, dir[1] / dn, dir[2] / dn};
     float Y[16], gX[16], gY[16], gZ[16];
     sh_eval_grad(DEG, d[0], d[1], d[2], Y, gX, gY, gZ);
-    float raw[3] = {0.5f, 0.5f, 0.5f};
+    // the gradient planes are read in the first pass too, so that one wait covers
+    // both streams
+    float raw[3] = {0.5f, 0.5f, 0.5f}, acc[NK * 3];
 #pragma unroll
     for (int k = 0; k < NK; ++k)
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) raw[ch] += Y[k] * __ldg(sh + (int64_t)(k * 3 + ch) * S);
+        for (int ch = 0; ch < 3; ++ch) {
+            raw[ch] += Y[k] * __ldg(sh + (int64_t)(k * 3 + ch) * S);
+            acc[k * 3 + ch] = dsh ? dsh[(int64_t)(k * 3 + ch) * S] : 0.0f;
+        }
     float db[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < NK; ++k)
@@ -370,7 +385,7 @@ __global__ void __launch_bounds__(256) k_colour_bwd(const ProjectBwdArgs a)
         for (int ch = 0; ch < 3; ++ch) {
             if (raw[ch] < 0.0f) continue;  // the colour was clamped to 0: no gradient
             const float gc = grgb[ch], shv = __ldg(sh + (int64_t)(k * 3 + ch) * S);
-            if (dsh) dsh[(int64_t)(k * 3 + ch) * S] += gc * Y[k];
+            if (dsh) dsh[(int64_t)(k * 3 + ch) * S] = acc[k * 3 + ch] + gc * Y[k];
             db[0] += gc * shv * gX[k];
             db[1] += gc * shv * gY[k];
             db[2] += gc * shv * gZ[k];
