@@ -120,8 +120,9 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_bwd(const BackwardArgs
                         const float al = e.al, om = 1.0f - al;
                         const float ax = e.capped ? 0.0f : -al * e.ex;
                         const float ay = e.capped ? 0.0f : -al * e.ey;
-                        const float Ti = T / om;
-                        const float rxi = rx + ax / om, ryi = ry + ay / om;
+                        const float inv = __frcp_rn(om);  // one reciprocal for the three quotients
+                        const float Ti = T * inv;
+                        const float rxi = rx + ax * inv, ryi = ry + ay * inv;
                         const float Txi = Ti * rxi, Tyi = Ti * ryi;
                         const float col[3] = {r1.w, r2.x, r2.y};
                         float Gc = 0.f, Gx = 0.f, Gy = 0.f;
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_bwd(const BackwardArgs
                         if (!e.capped) {
                             const float dx = e.dx, dy = e.dy, ex = e.ex, ey = e.ey;
                             const float Abar = dA - dAx * ex - dAy * ey;
-                            g10[5] = Abar * (al / r1.y);
+                            g10[5] = Abar * e.g;  // d a / d o = a / o
                             const float gQ = -0.5f * al * Abar;
                             const float gex = -al * dAx, gey = -al * dAy;
                             g10[2] = gQ * dx * dx + gex * dx;

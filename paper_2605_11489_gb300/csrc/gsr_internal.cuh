@@ -319,6 +319,7 @@ __device__ __forceinline__ float ex2_approx(float x)
 // skip/cap decisions. ex, ey = conic * d (the pixel-derivative factors).
 struct AlphaEval {
     float dx, dy, ex, ey, al;
+    float g;  // exp(-Q/2), the Gaussian's falloff before the opacity scales it
     bool capped;
 };
 __device__ __forceinline__ AlphaEval eval_alpha(const float4 &r0, const float4 &r1, float pxc, float pyc)
@@ -329,7 +330,8 @@ __device__ __forceinline__ AlphaEval eval_alpha(const float4 &r0, const float4 &
     e.ex = __fmaf_rn(r0.z, e.dx, __fmul_rn(r0.w, e.dy));
     e.ey = __fmaf_rn(r0.w, e.dx, __fmul_rn(r1.x, e.dy));
     const float Q = __fmaf_rn(e.dx, e.ex, __fmul_rn(e.dy, e.ey));
-    const float al = __fmul_rn(r1.y, ex2_approx(__fmul_rn(Q, -0.72134752044448170f)));
+    e.g = ex2_approx(__fmul_rn(Q, -0.72134752044448170f));
+    const float al = __fmul_rn(r1.y, e.g);
     e.capped = al > kAlphaCap;
     e.al = e.capped ? kAlphaCap : al;
     return e;
