@@ -23,7 +23,8 @@
 // with G_c = <g_rgb, c>, G_x = <g_dx, c>, G_y = <g_dy, c>. Through a = o exp(-Q/2)
 // and a_x = -a e_x, a_y = -a e_y (e = conic d), unless a was capped at 0.99.
 // The 10 adjoints (u, v, conic a/b/c, opacity, depth, rgb) of a Gaussian are
-// summed over the warp's pixels with shuffles; one lane adds them atomically.
+// summed over the warp's pixels by a reduce-scatter; ten lanes add the totals
+// atomically.
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -56,17 +57,21 @@ __device__ __forceinline__ int warp_reduce_scatter10(float (&v)[10], int lane)
     return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
+// K7: one warp per CTA, walking 32 pixels of a tile (32 / TILE rows, or part of a
+// row). The warps of a tile stage their own copies of its records (L2 hits after
+// the first) and each walks back only from its own pixels' last blended entry,
+// with no barrier between them.
 template <int TILE>
-__global__ void __launch_bounds__(TILE *TILE) k_composite_bwd(const BackwardArgs a)
+__global__ void __launch_bounds__(32) k_composite_bwd(const BackwardArgs a)
 {
-    constexpr int NT = TILE * TILE;
+    constexpr int WPT = TILE * TILE / 32;  // warps per tile
     __shared__ GaussRec s_rec[kBwdBatch];
     __shared__ uint32_t s_idx[kBwdBatch];
-    __shared__ uint32_t s_max;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int px = blockIdx.x * TILE + tid % TILE, py = blockIdx.y * TILE + tid / TILE;
+    const int lane = threadIdx.x;
+    const int tx = blockIdx.x / WPT, l = (blockIdx.x % WPT) * 32 + lane;
+    const int px = tx * TILE + l % TILE, py = blockIdx.y * TILE + l / TILE;
     const bool inside = px < a.width && py < a.height;
-    const uint2 range = a.ranges[blockIdx.y * a.tiles_x + blockIdx.x];
+    const uint2 range = a.ranges[blockIdx.y * a.tiles_x + tx];
     const int64_t HW = (int64_t)a.width * a.height;
     const int64_t p = (int64_t)py * a.width + px;
 
@@ -90,23 +95,19 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_bwd(const BackwardArgs
         if (a.g_depth) gd = a.g_depth[p];
         if (a.g_alpha) Tb -= a.g_alpha[p];
     }
-    if (tid == 0) s_max = 0;
-    __syncthreads();
-    atomicMax(&s_max, last);
-    __syncthreads();
-    const uint32_t n_walk = s_max;
+    const uint32_t n_walk = __reduce_max_sync(0xffffffffu, last);
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
 
     for (int64_t end = (int64_t)n_walk; end > 0; end -= kBwdBatch) {
         const int64_t beg = end - kBwdBatch > 0 ? end - kBwdBatch : 0;
         const int cnt = (int)(end - beg);
-        __syncthreads();
-        for (int t = tid; t < cnt; t += NT) {  // contiguous records when the sorted copy is there
+        __syncwarp();
+        for (int t = lane; t < cnt; t += 32) {  // contiguous records when the sorted copy is there
             const uint32_t idx = a.vals[range.x + beg + t];
             s_idx[t] = idx;
             s_rec[t] = a.rec_sorted ? a.rec_sorted[range.x + beg + t] : a.rec[idx];
         }
-        __syncthreads();
+        __syncwarp();
         for (int k = cnt - 1; k >= 0; --k) {
             const uint32_t pos = (uint32_t)(beg + k);
             float g10[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -402,11 +403,12 @@ __global__ void __launch_bounds__(256, 2) k_colour_bwd(const ProjectBwdArgs a)
 cudaError_t launch_composite_backward(const BackwardArgs &a, cudaStream_t s)
 {
     if (a.tiles_x == 0 || a.tiles_y == 0) return cudaSuccess;
-    const dim3 grid(a.tiles_x, a.tiles_y);
+    const unsigned wpt = (unsigned)(a.tile * a.tile / 32);  // one warp-sized CTA per 32 pixels of a tile
+    const dim3 grid((unsigned)a.tiles_x * wpt, (unsigned)a.tiles_y);
     switch (a.tile) {
-    case 8: k_composite_bwd<8><<<grid, 64, 0, s>>>(a); break;
-    case 32: k_composite_bwd<32><<<grid, 1024, 0, s>>>(a); break;
-    default: k_composite_bwd<16><<<grid, 256, 0, s>>>(a); break;
+    case 8: k_composite_bwd<8><<<grid, 32, 0, s>>>(a); break;
+    case 32: k_composite_bwd<32><<<grid, 32, 0, s>>>(a); break;
+    default: k_composite_bwd<16><<<grid, 32, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
