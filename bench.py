@@ -749,9 +749,9 @@ def run_pipeline(args):
 
 def algorithmic(stage, w, deg, n, K_avg, V_avg, tile_passes, pixels, pairs):
     """Algorithmic work of one launch of `stage` (bytes, or FP32 ops for compositing)."""
-    sh_bytes = 12 * (deg + 1) ** 2
-    if stage == "project":  # means of all; scales, quaternion, opacity, SH of the visible; 48-byte record out
-        return "hbm", 12.0 * n + (12 + 16 + 4 + sh_bytes + 48) * V_avg
+    if stage == "project":  # geometry: means of all; scales, quaternion, opacity of the visible; the record
+        # without its 12 colour bytes out (the SH colour runs on a parallel branch, outside this stage)
+        return "hbm", 12.0 * n + (12 + 16 + 4 + 36) * V_avg
     if stage == "scan":
         return "hbm", 8.0 * n / 1024
     if stage == "compact":  # tile count of all, depth of the visible; 4-byte key + 4-byte index out
@@ -1062,7 +1062,9 @@ def main():
                 "normals": nrm,
                 "stage_ms": stage_ms,
                 "stage_ms_source": "composite: CUDA events inside the timed replays; the other stages: a "
-                                   "second replay of the camera path with events at every stage boundary",
+                                   "second replay of the camera path with events at every stage boundary; "
+                                   "project is the geometry kernel, the SH colour kernel runs on a parallel "
+                                   "branch from project to ranges",
                 "instances_per_frame": K_avg, "visible_per_frame": V_avg,
                 "roofline": roof, "stage_roofline": stage_roofline, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu,
