@@ -416,14 +416,74 @@ def gai_upsample(weights, rgb, dcdx, dcdy, out=None, stream=None):
 
 
 # ----------------------------------------------------------------------------- frames to the host
+class FrameStream:
+    """Renders a camera sequence on the device with two frames in flight.
+    - Two captured graphs, each with its own output buffers and its own stream, take the
+      frames in turn. Frames t and t+1 are independent, so one frame's compositing runs
+      beside the next frame's projection and sorts.
+    - `render(cam)` returns the slot k that frame goes to. Its planes are `outs[k]`, complete
+      once `rendered[k]` has fired; make a stream wait on that event before reading them.
+    - A consumer that reads `outs[k]` on its own stream calls `release(k, stream)` when it
+      has enqueued those reads. The next frame rendered into slot k then waits for them.
+      Without a release, slot k is rewritten two frames later.
+    Every computation runs in libgsr.so."""
+
+    def __init__(self, ctx: "Context", scene: "Scene", cam0, capacity: int, tile=0, batch=0, chunk=0,
+                 keys=OUTPUT_KEYS, timed=False):
+        W, H = cam0.width, cam0.height
+        self.streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        self.outs = [alloc_outputs(W, H, tuple(keys)) for _ in range(2)]
+        self.graphs = [ctx.graph(scene, cam0, self.outs[k], capacity=capacity, tile=tile, batch=batch, chunk=chunk,
+                                 timed=timed, stream=self.streams[k]) for k in range(2)]
+        self.rendered = [torch.cuda.Event() for _ in range(2)]
+        self.released = [None, None]
+        self.t = 0
+        torch.cuda.synchronize()
+
+    def render(self, cam) -> int:
+        k = self.t % 2
+        if self.released[k] is not None:
+            self.streams[k].wait_event(self.released[k])
+            self.released[k] = None
+        self.graphs[k].render(cam, stream=self.streams[k])
+        self.rendered[k].record(self.streams[k])
+        self.t += 1
+        return k
+
+    def release(self, k: int, stream) -> None:
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        self.released[k] = ev
+
+    def join(self, stream) -> None:
+        """Makes `stream` wait for every frame submitted so far."""
+        for k in range(2):
+            stream.wait_event(self.rendered[k])
+
+    def synchronize(self) -> None:
+        """Waits for every submitted frame; raises if a frame overflowed the graphs'
+        instance capacity."""
+        for k in range(2):
+            self.streams[k].synchronize()
+            self.graphs[k].check(stream=self.streams[k])
+
+    def stats(self, reset=False) -> list:
+        return [self.graphs[k].stats(reset=reset, stream=self.streams[k]) for k in range(2)]
+
+    def close(self) -> None:
+        self.synchronize()
+        for g in self.graphs:
+            g.close()
+
+
 class HostFrameStream:
     """Renders a camera sequence into HOST planes (pinned memory), with each frame's
     device-to-host copies overlapping the next frame's render.
-    - Frames render on a high-priority stream by graph replay (two captured graphs, writing
-      to two device output buffers in turn).
-    - A copy stream moves a finished frame's planes to the caller's host buffers while the
-      next frame renders.
-    - Events order the two streams. A device buffer is rendered into again only after its
+    - Frames render by graph replay with two frames in flight: two captured graphs, each
+      with its own device output buffers and high-priority stream, take the frames in turn.
+    - A copy stream moves each finished frame's planes, in frame order, to the caller's host
+      buffers while the next frames render.
+    - Events order the streams. A device buffer is rendered into again only after its
       previous copy has completed.
     The caller owns the host buffers and must not touch a frame's buffers until
     `synchronize()` (or until two later frames have been submitted and synchronised). Every
@@ -433,11 +493,11 @@ class HostFrameStream:
                  keys=OUTPUT_KEYS):
         W, H = cam0.width, cam0.height
         self.keys = tuple(keys)
-        self.rs = torch.cuda.Stream(priority=-1)
+        self.rs = [torch.cuda.Stream(priority=-1) for _ in range(2)]
         self.cs = torch.cuda.Stream()
         self.outs = [alloc_outputs(W, H, self.keys) for _ in range(2)]
         self.graphs = [ctx.graph(scene, cam0, self.outs[k], capacity=capacity, tile=tile, batch=batch,
-                                 chunk=chunk, stream=self.rs) for k in range(2)]
+                                 chunk=chunk, stream=self.rs[k]) for k in range(2)]
         self.rendered = [torch.cuda.Event() for _ in range(2)]
         self.copied = [torch.cuda.Event() for _ in range(2)]
         self.used = [False, False]
@@ -449,9 +509,9 @@ class HostFrameStream:
         the output shapes, keyed like the device outputs)."""
         k = self.t % 2
         if self.used[k]:
-            self.rs.wait_event(self.copied[k])
-        self.graphs[k].render(cam, stream=self.rs)
-        self.rendered[k].record(self.rs)
+            self.rs[k].wait_event(self.copied[k])
+        self.graphs[k].render(cam, stream=self.rs[k])
+        self.rendered[k].record(self.rs[k])
         self.cs.wait_event(self.rendered[k])
         with torch.cuda.stream(self.cs):
             for key in self.keys:
@@ -463,10 +523,11 @@ class HostFrameStream:
     def synchronize(self):
         """Waits for every submitted frame's copies; raises if a frame overflowed the
         graphs' instance capacity."""
-        self.rs.synchronize()
+        for k in range(2):
+            self.rs[k].synchronize()
         self.cs.synchronize()
-        for g in self.graphs:
-            g.check(stream=self.rs)
+        for k in range(2):
+            self.graphs[k].check(stream=self.rs[k])
 
     def close(self):
         self.synchronize()

@@ -147,3 +147,33 @@ def test_host_frame_stream_equals_plain_forward(env):
         torch.cuda.synchronize()
         for k in ref:
             assert torch.equal(h[k], ref[k].cpu()), k
+
+
+def test_frame_stream_two_frames_in_flight(env):
+    """api.FrameStream: two graphs on two streams take the frames in turn. A consumer on its
+    own stream copies each frame's planes out and releases the slot; every copy equals the
+    plain forward of its camera bit for bit, so neither the overlap of consecutive frames
+    nor the reuse of a slot two frames later disturbs a frame."""
+    api, ctx = env
+    import torch
+
+    sc = synth.tiny_scene(4096, 0)
+    cams = synth.jittered_tiny_cameras(9, 21)
+    scene = api.Scene.from_arrays(sc)
+    fs = api.FrameStream(ctx, scene, cams[0], capacity=200_000, tile=16, batch=64)
+    consumer = torch.cuda.Stream()
+    copies = []
+    for cam in cams:
+        k = fs.render(cam)
+        consumer.wait_event(fs.rendered[k])
+        with torch.cuda.stream(consumer):
+            copies.append({key: v.clone() for key, v in fs.outs[k].items()})
+        fs.release(k, consumer)
+    fs.synchronize()
+    consumer.synchronize()
+    fs.close()
+    for cam, got in zip(cams, copies):
+        ref = ctx.forward(scene, cam, tile=16, batch=64)
+        torch.cuda.synchronize()
+        for key in ref:
+            assert torch.equal(got[key], ref[key]), key
