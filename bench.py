@@ -661,8 +661,8 @@ def run_gass(args):
         torch.distributed.destroy_process_group()
 
 
-PIPE_DESC = ("post-rendering chain of Sec. 4 on two streams: 960x540 render of the large scene (1M, SH 3) per "
-             "frame of the 60-frame orbit || x4 gradient-aware interpolation of colour, depth and alpha + forward "
+PIPE_DESC = ("post-rendering chain of Sec. 4 on three streams: 960x540 render of the large scene (1M, SH 3) per "
+             "frame of the 60-frame orbit (two render streams taking frames in turn) || x4 gradient-aware interpolation of colour, depth and alpha + forward "
              "warp of the previous 3840x2160 frame + backward warp of the current 960x540 frame toward the mid "
              "pose; serial = the same calls on one stream")
 
@@ -704,18 +704,25 @@ def run_pipeline(args):
         pipe.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        e0, e1, done = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(pipe.rs)
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        render_streams = [pipe.rs[0]] if pipe.rs[1] is pipe.rs[0] else pipe.rs
+        e0.record(pipe.ps)
+        for st_ in render_streams:
+            if st_ is not pipe.ps:
+                st_.wait_event(e0)
         for i in range(args.steps):
             t = args.warmup + i
             pipe.step(frames[t % len(frames)], mids[(t - 1) % len(mids)])
-        done.record(pipe.ps)
-        pipe.rs.wait_event(done)
-        e1.record(pipe.rs)
+        for st_ in render_streams:  # the post stream joins the render streams
+            if st_ is not pipe.ps:
+                done = torch.cuda.Event()
+                done.record(st_)
+                pipe.ps.wait_event(done)
+        e1.record(pipe.ps)
         e1.synchronize()
         ms = slowest_rank(e0.elapsed_time(e1), world, "cuda")
-        for g in pipe.graphs:
-            g.check(stream=pipe.rs)  # raises if a frame overflowed the instance capacity
+        for k, g in enumerate(pipe.graphs):
+            g.check(stream=pipe.rs[k])  # raises if a frame overflowed the instance capacity
         pipe.close()
         return ms
 
@@ -750,9 +757,9 @@ def run_pipeline(args):
 
 def algorithmic(stage, w, deg, n, K_avg, V_avg, tile_passes, pixels, pairs):
     """Algorithmic work of one launch of `stage` (bytes, or FP32 ops for compositing)."""
-    if stage == "project":  # geometry: means of all; scales, quaternion, opacity of the visible; the record
-        # without its 12 colour bytes out (the SH colour runs on a parallel branch, outside this stage)
-        return "hbm", 12.0 * n + (12 + 16 + 4 + 36) * V_avg
+    sh_bytes = 12 * (deg + 1) ** 2
+    if stage == "project":  # means of all; scales, quaternion, opacity, SH of the visible; 48-byte record out
+        return "hbm", 12.0 * n + (12 + 16 + 4 + sh_bytes + 48) * V_avg
     if stage == "scan":
         return "hbm", 8.0 * n / 1024
     if stage == "compact":  # tile count of all, depth of the visible; 4-byte key + 4-byte index out
@@ -1091,9 +1098,8 @@ def main():
                 "stage_ms": stage_ms,
                 "one_stream": one_stream,
                 "stage_ms_source": "a replay of the camera path one frame at a time with events at every "
-                                   "stage boundary; project is the geometry kernel, the SH colour kernel runs "
-                                   "on a parallel branch from project to ranges; the roofline's launch_ms is "
-                                   "compositing inside the timed region (two frames in flight)",
+                                   "stage boundary; the roofline's launch_ms is compositing inside the timed "
+                                   "region (two frames in flight)",
                 "instances_per_frame": K_avg, "visible_per_frame": V_avg,
                 "roofline": roof, "stage_roofline": stage_roofline, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu,

@@ -543,8 +543,9 @@ class FramePipeline:
     of Sec. 5.4).
 
     Per frame t (camera cams[t]; mid = the pose between frames t - 1 and t):
-      render stream:  frame t's colour, gradients, depth and alpha at low resolution
-                      (a captured graph per output buffer; two buffers, alternating)
+      render streams: frame t's colour, gradients, depth and alpha at low resolution
+                      (a captured graph per output buffer; two buffers, alternating, each
+                      on its own stream, so consecutive renders overlap too)
       post stream:    x S gradient-aware interpolation of the colour (Sec. 4.1) and of depth
                       and alpha (no gradients: a linear filter of the values);
                       forward warp of the x S frame t - 1 toward the mid pose (Sec. 4.2);
@@ -564,10 +565,14 @@ class FramePipeline:
         S = int(gai_weights[0])
         W, H = cam0.width, cam0.height
         self.ctx, self.scene, self.weights, self.S = ctx, scene, gai_weights, S
-        # the render stream has the higher priority: the post chain's large grids fill the SMs
-        # the render leaves idle instead of delaying it
-        self.rs = torch.cuda.Stream(priority=-1) if overlap else torch.cuda.Stream()
-        self.ps = torch.cuda.Stream(priority=0) if overlap else self.rs
+        # the render streams have the higher priority: the post chain's large grids fill the
+        # SMs the renders leave idle instead of delaying them
+        if overlap:
+            self.rs = [torch.cuda.Stream(priority=-1) for _ in range(2)]
+            self.ps = torch.cuda.Stream(priority=0)
+        else:
+            one = torch.cuda.Stream()
+            self.rs, self.ps = [one, one], one
         self.lr, self.da = [], []
         for _ in range(2):
             da = torch.empty((2, H, W), dtype=torch.float32, device="cuda")  # depth, alpha
@@ -577,7 +582,7 @@ class FramePipeline:
             self.da.append(da)
         self.zero_g = torch.zeros((2, H, W), dtype=torch.float32, device="cuda")
         self.graphs = [ctx.graph(scene, cam0, self.lr[k], capacity=capacity, tile=tile, batch=batch, chunk=chunk,
-                                 stream=self.rs) for k in range(2)]
+                                 stream=self.rs[k]) for k in range(2)]
         self.hr_rgb = [torch.empty((3, S * H, S * W), dtype=torch.float32, device="cuda") for _ in range(2)]
         self.hr_da = [torch.empty((2, S * H, S * W), dtype=torch.float32, device="cuda") for _ in range(2)]
         self.wctx = Context(ctx.device)  # the warps' scratch, used on the post stream only
@@ -595,9 +600,9 @@ class FramePipeline:
         (hr_rgb[k]), depth and alpha (hr_da[k]) and the two warps' outputs (fwd, bwd)."""
         k = 0 if self.prev_cam is None else 1 - self._k
         if self.used[k]:
-            self.rs.wait_event(self.consumed[k])
-        self.graphs[k].render(cam, stream=self.rs)
-        self.rendered[k].record(self.rs)
+            self.rs[k].wait_event(self.consumed[k])
+        self.graphs[k].render(cam, stream=self.rs[k])
+        self.rendered[k].record(self.rs[k])
         self.ps.wait_event(self.rendered[k])
         lr, S = self.lr[k], self.S
         gai_upsample(self.weights, lr["rgb"], lr["dcdx"], lr["dcdy"], out=self.hr_rgb[k], stream=self.ps)
@@ -614,7 +619,8 @@ class FramePipeline:
         return k
 
     def synchronize(self):
-        self.rs.synchronize()
+        for st in self.rs:
+            st.synchronize()
         self.ps.synchronize()
 
     def close(self):

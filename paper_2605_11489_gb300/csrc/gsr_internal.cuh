@@ -97,9 +97,8 @@ struct ProjectArgs {
     float4 *nrm;           // per Gaussian: camera-space normal (x, y, z, 0) of the visible ones (nullable)
 };
 int project_blocks(int64_t n);
-// geometry (records without colour, bin, tile counts, block sums) and the SH
-// colour of every Gaussian (the records' colour fields): independent, so the
-// render runs them on two branches; launch_project runs both on one stream
+// geometry (records without colour, bin, tile counts, block sums), then the SH
+// colour of the visible Gaussians; launch_project runs both on one stream
 cudaError_t launch_project_geometry(const ProjectArgs &a, cudaStream_t s);
 cudaError_t launch_colour(const ProjectArgs &a, cudaStream_t s);
 cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s);

@@ -15,11 +15,10 @@
 // bit.
 //
 // Layout: in k_project one thread owns one Gaussian, so a warp reads 128
-// contiguous bytes of every geometry plane; it writes every field of the
-// visible Gaussians' records except the colour. k_colour streams the SH planes
-// (192 B per Gaussian at degree 3), one thread per Gaussian, and writes the
-// colour fields. The two touch disjoint bytes and k_colour reads nothing
-// k_project writes, so they may run concurrently.
+// contiguous bytes of every geometry plane; it writes whole records with the
+// colour left at 0. k_colour then streams the SH
+// planes (192 B per Gaussian at degree 3) for the visible Gaussians only, one
+// thread each, and fills in the colour.
 #include "gsr_internal.cuh"
 #include <algorithm>
 
@@ -241,20 +240,19 @@ struct ShAccum<NK, NK> {
     __device__ __forceinline__ static void run(const float *, int64_t, int64_t, float, float, float, float (&)[3]) {}
 };
 
-// Colour of every Gaussian (one thread each, so a warp reads 128 contiguous
-// bytes of every SH plane): direction from the camera centre, the SH sum, +0.5,
-// clamped at 0, into the colour fields of its record. Kept apart from the
-// projection so that this stream of SH bytes, the bulk of the step's traffic at
-// degree 3, runs with few registers and many warps in flight (measured faster
-// than 4 Gaussians per thread with 16-byte loads). It reads nothing k_project
-// writes and writes only the bytes k_project leaves alone, so the two can run
-// at the same time; the culled few per cent get a colour nobody reads.
+// Colour of the visible Gaussians (one thread each, so a warp reads 128
+// contiguous bytes of every SH plane): direction from the camera centre, the
+// SH sum, +0.5, clamped at 0, into the colour fields of the record k_project
+// wrote. Kept apart from the projection so that this stream of SH bytes, the
+// bulk of the step's traffic at degree 3, runs with few registers and many
+// warps in flight (measured faster than 4 Gaussians per thread with 16-byte
+// loads).
 template <int DEG>
 __global__ void __launch_bounds__(256) k_colour(ProjectArgs a)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (i >= a.n) return;
+    if (i >= a.n || a.ntiles[i] == 0) return;
     const int64_t np = a.n_pad;
     const float ex = __ldg(a.means + i) - a.cam.campos[0];
     const float ey = __ldg(a.means + np + i) - a.cam.campos[1];
@@ -291,12 +289,12 @@ __global__ void __launch_bounds__(kGeomThreads, 1) k_project(ProjectArgs a)
                         ld(a.log_scales, 1), ld(a.log_scales, 2), ld(a.quats, 0), ld(a.quats, 1), ld(a.quats, 2),
                         ld(a.quats, 3), ld(a.logits, 0), Q);
         }
-        if (Q.vis) {  // every field but the colour (r1.w, r2.x, r2.y), which k_colour writes
-            float *r = reinterpret_cast<float *>(a.rec + i);
-            *reinterpret_cast<float4 *>(r) = make_float4(Q.u, Q.v, Q.ca, Q.cb);
-            *reinterpret_cast<float2 *>(r + 4) = make_float2(Q.cc, Q.o);
-            r[6] = Q.z;
-            *reinterpret_cast<float2 *>(r + 10) = make_float2(__uint_as_float(Q.rlo), __uint_as_float(Q.rhi));
+        if (Q.vis) {  // colour left 0 for k_colour
+            GaussRec r;
+            r.r0 = make_float4(Q.u, Q.v, Q.ca, Q.cb);
+            r.r1 = make_float4(Q.cc, Q.o, Q.z, 0.0f);
+            r.r2 = make_float4(0.0f, 0.0f, __uint_as_float(Q.rlo), __uint_as_float(Q.rhi));
+            a.rec[i] = r;
             a.bin[i] = make_uint4(__float_as_uint(Q.z), Q.rlo, Q.rhi, 0u);
             if (NRM) a.nrm[i] = make_float4(Q.n[0], Q.n[1], Q.n[2], 0.0f);
         }

@@ -270,17 +270,10 @@ struct gs_context {
     std::map<TuneKey, Tuned> tune;
     StageTimer timer;
     int64_t st_frames = 0, st_sum_k = 0, st_sum_v = 0, st_max_k = 0, st_pairs_eval = 0, st_pairs_blend = 0;
-    // the SH-colour branch of K1: its stream, and the events that fork it from and
-    // join it to the caller's stream
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~gs_context()
     {
         for (Frame *f : pool) delete f;
         if (h_counters) cudaFreeHost(h_counters);
-        if (ev_fork) cudaEventDestroy(ev_fork);
-        if (ev_join) cudaEventDestroy(ev_join);
-        if (side) cudaStreamDestroy(side);
     }
     Frame *acquire()
     {
@@ -498,24 +491,7 @@ cudaError_t mark(const Marks &m, int k, cudaStream_t st)
     return m.capture ? cudaEventRecordWithFlags(m.ev[k], st, cudaEventRecordExternal) : cudaEventRecord(m.ev[k], st);
 }
 
-// K1 on two branches from the same point of `st`: the geometry on `st`, the SH
-// colour on the context's side stream. ctx->ev_join marks the colour's end; the
-// gather of the sorted records (K5) waits for it, so the colour stream overlaps
-// the scan, the compaction and both sorts.
-cudaError_t launch_project_branches(gs_context *ctx, const ProjectArgs &pa, cudaStream_t st)
-{
-    cudaError_t e = cudaEventRecord(ctx->ev_fork, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-    if (e == cudaSuccess) e = launch_colour(pa, ctx->side);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
-    if (e == cudaSuccess) e = launch_project_geometry(pa, st);
-    return e;
-}
-
-// `colour_done`: the event of the projection's colour branch (nullable), waited
-// for before the sorted records are gathered.
-gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cudaStream_t st, cudaEvent_t colour_done,
-                             const Marks &mk = Marks{})
+gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cudaStream_t st, const Marks &mk = Marks{})
 {
     uint32_t *cnt = f->counters.as<uint32_t>();
     SortScratch scr;
@@ -542,7 +518,6 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     GSR_CUDA(launch_sort32(kk, vv, cnt + kCntEff, cnt + kCntErr, max_k, tbits, scr, &res, st, true));
     f->sorted = res;
     GSR_CUDA(mark(mk, 6, st));
-    if (colour_done) GSR_CUDA(cudaStreamWaitEvent(st, colour_done, 0));
     GSR_CUDA(launch_ranges(kk[res], vv[res], cnt, max_k, f->rec.as<GaussRec>(), f->rec_sorted.as<GaussRec>(),
                            f->ranges.as<uint2>(), f->n_tiles, f->bin.as<uint4>(),
                            f->has_state ? f->keys64.as<uint64_t>() : nullptr, st,
@@ -602,7 +577,7 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
     GSR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * kCntSlots, st));
     GSR_CUDA(mark(mk, 0, st));
     const ProjectArgs pa = proj_args(f, s);
-    GSR_CUDA(launch_project_branches(ctx, pa, st));
+    GSR_CUDA(launch_project(pa, st));
     GSR_CUDA(mark(mk, 1, st));
     GSR_CUDA(launch_scan_blocks(pa.block_sums, pa.block_vis, project_blocks(s->n), f->boffs.as<uint32_t>(),
                                 f->voffs.as<uint32_t>(), cnt, kMaxInstances, st));
@@ -623,7 +598,7 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
     if ((r = frame_plan(f, f->K)) != GS_OK) return r;
     if (nrm) GSR_CUDA(f->nrm_sorted.ensure(sizeof(float4) * (size_t)std::max<int64_t>(f->K, 1)));
     // counters[kCntEff] was clamped to kMaxInstances; K fits, so it equals K.
-    r = enqueue_after_scan(f, out, f->K, st, ctx->ev_join, mk);
+    r = enqueue_after_scan(f, out, f->K, st, mk);
     if (r != GS_OK || !f->count_pairs) return r;
     GSR_CUDA(cudaMemcpyAsync(ctx->h_counters, cnt, sizeof(uint32_t) * kCntSlots, cudaMemcpyDeviceToHost, st));
     GSR_CUDA(cudaStreamSynchronize(st));
@@ -675,12 +650,9 @@ gs_status gs_context_create(int device, gs_context **ctx)
     gs_context *c = new gs_context();
     c->device = device;
     cudaError_t e = cudaMallocHost(&c->h_counters, sizeof(uint32_t) * kCntSlots);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         delete c;
-        return cuda_fail(e, "context setup");
+        return cuda_fail(e, "cudaMallocHost");
     }
     *ctx = c;
     return GS_OK;
@@ -911,12 +883,12 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
             GSR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * kCntPerFrame, s2));
             GSR_CUDA(mark(evs, 0, s2));
             g->proj_args = proj_args(f, scene);
-            GSR_CUDA(launch_project_branches(ctx, g->proj_args, s2));
+            GSR_CUDA(launch_project(g->proj_args, s2));
             GSR_CUDA(mark(evs, 1, s2));
             GSR_CUDA(launch_scan_blocks(g->proj_args.block_sums, g->proj_args.block_vis, project_blocks(scene->n),
                                         f->boffs.as<uint32_t>(), f->voffs.as<uint32_t>(), cnt, capacity, s2));
             GSR_CUDA(mark(evs, 2, s2));
-            return enqueue_after_scan(f, out, capacity, s2, ctx->ev_join, evs);
+            return enqueue_after_scan(f, out, capacity, s2, evs);
         };
         if (r == GS_OK) r = enqueue(st, false);
         if (r == GS_OK) {
