@@ -3,8 +3,9 @@
 A step renders one frame of the workload's camera path through the whole hot
 path (projection + SH colour, scan, key duplication, radix sort, tile ranges,
 compositing with dC/dx, dC/dy, depth and alpha), replayed as a captured CUDA
-graph with the frame's camera (the fixed-resolution stream path), two frames in
-flight on two streams (api.FrameStream). The scene is
+graph with the frame's camera (the fixed-resolution stream path), with
+--frames-in-flight frames (default 4) rendering concurrently on their own streams
+(api.FrameStream). The scene is
 resident in HBM before timing starts and is larger than L2, so steps do not
 reuse each other's inputs from cache.
 
@@ -829,6 +830,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-backward", action="store_true", help="skip the forward+backward timing")
     ap.add_argument("--no-normals", action="store_true", help="skip the normal-channel timing")
+    ap.add_argument("--frames-in-flight", type=int, default=4,
+                    help="frames rendered concurrently, one graph and stream each (api.FrameStream)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -877,32 +880,33 @@ def main():
     pre = ctx.stats(reset=True, stream=stream)
     census = (pre["pairs_evaluated"] / len(cams), pre["pairs_blended"] / len(cams))
     capacity = int(pre["instances_max"] * 1.25) + 4096
-    # the timed replays: api.FrameStream, two frames in flight (two captured graphs on two
-    # streams taking the frames in turn, so one frame's compositing runs beside the next
-    # frame's projection and sorts). Each graph carries two events per frame around
-    # compositing (the dominant kernel, whose launch duration the roofline needs); the
-    # per-stage breakdown comes from a third graph, replayed alone afterwards, with events
+    # the timed replays: api.FrameStream, --frames-in-flight frames at once (one captured
+    # graph and stream per slot, taking the frames in turn, so one frame's compositing runs
+    # beside the next frames' projection and sorts). Each graph carries two events per frame
+    # around compositing (the dominant kernel, whose launch duration the roofline needs); the
+    # per-stage breakdown comes from one more graph, replayed alone afterwards, with events
     # at every stage boundary (nine event nodes per frame cost about 5 % of a frame)
-    fs = api.FrameStream(ctx, scene, cams[0], capacity, tile, batch, chunk, timed="composite")
+    fs = api.FrameStream(ctx, scene, cams[0], capacity, tile, batch, chunk, timed="composite",
+                         slots=args.frames_in_flight)
     for i in range(args.warmup):
         fs.render(cams[i % len(cams)])
     fs.synchronize()
     fs.stats(reset=True)
 
     def timed_replays(frame_stream, two):
-        """Times args.steps frames (CUDA events on `stream`, which joins both slots' streams);
-        with two=False both slots replay on one stream, one frame at a time."""
+        """Times args.steps frames (CUDA events on `stream`, which joins every slot's stream);
+        with two=False the slots' graphs replay on one stream, one frame at a time."""
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for k in range(2):
+        for k in range(frame_stream.slots):
             frame_stream.streams[k].wait_event(e0)
         for i in range(args.steps):
             cam = cams[(args.warmup + i) % len(cams)]
             if two:
                 frame_stream.render(cam)
             else:
-                frame_stream.graphs[i % 2].render(cam, stream=stream)
+                frame_stream.graphs[i % frame_stream.slots].render(cam, stream=stream)
         frame_stream.join(stream)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -926,7 +930,7 @@ def main():
     st = {key: sum(x[key] for x in sts) for key in ("frames", "instances_total", "visible_total", "timed_frames")}
     ms = slowest_rank(ms, world, "cuda")
     value = job_throughput(W * H * args.steps, world, ms * 1e-3)
-    # the dominant kernel's launch duration inside the timed region (both slots' frames)
+    # the dominant kernel's launch duration inside the timed region (every slot's frames)
     composite_ms_timed = (sum(x["stage_ms"]["composite"] * x["timed_frames"] for x in sts)
                           / max(1, sum(x["timed_frames"] for x in sts)))
     # for context: the same replays one frame at a time on one stream (after the timed region)
@@ -975,6 +979,9 @@ def main():
     # the dominant kernel at its launch duration inside the timed region (sharing the GPU
     # with the other slot's frame); the per-stage table from the one-frame-at-a-time breakdown
     roof = roofline(dom, composite_ms_timed if dom == "composite" else None)
+    # the same kernel one frame at a time (the stage breakdown), where nothing shares the GPU
+    alone = roofline(dom)
+    roof["one_frame_at_a_time"] = {"launch_ms": stage_ms[dom], "achieved": alone["achieved"], "frac": alone["frac"]}
     stage_roofline = {k: {kk: v[kk] for kk in ("bound", "achieved", "unit", "frac")}
                       for k, v in ((s, roofline(s)) for s in abi.STAGES)}
 
@@ -986,7 +993,7 @@ def main():
     if not args.no_e2e:
         hosts = [{k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in out.items()}
                  for _ in range(2)]
-        fs = api.HostFrameStream(ctx, scene, cams[0], capacity, tile, batch, chunk)
+        fs = api.HostFrameStream(ctx, scene, cams[0], capacity, tile, batch, chunk, slots=args.frames_in_flight)
         for i in range(3):
             fs.render(cams[i % len(cams)], hosts[i % 2])
         fs.synchronize()
@@ -1009,9 +1016,9 @@ def main():
         dt_sync = slowest_rank(time.perf_counter() - t0, world, "cuda")
         e2e = {"value": job_throughput(W * H * e2e_steps, world, dt), "unit": "Mpix/s",
                "h2d_bytes_per_step": GS_CAMERA_BYTES, "d2h_bytes_per_step": 11 * W * H * 4,
-               "path": "api.HostFrameStream: graph replay per frame with the camera from the host, two frames in "
-                       "flight on two streams, D2H of rgb, dC/dx, dC/dy, depth, alpha into pinned host memory, "
-                       "copies overlapping the next renders",
+               "path": "api.HostFrameStream: graph replay per frame with the camera from the host, "
+                       "--frames-in-flight frames on their own streams, D2H of rgb, dC/dx, dC/dy, depth, "
+                       "alpha into pinned host memory, copies overlapping the next renders",
                "sync_call": {"value": job_throughput(W * H * n_sync, world, dt_sync), "unit": "Mpix/s",
                              "path": "gs_render_forward_to_host per frame (plain forward + D2H, synchronous)"}}
 
@@ -1089,7 +1096,8 @@ def main():
                 "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
                            "width": W, "height": H, "gaussians": sc.n, "sh_degree": sc.deg,
                            "tile": tile, "batch": batch, "chunk": chunk,
-                           "path": "CUDA graph replay per frame, two frames in flight (api.FrameStream)",
+                           "path": "CUDA graph replay per frame, %d frames in flight (api.FrameStream)"
+                                   % args.frames_in_flight, "frames_in_flight": args.frames_in_flight,
                            "l2": "inputs larger than L2 (scene %.0f MB)" % (sc.nbytes() / 1e6),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "frames_per_s": 1e3 * args.steps * world / ms,
@@ -1099,7 +1107,7 @@ def main():
                 "one_stream": one_stream,
                 "stage_ms_source": "a replay of the camera path one frame at a time with events at every "
                                    "stage boundary; the roofline's launch_ms is compositing inside the timed "
-                                   "region (two frames in flight)",
+                                   "region (frames in flight sharing the GPU)",
                 "instances_per_frame": K_avg, "visible_per_frame": V_avg,
                 "roofline": roof, "stage_roofline": stage_roofline, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu,

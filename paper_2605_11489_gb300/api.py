@@ -417,31 +417,34 @@ def gai_upsample(weights, rgb, dcdx, dcdy, out=None, stream=None):
 
 # ----------------------------------------------------------------------------- frames to the host
 class FrameStream:
-    """Renders a camera sequence on the device with two frames in flight.
-    - Two captured graphs, each with its own output buffers and its own stream, take the
-      frames in turn. Frames t and t+1 are independent, so one frame's compositing runs
-      beside the next frame's projection and sorts.
+    """Renders a camera sequence on the device with `slots` frames in flight (default 2).
+    - One captured graph per slot, each with its own output buffers and its own stream, takes
+      the frames in turn. Consecutive frames are independent, so one frame's compositing runs
+      beside the next frames' projection and sorts.
     - `render(cam)` returns the slot k that frame goes to. Its planes are `outs[k]`, complete
       once `rendered[k]` has fired; make a stream wait on that event before reading them.
     - A consumer that reads `outs[k]` on its own stream calls `release(k, stream)` when it
       has enqueued those reads. The next frame rendered into slot k then waits for them.
-      Without a release, slot k is rewritten two frames later.
+      Without a release, slot k is rewritten `slots` frames later.
     Every computation runs in libgsr.so."""
 
     def __init__(self, ctx: "Context", scene: "Scene", cam0, capacity: int, tile=0, batch=0, chunk=0,
-                 keys=OUTPUT_KEYS, timed=False):
+                 keys=OUTPUT_KEYS, timed=False, slots=2):
         W, H = cam0.width, cam0.height
-        self.streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-        self.outs = [alloc_outputs(W, H, tuple(keys)) for _ in range(2)]
+        self.slots = n = int(slots)
+        if n < 1:
+            raise ValueError("slots must be >= 1")
+        self.streams = [torch.cuda.Stream() for _ in range(n)]
+        self.outs = [alloc_outputs(W, H, tuple(keys)) for _ in range(n)]
         self.graphs = [ctx.graph(scene, cam0, self.outs[k], capacity=capacity, tile=tile, batch=batch, chunk=chunk,
-                                 timed=timed, stream=self.streams[k]) for k in range(2)]
-        self.rendered = [torch.cuda.Event() for _ in range(2)]
-        self.released = [None, None]
+                                 timed=timed, stream=self.streams[k]) for k in range(n)]
+        self.rendered = [torch.cuda.Event() for _ in range(n)]
+        self.released = [None] * n
         self.t = 0
         torch.cuda.synchronize()
 
     def render(self, cam) -> int:
-        k = self.t % 2
+        k = self.t % self.slots
         if self.released[k] is not None:
             self.streams[k].wait_event(self.released[k])
             self.released[k] = None
@@ -457,18 +460,18 @@ class FrameStream:
 
     def join(self, stream) -> None:
         """Makes `stream` wait for every frame submitted so far."""
-        for k in range(2):
+        for k in range(self.slots):
             stream.wait_event(self.rendered[k])
 
     def synchronize(self) -> None:
         """Waits for every submitted frame; raises if a frame overflowed the graphs'
         instance capacity."""
-        for k in range(2):
+        for k in range(self.slots):
             self.streams[k].synchronize()
             self.graphs[k].check(stream=self.streams[k])
 
     def stats(self, reset=False) -> list:
-        return [self.graphs[k].stats(reset=reset, stream=self.streams[k]) for k in range(2)]
+        return [self.graphs[k].stats(reset=reset, stream=self.streams[k]) for k in range(self.slots)]
 
     def close(self) -> None:
         self.synchronize()
@@ -479,8 +482,9 @@ class FrameStream:
 class HostFrameStream:
     """Renders a camera sequence into HOST planes (pinned memory), with each frame's
     device-to-host copies overlapping the next frame's render.
-    - Frames render by graph replay with two frames in flight: two captured graphs, each
-      with its own device output buffers and high-priority stream, take the frames in turn.
+    - Frames render by graph replay with `slots` frames in flight (default 2): one captured
+      graph per slot, each with its own device output buffers and high-priority stream, takes
+      the frames in turn.
     - A copy stream moves each finished frame's planes, in frame order, to the caller's host
       buffers while the next frames render.
     - Events order the streams. A device buffer is rendered into again only after its
@@ -490,24 +494,27 @@ class HostFrameStream:
     computation runs in libgsr.so; the copies are cudaMemcpyAsync."""
 
     def __init__(self, ctx: "Context", scene: "Scene", cam0, capacity: int, tile=0, batch=0, chunk=0,
-                 keys=OUTPUT_KEYS):
+                 keys=OUTPUT_KEYS, slots=2):
         W, H = cam0.width, cam0.height
         self.keys = tuple(keys)
-        self.rs = [torch.cuda.Stream(priority=-1) for _ in range(2)]
+        self.slots = n = int(slots)
+        if n < 1:
+            raise ValueError("slots must be >= 1")
+        self.rs = [torch.cuda.Stream(priority=-1) for _ in range(n)]
         self.cs = torch.cuda.Stream()
-        self.outs = [alloc_outputs(W, H, self.keys) for _ in range(2)]
+        self.outs = [alloc_outputs(W, H, self.keys) for _ in range(n)]
         self.graphs = [ctx.graph(scene, cam0, self.outs[k], capacity=capacity, tile=tile, batch=batch,
-                                 chunk=chunk, stream=self.rs[k]) for k in range(2)]
-        self.rendered = [torch.cuda.Event() for _ in range(2)]
-        self.copied = [torch.cuda.Event() for _ in range(2)]
-        self.used = [False, False]
+                                 chunk=chunk, stream=self.rs[k]) for k in range(n)]
+        self.rendered = [torch.cuda.Event() for _ in range(n)]
+        self.copied = [torch.cuda.Event() for _ in range(n)]
+        self.used = [False] * n
         self.t = 0
         torch.cuda.synchronize()
 
     def render(self, cam, host_out: dict):
         """Enqueue frame `cam`; its planes land in `host_out` (pinned fp32 CPU tensors of
         the output shapes, keyed like the device outputs)."""
-        k = self.t % 2
+        k = self.t % self.slots
         if self.used[k]:
             self.rs[k].wait_event(self.copied[k])
         self.graphs[k].render(cam, stream=self.rs[k])
@@ -523,10 +530,10 @@ class HostFrameStream:
     def synchronize(self):
         """Waits for every submitted frame's copies; raises if a frame overflowed the
         graphs' instance capacity."""
-        for k in range(2):
+        for k in range(self.slots):
             self.rs[k].synchronize()
         self.cs.synchronize()
-        for k in range(2):
+        for k in range(self.slots):
             self.graphs[k].check(stream=self.rs[k])
 
     def close(self):

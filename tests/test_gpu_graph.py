@@ -125,9 +125,9 @@ def test_autotune_picks_a_supported_config_and_caches_it(env):
 
 
 def test_host_frame_stream_equals_plain_forward(env):
-    """api.HostFrameStream: frames rendered by graph replay into two device buffers in turn,
-    each frame's planes copied to its host buffers while the next one renders. Every host
-    plane equals the plain forward of its camera bit for bit."""
+    """api.HostFrameStream: frames rendered by graph replay into three device buffers in turn
+    (three frames in flight), each frame's planes copied to its host buffers while the next
+    ones render. Every host plane equals the plain forward of its camera bit for bit."""
     api, ctx = env
     import torch
 
@@ -137,7 +137,7 @@ def test_host_frame_stream_equals_plain_forward(env):
     W, H = cams[0].width, cams[0].height
     shapes = {k: v.shape for k, v in api.alloc_outputs(W, H).items()}
     hosts = [{k: torch.empty(s, dtype=torch.float32).pin_memory() for k, s in shapes.items()} for _ in cams]
-    fs = api.HostFrameStream(ctx, scene, cams[0], capacity=200_000, tile=16, batch=64)
+    fs = api.HostFrameStream(ctx, scene, cams[0], capacity=200_000, tile=16, batch=64, slots=3)
     for cam, h in zip(cams, hosts):
         fs.render(cam, h)
     fs.synchronize()
@@ -149,18 +149,19 @@ def test_host_frame_stream_equals_plain_forward(env):
             assert torch.equal(h[k], ref[k].cpu()), k
 
 
-def test_frame_stream_two_frames_in_flight(env):
-    """api.FrameStream: two graphs on two streams take the frames in turn. A consumer on its
-    own stream copies each frame's planes out and releases the slot; every copy equals the
-    plain forward of its camera bit for bit, so neither the overlap of consecutive frames
-    nor the reuse of a slot two frames later disturbs a frame."""
+@pytest.mark.parametrize("slots", [2, 3])
+def test_frame_stream_frames_in_flight(env, slots):
+    """api.FrameStream: one graph and stream per slot take the frames in turn. A consumer on
+    its own stream copies each frame's planes out and releases the slot; every copy equals
+    the plain forward of its camera bit for bit, so neither the overlap of consecutive
+    frames nor the reuse of a slot `slots` frames later disturbs a frame."""
     api, ctx = env
     import torch
 
     sc = synth.tiny_scene(4096, 0)
     cams = synth.jittered_tiny_cameras(9, 21)
     scene = api.Scene.from_arrays(sc)
-    fs = api.FrameStream(ctx, scene, cams[0], capacity=200_000, tile=16, batch=64)
+    fs = api.FrameStream(ctx, scene, cams[0], capacity=200_000, tile=16, batch=64, slots=slots)
     consumer = torch.cuda.Stream()
     copies = []
     for cam in cams:
