@@ -977,7 +977,7 @@ def main():
                 "pairs_evaluated_per_frame": census[0], "pairs_blended_per_frame": census[1]}
 
     # the dominant kernel at its launch duration inside the timed region (sharing the GPU
-    # with the other slot's frame); the per-stage table from the one-frame-at-a-time breakdown
+    # with the other slots' frames); the per-stage table from the one-frame-at-a-time breakdown
     roof = roofline(dom, composite_ms_timed if dom == "composite" else None)
     # the same kernel one frame at a time (the stage breakdown), where nothing shares the GPU
     alone = roofline(dom)
