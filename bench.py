@@ -663,7 +663,7 @@ def run_gass(args):
 
 
 PIPE_DESC = ("post-rendering chain of Sec. 4 on three streams: 960x540 render of the large scene (1M, SH 3) per "
-             "frame of the 60-frame orbit (two render streams taking frames in turn) || x4 gradient-aware interpolation of colour, depth and alpha + forward "
+             "frame of the 60-frame orbit (--frames-in-flight render streams taking frames in turn) || x4 gradient-aware interpolation of colour, depth and alpha + forward "
              "warp of the previous 3840x2160 frame + backward warp of the current 960x540 frame toward the mid "
              "pose; serial = the same calls on one stream")
 
@@ -699,7 +699,8 @@ def run_pipeline(args):
     del out
 
     def timed(overlap):
-        pipe = api.FramePipeline(ctx, scene, frames[0], weights, capacity, tile, batch, chunk, overlap=overlap)
+        pipe = api.FramePipeline(ctx, scene, frames[0], weights, capacity, tile, batch, chunk, overlap=overlap,
+                                 slots=args.frames_in_flight)
         for t in range(args.warmup):
             pipe.step(frames[t % len(frames)], mids[(t - 1) % len(mids)])
         pipe.synchronize()

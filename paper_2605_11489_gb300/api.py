@@ -551,15 +551,15 @@ class FramePipeline:
 
     Per frame t (camera cams[t]; mid = the pose between frames t - 1 and t):
       render streams: frame t's colour, gradients, depth and alpha at low resolution
-                      (a captured graph per output buffer; two buffers, alternating, each
-                      on its own stream, so consecutive renders overlap too)
+                      (a captured graph per output buffer; `slots` buffers in turn, each on
+                      its own stream, so consecutive renders overlap too)
       post stream:    x S gradient-aware interpolation of the colour (Sec. 4.1) and of depth
                       and alpha (no gradients: a linear filter of the values);
                       forward warp of the x S frame t - 1 toward the mid pose (Sec. 4.2);
                       backward warp of the low-resolution frame t, with its gradients,
                       toward the mid pose.
-    Events order the two streams: the post chain of frame t waits for its render, and the
-    render of frame t + 2 waits until the chain of frame t has read their shared buffer.
+    Events order the streams: the post chain of frame t waits for its render, and the
+    render of frame t + slots waits until the chain of frame t has read their shared buffer.
     overlap=False runs both on one stream (the serial baseline). Every computation runs in
     libgsr.so; this class only orders the calls."""
 
@@ -568,20 +568,23 @@ class FramePipeline:
     HR_ALPHA_MIN = 0.01
 
     def __init__(self, ctx: "Context", scene: "Scene", cam0, gai_weights, capacity: int, tile=0, batch=0,
-                 chunk=0, overlap=True):
+                 chunk=0, overlap=True, slots=2):
         S = int(gai_weights[0])
+        self.slots = n = int(slots) if overlap else 2
+        if n < 2:
+            raise ValueError("slots must be >= 2")
         W, H = cam0.width, cam0.height
         self.ctx, self.scene, self.weights, self.S = ctx, scene, gai_weights, S
         # the render streams have the higher priority: the post chain's large grids fill the
         # SMs the renders leave idle instead of delaying them
         if overlap:
-            self.rs = [torch.cuda.Stream(priority=-1) for _ in range(2)]
+            self.rs = [torch.cuda.Stream(priority=-1) for _ in range(n)]
             self.ps = torch.cuda.Stream(priority=0)
         else:
             one = torch.cuda.Stream()
-            self.rs, self.ps = [one, one], one
+            self.rs, self.ps = [one] * n, one
         self.lr, self.da = [], []
-        for _ in range(2):
+        for _ in range(n):
             da = torch.empty((2, H, W), dtype=torch.float32, device="cuda")  # depth, alpha
             out = alloc_outputs(W, H, keys=("rgb", "dcdx", "dcdy"))
             out["depth"], out["alpha"] = da[0], da[1]
@@ -589,15 +592,15 @@ class FramePipeline:
             self.da.append(da)
         self.zero_g = torch.zeros((2, H, W), dtype=torch.float32, device="cuda")
         self.graphs = [ctx.graph(scene, cam0, self.lr[k], capacity=capacity, tile=tile, batch=batch, chunk=chunk,
-                                 stream=self.rs[k]) for k in range(2)]
-        self.hr_rgb = [torch.empty((3, S * H, S * W), dtype=torch.float32, device="cuda") for _ in range(2)]
-        self.hr_da = [torch.empty((2, S * H, S * W), dtype=torch.float32, device="cuda") for _ in range(2)]
+                                 stream=self.rs[k]) for k in range(n)]
+        self.hr_rgb = [torch.empty((3, S * H, S * W), dtype=torch.float32, device="cuda") for _ in range(n)]
+        self.hr_da = [torch.empty((2, S * H, S * W), dtype=torch.float32, device="cuda") for _ in range(n)]
         self.wctx = Context(ctx.device)  # the warps' scratch, used on the post stream only
         self.fwd = alloc_warp_outputs(S * W, S * H, S * W, S * H, 3, 0, keys=("motion", "index", "z", "planes"))
         self.bwd = alloc_warp_outputs(W, H, W, H, 3, 3)
-        self.rendered = [torch.cuda.Event() for _ in range(2)]
-        self.consumed = [torch.cuda.Event() for _ in range(2)]
-        self.used = [False, False]
+        self.rendered = [torch.cuda.Event() for _ in range(n)]
+        self.consumed = [torch.cuda.Event() for _ in range(n)]
+        self.used = [False] * n
         self.prev_cam = None
         torch.cuda.synchronize()
 
@@ -605,7 +608,7 @@ class FramePipeline:
         """Frame `cam` through the chain; `mid` is the pose between the previous frame and it.
         Asynchronous: after it, the post stream holds this frame's interpolated colour
         (hr_rgb[k]), depth and alpha (hr_da[k]) and the two warps' outputs (fwd, bwd)."""
-        k = 0 if self.prev_cam is None else 1 - self._k
+        k = 0 if self.prev_cam is None else (self._k + 1) % self.slots
         if self.used[k]:
             self.rs[k].wait_event(self.consumed[k])
         self.graphs[k].render(cam, stream=self.rs[k])
@@ -615,7 +618,7 @@ class FramePipeline:
         gai_upsample(self.weights, lr["rgb"], lr["dcdx"], lr["dcdy"], out=self.hr_rgb[k], stream=self.ps)
         gai_upsample(self.weights, self.da[k], self.zero_g, self.zero_g, out=self.hr_da[k], stream=self.ps)
         if self.prev_cam is not None:
-            j = 1 - k
+            j = self._k
             self.wctx.warp(self.prev_cam.scaled(S), mid.scaled(S), self.hr_da[j][0], self.hr_da[j][1],
                            self.HR_ALPHA_MIN, self.hr_rgb[j], out=self.fwd, stream=self.ps)
         self.wctx.warp(cam, mid, lr["depth"], lr["alpha"], 0.0, lr["rgb"], lr["dcdx"], lr["dcdy"], out=self.bwd,

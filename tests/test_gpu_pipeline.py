@@ -36,12 +36,12 @@ def env():
     return api
 
 
-def _run(api, ctx, scene, cams, weights, overlap):
+def _run(api, ctx, scene, cams, weights, overlap, slots=2):
     import torch
 
     dense = cams
     frames, mids = dense[0::2], dense[1::2]
-    pipe = api.FramePipeline(ctx, scene, frames[0], weights, capacity=200000, tile=16, overlap=overlap)
+    pipe = api.FramePipeline(ctx, scene, frames[0], weights, capacity=200000, tile=16, overlap=overlap, slots=slots)
     got = []
     for t, cam in enumerate(frames):
         mid = mids[t - 1] if t > 0 else cam
@@ -61,7 +61,8 @@ def _same(a, b):
     return np.array_equal(a, b, equal_nan=True)
 
 
-def test_overlapped_equals_serial_and_direct_calls(env):
+@pytest.mark.parametrize("slots", [2, 4])
+def test_overlapped_equals_serial_and_direct_calls(env, slots):
     import torch
 
     api = env
@@ -69,7 +70,7 @@ def test_overlapped_equals_serial_and_direct_calls(env):
     scene = api.Scene.from_arrays(synth.tiny_scene(4096, 0))
     weights = synth.gai_weights(4, 32)
     cams = _orbit(13)
-    over, frames, mids = _run(api, ctx, scene, cams, weights, True)
+    over, frames, mids = _run(api, ctx, scene, cams, weights, True, slots)
     serial, _, _ = _run(api, ctx, scene, cams, weights, False)
     assert len(over) == len(serial) == 7
     for t, (a, b) in enumerate(zip(over, serial)):
