@@ -141,7 +141,10 @@ typedef struct {
     const uint32_t *vals;         /* [K] Gaussian index of each sorted key */
     const uint32_t *ranges;       /* [n_tiles][2] [start, end) into keys */
     const uint32_t *ntiles;       /* [n] tiles touched by each Gaussian (0 = culled) */
-    const float *records;         /* [n][12] u, v, conic a, b, c, opacity, depth, r, g, b, rect, rect */
+    const float *records;         /* [n][12] u', v', conic a, b, c, opacity, depth, r, g, b, rect_lo, rect_hi:
+                                     rect_lo/hi = x | y << 16 (inclusive pixel rectangle, as bits);
+                                     (u', v') = projected centre minus the centre (x0 + 0.5, y0 + 0.5)
+                                     of the rectangle's first pixel */
     const float *final_T;         /* [H][W] (with GS_EMIT_BWD_STATE) */
     const uint32_t *n_contrib;    /* [H][W] list positions walked up to the last blended one */
 } gs_state_view;
@@ -178,7 +181,13 @@ gs_status gs_context_destroy(gs_context *ctx);
  * backward pass needs (free with gs_state_free); GS_EMIT_BWD_STATE must be set.
  * Errors: GS_ERR_INVALID_ARG (NULL scene/camera/opts/outputs, misaligned or
  * negative sizes, unsupported tile/batch/degree), GS_ERR_OOM, GS_ERR_CUDA,
- * GS_ERR_TIMEOUT (a bounded device wait gave up). */
+ * GS_ERR_TIMEOUT (a bounded device wait gave up: the sort's lookback or a
+ * compositing batch wait). The sort and compositing run after the call's one
+ * synchronisation, so their device errors are kept in the context and
+ * reported by the next call that synchronises: the next gs_render_forward
+ * (which then renders nothing and returns the error) or gs_context_check. The
+ * outputs of a frame whose wait gave up are unspecified; nothing is read or
+ * written out of bounds, and the context stays usable. */
 gs_status gs_render_forward(gs_context *ctx, const gs_scene *scene, const gs_camera *cam,
                             const gs_render_opts *opts, const gs_outputs *out, gs_fwd_state **state,
                             gs_stream stream);
@@ -201,6 +210,18 @@ gs_status gs_render_backward(gs_context *ctx, const gs_fwd_state *state, const g
                              const gs_outputs *grad_in, const gs_scene_grads *grads, gs_stream stream);
 
 gs_status gs_state_view_get(const gs_fwd_state *state, gs_state_view *view);
+/* Synchronises `stream` and returns the device error status of the plain
+ * forward frames rendered on the context since the last report (GS_OK, or
+ * GS_ERR_TIMEOUT when a bounded wait gave up), then clears it. */
+gs_status gs_context_check(gs_context *ctx, gs_stream stream);
+/* Diagnostic for testing the failure path without a stuck GPU: with
+ * give_up != 0, every bounded device wait of the context's later plain forwards
+ * gives up at once instead of after its ~4M polls (each radix-sort lookback
+ * before its first look, each warp's first compositing batch wait before its
+ * first poll; a warp that gave up still waits, with the normal bound, for the
+ * copies it has in flight). Those frames report GS_ERR_TIMEOUT through
+ * gs_context_check; 0 restores the normal bound. */
+gs_status gs_context_debug_waits(gs_context *ctx, int32_t give_up);
 /* Synchronises `stream` and returns the context's frame statistics (plain
  * forward calls); `reset` != 0 clears them afterwards. */
 gs_status gs_context_stats(gs_context *ctx, gs_stream stream, int reset, gs_frame_stats *stats);
@@ -259,8 +280,9 @@ gs_status gs_server_destroy(gs_server *srv);
 
 /* ---------------------------------------------------------------- sorting without allocation
  * No counterpart in the paper: an entry point for callers that cannot call
- * cudaMalloc (code inside a CUDA-graph capture, under a framework whose memory
- * pool owns the device, or in a loop that must not allocate after start-up).
+ * cudaMalloc -- a host framework whose caching allocator owns all of the
+ * device's memory, or a real-time loop that must not allocate after start-up
+ * (cudaMalloc can synchronise the device and take milliseconds).
  * Stable LSD radix sort of n (key, value) pairs by the low `bits` bits of the
  * key -- the same onesweep kernels that sort the render's (tile, depth) keys.
  * keys_in/vals_in (device, read only) are sorted into keys_out/vals_out
@@ -269,13 +291,14 @@ gs_status gs_server_destroy(gs_server *srv);
  * Scratch comes from one static device array of about 14 MB that the library
  * image holds on every GPU it is loaded on, until the process exits; n is at
  * most 1,048,576 (GS_ERR_INVALID_ARG beyond). It allocates nothing: the first
- * call on a device looks up the array's device address once (so make that
- * first call before any stream capture). Every call reuses the same array:
+ * call on a device looks up the array's device address once, so make that
+ * first call before any stream capture. Every call reuses the same array:
  * calls whose work overlaps on the GPU race and must be ordered by the caller.
- * A bounded lookback wait that gives up leaves the output unsorted without
- * returning an error from this asynchronous call. */
+ * status (nullable, device, 4-byte aligned): receives, in stream order, the
+ * call's device error bits -- 0, or nonzero when a bounded lookback wait gave
+ * up and the output is not sorted (the sort never waits without bound). */
 gs_status gs_sort_pairs_static(const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out,
-                               uint32_t *vals_out, int64_t n, int32_t bits, gs_stream stream);
+                               uint32_t *vals_out, int64_t n, int32_t bits, uint32_t *status, gs_stream stream);
 
 /* ---------------------------------------------------------------- frame-interpolation warp
  * The geometric half of the paper's frame interpolation (Sec. 4.2, "Forward-

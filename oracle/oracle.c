@@ -152,62 +152,50 @@ static void disc_project(const or_scene *sc, const or_camera *cam, int64_t i, or
     /* D3: scales */
     float s[3];
     for (int k = 0; k < 3; ++k) s[k] = or_spec_exp((float)sc->log_scales[k * S + i]);
-    /* D4: quaternion normalisation */
+    /* D4: the quaternion's squared norm and f = 2 / |q|^2, so that R(q / |q|) is formed
+     * from the unnormalised components with one division */
     float qw = (float)sc->quats[i], qx = (float)sc->quats[S + i], qy = (float)sc->quats[2 * S + i],
           qz = (float)sc->quats[3 * S + i];
-    float qn = sqrtf(((qw * qw + qx * qx) + qy * qy) + qz * qz);
-    if (!(qn > 0.0f)) return;
-    float w = qw / qn, x = qx / qn, y = qy / qn, z = qz / qn;
-    /* D5: rotation matrix */
+    float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
+    if (!(n2 > 0.0f)) return;
+    float f = 2.0f / n2;
+    /* D5: rotation matrix R(q / |q|) = I + f [...] */
     float R[9];
-    R[0] = 1.0f - 2.0f * (y * y + z * z);
-    R[1] = 2.0f * (x * y - w * z);
-    R[2] = 2.0f * (x * z + w * y);
-    R[3] = 2.0f * (x * y + w * z);
-    R[4] = 1.0f - 2.0f * (x * x + z * z);
-    R[5] = 2.0f * (y * z - w * x);
-    R[6] = 2.0f * (x * z - w * y);
-    R[7] = 2.0f * (y * z + w * x);
-    R[8] = 1.0f - 2.0f * (x * x + y * y);
-    /* D6: M = R diag(s) */
+    R[0] = 1.0f - f * (qy * qy + qz * qz);
+    R[1] = f * (qx * qy - qw * qz);
+    R[2] = f * (qx * qz + qw * qy);
+    R[3] = f * (qx * qy + qw * qz);
+    R[4] = 1.0f - f * (qx * qx + qz * qz);
+    R[5] = f * (qy * qz - qw * qx);
+    R[6] = f * (qx * qz - qw * qy);
+    R[7] = f * (qy * qz + qw * qx);
+    R[8] = 1.0f - f * (qx * qx + qy * qy);
+    /* D6: M = R diag(s), so Sigma = M M^T */
     float M[9];
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) M[3 * r + c] = R[3 * r + c] * s[c];
-    /* D7: Sigma = M M^T (symmetric, 6 entries) */
-    float Sg[9];
+    /* D7: V = W M (the camera rotation applied to M's columns) */
+    float V[9];
     for (int r = 0; r < 3; ++r)
-        for (int c = r; c < 3; ++c) {
-            float v = (M[3 * r] * M[3 * c] + M[3 * r + 1] * M[3 * c + 1]) + M[3 * r + 2] * M[3 * c + 2];
-            Sg[3 * r + c] = v;
-            Sg[3 * c + r] = v;
-        }
-    /* D8: guard clamp of x/z, y/z */
+        for (int c = 0; c < 3; ++c) V[3 * r + c] = (vm[4 * r] * M[c] + vm[4 * r + 1] * M[3 + c]) + vm[4 * r + 2] * M[6 + c];
+    /* D8: one reciprocal of the depth; x/z, y/z, clamped to the guard for the Jacobian */
+    float rz = 1.0f / tz;
+    float xz = tx * rz, yz = ty * rz;
     float limx = 1.29999995f * ((0.5f * (float)cam->width) / fx);
     float limy = 1.29999995f * ((0.5f * (float)cam->height) / fy);
-    float txtz = tx / tz, tytz = ty / tz;
-    float txc = fminf(limx, fmaxf(-limx, txtz)) * tz;
-    float tyc = fminf(limy, fmaxf(-limy, tytz)) * tz;
-    /* D9: Jacobian */
-    float tz2 = tz * tz;
-    float J00 = fx / tz, J02 = -((fx * txc) / tz2);
-    float J11 = fy / tz, J12 = -((fy * tyc) / tz2);
-    /* D10: T3 = J W (2x3) */
-    float T3[6];
+    float xc = fminf(limx, fmaxf(-limx, xz)), yc = fminf(limy, fmaxf(-limy, yz));
+    /* D9: N = J V with J = [[fx/z, 0, -fx x'/z], [0, fy/z, -fy y'/z]] (x', y' the clamped x/z,
+     * y/z), row by row: N0 = (fx/z) (V0 - x' V2), N1 = (fy/z) (V1 - y' V2) */
+    float ax = fx * rz, ay = fy * rz;
+    float N[6];
     for (int k = 0; k < 3; ++k) {
-        T3[k] = J00 * vm[k] + J02 * vm[8 + k];
-        T3[3 + k] = J11 * vm[4 + k] + J12 * vm[8 + k];
+        N[k] = ax * (V[k] - xc * V[6 + k]);
+        N[3 + k] = ay * (V[3 + k] - yc * V[6 + k]);
     }
-    /* D11: U = T3 Sigma, then Sigma2D = U T3^T + 0.3 I */
-    float U[6];
-    for (int r = 0; r < 2; ++r)
-        for (int k = 0; k < 3; ++k)
-            U[3 * r + k] = (T3[3 * r] * Sg[k] + T3[3 * r + 1] * Sg[3 + k]) + T3[3 * r + 2] * Sg[6 + k];
-    float A = ((U[0] * T3[0] + U[1] * T3[1]) + U[2] * T3[2]) + 3.00000012e-01f;
-    float B = ((U[0] * T3[3] + U[1] * T3[4]) + U[2] * T3[5]);
-    float C = ((U[3] * T3[3] + U[4] * T3[4]) + U[5] * T3[5]) + 3.00000012e-01f;
-    /* D12 */
-    float det = A * C - B * B;
-    if (!(det > 0.0f)) return;
+    /* D10: the diagonal of Sigma2D = N N^T + 0.3 I */
+    float A = ((N[0] * N[0] + N[1] * N[1]) + N[2] * N[2]) + 3.00000012e-01f;
+    float C = ((N[3] * N[3] + N[4] * N[4]) + N[5] * N[5]) + 3.00000012e-01f;
+    /* D11: (Sigma2D's determinant is |N0 x N1|^2 + 0.3 (|N0|^2 + |N1|^2) + 0.09 > 0: no cull) */
     /* D13: opacity and the alpha-cut level */
     float o = 1.0f / (1.0f + or_spec_exp(-(float)sc->logits[i]));
     if (!(255.0f * o >= 1.0f)) return;
@@ -215,8 +203,8 @@ static void disc_project(const or_scene *sc, const or_camera *cam, int64_t i, or
     /* D14: half-extents of the ellipse's bounding box */
     float ex = sqrtf(kk * A), ey = sqrtf(kk * C);
     /* D15: projected centre */
-    float u = ((fx * tx) / tz) + cx;
-    float v = ((fy * ty) / tz) + cy;
+    float u = fx * xz + cx;
+    float v = fy * yz + cy;
     /* D16: pixel rectangle */
     float xlo = (u - ex) - 0.5f, xhi = (u + ex) - 0.5f;
     float ylo = (v - ey) - 0.5f, yhi = (v + ey) - 0.5f;
@@ -450,13 +438,20 @@ typedef struct {
     double rgb[3], gx[3], gy[3], depth, alpha, T, Tx, Ty;
     double normal[3];  /* sum of n_i a_i T_i (camera space) */
     int32_t nrm_amb;   /* a blended Gaussian's normal orientation is open (or_cont.nrm_amb) */
-    double gx_abs[3], gy_abs[3]; /* sum of |terms| of Eq. 3 (incl. the bg term): the scale of dI/dx, dI/dy */
+    double gx_abs[3], gy_abs[3]; /* the scale of an fp32 evaluation's error of dI/dx, dI/dy (below) */
     int32_t n_blended;
     uint32_t sig;
-    int32_t amb; /* a discrete decision (cap, cut, stop) lies within 1e-5 relative of its threshold */
+    int32_t amb; /* a discrete decision (cap, cut, stop) lies within its band (below) of its threshold */
 } or_pix;
 
-#define OR_AMB_REL 1e-5
+/* The band around a threshold inside which a decision counts as open (amb): 1e-5
+ * relative, plus, per Gaussian, u * kappa with u = 2^-24 and kappa = max|conic| * |d|^2.
+ * kappa bounds how much a one-ulp perturbation of the footprint's shape or direction
+ * moves Q at this pixel, relative to u: about Q for a round footprint, far more for a
+ * long thin one seen far along its long axis, whose alpha an fp32 evaluation from the
+ * same fp32 inputs can only get to ~1e-4 of itself there. */
+#define OR_AMB_REL 3e-5
+#define OR_U32 5.9604644775390625e-08
 
 /* Eq. 2-4 for one pixel over the depth-ordered candidate list. */
 static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, int px, int py,
@@ -474,12 +469,14 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
         double dx = X - g->u, dy = Yp - g->v;
         double Q = g->ca * dx * dx + 2.0 * g->cb * dx * dy + g->cc * dy * dy;
         double a = g->o * exp(-0.5 * Q);
-        if (fabs(a - OR_ALPHA_CAP) <= OR_AMB_REL * OR_ALPHA_CAP || fabs(a - OR_ALPHA_MIN) <= OR_AMB_REL * OR_ALPHA_MIN)
+        const double cmax = fmax(fabs(g->ca), fmax(fabs(g->cb), fabs(g->cc)));
+        const double band = OR_AMB_REL + OR_U32 * cmax * (dx * dx + dy * dy);
+        if (fabs(a - OR_ALPHA_CAP) <= band * OR_ALPHA_CAP || fabs(a - OR_ALPHA_MIN) <= band * OR_ALPHA_MIN)
             amb = 1;
         int capped = 0;
         if (a > OR_ALPHA_CAP) { a = OR_ALPHA_CAP; capped = 1; }
         if (a < OR_ALPHA_MIN) continue;
-        if (fabs(T * (1.0 - a) - OR_T_MIN) <= OR_AMB_REL * OR_T_MIN) amb = 1;
+        if (fabs(T * (1.0 - a) - OR_T_MIN) <= band * OR_T_MIN) amb = 1;
         if (T * (1.0 - a) < OR_T_MIN) { sig = (sig ^ 0xA5A5A5A5u) * 16777619u; break; }
         double ax = capped ? 0.0 : -a * (g->ca * dx + g->cb * dy);
         double ay = capped ? 0.0 : -a * (g->cb * dx + g->cc * dy);
@@ -489,12 +486,19 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
             s->dx = dx; s->dy = dy; s->capped = capped;
         }
         ++nt;
+        /* Error scale of the x and y terms (a tolerance, not part of the render): the
+         * magnitudes of their operands -- c T_x a and c T a (|a' dx| + |b' dy|), the
+         * products inside (conic d) included -- each weighted by 1 + u kappa / 2e-4,
+         * the conditioning of alpha at this pixel (kappa as in the decision band). */
+        const double wk = 1.0 + OR_U32 * cmax * (dx * dx + dy * dy) / 2e-4;
+        const double mx = capped ? 0.0 : a * (fabs(g->ca * dx) + fabs(g->cb * dy));
+        const double my = capped ? 0.0 : a * (fabs(g->cb * dx) + fabs(g->cc * dy));
         for (int c = 0; c < 3; ++c) {
             C[c] += g->rgb[c] * a * T;                 /* Eq. 2 */
             Cx[c] += g->rgb[c] * (Tx * a + T * ax);    /* Eq. 3 */
             Cy[c] += g->rgb[c] * (Ty * a + T * ay);
-            Ax[c] += fabs(g->rgb[c] * Tx * a) + fabs(g->rgb[c] * T * ax);
-            Ay[c] += fabs(g->rgb[c] * Ty * a) + fabs(g->rgb[c] * T * ay);
+            Ax[c] += fabs(g->rgb[c]) * (fabs(Tx) * a + T * mx) * wk;
+            Ay[c] += fabs(g->rgb[c]) * (fabs(Ty) * a + T * my) * wk;
         }
         D += g->z * a * T;
         for (int c = 0; c < 3; ++c) N[c] += g->nrm[c] * a * T;  /* blended like the colour */

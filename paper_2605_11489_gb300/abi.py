@@ -33,7 +33,8 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_NOT_READY", -1: "GS_ERR_INVALID_ARG", -2: "GS
 # every entry point declared in include/gsr.h
 ENTRY_POINTS = (
     "gs_context_create", "gs_context_destroy", "gs_render_forward", "gs_render_forward_to_host",
-    "gs_render_backward", "gs_state_view_get", "gs_context_stats", "gs_state_free", "gs_graph_create",
+    "gs_render_backward", "gs_state_view_get", "gs_context_stats", "gs_context_check", "gs_context_debug_waits",
+    "gs_state_free", "gs_graph_create",
     "gs_graph_render", "gs_graph_check", "gs_graph_stats", "gs_graph_destroy", "gs_autotune", "gs_server_create", "gs_server_load_scene",
     "gs_server_submit", "gs_server_poll", "gs_server_cancel", "gs_server_drain", "gs_server_destroy",
     "gs_sort_pairs_static", "gs_warp", "gs_gai_upsample", "gs_last_error", "gs_version",
@@ -124,6 +125,8 @@ def _declare(L):
         "gs_graph_destroy": [P],
         "gs_graph_stats": [P, P, C.c_int, C.POINTER(GsFrameStats)],
         "gs_context_stats": [P, P, C.c_int, C.POINTER(GsFrameStats)],
+        "gs_context_check": [P, P],
+        "gs_context_debug_waits": [P, I32],
         "gs_autotune": [P, C.POINTER(GsScene), C.POINTER(GsCamera), C.POINTER(GsOutputs), C.c_int, P,
                         C.POINTER(I32), C.POINTER(I32), C.POINTER(I32), C.POINTER(C.c_float)],
         "gs_server_create": [C.c_int, C.c_size_t, C.c_int, C.POINTER(P)],
@@ -134,7 +137,7 @@ def _declare(L):
         "gs_server_cancel": [P, U64],
         "gs_server_drain": [P],
         "gs_server_destroy": [P],
-        "gs_sort_pairs_static": [P, P, P, P, I64, I32, P],
+        "gs_sort_pairs_static": [P, P, P, P, I64, I32, P, P],
         "gs_warp": [P, C.POINTER(GsCamera), C.POINTER(GsCamera), C.POINTER(GsWarpInput), C.POINTER(GsWarpOutput),
                     P],
         "gs_gai_upsample": [C.POINTER(GsGaiWeights), P, P, P, I32, I32, I32, P, P],

@@ -287,6 +287,16 @@ class Context:
         check(abi.lib().gs_context_stats(self.h, _stream_ptr(stream), int(reset), C.byref(st)))
         return _stats_dict(st)
 
+    def check(self, stream=None) -> int:
+        """Device error status of the plain frames since the last report (gs_context_check):
+        returns the status code (0 = GS_OK) without raising."""
+        return abi.lib().gs_context_check(self.h, _stream_ptr(stream))
+
+    def debug_waits(self, give_up: bool) -> None:
+        """Diagnostic (gs_context_debug_waits): make every bounded device wait of the later
+        plain forwards give up at once, to exercise the GS_ERR_TIMEOUT path."""
+        check(abi.lib().gs_context_debug_waits(self.h, 1 if give_up else 0))
+
     def graph(self, scene: Scene, cam, out: dict, capacity=0, tile=0, batch=0, bg=(0.0, 0.0, 0.0), timed=False,
               stream=None, chunk=0, head=0):
         return Graph(self, scene, cam, out, capacity, tile, batch, bg, stream, timed, chunk, head)

@@ -83,6 +83,8 @@ __global__ void __launch_bounds__(32) k_composite_bwd(const BackwardArgs a)
         rx = a.final_Tx[p] / T;
         ry = a.final_Ty[p] / T;
         last = a.n_contrib[p];
+        // never past the tile's list (a frame whose waits gave up leaves n_contrib unspecified)
+        last = min(last, range.y > range.x ? range.y - range.x : 0u);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (a.g_rgb) gr[c] = a.g_rgb[c * HW + p];
@@ -96,16 +98,18 @@ __global__ void __launch_bounds__(32) k_composite_bwd(const BackwardArgs a)
         if (a.g_alpha) Tb -= a.g_alpha[p];
     }
     const uint32_t n_walk = __reduce_max_sync(0xffffffffu, last);
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const float pxb = pixel_bias(px), pyb = pixel_bias(py);
 
     for (int64_t end = (int64_t)n_walk; end > 0; end -= kBwdBatch) {
         const int64_t beg = end - kBwdBatch > 0 ? end - kBwdBatch : 0;
         const int cnt = (int)(end - beg);
         __syncwarp();
-        for (int t = lane; t < cnt; t += 32) {  // contiguous records when the sorted copy is there
+        for (int t = lane; t < cnt; t += 32) {  // the tile's contiguous sorted records
             const uint32_t idx = a.vals[range.x + beg + t];
             s_idx[t] = idx;
-            s_rec[t] = a.rec_sorted ? a.rec_sorted[range.x + beg + t] : a.rec[idx];
+            GaussRec r = a.rec_sorted[range.x + beg + t];
+            if (idx >= a.n) r.r2.z = r.r2.w = __uint_as_float(0xFFFFFFFFu);  // no pixel: never blended
+            s_rec[t] = r;
         }
         __syncwarp();
         for (int k = cnt - 1; k >= 0; --k) {
@@ -115,7 +119,7 @@ __global__ void __launch_bounds__(32) k_composite_bwd(const BackwardArgs a)
             if (pos < last) {
                 const float4 r0 = s_rec[k].r0, r1 = s_rec[k].r1, r2 = s_rec[k].r2;
                 if (rect_contains(r2, (uint32_t)px, (uint32_t)py)) {
-                    const AlphaEval e = eval_alpha(r0, r1, pxc, pyc);
+                    const AlphaEval e = eval_alpha(r0, r1, r2, pxb, pyb);
                     if (e.al >= kAlphaMin) {
                         contrib = true;
                         const float al = e.al, om = 1.0f - al;

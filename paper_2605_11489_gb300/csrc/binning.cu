@@ -16,6 +16,8 @@
 //   K5  per-tile ranges, with the records gathered into sorted order.
 // Equal (tile, depth) keep index order because K3a emits in index order and
 // both sorts are stable.
+#include <algorithm>
+
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -159,18 +161,22 @@ __global__ void __launch_bounds__(kProjThreads) k_compact(const uint32_t *__rest
 
 // K3b, first half: per 1,024 depth-sorted Gaussians (256 threads x 4), the
 // sum of their tile counts.
+// An index >= n (only possible when the depth sort gave up and left its output
+// unsorted, holes included) counts as a Gaussian with no tiles.
 __global__ void __launch_bounds__(kProjThreads) k_sorted_counts(const uint32_t *__restrict__ dvals,
                                                                 const uint32_t *__restrict__ vcount,
                                                                 const uint32_t *__restrict__ ntiles,
-                                                                uint32_t *__restrict__ sums)
+                                                                uint32_t *__restrict__ sums, uint32_t n)
 {
     __shared__ uint32_t s_warp[kProjThreads / 32];
     const uint32_t V = *vcount;
     const uint32_t i0 = (blockIdx.x * kProjThreads + threadIdx.x) * 4;
     uint32_t mine = 0;
 #pragma unroll
-    for (int g = 0; g < 4; ++g)
-        if (i0 + g < V) mine += ntiles[dvals[i0 + g]];
+    for (int g = 0; g < 4; ++g) {
+        const uint32_t idx = i0 + g < V ? dvals[i0 + g] : n;
+        if (idx < n) mine += ntiles[idx];
+    }
     uint32_t total;
     block_excl(mine, s_warp, total);
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
@@ -191,7 +197,8 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
                                                             const uint32_t *__restrict__ block_offs, int tile_shift,
                                                             int tiles_x, uint32_t *__restrict__ keys,
                                                             uint32_t *__restrict__ vals, unsigned long long capacity,
-                                                            uint32_t *counters, uint32_t *__restrict__ hist, int passes)
+                                                            uint32_t *counters, uint32_t *__restrict__ hist, int passes,
+                                                            uint32_t n)
 {
     constexpr int kWarps = kProjThreads / 32, kPerWarp = 128;
     __shared__ uint32_t s_warp[kWarps];
@@ -207,8 +214,9 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
     uint32_t cnt[4], mine = 0;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        const uint32_t idx = i0 + g < V ? dvals[i0 + g] : 0u;
-        cnt[g] = i0 + g < V ? ntiles[idx] : 0u;
+        uint32_t idx = i0 + g < V ? dvals[i0 + g] : 0u;
+        if (idx >= n) idx = 0u;  // (an unsorted depth order, see k_sorted_counts): no tiles
+        cnt[g] = i0 + g < V && dvals[i0 + g] < n ? ntiles[idx] : 0u;
         uint32_t org = 0, wid = 1;
         if (cnt[g]) {
             const uint4 b = bin[idx];
@@ -279,8 +287,12 @@ __global__ void __launch_bounds__(kRangeThreads)
     k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
              const uint32_t *__restrict__ counters, const GaussRec *__restrict__ rec,
              GaussRec *__restrict__ rec_sorted, uint2 *ranges, const uint4 *__restrict__ bin,
-             uint64_t *__restrict__ keys64, const float4 *__restrict__ nrm, float4 *__restrict__ nrm_sorted)
+             uint64_t *__restrict__ keys64, const float4 *__restrict__ nrm, float4 *__restrict__ nrm_sorted,
+             uint32_t n, uint32_t n_tiles)
 {
+    // Indices and tile ids are checked against n and n_tiles: after a sort that gave up
+    // (kErrSortTimeout) the keys are not sorted and may hold stale words, and the frame is
+    // reported as failed, but nothing is read or written out of bounds.
     const uint32_t K = counters[kCntEff];
     const uint32_t P = 3u * K;  // 16-byte pieces (K < 2^30)
     const uint32_t e0 = blockIdx.x * (kRangeThreads * kRangePer) + threadIdx.x;
@@ -292,6 +304,7 @@ __global__ void __launch_bounds__(kRangeThreads)
     for (int k = 0; k < kRangePer; ++k) {
         const uint32_t e = e0 + (uint32_t)k * kRangeThreads;
         g[k] = e < P ? vals[e / 3u] : 0u;
+        if (g[k] >= n) g[k] = 0u;
     }
     if (rec_sorted) {
 #pragma unroll
@@ -311,8 +324,10 @@ __global__ void __launch_bounds__(kRangeThreads)
         if (e >= P || e % 3u != 0u) continue;
         const uint32_t i = e / 3u;
         const uint32_t t = keys[i];
-        if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-        if (i == K - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
+        if (t < n_tiles) {
+            if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
+            if (i == K - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
+        }
         if (keys64) keys64[i] = ((uint64_t)t << 32) | (uint64_t)bin[g[k]].x;
         if (nrm_sorted) nrm_sorted[i] = __ldg(nrm + g[k]);
     }
@@ -365,19 +380,32 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
 // slots, so that both come in the same order and the later chunks before a
 // tile's own number slot - split index. Whole tiles are bucketed by
 // floor(log2(length)), with one atomic per bucket and warp.
+// The plan's buffers hold max_split split tiles and max_slots slots, enough for
+// ranges that partition the K sorted instances. After a sort gave up
+// (kErrSortTimeout in *err) the ranges need not partition anything, so the plan
+// is left empty; and every write is checked against the capacities anyway: a
+// plan that would not fit is left empty with kErrCapacity set. Nothing is then
+// composited and the frame reports the error.
 __global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges, int n_tiles, uint32_t chunk,
                                                uint32_t head, uint4 *__restrict__ items,
                                                uint32_t *__restrict__ split_tiles,
                                                uint32_t *__restrict__ split_slot0, uint32_t *__restrict__ slot_split,
-                                               uint32_t *__restrict__ counts)
+                                               uint32_t *__restrict__ counts, uint32_t *err, uint32_t max_split,
+                                               uint32_t max_slots)
 {
     __shared__ unsigned long long s_alloc;  // (split tiles << 32) | slots handed out so far
     __shared__ uint32_t s_bucket[33];       // whole tiles per bucket, then next free item per bucket
+    __shared__ bool s_skip;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    if (threadIdx.x == 0) s_alloc = 0ull;
+    if (threadIdx.x == 0) {
+        s_alloc = 0ull;
+        s_skip = (*reinterpret_cast<volatile uint32_t *>(err) & kErrSortTimeout) != 0u;
+        if (s_skip) counts[0] = counts[1] = counts[2] = counts[3] = 0u;
+    }
     if (threadIdx.x < 33) s_bucket[threadIdx.x] = 0u;
     __syncthreads();
+    if (s_skip) return;
     auto bucket_of = [](uint32_t len) { return len == 0 ? 32u : (uint32_t)__clz(len); };  // longer -> smaller
 
     // pass 1: split tiles are placed; whole tiles are counted per bucket
@@ -404,15 +432,18 @@ __global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges,
         if (split) {
             const uint32_t sp = (uint32_t)(got >> 32) + (uint32_t)__popc(smask & lt);
             const uint32_t slot = (uint32_t)(got & 0xffffffffull) + inc - c;
-            split_tiles[sp] = (uint32_t)t;
-            split_slot0[sp] = slot;
-            items[sp] = make_uint4((uint32_t)t, r.x, r.x + head, slot);  // wave A: first chunk
-            const uint32_t later = (uint32_t)n_tiles + (slot - sp);      // wave B: later chunks before ours
-            for (uint32_t k = 0; k < c; ++k) {
-                slot_split[slot + k] = sp;
-                if (k == 0) continue;
-                const uint32_t s0 = r.x + chunk_start(k, head, chunk);
-                items[later + k - 1] = make_uint4((uint32_t)t, s0, min(r.y, s0 + chunk), slot + k);
+            // written only if the whole tile fits (items hold n_tiles + max_slots entries)
+            if (sp < max_split && slot + c <= max_slots) {
+                split_tiles[sp] = (uint32_t)t;
+                split_slot0[sp] = slot;
+                items[sp] = make_uint4((uint32_t)t, r.x, r.x + head, slot);  // wave A: first chunk
+                const uint32_t later = (uint32_t)n_tiles + (slot - sp);      // wave B: later chunks before ours
+                for (uint32_t k = 0; k < c; ++k) {
+                    slot_split[slot + k] = sp;
+                    if (k == 0) continue;
+                    const uint32_t s0 = r.x + chunk_start(k, head, chunk);
+                    items[later + k - 1] = make_uint4((uint32_t)t, s0, min(r.y, s0 + chunk), slot + k);
+                }
             }
         }
         const uint32_t b = whole ? bucket_of(len) : 64u;
@@ -420,6 +451,13 @@ __global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges,
         if (whole && lane == __ffs(peers) - 1) atomicAdd(&s_bucket[b], (uint32_t)__popc(peers));
     }
     __syncthreads();
+    if ((uint32_t)(s_alloc >> 32) > max_split || (uint32_t)(s_alloc & 0xffffffffull) > max_slots) {
+        if (threadIdx.x == 0) {  // does not fit: nothing is composited, the frame reports it
+            counts[0] = counts[1] = counts[2] = counts[3] = 0u;
+            atomicOr(err, kErrCapacity);
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
         const uint32_t n_split = (uint32_t)(s_alloc >> 32), n_slots = (uint32_t)(s_alloc & 0xffffffffull);
         uint32_t run = n_split;  // whole tiles follow the first chunks
@@ -458,11 +496,13 @@ int64_t plan_max_slots(int64_t max_k, int chunk) { return 3 * (max_k / chunk) + 
 int64_t plan_max_items(int n_tiles, int64_t max_k, int chunk) { return n_tiles + plan_max_slots(max_k, chunk); }
 
 cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, int head, uint4 *items, uint32_t *split_tiles,
-                        uint32_t *split_slot0, uint32_t *slot_split, uint32_t *counts, cudaStream_t s)
+                        uint32_t *split_slot0, uint32_t *slot_split, uint32_t *counts, uint32_t *err,
+                        int64_t max_split, int64_t max_slots, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 4, s);
     k_plan<<<1, 1024, 0, s>>>(ranges, n_tiles, (uint32_t)chunk, (uint32_t)head, items, split_tiles, split_slot0,
-                              slot_split, counts);
+                              slot_split, counts, err, (uint32_t)std::min<int64_t>(max_split, 0xFFFFFFFFll),
+                              (uint32_t)std::min<int64_t>(max_slots, 0xFFFFFFFFll));
     return cudaGetLastError();
 }
 
@@ -503,18 +543,18 @@ cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int6
     if (e != cudaSuccess) return e;
     const int nb = project_blocks(max_v);
     if (nb == 0) return cudaSuccess;
-    k_sorted_counts<<<nb, kProjThreads, 0, s>>>(dvals, vcount, ntiles, bsums);
+    k_sorted_counts<<<nb, kProjThreads, 0, s>>>(dvals, vcount, ntiles, bsums, (uint32_t)max_v);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_scan_plain<<<1, kScanThreads, 0, s>>>(bsums, nb, boffs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_duplicate<<<nb, kProjThreads, 0, s>>>(dvals, vcount, ntiles, bin, boffs, tile_shift, tiles_x, keys, vals,
-                                            (unsigned long long)capacity, counters, hist, passes);
+                                            (unsigned long long)capacity, counters, hist, passes, (uint32_t)max_v);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
-                          const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, const uint4 *bin,
-                          uint64_t *keys64, cudaStream_t s, const float4 *nrm, float4 *nrm_sorted)
+                          int64_t n, const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles,
+                          const uint4 *bin, uint64_t *keys64, cudaStream_t s, const float4 *nrm, float4 *nrm_sorted)
 {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess) return e;
@@ -522,7 +562,8 @@ cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint
     const int64_t per_block = (int64_t)kRangeThreads * kRangePer;
     const int64_t nb = (3 * max_k + per_block - 1) / per_block;
     k_ranges<<<(unsigned)nb, kRangeThreads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges, bin, keys64,
-                                                    nrm, nrm_sorted);
+                                                    nrm, nrm_sorted, (uint32_t)std::max<int64_t>(n, 1),
+                                                    (uint32_t)n_tiles);
     return cudaGetLastError();
 }
 

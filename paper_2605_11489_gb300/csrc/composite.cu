@@ -102,11 +102,11 @@ __device__ __forceinline__ void tile_pixel(int tid, int tile_x, int tile_y, int 
 // One Gaussian record at one pixel (Eq. 2-4). Returns true when the pixel
 // stops (the record would take T below 1e-4; it is not blended).
 template <bool GRAD, bool STATE, bool COUNT = false, bool NRM = false>
-__device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float4 &r1, const float4 &r2, float pxc,
-                                      float pyc, uint32_t pos, const float4 *nrm = nullptr)
+__device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float4 &r1, const float4 &r2, float pxb,
+                                      float pyb, uint32_t pos, const float4 *nrm = nullptr)
 {
     if (COUNT) ++s.n_eval;
-    const AlphaEval e = eval_alpha(r0, r1, pxc, pyc);
+    const AlphaEval e = eval_alpha(r0, r1, r2, pxb, pyb);
     const float al = e.al;
     if (al < kAlphaMin) return false;
     const float om = __fsub_rn(1.0f, al);
@@ -201,20 +201,21 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
         }
     };
 
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const float pxb = pixel_bias(px), pyb = pixel_bias(py);
     bool ok = true;
 
     for (int b = 0; b < kStages - 1 && b < nbatches; ++b) issue(b);
     int b = 0;
+    const uint32_t first_tries = a.give_up ? 0u : kWaitTries;
     for (; b < nbatches; ++b) {
         const int buf = b % kStages;
         if (b + kStages - 1 < nbatches) issue(b + kStages - 1);
-        if (!mbar_wait_bounded(&ring.bar[buf], phase[buf], kWaitTries)) ok = false;
-        phase[buf] ^= 1u;
-        if (!__all_sync(0xffffffffu, ok)) {
-            ++b;
+        if (!mbar_wait_bounded(&ring.bar[buf], phase[buf], first_tries)) ok = false;
+        if (!__all_sync(0xffffffffu, ok)) {  // batch b is still in flight: drained below
+            ok = false;                      // (the same on every lane, so the drain is too)
             break;
         }
+        phase[buf] ^= 1u;
         const uint32_t cnt = min((uint32_t)BATCH, s1 - (s0 + (uint32_t)b * BATCH));
         const GaussRec *recs = ring.rec[buf];
         const uint32_t pos_b = pos0 + (uint32_t)b * BATCH + 1u;
@@ -251,7 +252,7 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
                     mine &= mine - 1u;
                     const float4 b0 = recs[kn].r0, b1 = recs[kn].r1, b2 = recs[kn].r2;
                     if (blend<GRAD, STATE, COUNT, NRM>(
-                            s, a0, a1, a2, pxc, pyc, pos_b + k,
+                            s, a0, a1, a2, pxb, pyb, pos_b + k,
                             NRM ? a.nrm_sorted + (s0 + (uint32_t)b * BATCH + k) : nullptr)) {
                         s.done = true;
                         s.stopped = true;
@@ -270,8 +271,12 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
             break;
         }
     }
-    // batches issued ahead of an early exit must land before their slots are reused or the CTA exits
-    for (int q = b; q < nbatches && q < b + kStages - 1; ++q) {
+    // Batches issued ahead of an early exit must land before their slots are reused or the
+    // CTA exits: after a warp finishes batch b - 1 early, batches b .. b + kStages - 2 are in
+    // flight; after a wait on batch b gives up, batches b .. b + kStages - 1 are (b's own copy
+    // included). Each is waited for with the full bound.
+    const int in_flight_end = ok ? b + kStages - 1 : b + kStages;
+    for (int q = b; q < nbatches && q < in_flight_end; ++q) {
         if (!mbar_wait_bounded(&ring.bar[q % kStages], phase[q % kStages], kWaitTries)) ok = false;
         phase[q % kStages] ^= 1u;
     }

@@ -24,7 +24,6 @@ enum : uint32_t {
     kErrSortTimeout = 1u,       // radix-sort lookback gave up waiting
     kErrTmaTimeout = 2u,        // compositing waited too long for a staged batch
     kErrCapacity = 4u,          // instance list exceeded the buffers' capacity
-    kErrQueueTimeout = 8u,      // serving work list wait gave up
 };
 
 // ---------------------------------------------------------------- device-side camera
@@ -32,6 +31,7 @@ struct CamParams {
     float vm[12];      // world -> camera [R | t], row-major
     float fx, fy, cx, cy;
     float near_plane;
+    float limx, limy;  // guard of the EWA Jacobian: x/z and y/z clamped to 1.3x the half field of view
     float campos[3];   // camera centre in world space, -R^T t
     int32_t width, height;
     int32_t tile_shift;  // log2(tile)
@@ -40,9 +40,15 @@ struct CamParams {
 
 // Per-Gaussian compositing record, 48 bytes (3 x float4), written by the
 // projection kernel for visible Gaussians and gathered by compositing:
-//   r0 = (u, v, conic_a, conic_b)       projected centre, conic (Sigma2D^-1)
+//   r0 = (u', v', conic_a, conic_b)     projected centre, conic (Sigma2D^-1)
 //   r1 = (conic_c, opacity, depth, red)
 //   r2 = (green, blue, rect_lo, rect_hi)   rect as bits: x | y << 16 (inclusive)
+// (u', v') is the centre relative to the centre of the rectangle's first pixel (x0, y0):
+// u' = u - (x0 + 0.5), computed in float-float and rounded once. A pixel's offset
+// d = (px + 0.5) - u is then (px - x0) - u', where px - x0 is an exact small integer, so d
+// carries the rounding of u' (~1e-7 of the footprint) instead of that of the absolute
+// coordinate u (up to ~1e-4 px at 1,000 px). The record, and so the arithmetic of every
+// pixel, is the same whatever the tile size: the image does not depend on it, bit for bit.
 struct __align__(16) GaussRec {
     float4 r0, r1, r2;
 };
@@ -81,6 +87,8 @@ CamParams make_cam(const gs_camera &c, int tile);
 gs_status check_scene(const gs_scene *s);
 gs_status check_cam(const gs_camera *c);
 int ilog2(int v);
+// device error bits (counters[kCntErr]) -> the status they stand for (GS_OK for none)
+gs_status err_status(uint32_t err);
 
 // ---------------------------------------------------------------- launchers
 struct ProjectArgs {
@@ -122,8 +130,8 @@ cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int6
 // K5: per-tile [start, end) from the sorted tile keys, the records gathered into
 // sorted order, and (keys64 != NULL) each instance's (tile << 32 | depth bits)
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
-                          const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles, const uint4 *bin,
-                          uint64_t *keys64, cudaStream_t s, const float4 *nrm = nullptr,
+                          int64_t n, const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles,
+                          const uint4 *bin, uint64_t *keys64, cudaStream_t s, const float4 *nrm = nullptr,
                           float4 *nrm_sorted = nullptr);
 
 // onesweep LSD radix sort of (keys, vals) on the low `bits` bits, K from counters[kCntEff]
@@ -138,14 +146,15 @@ void sort_scratch_carve(void *base, int64_t capacity, SortScratch *s);
 int sort_passes(int bits);
 // Sorts keys[0]/vals[0] into the buffer pair returned in *result (0 or 1).
 // hist_ready: scr.hist already holds the digit histograms of the keys (built
-// by launch_duplicate), so the histogram pass is skipped.
+// by launch_duplicate), so the histogram pass is skipped. give_up: every
+// lookback gives up at once (diagnostic; sets kErrSortTimeout, output unsorted).
 cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *counters, uint32_t *err_word,
                         int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s,
-                        bool hist_ready = false);
+                        bool hist_ready = false, bool give_up = false);
 // The same over 32-bit keys; the element count is the device word *count.
 cudaError_t launch_sort32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *count, uint32_t *err_word,
                           int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s,
-                          bool hist_ready);
+                          bool hist_ready, bool give_up = false);
 
 struct CompositeArgs {
     const GaussRec *rec;  // records in sorted (instance) order: tile t's list is rec[ranges[t].x, ranges[t].y)
@@ -173,6 +182,8 @@ struct CompositeArgs {
     const float4 *nrm_sorted;      // normals in sorted (instance) order, like rec
     float *normal, *nv;
     float fx, fy, cx, cy;          // intrinsics: nv's pixel rays
+    uint32_t give_up;              // diagnostic: each warp's first batch wait gives up without polling
+                                   // (kErrTmaTimeout), then waits for its copies in flight
 };
 constexpr uint32_t kWholeTile = 0xFFFFFFFFu;
 // A tile list longer than `head` records (default kHeadChunks * chunk) is split
@@ -195,8 +206,11 @@ __host__ __device__ inline uint32_t chunk_count(uint32_t len, uint32_t head, uin
 }
 int64_t plan_max_slots(int64_t max_k, int chunk);
 int64_t plan_max_items(int n_tiles, int64_t max_k, int chunk);
+// The plan holds at most max_split split tiles and max_slots slots (frame_plan's sizes);
+// it is left empty after a sort timeout or when it would not fit (kErrCapacity in *err).
 cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, int head, uint4 *items, uint32_t *split_tiles,
-                        uint32_t *split_slot0, uint32_t *slot_split, uint32_t *counts, cudaStream_t s);
+                        uint32_t *split_slot0, uint32_t *slot_split, uint32_t *counts, uint32_t *err,
+                        int64_t max_split, int64_t max_slots, cudaStream_t s);
 // merge of split tiles' chunks (after launch_composite with a plan)
 cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, int64_t max_slots, cudaStream_t s);
 // order tiles by decreasing list length (power-of-two buckets)
@@ -222,7 +236,7 @@ int composite_persistent_grid(int tile, int batch);
 struct BackwardArgs {
     // compositing side
     const GaussRec *rec;
-    const GaussRec *rec_sorted;  // the records in sorted (instance) order, as the forward gathered them (nullable)
+    const GaussRec *rec_sorted;  // the records in sorted (instance) order, as the forward gathered them
     const uint32_t *vals;
     const uint2 *ranges;
     int32_t width, height, tiles_x, tiles_y, tile;
@@ -231,6 +245,7 @@ struct BackwardArgs {
     const uint32_t *n_contrib;
     const float *g_rgb, *g_dcdx, *g_dcdy, *g_depth, *g_alpha;
     float *g2d;  // [n][10] per-Gaussian 2D adjoints: u, v, ca, cb, cc, o, z, r, g, b
+    uint32_t n;  // Gaussians: a sorted index >= n (an unsorted list after a sort gave up) is skipped
 };
 cudaError_t launch_composite_backward(const BackwardArgs &a, cudaStream_t s);
 
@@ -322,11 +337,19 @@ struct AlphaEval {
     float g;  // exp(-Q/2), the Gaussian's falloff before the opacity scales it
     bool capped;
 };
-__device__ __forceinline__ AlphaEval eval_alpha(const float4 &r0, const float4 &r1, float pxc, float pyc)
+// (pxb, pyb) = (2^23 + px, 2^23 + py) as floats (pixel_bias); the rectangle origin comes
+// from the record's rect_lo bits as 2^23 + x0 (one byte permute), so pxb - x0b = px - x0
+// exactly and d = (px - x0) - u' (see GaussRec).
+__device__ __forceinline__ float pixel_bias(int p) { return __uint_as_float(0x4B000000u | (uint32_t)p); }
+__device__ __forceinline__ AlphaEval eval_alpha(const float4 &r0, const float4 &r1, const float4 &r2, float pxb,
+                                                float pyb)
 {
     AlphaEval e;
-    e.dx = __fsub_rn(pxc, r0.x);
-    e.dy = __fsub_rn(pyc, r0.y);
+    const uint32_t lo = __float_as_uint(r2.z);
+    const float x0b = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7610));
+    const float y0b = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7632));
+    e.dx = __fsub_rn(__fsub_rn(pxb, x0b), r0.x);
+    e.dy = __fsub_rn(__fsub_rn(pyb, y0b), r0.y);
     e.ex = __fmaf_rn(r0.z, e.dx, __fmul_rn(r0.w, e.dy));
     e.ey = __fmaf_rn(r0.w, e.dx, __fmul_rn(r1.x, e.dy));
     const float Q = __fmaf_rn(e.dx, e.ex, __fmul_rn(e.dy, e.ey));

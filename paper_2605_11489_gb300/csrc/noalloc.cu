@@ -2,12 +2,12 @@
 // pairs, for callers that may not allocate device memory.
 //
 // Who needs this: code that runs where cudaMalloc is not allowed or not
-// wanted after start-up -- inside a region being captured into a CUDA graph,
-// under a host framework whose memory pool owns the whole device, or in a
-// real-time loop that must not allocate -- still needs to sort keys. This
-// entry point takes its scratch (digit histograms, decoupled-lookback status
-// words, partition tickets and the ping-pong buffer of the passes) from one
-// file-scope __device__ array of fixed size instead of allocating it.
+// wanted after start-up -- under a host framework whose caching allocator owns
+// the whole device, or in a real-time loop that must not allocate (cudaMalloc
+// can synchronise the device and take milliseconds) -- still needs to sort
+// keys. This entry point takes its scratch (digit histograms, decoupled-lookback
+// status words, partition tickets and the ping-pong buffer of the passes) from
+// one file-scope __device__ array of fixed size instead of allocating it.
 //
 // The array is part of the library image: every GPU that loads the library
 // holds it (about 14 MB) until the process exits. Every call shares it and it
@@ -15,6 +15,8 @@
 // zero itself, and calls whose work overlaps on the GPU (different streams
 // without ordering) race on it.
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "gsr_internal.cuh"
 
@@ -43,15 +45,22 @@ __global__ void k_set_count(uint32_t *counters, uint32_t n)
     counters[kCntErr] = 0u;
 }
 
+// copies the sort's error bits (0, or kErrSortTimeout) to the caller's word
+__global__ void k_report(const uint32_t *counters, uint32_t *status) { *status = counters[kCntErr]; }
+
 // Device address of the scratch array for the current device, looked up once
 // per device (host code cannot use the symbol itself as a device pointer).
+// The library's own threads (the server's scheduler) may sort at the same time
+// as a caller's thread, so the lookup is serialised.
 cudaError_t scratch_address(unsigned char **out)
 {
     static unsigned char *addr[64] = {};
+    static std::mutex mu;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
     if (!addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_sort_scratch);
@@ -68,12 +77,18 @@ cudaError_t scratch_address(unsigned char **out)
 using namespace gsr;
 
 extern "C" gs_status gs_sort_pairs_static(const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out,
-                                          uint32_t *vals_out, int64_t n, int32_t bits, gs_stream stream)
+                                          uint32_t *vals_out, int64_t n, int32_t bits, uint32_t *status,
+                                          gs_stream stream)
 {
     if (n < 0 || n > kStaticMaxPairs)
         return fail(GS_ERR_INVALID_ARG, "gs_sort_pairs_static: n must be 0..1048576 (the static scratch's capacity)");
     if (bits < 1 || bits > 64) return fail(GS_ERR_INVALID_ARG, "gs_sort_pairs_static: bits must be 1..64");
-    if (n == 0) return GS_OK;
+    if (reinterpret_cast<uintptr_t>(status) & 3)
+        return fail(GS_ERR_INVALID_ARG, "gs_sort_pairs_static: the status word must be 4-byte aligned");
+    if (n == 0) {
+        if (status) GSR_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), (cudaStream_t)stream));
+        return GS_OK;
+    }
     if (!keys_in || !vals_in || !keys_out || !vals_out)
         return fail(GS_ERR_INVALID_ARG, "gs_sort_pairs_static: NULL buffer");
     if ((reinterpret_cast<uintptr_t>(keys_in) | reinterpret_cast<uintptr_t>(keys_out)) & 7 ||
@@ -107,5 +122,9 @@ extern "C" gs_status gs_sort_pairs_static(const uint64_t *keys_in, const uint32_
     GSR_CUDA(cudaGetLastError());
     int result = 0;
     GSR_CUDA(launch_sort(k, v, counters, counters + kCntErr, n, bits, scr, &result, st));
+    if (status) {
+        k_report<<<1, 1, 0, st>>>(counters, status);
+        GSR_CUDA(cudaGetLastError());
+    }
     return GS_OK;
 }

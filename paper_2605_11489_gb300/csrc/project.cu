@@ -77,11 +77,59 @@ __device__ float rn_log(float x)
 
 struct Proj {
     bool vis;
-    float u, v, ca, cb, cc, o, z;
+    float u, v, ca, cb, cc, o, z;  // u, v: the centre relative to the rectangle's first pixel centre
     uint32_t rlo, rhi, nt;
     float n[3];  // camera-space normal (with NRM only)
 };
 
+// Error-free transformations (Dekker, Knuth): a * b = p + e and a + b = s + e exactly.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = M(a, b);
+    e = F(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = A(a, b);
+    const float bb = S(s, a);
+    e = A(S(a, S(s, bb)), S(b, bb));
+}
+// w . m + t as an unevaluated sum hi + lo (about 44 significant bits)
+__device__ __forceinline__ void ff_affine(const float *w, float m0, float m1, float m2, float t, float &hi, float &lo)
+{
+    float p0, e0, p1, e1, p2, e2, s, q1, q2, q3;
+    two_prod(w[0], m0, p0, e0);
+    two_prod(w[1], m1, p1, e1);
+    two_prod(w[2], m2, p2, e2);
+    two_sum(p0, p1, s, q1);
+    two_sum(s, p2, s, q2);
+    two_sum(s, t, hi, q3);
+    lo = A(A(A(e0, e1), A(e2, q1)), A(q2, q3));
+}
+// f * (x / z) + c - origin, with x, z float-float and rz ~ 1/z: the projected centre
+// relative to an integer pixel origin, rounded once at the end
+__device__ __forceinline__ float ff_centre(float xh, float xl, float zh, float zl, float rz, float f, float c,
+                                           float origin)
+{
+    const float qh = M(xh, rz);
+    float p, pe;
+    two_prod(qh, zh, p, pe);
+    const float r = A(S(S(xh, p), pe), F(-qh, zl, xl));  // x - qh z
+    const float ql = M(r, rz);
+    float fp, fe, s, se;
+    two_prod(f, qh, fp, fe);
+    two_sum(fp, c, s, se);
+    return A(S(s, origin), A(se, F(f, ql, fe)));
+}
+
+// Projection of one Gaussian (Sec. 3: Sigma = R S S^T R^T, EWA Sigma2D = J W Sigma W^T J^T + 0.3 I).
+// The depth key and the support rectangle follow the fixed fp32 round-to-nearest sequence below
+// (the same as the oracle's discrete spec, step by step). The centre and the conic, which only
+// scale the compositing arithmetic, are computed for accuracy instead: the centre in float-float,
+// relative to the rectangle's first pixel, so that its error is ~1e-7 of the distance to a pixel
+// rather than of the absolute pixel coordinate; the determinant of Sigma2D = N N^T + 0.3 I as
+// |N0 x N1|^2 + 0.3 (|N0|^2 + |N1|^2) + 0.09 (Binet-Cauchy), a sum of positive terms that
+// does not cancel for elongated footprints.
 template <bool NRM = false>
 __device__ __forceinline__ void project_one(const CamParams &c, float mx, float my, float mz, float ls0, float ls1,
                                             float ls2, float qw, float qx, float qy, float qz, float logit,
@@ -90,70 +138,58 @@ __device__ __forceinline__ void project_one(const CamParams &c, float mx, float 
     P.vis = false;
     P.nt = 0;
     const float *vm = c.vm;
+    // D1, D2: camera-space position
     const float tz = A(A(A(M(vm[8], mx), M(vm[9], my)), M(vm[10], mz)), vm[11]);
     if (!(tz > c.near_plane)) return;
     const float tx = A(A(A(M(vm[0], mx), M(vm[1], my)), M(vm[2], mz)), vm[3]);
     const float ty = A(A(A(M(vm[4], mx), M(vm[5], my)), M(vm[6], mz)), vm[7]);
+    // D3: scales; D4, D5: R(q / |q|) from the unnormalised quaternion with f = 2 / |q|^2
     const float s0 = rn_exp(ls0), s1 = rn_exp(ls1), s2 = rn_exp(ls2);
-    const float qn = __fsqrt_rn(A(A(A(M(qw, qw), M(qx, qx)), M(qy, qy)), M(qz, qz)));
-    if (!(qn > 0.0f)) return;
-    const float w = D(qw, qn), x = D(qx, qn), y = D(qy, qn), z = D(qz, qn);
+    const float n2 = A(A(A(M(qw, qw), M(qx, qx)), M(qy, qy)), M(qz, qz));
+    if (!(n2 > 0.0f)) return;
+    const float f = D(2.0f, n2);
     float R[9];
-    R[0] = S(1.0f, M(2.0f, A(M(y, y), M(z, z))));
-    R[1] = M(2.0f, S(M(x, y), M(w, z)));
-    R[2] = M(2.0f, A(M(x, z), M(w, y)));
-    R[3] = M(2.0f, A(M(x, y), M(w, z)));
-    R[4] = S(1.0f, M(2.0f, A(M(x, x), M(z, z))));
-    R[5] = M(2.0f, S(M(y, z), M(w, x)));
-    R[6] = M(2.0f, S(M(x, z), M(w, y)));
-    R[7] = M(2.0f, A(M(y, z), M(w, x)));
-    R[8] = S(1.0f, M(2.0f, A(M(x, x), M(y, y))));
-    float Mx[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        Mx[3 * r + 0] = M(R[3 * r + 0], s0);
-        Mx[3 * r + 1] = M(R[3 * r + 1], s1);
-        Mx[3 * r + 2] = M(R[3 * r + 2], s2);
-    }
-    float Sg[9];
+    R[0] = S(1.0f, M(f, A(M(qy, qy), M(qz, qz))));
+    R[1] = M(f, S(M(qx, qy), M(qw, qz)));
+    R[2] = M(f, A(M(qx, qz), M(qw, qy)));
+    R[3] = M(f, A(M(qx, qy), M(qw, qz)));
+    R[4] = S(1.0f, M(f, A(M(qx, qx), M(qz, qz))));
+    R[5] = M(f, S(M(qy, qz), M(qw, qx)));
+    R[6] = M(f, S(M(qx, qz), M(qw, qy)));
+    R[7] = M(f, A(M(qy, qz), M(qw, qx)));
+    R[8] = S(1.0f, M(f, A(M(qx, qx), M(qy, qy))));
+    // D6: M = R diag(s); D7: V = W M
+    const float sc[3] = {s0, s1, s2};
+    float V[9];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int q = r; q < 3; ++q) {
-            const float v = A(A(M(Mx[3 * r], Mx[3 * q]), M(Mx[3 * r + 1], Mx[3 * q + 1])), M(Mx[3 * r + 2], Mx[3 * q + 2]));
-            Sg[3 * r + q] = v;
-            Sg[3 * q + r] = v;
-        }
-    const float limx = M(1.29999995f, D(M(0.5f, (float)c.width), c.fx));
-    const float limy = M(1.29999995f, D(M(0.5f, (float)c.height), c.fy));
-    const float txc = M(fminf(limx, fmaxf(-limx, D(tx, tz))), tz);
-    const float tyc = M(fminf(limy, fmaxf(-limy, D(ty, tz))), tz);
-    const float tz2 = M(tz, tz);
-    const float J00 = D(c.fx, tz), J02 = -D(M(c.fx, txc), tz2);
-    const float J11 = D(c.fy, tz), J12 = -D(M(c.fy, tyc), tz2);
-    float T3[6];
+        for (int k = 0; k < 3; ++k)
+            V[3 * r + k] = A(A(M(vm[4 * r], M(R[k], sc[k])), M(vm[4 * r + 1], M(R[3 + k], sc[k]))),
+                             M(vm[4 * r + 2], M(R[6 + k], sc[k])));
+    // D8: one reciprocal of the depth; the guard-clamped x/z, y/z for the Jacobian
+    const float rz = D(1.0f, tz);
+    const float xz = M(tx, rz), yz = M(ty, rz);
+    const float xc = fminf(c.limx, fmaxf(-c.limx, xz)), yc = fminf(c.limy, fmaxf(-c.limy, yz));
+    // D9: N = J V, row by row: N0 = (fx/z)(V0 - x' V2), N1 = (fy/z)(V1 - y' V2)
+    const float ax = M(c.fx, rz), ay = M(c.fy, rz);
+    float N[6];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        T3[k] = A(M(J00, vm[k]), M(J02, vm[8 + k]));
-        T3[3 + k] = A(M(J11, vm[4 + k]), M(J12, vm[8 + k]));
+        N[k] = M(ax, S(V[k], M(xc, V[6 + k])));
+        N[3 + k] = M(ay, S(V[3 + k], M(yc, V[6 + k])));
     }
-    float U[6];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            U[3 * r + k] = A(A(M(T3[3 * r], Sg[k]), M(T3[3 * r + 1], Sg[3 + k])), M(T3[3 * r + 2], Sg[6 + k]));
-    const float Aa = A(A(A(M(U[0], T3[0]), M(U[1], T3[1])), M(U[2], T3[2])), 3.00000012e-01f);
-    const float Bb = A(A(M(U[0], T3[3]), M(U[1], T3[4])), M(U[2], T3[5]));
-    const float Cc = A(A(A(M(U[3], T3[3]), M(U[4], T3[4])), M(U[5], T3[5])), 3.00000012e-01f);
-    const float det = S(M(Aa, Cc), M(Bb, Bb));
-    if (!(det > 0.0f)) return;
+    // D10: diagonal of Sigma2D
+    const float A0 = A(A(M(N[0], N[0]), M(N[1], N[1])), M(N[2], N[2]));
+    const float C0 = A(A(M(N[3], N[3]), M(N[4], N[4])), M(N[5], N[5]));
+    const float Aa = A(A0, 3.00000012e-01f), Cc = A(C0, 3.00000012e-01f);
+    // D13: opacity, the alpha-cut level; D14: half-extents; D15: centre; D16: rectangle
     const float o = D(1.0f, A(1.0f, rn_exp(-logit)));
     if (!(M(255.0f, o) >= 1.0f)) return;
     const float kk = M(2.0f, rn_log(M(255.0f, o)));
     const float ex = __fsqrt_rn(M(kk, Aa)), ey = __fsqrt_rn(M(kk, Cc));
-    const float u = A(D(M(c.fx, tx), tz), c.cx);
-    const float v = A(D(M(c.fy, ty), tz), c.cy);
+    const float u = A(M(c.fx, xz), c.cx);
+    const float v = A(M(c.fy, yz), c.cy);
     const float xlo = S(S(u, ex), 0.5f), xhi = S(A(u, ex), 0.5f);
     const float ylo = S(S(v, ey), 0.5f), yhi = S(A(v, ey), 0.5f);
     const float wm1 = (float)(c.width - 1), hm1 = (float)(c.height - 1);
@@ -162,11 +198,24 @@ __device__ __forceinline__ void project_one(const CamParams &c, float mx, float 
     const int y0 = (int)fmaxf(0.0f, ceilf(ylo)), y1 = (int)fminf(hm1, floorf(yhi));
     if (x0 > x1 || y0 > y1) return;
     P.vis = true;
-    P.u = u;
-    P.v = v;
-    P.ca = D(Cc, det);
-    P.cb = -D(Bb, det);
-    P.cc = D(Aa, det);
+    // continuous part: the centre relative to pixel (x0, y0)'s centre, in float-float
+    float Xh, Xl, Yh, Yl, Zh, Zl;
+    ff_affine(vm + 0, mx, my, mz, vm[3], Xh, Xl);
+    ff_affine(vm + 4, mx, my, mz, vm[7], Yh, Yl);
+    ff_affine(vm + 8, mx, my, mz, vm[11], Zh, Zl);
+    const float rzh = D(1.0f, Zh);
+    P.u = ff_centre(Xh, Xl, Zh, Zl, rzh, c.fx, c.cx, A((float)x0, 0.5f));
+    P.v = ff_centre(Yh, Yl, Zh, Zl, rzh, c.fy, c.cy, A((float)y0, 0.5f));
+    // the conic Sigma2D^-1 with the non-cancelling determinant
+    const float B = F(N[0], N[3], F(N[1], N[4], M(N[2], N[5])));
+    const float cr0 = F(N[1], N[5], -M(N[2], N[4]));
+    const float cr1 = F(N[2], N[3], -M(N[0], N[5]));
+    const float cr2 = F(N[0], N[4], -M(N[1], N[3]));
+    const float det = A(F(0.3f, A(A0, C0), F(cr0, cr0, F(cr1, cr1, M(cr2, cr2)))), 0.09f);
+    const float inv = __frcp_rn(det);
+    P.ca = M(Cc, inv);
+    P.cb = -M(B, inv);
+    P.cc = M(Aa, inv);
     P.o = o;
     P.z = tz;
     P.rlo = (uint32_t)x0 | ((uint32_t)y0 << 16);

@@ -98,6 +98,10 @@ struct Frame {
     CamParams cam{};
     bool has_state = false;
     bool count_pairs = false;
+    // device word the sort and compositing kernels raise their error bits in: the
+    // context's sticky word for plain frames, the frame's counters for graphs
+    uint32_t *err_word = nullptr;
+    bool give_up = false;  // diagnostic: every bounded wait gives up at once
 };
 
 // Per-stage CUDA-event timer: a ring of event sets, one set of kBounds events
@@ -217,6 +221,12 @@ CamParams make_cam(const gs_camera &c, int tile)
     }
     p.width = c.width;
     p.height = c.height;
+    // the Jacobian guard, 1.3 x the half field of view in x/z and y/z, by the discrete spec's
+    // fp32 sequence (products and quotients only, so no contraction can change it)
+    const volatile float hw = 0.5f * (float)c.width, hh = 0.5f * (float)c.height;
+    const volatile float qx = hw / c.fx, qy = hh / c.fy;
+    p.limx = 1.29999995f * qx;
+    p.limy = 1.29999995f * qy;
     p.tile_shift = ilog2(tile);
     p.tiles_x = (c.width + tile - 1) / tile;
     p.tiles_y = (c.height + tile - 1) / tile;
@@ -259,7 +269,9 @@ using namespace gsr;
 struct gs_context {
     int device = 0;
     std::vector<Frame *> pool;
-    uint32_t *h_counters = nullptr;  // pinned
+    uint32_t *h_counters = nullptr;  // pinned: kCntSlots words, then the sticky error word's copy
+    Buf err;                         // device: error bits of plain frames, kept until reported
+    bool give_up = false;            // gs_context_debug_waits
     Buf g2d;
     Buf host_planes;
     Buf warp_pos, warp_best;    // frame-interpolation warp: landing positions, depth-test slots
@@ -460,7 +472,8 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
         c.final_Ty = f->fTy.as<float>();
         c.n_contrib = f->ncontrib.as<uint32_t>();
     }
-    c.err_word = f->counters.as<uint32_t>() + kCntErr;
+    c.err_word = f->err_word ? f->err_word : f->counters.as<uint32_t>() + kCntErr;
+    c.give_up = f->give_up ? 1u : 0u;
     c.tile_order = f->order.as<uint32_t>();
     c.items = f->items.as<uint4>();
     c.plan_counts = f->plan_counts.as<uint32_t>();
@@ -494,6 +507,7 @@ cudaError_t mark(const Marks &m, int k, cudaStream_t st)
 gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cudaStream_t st, const Marks &mk = Marks{})
 {
     uint32_t *cnt = f->counters.as<uint32_t>();
+    uint32_t *err = f->err_word ? f->err_word : cnt + kCntErr;
     SortScratch scr;
     sort_scratch_carve(f->sort_scr.p, std::max<int64_t>(f->key_cap, f->n), &scr);
     // K3a, K4a: the visible Gaussians in depth order
@@ -503,7 +517,7 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     uint32_t *dk[2] = {f->dkeys[0].as<uint32_t>(), f->dkeys[1].as<uint32_t>()};
     uint32_t *dv[2] = {f->dvals[0].as<uint32_t>(), f->dvals[1].as<uint32_t>()};
     int dres = 0;
-    GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, cnt + kCntErr, f->n, 32, scr, &dres, st, true));
+    GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, err, f->n, 32, scr, &dres, st, true, f->give_up));
     GSR_CUDA(mark(mk, 4, st));
     // K3b, K4b: tile keys in depth order, then stable by tile
     const int tbits = f->bits - 32;
@@ -515,17 +529,17 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     uint32_t *kk[2] = {f->keys[0].as<uint32_t>(), f->keys[1].as<uint32_t>()};
     uint32_t *vv[2] = {f->vals[0].as<uint32_t>(), f->vals[1].as<uint32_t>()};
     int res = 0;
-    GSR_CUDA(launch_sort32(kk, vv, cnt + kCntEff, cnt + kCntErr, max_k, tbits, scr, &res, st, true));
+    GSR_CUDA(launch_sort32(kk, vv, cnt + kCntEff, err, max_k, tbits, scr, &res, st, true, f->give_up));
     f->sorted = res;
     GSR_CUDA(mark(mk, 6, st));
-    GSR_CUDA(launch_ranges(kk[res], vv[res], cnt, max_k, f->rec.as<GaussRec>(), f->rec_sorted.as<GaussRec>(),
+    GSR_CUDA(launch_ranges(kk[res], vv[res], cnt, max_k, f->n, f->rec.as<GaussRec>(), f->rec_sorted.as<GaussRec>(),
                            f->ranges.as<uint2>(), f->n_tiles, f->bin.as<uint4>(),
                            f->has_state ? f->keys64.as<uint64_t>() : nullptr, st,
                            f->want_nrm ? f->nrm.as<float4>() : nullptr,
                            f->want_nrm ? f->nrm_sorted.as<float4>() : nullptr));
     GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->chunk, f->head, f->items.as<uint4>(),
                          f->split_tiles.as<uint32_t>(), f->split_slot0.as<uint32_t>(), f->slot_split.as<uint32_t>(),
-                         f->plan_counts.as<uint32_t>(), st));
+                         f->plan_counts.as<uint32_t>(), err, f->max_split, f->max_slots, st));
     GSR_CUDA(mark(mk, 7, st));
     const CompositeArgs ca = comp_args(f, out);
     GSR_CUDA(launch_composite(ca, f->tile, f->batch, f->n_tiles, f->max_slots, st));
@@ -534,14 +548,17 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     return GS_OK;
 }
 
+}  // namespace
+
 gs_status err_status(uint32_t err)
 {
     if (err & kErrSortTimeout) return fail(GS_ERR_TIMEOUT, "radix sort lookback wait gave up");
     if (err & kErrTmaTimeout) return fail(GS_ERR_TIMEOUT, "compositing batch wait gave up");
-    if (err & kErrQueueTimeout) return fail(GS_ERR_TIMEOUT, "serving wait gave up");
     if (err & kErrCapacity) return fail(GS_ERR_CAPACITY, "instance count exceeded capacity");
     return GS_OK;
 }
+
+namespace {
 
 gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, const gs_render_opts *o,
                         const gs_outputs *out, Frame *f, cudaStream_t st)
@@ -565,6 +582,8 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
     gs_status r = frame_setup(f, s, c, &on, tile, batch, chunk, state);
     f->count_pairs = (o->flags & GS_COUNT_PAIRS) != 0;
     if (r != GS_OK) return r;
+    f->err_word = ctx->err.as<uint32_t>();
+    f->give_up = ctx->give_up;
     f->want_nrm = nrm;
     if (nrm) GSR_CUDA(f->nrm.ensure(sizeof(float4) * (size_t)std::max<int64_t>(s->n, 1)));
     uint32_t *cnt = f->counters.as<uint32_t>();
@@ -583,7 +602,13 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
                                 f->voffs.as<uint32_t>(), cnt, kMaxInstances, st));
     GSR_CUDA(mark(mk, 2, st));
     GSR_CUDA(cudaMemcpyAsync(ctx->h_counters, cnt, sizeof(uint32_t) * kCntSlots, cudaMemcpyDeviceToHost, st));
+    GSR_CUDA(cudaMemcpyAsync(ctx->h_counters + kCntSlots, f->err_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     GSR_CUDA(cudaStreamSynchronize(st));
+    if (ctx->h_counters[kCntSlots]) {  // a wait of an earlier frame on this context gave up
+        const uint32_t bits = ctx->h_counters[kCntSlots];
+        GSR_CUDA(cudaMemsetAsync(f->err_word, 0, sizeof(uint32_t), st));
+        return err_status(bits);
+    }
     const uint64_t K = (uint64_t)ctx->h_counters[kCntTotal] | ((uint64_t)ctx->h_counters[kCntTotalHi] << 32);
     if ((int64_t)K > kMaxInstances) return fail(GS_ERR_CAPACITY, "more than 2^30 - 1 (Gaussian, tile) instances");
     f->K = (int64_t)K;
@@ -649,12 +674,35 @@ gs_status gs_context_create(int device, gs_context **ctx)
     GSR_CUDA(cudaSetDevice(device));
     gs_context *c = new gs_context();
     c->device = device;
-    cudaError_t e = cudaMallocHost(&c->h_counters, sizeof(uint32_t) * kCntSlots);
+    cudaError_t e = cudaMallocHost(&c->h_counters, sizeof(uint32_t) * (kCntSlots + 1));
+    if (e == cudaSuccess) e = c->err.ensure(sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->err.p, 0, sizeof(uint32_t));
     if (e != cudaSuccess) {
         delete c;
-        return cuda_fail(e, "cudaMallocHost");
+        return cuda_fail(e, "gs_context_create");
     }
     *ctx = c;
+    return GS_OK;
+}
+
+gs_status gs_context_check(gs_context *ctx, gs_stream stream)
+{
+    if (!ctx) return fail(GS_ERR_INVALID_ARG, "ctx is NULL");
+    GSR_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    GSR_CUDA(cudaMemcpyAsync(ctx->h_counters + kCntSlots, ctx->err.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    GSR_CUDA(cudaStreamSynchronize(st));
+    const uint32_t bits = ctx->h_counters[kCntSlots];
+    if (!bits) return GS_OK;
+    GSR_CUDA(cudaMemsetAsync(ctx->err.p, 0, sizeof(uint32_t), st));
+    GSR_CUDA(cudaStreamSynchronize(st));
+    return err_status(bits);
+}
+
+gs_status gs_context_debug_waits(gs_context *ctx, int32_t give_up)
+{
+    if (!ctx) return fail(GS_ERR_INVALID_ARG, "ctx is NULL");
+    ctx->give_up = give_up != 0;
     return GS_OK;
 }
 
@@ -774,6 +822,7 @@ gs_status gs_render_backward(gs_context *ctx, const gs_fwd_state *state, const g
     b.g_depth = grad_in->depth;
     b.g_alpha = grad_in->alpha;
     b.g2d = ctx->g2d.as<float>();
+    b.n = (uint32_t)f->n;
     GSR_CUDA(launch_composite_backward(b, st));
     ProjectBwdArgs p{};
     p.means = scene->means;

@@ -20,7 +20,10 @@
 //
 // Host-side fault injection for tests: GSR_FAULT=alloc:<k> makes the k-th sort
 // allocation fail (that request finishes with GS_ERR_OOM, others proceed);
-// GSR_FAULT=enqueue:<k> makes the k-th admission's first launch fail.
+// GSR_FAULT=enqueue:<k> makes the k-th admission's first launch fail;
+// GSR_FAULT=wait:<k> runs the k-th admitted request's kernels with waits that give
+// up at once (its sort lookbacks and compositing batch waits), so that request
+// finishes with GS_ERR_TIMEOUT through its device error word, others proceed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -166,8 +169,16 @@ struct Slot {
     int n_tiles = 0, bits = 32;
     int64_t K = 0;
     int sorted = 0;
+    bool give_up = false;  // GSR_FAULT=wait: this request's waits give up at once
     uint32_t *keys[2] = {nullptr, nullptr};  // tile keys, in the sort memory
     uint32_t *vals[2] = {nullptr, nullptr};
+    // every device buffer the slot owns (the sort memory belongs to the arena)
+    void release_buffers()
+    {
+        DevBuf *all[] = {&rec, &bin, &ntiles, &bsums, &boffs, &ranges, &order, &counters, &vsums, &voffs,
+                         &bsums2, &boffs2, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1], &dscr};
+        for (DevBuf *b : all) b->release();
+    }
 };
 
 int fault_at(const char *kind)
@@ -208,8 +219,8 @@ struct gs_server {
     ServeItem *d_items = nullptr;
     uint32_t *d_work = nullptr;
     int comp_grid = 0;
-    int alloc_count = 0, enqueue_count = 0;
-    int fault_alloc = -1, fault_enqueue = -1;
+    int alloc_count = 0, enqueue_count = 0, admit_count = 0;
+    int fault_alloc = -1, fault_enqueue = -1, fault_wait = -1;
     std::atomic<uint32_t> thread_err{0};
     std::string thread_msg;
 };
@@ -247,6 +258,8 @@ gs_status admit(gs_server *S, int si, Request *r)
     const gs_scene &s = sc.view;
     if (S->fault_enqueue >= 0 && S->enqueue_count++ == S->fault_enqueue)
         return fail(GS_ERR_CUDA, "injected enqueue failure");
+    sl.give_up = S->fault_wait >= 0 && S->admit_count == S->fault_wait;
+    ++S->admit_count;
     sl.cam = make_cam(r->cam, kServeTile);
     sl.n_tiles = sl.cam.tiles_x * sl.cam.tiles_y;
     sl.bits = 32 + ilog2(std::max(sl.n_tiles, 1));
@@ -327,16 +340,18 @@ gs_status enqueue_sort(gs_server *S, Slot &sl)
     GSR_CUDA(launch_compact(static_cast<uint32_t *>(sl.ntiles.p), static_cast<uint4 *>(sl.bin.p),
                             static_cast<uint32_t *>(sl.voffs.p), s.n, dk[0], dv[0], dscr.hist, sl.stream));
     int dres = 0;
-    GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, cnt + kCntErr, s.n, 32, dscr, &dres, sl.stream, true));
+    GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, cnt + kCntErr, s.n, 32, dscr, &dres, sl.stream, true,
+                           sl.give_up));
     const int tbits = sl.bits - 32;
     GSR_CUDA(launch_duplicate(dv[dres], cnt + kCntVisible, s.n, static_cast<uint32_t *>(sl.ntiles.p),
                               static_cast<uint4 *>(sl.bin.p), static_cast<uint32_t *>(sl.bsums2.p),
                               static_cast<uint32_t *>(sl.boffs2.p), sl.cam.tile_shift, sl.cam.tiles_x, sl.keys[0],
                               sl.vals[0], K, cnt, scr.hist, sort_passes(tbits), sl.stream));
     int res = 0;
-    GSR_CUDA(launch_sort32(sl.keys, sl.vals, cnt + kCntEff, cnt + kCntErr, K, tbits, scr, &res, sl.stream, true));
+    GSR_CUDA(launch_sort32(sl.keys, sl.vals, cnt + kCntEff, cnt + kCntErr, K, tbits, scr, &res, sl.stream, true,
+                           sl.give_up));
     sl.sorted = res;
-    GSR_CUDA(launch_ranges(sl.keys[res], sl.vals[res], cnt, K, static_cast<const GaussRec *>(sl.rec.p), sl.rec_sorted,
+    GSR_CUDA(launch_ranges(sl.keys[res], sl.vals[res], cnt, K, s.n, static_cast<const GaussRec *>(sl.rec.p), sl.rec_sorted,
                            static_cast<uint2 *>(sl.ranges.p), sl.n_tiles, static_cast<const uint4 *>(sl.bin.p),
                            nullptr, sl.stream));
     GSR_CUDA(launch_tile_order(static_cast<const uint2 *>(sl.ranges.p), sl.n_tiles, static_cast<uint32_t *>(sl.order.p),
@@ -365,6 +380,7 @@ CompositeArgs slot_comp_args(Slot &sl)
     c.depth = r->out.depth;
     c.alpha = r->out.alpha;
     c.err_word = static_cast<uint32_t *>(sl.counters.p) + kCntErr;
+    c.give_up = sl.give_up ? 1u : 0u;
     return c;
 }
 
@@ -379,11 +395,12 @@ void scheduler(gs_server *S)
             for (int si : S->comp_slots) {
                 Slot &sl = S->slots[si];
                 cudaStreamSynchronize(sl.stream);
+                // the slot's device error bits, copied after its compositing (sort lookback,
+                // batch waits); a request whose kernels gave up finishes with that error
                 const uint32_t err = sl.h_counters[kCntErr];
-                (void)err;
                 Request *r = sl.req;
                 slot_free(S, sl);
-                finish(S, r, GS_OK);
+                finish(S, r, err ? err_status(err) : GS_OK);
             }
             S->comp_slots.clear();
             S->comp_busy = false;
@@ -466,6 +483,12 @@ void scheduler(gs_server *S)
                 if (e == cudaSuccess)
                     e = launch_composite_persistent(S->d_items, n, total, kServeTile, kServeBatch, S->d_work,
                                                     S->comp_grid, S->comp_stream);
+                for (int si : S->comp_slots) {  // each request's error bits, after its last kernel
+                    Slot &sl = S->slots[si];
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(sl.h_counters + kCntErr, static_cast<uint32_t *>(sl.counters.p) + kCntErr,
+                                            sizeof(uint32_t), cudaMemcpyDeviceToHost, S->comp_stream);
+                }
                 if (e == cudaSuccess) e = cudaEventRecord(S->comp_done, S->comp_stream);
                 if (e != cudaSuccess) {
                     for (int si : S->comp_slots) {
@@ -514,6 +537,7 @@ gs_status gs_server_create(int device, size_t sort_budget_bytes, int max_infligh
     S->max_inflight = max_inflight;
     S->fault_alloc = fault_at("alloc");
     S->fault_enqueue = fault_at("enqueue");
+    S->fault_wait = fault_at("wait");
     cudaError_t e = S->arena.init(sort_budget_bytes);
     S->slots.resize(max_inflight);
     for (Slot &sl : S->slots) {
@@ -664,14 +688,7 @@ gs_status gs_server_destroy(gs_server *S)
         if (sl.ev_scan) cudaEventDestroy(sl.ev_scan);
         if (sl.ev_sorted) cudaEventDestroy(sl.ev_sorted);
         if (sl.h_counters) cudaFreeHost(sl.h_counters);
-        sl.rec.release();
-        sl.bin.release();
-        sl.ntiles.release();
-        sl.bsums.release();
-        sl.boffs.release();
-        sl.ranges.release();
-        sl.order.release();
-        sl.counters.release();
+        sl.release_buffers();
     }
     for (SceneRes &s : S->scenes)
         if (s.mem) cudaFree(s.mem);

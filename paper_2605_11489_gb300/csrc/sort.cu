@@ -16,6 +16,7 @@
 // for partitions that are already running. Every wait is still bounded: a
 // partition that gives up sets kErrSortTimeout and publishes what it has.
 #include <algorithm>
+#include <mutex>
 
 #include "gsr_internal.cuh"
 
@@ -118,11 +119,18 @@ __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_
 
 // 64-bit keys: 80 registers and the largest carveout fit three partitions per
 // SM; 32-bit keys fit four.
+// max_spins: polls of a predecessor's word before the lookback gives up; 0 gives up before
+// the first look (a diagnostic setting that exercises the give-up path deterministically).
+// A partition that gave up publishes its own count as its prefix: the output is then not
+// sorted, but every element is still written inside [0, K). The scatter also keeps inside
+// [0, K) when the input itself is the unsorted output of a pass that gave up (whose digit
+// counts no longer match the histogram).
 template <typename KeyT, bool kBallot>
 __global__ void __launch_bounds__(kThreads, sizeof(KeyT) == 8 ? 3 : 4)
     k_sort_pass(const KeyT *__restrict__ kin, const uint32_t *__restrict__ vin, KeyT *__restrict__ kout,
                 uint32_t *__restrict__ vout, const uint32_t *__restrict__ count, int shift,
-                const uint32_t *__restrict__ hist, uint32_t *status, uint32_t *part_ctr, uint32_t *err)
+                const uint32_t *__restrict__ hist, uint32_t *status, uint32_t *part_ctr, uint32_t *err,
+                uint32_t max_spins)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     KeyT *s_keys = reinterpret_cast<KeyT *>(smem);
@@ -198,6 +206,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(KeyT) == 8 ? 3 : 4)
         int p = (int)part - 1;
         uint32_t spins = 0;
         bool done = false;
+        if (max_spins == 0u) {  // diagnostic: give up before the first look
+            atomicOr(err, kErrSortTimeout);
+            done = true;
+        }
         while (!done && p >= 0) {
             uint32_t w[kLook];
 #pragma unroll
@@ -207,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(KeyT) == 8 ? 3 : 4)
                 if (done || p < 0) break;
                 uint32_t s = w[u];
                 while ((s & kFlagMask) == 0u) {
-                    if (++spins > kMaxSpins) {
+                    if (++spins > max_spins) {
                         atomicOr(err, kErrSortTimeout);
                         break;
                     }
@@ -245,8 +257,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(KeyT) == 8 ? 3 : 4)
         const KeyT key = s_keys[i];
         const uint32_t d = (uint32_t)(key >> shift) & 0xFFu;
         const uint32_t g = s_base[d] + (i - s_start[d]);
-        kout[g] = key;
-        vout[g] = s_vals[i];
+        if (g < K) {
+            kout[g] = key;
+            vout[g] = s_vals[i];
+        }
     }
 }
 
@@ -275,7 +289,7 @@ namespace {
 
 template <typename KeyT>
 cudaError_t sort_impl(KeyT *keys[2], uint32_t *vals[2], const uint32_t *count, uint32_t *err_word, int64_t max_k,
-                      int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready)
+                      int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready, bool give_up)
 {
     const int passes = sort_passes(bits);
     *result = passes & 1;
@@ -283,11 +297,14 @@ cudaError_t sort_impl(KeyT *keys[2], uint32_t *vals[2], const uint32_t *count, u
     const int64_t parts = parts_for(max_k);
     if (parts > scr.max_parts || passes > (int)sizeof(KeyT)) return cudaErrorInvalidValue;
     constexpr size_t smem = pass_smem<KeyT>();
-    // once per device, outside any stream capture (the first sort on a device is never captured)
+    // once per device, outside any stream capture (the first sort on a device is never
+    // captured); serialised, because the server's scheduler thread sorts too
     static bool attr_set[64] = {};
+    static std::mutex attr_mu;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(attr_mu);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
         const void *fns[2] = {reinterpret_cast<const void *>(k_sort_pass<KeyT, false>),
                               reinterpret_cast<const void *>(k_sort_pass<KeyT, true>)};
@@ -318,7 +335,7 @@ cudaError_t sort_impl(KeyT *keys[2], uint32_t *vals[2], const uint32_t *count, u
         auto kern = p + 1 < passes ? k_sort_pass<KeyT, true> : k_sort_pass<KeyT, false>;
         kern<<<(unsigned)parts, kThreads, smem, s>>>(keys[src], vals[src], keys[dst], vals[dst], count, 8 * p,
                                                      scr.hist + p * kRadix, scr.status + (size_t)p * parts * kRadix,
-                                                     scr.part_ctr + p, err_word);
+                                                     scr.part_ctr + p, err_word, give_up ? 0u : kMaxSpins);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -327,15 +344,18 @@ cudaError_t sort_impl(KeyT *keys[2], uint32_t *vals[2], const uint32_t *count, u
 }  // namespace
 
 cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *counters, uint32_t *err_word,
-                        int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready)
+                        int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready,
+                        bool give_up)
 {
-    return sort_impl<uint64_t>(keys, vals, counters + kCntEff, err_word, max_k, bits, scr, result, s, hist_ready);
+    return sort_impl<uint64_t>(keys, vals, counters + kCntEff, err_word, max_k, bits, scr, result, s, hist_ready,
+                               give_up);
 }
 
 cudaError_t launch_sort32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *count, uint32_t *err_word,
-                          int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready)
+                          int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s, bool hist_ready,
+                          bool give_up)
 {
-    return sort_impl<uint32_t>(keys, vals, count, err_word, max_k, bits, scr, result, s, hist_ready);
+    return sort_impl<uint32_t>(keys, vals, count, err_word, max_k, bits, scr, result, s, hist_ready, give_up);
 }
 
 }  // namespace gsr

@@ -96,8 +96,9 @@ class Camera:
     def scaled(self, factor: int) -> "Camera":
         """Same pose at ``factor`` times the resolution (the high-resolution frame of a
         super-sampling factor S = factor)."""
-        return Camera(self.viewmat.copy(), self.fx * factor, self.fy * factor, self.cx * factor,
-                      self.cy * factor, self.width * factor, self.height * factor, self.near, self.eye)
+        return Camera(self.viewmat.copy(), _fp32(self.fx * factor), _fp32(self.fy * factor),
+                      _fp32(self.cx * factor), _fp32(self.cy * factor), self.width * factor,
+                      self.height * factor, self.near, self.eye)
 
 
 # ----------------------------------------------------------------------------- scenes
@@ -195,13 +196,19 @@ def look_at(eye, target, up) -> np.ndarray:
     return np.concatenate([rot, t[:, None]], axis=1).reshape(12).astype(np.float32)
 
 
+def _fp32(v: float) -> float:
+    """The nearest fp32 value: the render's camera carries fp32 intrinsics, so the
+    generated cameras hold exactly the numbers every consumer receives."""
+    return float(np.float32(v))
+
+
 def make_camera(eye, target, up, width: int, height: int, vfov_deg: float = 60.0,
                 near: float = 0.2) -> Camera:
-    """Pinhole camera; the field of view is vertical: fy = fx = (H/2) / tan(vfov/2),
-    principal point at the image centre."""
-    f = (height / 2.0) / math.tan(math.radians(vfov_deg) / 2.0)
+    """Pinhole camera; the field of view is vertical: fy = fx = (H/2) / tan(vfov/2)
+    (rounded to fp32), principal point at the image centre."""
+    f = _fp32((height / 2.0) / math.tan(math.radians(vfov_deg) / 2.0))
     return Camera(look_at(eye, target, up), f, f, width / 2.0, height / 2.0, int(width),
-                  int(height), near, np.asarray(eye, dtype=np.float64))
+                  int(height), _fp32(near), np.asarray(eye, dtype=np.float64))
 
 
 def tiny_camera(width: int = 256, height: int = 144) -> Camera:

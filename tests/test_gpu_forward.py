@@ -76,7 +76,9 @@ def test_projection_records_match_oracle(env):
     assert np.array_equal(rect[:, 1] & 0xFFFF, p["rect"][vis, 2])
     assert np.array_equal(rect[:, 1] >> 16, p["rect"][vis, 3])
     assert np.array_equal(r[:, 6], p["z32"][vis])  # depth key value, bit-exact
-    np.testing.assert_allclose(r[:, 0:2], p["uv"][vis], rtol=0, atol=2e-4)
+    # the centre is stored relative to the rectangle's first pixel centre
+    origin = np.stack([rect[:, 0] & 0xFFFF, rect[:, 0] >> 16], 1).astype(np.float64) + 0.5
+    np.testing.assert_allclose(r[:, 0:2] + origin, p["uv"][vis], rtol=0, atol=5e-6)
     np.testing.assert_allclose(r[:, 2:5], p["conic"][vis], rtol=2e-5, atol=1e-6)
     np.testing.assert_allclose(r[:, 5], p["opacity"][vis], rtol=2e-6, atol=1e-7)
     np.testing.assert_allclose(np.stack([r[:, 7], r[:, 8], r[:, 9]], 1), p["rgb"][vis], rtol=0, atol=2e-6)

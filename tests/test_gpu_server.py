@@ -54,8 +54,11 @@ def test_requests_same_alone_and_in_the_mix(env):
     api, ctx = env
     import torch
 
-    scenes = [api.Scene.from_arrays(synth.tiny_scene(4096, 0)),
-              api.Scene.from_arrays(synth.clustered_scene(20_000, 5, (2.0, 2.0, 2.0), 8, 3))]
+    import oracle
+    from gpu_util import GRAD_FRAC, GRAD_FRAC_STRESS, check_render
+
+    arrays = [synth.tiny_scene(4096, 0), synth.clustered_scene(20_000, 5, (2.0, 2.0, 2.0), 8, 3)]
+    scenes = [api.Scene.from_arrays(a) for a in arrays]
     srv = api.Server(sort_budget_bytes=256 << 20, max_inflight=6)
     ids = [srv.load_scene(s) for s in scenes]
     reqs = _mixed_requests(40, 1)
@@ -80,6 +83,15 @@ def test_requests_same_alone_and_in_the_mix(env):
         for k in ref:
             assert torch.equal(o[k], whole[k]), k
             assert (o[k] - ref[k]).abs().max().item() < 2e-5, k
+    # and served requests of every resolution against the FP64 oracle, every pixel
+    seen = set()
+    for (sid, cam), o in zip(reqs, outs):
+        if (sid, cam.width) in seen:
+            continue
+        seen.add((sid, cam.width))
+        # scene 1 is a close-range stress scene (see gpu_util)
+        check_render(o, oracle.render(arrays[sid], cam, bg=bg), grad_frac=GRAD_FRAC_STRESS if sid else GRAD_FRAC)
+    assert len(seen) >= 6
     srv.close()
 
 
