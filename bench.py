@@ -164,7 +164,7 @@ def cpu_baseline(sc, cams, name, max_seconds=20.0):
 
 def run_reference(args):
     """--impl reference: the CPU FP64 oracle timed on the same workload, metric and
-    unit; each step renders a band of rows of one frame (bounded)."""
+    unit; each step renders one whole frame of the camera path (binned mode, all host cores)."""
     rank, _, world = dist_env()
     if rank != 0:
         return
@@ -183,13 +183,11 @@ def run_reference(args):
     sc, cams = make_workload(args.workload)
     osc = oracle.OScene(sc)
     cores = oracle.max_threads()
-    band = max(1, cams[0].height // 16)
 
-    def step(i):
+    def step(i):  # one whole frame of the camera path, like the GPU arm's step
         cam = cams[i % len(cams)]
-        y0 = (i * band) % cam.height
-        oracle.render_band(osc, cam, y0, min(cam.height, y0 + band))
-        return cam.width * (min(cam.height, y0 + band) - y0)
+        oracle.render(osc, cam)
+        return cam.width * cam.height
 
     for i in range(args.warmup):
         step(i)
@@ -203,9 +201,9 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
-                       "step": "one band of %d rows of a frame" % band},
+                       "step": "one whole frame of the camera path"},
             "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d steps x %d rows" % (args.steps, band)},
+                             "sample": "%d whole frames of the %s camera path" % (args.steps, args.workload)},
             "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -371,7 +369,7 @@ def run_serving(args):
                         "p99_ms": pct(0.99), "mean_ms": sum(lat_p) / n_req,
                         "throughput_mpix_s": px_total / t_poisson / 1e6},
             "burst_p50_ms": sorted(lat_burst)[n_req // 2]}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 INTERP_DESC = ("frame-interpolation warp pair of Sec. 4.2: frame 0 at 3840x2160 (7 planes: colour, depth, "
@@ -812,58 +810,15 @@ def recorded_traffic(stage, tile, batch, chunk, workload):
     return None
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=120)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["serve", "interp", "gass", "pipeline"])
-    ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
-    ap.add_argument("--serve-scale", type=float, default=1.0, help="serve: scale of the scene sizes")
-    ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: sort-buffer budget")
-    ap.add_argument("--inflight", type=int, default=16, help="serve: in-flight request slots")
-    ap.add_argument("--load", type=float, default=0.8, help="serve: Poisson rate / plain renderer's rate")
-    ap.add_argument("--tile", type=int, default=0, help="tile side 8/16/32 (0 = autotune)")
-    ap.add_argument("--batch", type=int, default=0, help="Gaussians per shared-memory batch (0 = autotune)")
-    ap.add_argument("--chunk", type=int, default=0, help="records per chunk of a split tile list (0 = autotune)")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-backward", action="store_true", help="skip the forward+backward timing")
-    ap.add_argument("--no-normals", action="store_true", help="skip the normal-channel timing")
-    ap.add_argument("--frames-in-flight", type=int, default=4,
-                    help="frames rendered concurrently, one graph and stream each (api.FrameStream)")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "serve":
-        return run_serving(args)
-    if args.workload == "interp":
-        return run_interp(args)
-    if args.workload == "gass":
-        return run_gass(args)
-    if args.workload == "pipeline":
-        return run_pipeline(args)
-
+def measure_render(args, name, ctx, stream, sc, cams, world, rank, local_rank, full=True, cpu_seconds=12.0):
+    """Times one render workload the way the headline is timed and returns its fields:
+    value (whole-job Mpix/s), the per-stage breakdown and rooflines, e2e through the
+    host frame stream, and (full=True) the backward and normal-channel timings."""
     import torch
 
-    rank, local_rank, world = dist_env()
-    if world > 1:
-        import torch.distributed as dist
+    from paper_2605_11489_gb300 import abi, api, synth
 
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local_rank)
-    import __graft_entry__
-
-    __graft_entry__.build()
-    from paper_2605_11489_gb300 import abi, api, synth  # noqa: F401
-
-    sc, cams = make_workload(args.workload)
     W, H = cams[0].width, cams[0].height
-    stream = torch.cuda.Stream()
-    ctx = api.Context(local_rank)
     with torch.cuda.stream(stream):
         scene = api.Scene.from_arrays(sc)
         out = api.alloc_outputs(W, H)
@@ -913,7 +868,7 @@ def main():
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    clk_path = os.path.join(tempfile.gettempdir(), "gsr_clocks_%d_%d.csv" % (os.getpid(), rank))
+    clk_path = os.path.join(tempfile.gettempdir(), "gsr_clocks_%d_%d_%s.csv" % (os.getpid(), rank, name))
     smi, smi_f = start_clock_sampler(clk_path, local_rank)
     time.sleep(0.3)
     if world > 1:
@@ -931,13 +886,17 @@ def main():
     st = {key: sum(x[key] for x in sts) for key in ("frames", "instances_total", "visible_total", "timed_frames")}
     ms = slowest_rank(ms, world, "cuda")
     value = job_throughput(W * H * args.steps, world, ms * 1e-3)
-    # the dominant kernel's launch duration inside the timed region (every slot's frames)
-    composite_ms_timed = (sum(x["stage_ms"]["composite"] * x["timed_frames"] for x in sts)
-                          / max(1, sum(x["timed_frames"] for x in sts)))
-    # for context: the same replays one frame at a time on one stream (after the timed region)
+    # the dominant kernel's launch duration inside the timed region (every slot's frames,
+    # sharing the GPU with the other frames in flight)
+    composite_ms_in_flight = (sum(x["stage_ms"]["composite"] * x["timed_frames"] for x in sts)
+                              / max(1, sum(x["timed_frames"] for x in sts)))
+    # the same replays one frame at a time on one stream: a timed region of its own, where
+    # the compositing events measure the kernel alone (the roofline's launch duration)
     ms_one = slowest_rank(timed_replays(fs, False), world, "cuda")
+    sts1 = fs.stats(reset=True)
+    composite_ms_alone = (sum(x["stage_ms"]["composite"] * x["timed_frames"] for x in sts1)
+                          / max(1, sum(x["timed_frames"] for x in sts1)))
     fs.synchronize()
-    fs.stats(reset=True)
     one_stream = {"value": job_throughput(W * H * args.steps, world, ms_one * 1e-3), "unit": "Mpix/s",
                   "ms_per_step": ms_one / args.steps}
     fs.close()
@@ -959,6 +918,7 @@ def main():
     tile_passes = math.ceil(max(1, math.ceil(math.log2(max(n_tiles, 2)))) / 8)
     dom = max(stage_ms, key=lambda k: stage_ms[k])
     hbm_peak, sm_max_mhz, peak_src = measured_peaks()
+
     def roofline(stage, ms_stage=None):
         bound, amount = algorithmic(stage, (W, H), sc.deg, sc.n, K_avg, V_avg, tile_passes, W * H, census)
         ms_stage = stage_ms[stage] if ms_stage is None else ms_stage
@@ -966,25 +926,31 @@ def main():
             achieved = amount / (ms_stage * 1e-3) / 1e9
             return {"bound": "hbm", "kernel": stage, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak,
-                    "traffic": recorded_traffic(stage, tile, batch, chunk, args.workload),
+                    "traffic": recorded_traffic(stage, tile, batch, chunk, name),
                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src,
                     "algorithmic_bytes_per_launch": amount, "launch_ms": ms_stage}
         peak = fp32_peak_tflops(sm_max_mhz)
         achieved = amount / (ms_stage * 1e-3) / 1e12
         return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(stage, tile, batch, chunk, args.workload),
+                "frac": achieved / peak, "traffic": recorded_traffic(stage, tile, batch, chunk, name),
                 "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz" % (SMS, FP32_LANES, sm_max_mhz),
                 "algorithmic_flop_per_launch": amount, "launch_ms": ms_stage,
                 "pairs_evaluated_per_frame": census[0], "pairs_blended_per_frame": census[1]}
 
-    # the dominant kernel at its launch duration inside the timed region (sharing the GPU
-    # with the other slots' frames); the per-stage table from the one-frame-at-a-time breakdown
-    roof = roofline(dom, composite_ms_timed if dom == "composite" else None)
-    # the same kernel one frame at a time (the stage breakdown), where nothing shares the GPU
-    alone = roofline(dom)
-    roof["one_frame_at_a_time"] = {"launch_ms": stage_ms[dom], "achieved": alone["achieved"], "frac": alone["frac"]}
+    # the dominant kernel at its launch duration measured one frame at a time (the one-stream
+    # timed replays); beside it, the same kernel while the other frames in flight share the GPU
+    alone_ms = composite_ms_alone if dom == "composite" and composite_ms_alone > 0 else None
+    roof = roofline(dom, alone_ms)
+    roof["launch_ms_source"] = ("CUDA events around compositing in each replay of the one-stream timed region "
+                                "(one frame at a time)")
+    if dom == "composite":
+        shared = roofline(dom, composite_ms_in_flight)
+        roof["in_flight"] = {"launch_ms": composite_ms_in_flight, "achieved": shared["achieved"],
+                             "frac": shared["frac"],
+                             "note": "compositing's events inside the frames-in-flight timed region, where "
+                                     "the other frames' kernels share the SMs: not a kernel duration"}
     stage_roofline = {k: {kk: v[kk] for kk in ("bound", "achieved", "unit", "frac")}
-                      for k, v in ((s, roofline(s)) for s in abi.STAGES)}
+                      for k, v in ((s_, roofline(s_)) for s_ in abi.STAGES)}
 
     # end to end through the public API: each frame's camera from the host, all five output
     # planes back to pinned host memory, every step (api.HostFrameStream: graph replay with
@@ -994,19 +960,19 @@ def main():
     if not args.no_e2e:
         hosts = [{k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in out.items()}
                  for _ in range(2)]
-        fs = api.HostFrameStream(ctx, scene, cams[0], capacity, tile, batch, chunk, slots=args.frames_in_flight)
+        hfs = api.HostFrameStream(ctx, scene, cams[0], capacity, tile, batch, chunk, slots=args.frames_in_flight)
         for i in range(3):
-            fs.render(cams[i % len(cams)], hosts[i % 2])
-        fs.synchronize()
+            hfs.render(cams[i % len(cams)], hosts[i % 2])
+        hfs.synchronize()
         e2e_steps = min(args.steps, 60)
         if world > 1:
             torch.distributed.barrier()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
-            fs.render(cams[i % len(cams)], hosts[i % 2])
-        fs.synchronize()
+            hfs.render(cams[i % len(cams)], hosts[i % 2])
+        hfs.synchronize()
         dt = slowest_rank(time.perf_counter() - t0, world, "cuda")
-        fs.close()
+        hfs.close()
         host = hosts[0]
         for i in range(2):
             ctx.forward_to_host(scene, cams[i], host, tile=tile, batch=batch, stream=stream)
@@ -1026,7 +992,7 @@ def main():
     # the backward workload: forward keeping the state, then the backward of
     # N(0,1) upstream gradients on rgb, dC/dx and dC/dy (CUDA events, plain calls)
     bwd = None
-    if not args.no_backward:
+    if full and not args.no_backward:
         ups = synth.upstream_grads(W, H, 3)
         g_in = {k: torch.from_numpy(v).to("cuda") for k, v in ups.items()}
         grads = scene.zeros_like_grads()
@@ -1066,7 +1032,7 @@ def main():
     # the normal channel (plain forward, whole tile lists) against the same plain forward
     # without it, CUDA events, after two warm-up frames each
     nrm = None
-    if not args.no_normals:
+    if full and not args.no_normals:
         def plain_ms(keys, chunk_):
             o = api.alloc_outputs(W, H, keys)
             for i in range(2):
@@ -1088,34 +1054,112 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(sc, cams, args.workload)
+        cpu = cpu_baseline(sc, cams, name, max_seconds=cpu_seconds)
+    del scene, out
+    return {"value": value, "ms_per_step": ms / args.steps, "frames_per_s": 1e3 * args.steps * world / ms,
+            "config": {"workload": name, "desc": WORKLOADS[name]["desc"], "width": W, "height": H,
+                       "gaussians": sc.n, "sh_degree": sc.deg, "tile": tile, "batch": batch, "chunk": chunk,
+                       "path": "CUDA graph replay per frame, %d frames in flight (api.FrameStream)"
+                               % args.frames_in_flight, "frames_in_flight": args.frames_in_flight,
+                       "l2": "inputs larger than L2 (scene %.0f MB)" % (sc.nbytes() / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "backward": bwd, "normals": nrm, "stage_ms": stage_ms, "one_stream": one_stream,
+            "stage_ms_source": "a replay of the camera path one frame at a time with events at every stage "
+                               "boundary",
+            "instances_per_frame": K_avg, "visible_per_frame": V_avg,
+            "roofline": roof, "stage_roofline": stage_roofline, "clocks": clocks, "e2e": e2e,
+            "cpu_baseline": cpu,
+            # kernels per frame: projection, colour, block scan, compaction, 4 depth-sort
+            # passes, tile-count sums, their scan, duplication, `tile_passes` tile-sort
+            # passes, ranges, plan, two compositing waves, re-walk, finish
+            "gpu_launches": args.steps * (17 + tile_passes)}
 
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["serve", "interp", "gass", "pipeline"])
+    ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
+    ap.add_argument("--serve-scale", type=float, default=1.0, help="serve: scale of the scene sizes")
+    ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: sort-buffer budget")
+    ap.add_argument("--inflight", type=int, default=16, help="serve: in-flight request slots")
+    ap.add_argument("--load", type=float, default=0.8, help="serve: Poisson rate / plain renderer's rate")
+    ap.add_argument("--tile", type=int, default=0, help="tile side 8/16/32 (0 = autotune)")
+    ap.add_argument("--batch", type=int, default=0, help="Gaussians per shared-memory batch (0 = autotune)")
+    ap.add_argument("--chunk", type=int, default=0, help="records per chunk of a split tile list (0 = autotune)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-backward", action="store_true", help="skip the forward+backward timing")
+    ap.add_argument("--no-normals", action="store_true", help="skip the normal-channel timing")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="the headline workload only (without the 6M and serving legs of the default line)")
+    ap.add_argument("--frames-in-flight", type=int, default=4,
+                    help="frames rendered concurrently, one graph and stream each (api.FrameStream)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "serve":
+        print(json.dumps(run_serving(args)), flush=True)
+        return
+    if args.workload == "interp":
+        return run_interp(args)
+    if args.workload == "gass":
+        return run_gass(args)
+    if args.workload == "pipeline":
+        return run_pipeline(args)
+
+    import torch
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2605_11489_gb300 import api, synth  # noqa: F401
+
+    stream = torch.cuda.Stream()
+    ctx = api.Context(local_rank)
+    sc, cams = make_workload(args.workload)
+    head = measure_render(args, args.workload, ctx, stream, sc, cams, world, rank, local_rank, full=True)
+    del sc
+    # The metric's other legs, in the same line, for the default workload: the 6M scene
+    # (1920x1080 and 480x270 fly-throughs), and the serving stream (p50 / p99 latency and
+    # Mpix/s against the plain one-request-per-launch renderer).
+    legs = None
+    if args.workload == "large" and not args.no_legs:
+        legs = {}
+        sc6, _ = make_workload("ultra")
+        for leg in ("ultra", "ultra_lr"):
+            w = WORKLOADS[leg]
+            cams6 = synth.flythrough_cameras(60, w["width"], w["height"])
+            legs[leg] = measure_render(args, leg, ctx, stream, sc6, cams6, world, rank, local_rank, full=False,
+                                       cpu_seconds=8.0)
+        del sc6
+        torch.cuda.empty_cache()
+        if world == 1:
+            legs["serve"] = run_serving(args)
+        else:
+            legs["serve"] = {"skipped": "the serving leg runs at N = 1"}
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
-                           "width": W, "height": H, "gaussians": sc.n, "sh_degree": sc.deg,
-                           "tile": tile, "batch": batch, "chunk": chunk,
-                           "path": "CUDA graph replay per frame, %d frames in flight (api.FrameStream)"
-                                   % args.frames_in_flight, "frames_in_flight": args.frames_in_flight,
-                           "l2": "inputs larger than L2 (scene %.0f MB)" % (sc.nbytes() / 1e6),
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
-                "frames_per_s": 1e3 * args.steps * world / ms,
-                "backward": bwd,
-                "normals": nrm,
-                "stage_ms": stage_ms,
-                "one_stream": one_stream,
-                "stage_ms_source": "a replay of the camera path one frame at a time with events at every "
-                                   "stage boundary; the roofline's launch_ms is compositing inside the timed "
-                                   "region (frames in flight sharing the GPU)",
-                "instances_per_frame": K_avg, "visible_per_frame": V_avg,
-                "roofline": roof, "stage_roofline": stage_roofline, "clocks": clocks, "e2e": e2e,
-                "cpu_baseline": cpu,
-                # kernels per frame: projection, colour, block scan, compaction, 4 depth-sort
-                # passes, tile-count sums, their scan, duplication, `tile_passes` tile-sort
-                # passes, ranges, plan, two compositing waves, re-walk, finish
-                "gpu_launches": args.steps * (17 + tile_passes)}
+        line = {"metric": METRIC, "value": head["value"], "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+        line.update({k: v for k, v in head.items() if k not in ("value", "ms_per_step")})
+        if legs is not None:
+            line["legs"] = legs
+            launches = line["gpu_launches"]
+            for leg in ("ultra", "ultra_lr"):
+                launches += legs[leg]["gpu_launches"]
+            line["gpu_launches_all_legs"] = launches
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

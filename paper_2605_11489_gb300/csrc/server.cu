@@ -250,6 +250,32 @@ size_t sort_bytes(int64_t K)
     return 4 * up(sizeof(uint32_t) * k) + up(sizeof(GaussRec) * k) + up(sort_scratch_bytes(k));
 }
 
+// The slot's per-Gaussian and per-tile buffers for n Gaussians and n_tiles tiles.
+// Growing one frees and allocates device memory, and cudaFree waits for the whole
+// device; gs_server_load_scene therefore sizes every slot for the largest scene
+// before requests arrive, so that admission never reallocates while others render.
+cudaError_t slot_reserve(Slot &sl, int64_t n, int n_tiles)
+{
+    const int64_t n1 = std::max<int64_t>(n, 1), n4 = (n + 3) / 4 * 4;
+    const int nb = std::max(project_blocks(n), 1);
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    ok(sl.rec.ensure(sizeof(GaussRec) * (size_t)n1));
+    ok(sl.bin.ensure(sizeof(uint4) * (size_t)n1));
+    ok(sl.ntiles.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(n4, 4)));
+    DevBuf *per_block[] = {&sl.bsums, &sl.boffs, &sl.vsums, &sl.voffs, &sl.bsums2, &sl.boffs2};
+    for (DevBuf *b : per_block) ok(b->ensure(sizeof(uint32_t) * (size_t)nb));
+    for (int k = 0; k < 2; ++k) {
+        ok(sl.dkeys[k].ensure(sizeof(uint32_t) * (size_t)n1));
+        ok(sl.dvals[k].ensure(sizeof(uint32_t) * (size_t)n1));
+    }
+    ok(sl.dscr.ensure(sort_scratch_bytes(n1)));
+    ok(sl.ranges.ensure(sizeof(uint2) * (size_t)std::max(n_tiles, 1)));
+    ok(sl.order.ensure(sizeof(uint32_t) * (size_t)std::max(n_tiles, 1)));
+    ok(sl.counters.ensure(sizeof(uint32_t) * kCntSlots));
+    return e;
+}
+
 // Stage 1: projection + scan on the slot's stream; K copied back.
 gs_status admit(gs_server *S, int si, Request *r)
 {
@@ -263,25 +289,8 @@ gs_status admit(gs_server *S, int si, Request *r)
     sl.cam = make_cam(r->cam, kServeTile);
     sl.n_tiles = sl.cam.tiles_x * sl.cam.tiles_y;
     sl.bits = 32 + ilog2(std::max(sl.n_tiles, 1));
-    const int64_t n4 = (s.n + 3) / 4 * 4;
     const int nb = project_blocks(s.n);
-    GSR_CUDA(sl.rec.ensure(sizeof(GaussRec) * (size_t)std::max<int64_t>(s.n, 1)));
-    GSR_CUDA(sl.bin.ensure(sizeof(uint4) * (size_t)std::max<int64_t>(s.n, 1)));
-    GSR_CUDA(sl.ntiles.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(n4, 4)));
-    GSR_CUDA(sl.bsums.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
-    GSR_CUDA(sl.boffs.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
-    GSR_CUDA(sl.vsums.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
-    GSR_CUDA(sl.voffs.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
-    GSR_CUDA(sl.bsums2.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
-    GSR_CUDA(sl.boffs2.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
-    for (int k = 0; k < 2; ++k) {
-        GSR_CUDA(sl.dkeys[k].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(s.n, 1)));
-        GSR_CUDA(sl.dvals[k].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(s.n, 1)));
-    }
-    GSR_CUDA(sl.dscr.ensure(sort_scratch_bytes(std::max<int64_t>(s.n, 1))));
-    GSR_CUDA(sl.ranges.ensure(sizeof(uint2) * (size_t)sl.n_tiles));
-    GSR_CUDA(sl.order.ensure(sizeof(uint32_t) * (size_t)sl.n_tiles));
-    GSR_CUDA(sl.counters.ensure(sizeof(uint32_t) * kCntSlots));
+    GSR_CUDA(slot_reserve(sl, s.n, sl.n_tiles));
     uint32_t *cnt = static_cast<uint32_t *>(sl.counters.p);
     GSR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * kCntSlots, sl.stream));
     ProjectArgs a{};
@@ -591,6 +600,17 @@ gs_status gs_server_load_scene(gs_server *S, const gs_scene *scene, int32_t *sce
         }
     }
     std::lock_guard<std::mutex> g(S->mu);
+    // every slot sized for the largest scene and a 1920x1080 frame at the serving tile
+    // (larger frames still grow a slot on first use)
+    const int tiles_1080p = ((1920 + kServeTile - 1) / kServeTile) * ((1080 + kServeTile - 1) / kServeTile);
+    for (Slot &sl : S->slots) {
+        if (sl.req) continue;  // busy: it grows on its next admission if it has to
+        cudaError_t e = slot_reserve(sl, scene->n, tiles_1080p);
+        if (e != cudaSuccess) {
+            if (res.mem) cudaFree(res.mem);
+            return cuda_fail(e, "serving slot buffers");
+        }
+    }
     S->scenes.push_back(res);
     *scene_id = (int32_t)S->scenes.size() - 1;
     return GS_OK;
