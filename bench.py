@@ -690,7 +690,7 @@ def run_pipeline(args):
     scene = api.Scene.from_arrays(sc)
     out = api.alloc_outputs(W, H)
     stream = torch.cuda.Stream()
-    tile, batch, chunk, _ = ctx.autotune(scene, frames[0], out, iters=3, stream=stream)
+    tile, batch, chunk, _ = ctx.autotune(scene, frames[0], out, iters=10, stream=stream)
     for cam in frames:
         ctx.forward(scene, cam, out=out, tile=tile, batch=batch, chunk=chunk, stream=stream)
     capacity = int(ctx.stats(reset=True, stream=stream)["instances_max"] * 1.25) + 4096
@@ -827,7 +827,7 @@ def measure_render(args, name, ctx, stream, sc, cams, world, rank, local_rank, f
     # plain renders of every camera for the instance counts that size the graph
     tile, batch, chunk = args.tile, args.batch, args.chunk
     if not (tile and batch and chunk):
-        t, b, c, _ = ctx.autotune(scene, cams[0], out, iters=3, stream=stream)
+        t, b, c, _ = ctx.autotune(scene, cams[0], out, iters=10, stream=stream)
         tile, batch, chunk = tile or t, batch or b, chunk or c
     # the pair census runs the sequential pass (no list splitting), so its counts are
     # the method's own: pairs up to each pixel's stop

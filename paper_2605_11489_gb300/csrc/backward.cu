@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(32) k_composite_bwd(const BackwardArgs a)
         if (a.g_alpha) Tb -= a.g_alpha[p];
     }
     const uint32_t n_walk = __reduce_max_sync(0xffffffffu, last);
-    const float pxb = pixel_bias(px), pyb = pixel_bias(py);
+    const float pxb = block_px(px), pyb = block_py(py);
+    const int bx0 = px & ~7, by0 = py & ~3;  // the pixel's 8x4 block, as in the forward
 
     for (int64_t end = (int64_t)n_walk; end > 0; end -= kBwdBatch) {
         const int64_t beg = end - kBwdBatch > 0 ? end - kBwdBatch : 0;
@@ -119,7 +120,8 @@ __global__ void __launch_bounds__(32) k_composite_bwd(const BackwardArgs a)
             if (pos < last) {
                 const float4 r0 = s_rec[k].r0, r1 = s_rec[k].r1, r2 = s_rec[k].r2;
                 if (rect_contains(r2, (uint32_t)px, (uint32_t)py)) {
-                    const AlphaEval e = eval_alpha(r0, r1, r2, pxb, pyb);
+                    const float2 cb = block_centre(r0, r2, bx0, by0);  // the forward's exact arithmetic
+                    const AlphaEval e = eval_alpha(make_float4(cb.x, cb.y, r0.z, r0.w), r1, pxb, pyb);
                     if (e.al >= kAlphaMin) {
                         contrib = true;
                         const float al = e.al, om = 1.0f - al;

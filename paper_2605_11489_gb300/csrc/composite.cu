@@ -21,7 +21,9 @@
 // group of 32 records, each lane forms the mask of block pixels inside one
 // record's rectangle, and a warp-wide bit transpose of those masks gives each
 // lane the records whose rectangle holds its own pixel; it blends only these,
-// in order. No barrier
+// in order. While forming the masks each lane also rewrites its record's centre
+// in the warp's ring copy relative to the warp's block (block_centre), so a
+// pixel's offset from it is one subtraction of small numbers. No barrier
 // spans warps: a warp whose pixels are all saturated stops on its own. The
 // tile's list is read once per warp from L2 (DRAM once). Waits are bounded.
 //
@@ -102,11 +104,11 @@ __device__ __forceinline__ void tile_pixel(int tid, int tile_x, int tile_y, int 
 // One Gaussian record at one pixel (Eq. 2-4). Returns true when the pixel
 // stops (the record would take T below 1e-4; it is not blended).
 template <bool GRAD, bool STATE, bool COUNT = false, bool NRM = false>
-__device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float4 &r1, const float4 &r2, float pxb,
-                                      float pyb, uint32_t pos, const float4 *nrm = nullptr)
+__device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float4 &r1, const float4 &r2, float lx,
+                                      float ly, uint32_t pos, const float4 *nrm = nullptr)
 {
     if (COUNT) ++s.n_eval;
-    const AlphaEval e = eval_alpha(r0, r1, r2, pxb, pyb);
+    const AlphaEval e = eval_alpha(r0, r1, lx, ly);  // r0's centre relative to the block (block_centre)
     const float al = e.al;
     if (al < kAlphaMin) return false;
     const float om = __fsub_rn(1.0f, al);
@@ -201,7 +203,7 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
         }
     };
 
-    const float pxb = pixel_bias(px), pyb = pixel_bias(py);
+    const float lx = block_px(px), ly = block_py(py);
     bool ok = true;
 
     for (int b = 0; b < kStages - 1 && b < nbatches; ++b) issue(b);
@@ -209,6 +211,7 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
     const uint32_t first_tries = a.give_up ? 0u : kWaitTries;
     for (; b < nbatches; ++b) {
         const int buf = b % kStages;
+        __syncwarp();  // the lanes' writes of block centres into the slot precede its refill
         if (b + kStages - 1 < nbatches) issue(b + kStages - 1);
         if (!mbar_wait_bounded(&ring.bar[buf], phase[buf], first_tries)) ok = false;
         if (!__all_sync(0xffffffffu, ok)) {  // batch b is still in flight: drained below
@@ -217,7 +220,7 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
         }
         phase[buf] ^= 1u;
         const uint32_t cnt = min((uint32_t)BATCH, s1 - (s0 + (uint32_t)b * BATCH));
-        const GaussRec *recs = ring.rec[buf];
+        GaussRec *recs = ring.rec[buf];  // this warp's own staged copy
         const uint32_t pos_b = pos0 + (uint32_t)b * BATCH + 1u;
 #pragma unroll
         for (int w = 0; w < BATCH / 32; ++w) {
@@ -237,9 +240,14 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
                     const uint32_t xm = (0xFFu >> (7 - x1)) & (0xFFu << x0);
                     const uint32_t rows = (0xFu >> (3 - y1)) & (0xFu << y0);
                     cover = xm * ((rows & 1u) | ((rows & 2u) << 7) | ((rows & 4u) << 14) | ((rows & 8u) << 21));
+                    // the record's centre relative to this warp's block, once per record
+                    const float2 cb = block_centre(recs[kk].r0, recs[kk].r2, bx0, by0);
+                    recs[kk].r0.x = cb.x;
+                    recs[kk].r0.y = cb.y;
                 }
             }
             if (!__any_sync(0xffffffffu, cover != 0u)) continue;
+            __syncwarp();  // the block-relative centres are written before other lanes read them
             uint32_t mine = warp_transpose32(cover, lane);
             if (s.done) mine = 0u;
             if (mine) {  // the next record's loads are issued before the current one is blended
@@ -252,7 +260,7 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
                     mine &= mine - 1u;
                     const float4 b0 = recs[kn].r0, b1 = recs[kn].r1, b2 = recs[kn].r2;
                     if (blend<GRAD, STATE, COUNT, NRM>(
-                            s, a0, a1, a2, pxb, pyb, pos_b + k,
+                            s, a0, a1, a2, lx, ly, pos_b + k,
                             NRM ? a.nrm_sorted + (s0 + (uint32_t)b * BATCH + k) : nullptr)) {
                         s.done = true;
                         s.stopped = true;

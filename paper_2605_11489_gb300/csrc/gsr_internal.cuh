@@ -337,19 +337,28 @@ struct AlphaEval {
     float g;  // exp(-Q/2), the Gaussian's falloff before the opacity scales it
     bool capped;
 };
-// (pxb, pyb) = (2^23 + px, 2^23 + py) as floats (pixel_bias); the rectangle origin comes
-// from the record's rect_lo bits as 2^23 + x0 (one byte permute), so pxb - x0b = px - x0
-// exactly and d = (px - x0) - u' (see GaussRec).
-__device__ __forceinline__ float pixel_bias(int p) { return __uint_as_float(0x4B000000u | (uint32_t)p); }
-__device__ __forceinline__ AlphaEval eval_alpha(const float4 &r0, const float4 &r1, const float4 &r2, float pxb,
-                                                float pyb)
+// Compositing evaluates a record at the pixels of one 8x4 block of the absolute pixel grid
+// (a warp's block in the forward; the block of the pixel in the backward), with the centre
+// taken relative to the block's middle, (bx0 + 4, by0 + 2):
+//   c = u' + ((x0 - bx0) - 4, (y0 - by0) - 2)   (block_centre; u' of GaussRec, (x0, y0) its
+//                                                rectangle's first pixel)
+//   d = ((px - bx0) - 4, (py - by0) - 2) - c    (both small: c's rounding is ~1e-7 of it)
+// Blocks are the same for every tile size, so the image does not depend on it, bit for bit.
+__device__ __forceinline__ float2 block_centre(const float4 &r0, const float4 &r2, int bx0, int by0)
+{
+    const uint32_t lo = __float_as_uint(r2.z);
+    return make_float2(__fadd_rn(r0.x, (float)((int)(lo & 0xFFFFu) - bx0 - 4)),
+                       __fadd_rn(r0.y, (float)((int)(lo >> 16) - by0 - 2)));
+}
+// The pixel's place in its block, relative to the block's middle: exact small floats.
+__device__ __forceinline__ float block_px(int px) { return (float)((px & 7) - 4); }
+__device__ __forceinline__ float block_py(int py) { return (float)((py & 3) - 2); }
+// r0.x, r0.y: the block-relative centre (block_centre); (lx, ly) = (block_px, block_py).
+__device__ __forceinline__ AlphaEval eval_alpha(const float4 &r0, const float4 &r1, float lx, float ly)
 {
     AlphaEval e;
-    const uint32_t lo = __float_as_uint(r2.z);
-    const float x0b = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7610));
-    const float y0b = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7632));
-    e.dx = __fsub_rn(__fsub_rn(pxb, x0b), r0.x);
-    e.dy = __fsub_rn(__fsub_rn(pyb, y0b), r0.y);
+    e.dx = __fsub_rn(lx, r0.x);
+    e.dy = __fsub_rn(ly, r0.y);
     e.ex = __fmaf_rn(r0.z, e.dx, __fmul_rn(r0.w, e.dy));
     e.ey = __fmaf_rn(r0.w, e.dx, __fmul_rn(r1.x, e.dy));
     const float Q = __fmaf_rn(e.dx, e.ex, __fmul_rn(e.dy, e.ey));

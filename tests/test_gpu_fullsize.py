@@ -49,7 +49,7 @@ def _stream_frames(api, ctx, scene, cams, frames, config, slots=BENCH_SLOTS):
     s = torch.cuda.Stream()
     out = api.alloc_outputs(cams[0].width, cams[0].height)
     if config is None:
-        t, b, c, _ = ctx.autotune(scene, cams[0], out, iters=3, stream=s)
+        t, b, c, _ = ctx.autotune(scene, cams[0], out, iters=10, stream=s)
         config = (t, b, c)
     tile, batch, chunk = config
     for cam in cams:
