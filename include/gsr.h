@@ -95,12 +95,14 @@ typedef struct {
     int32_t batch;                /* Gaussians per shared-memory batch: 32/64/128/256; 0 = default */
     float bg[3];                  /* background colour */
     uint32_t flags;               /* GS_EMIT_* */
-    int32_t chunk;                /* records per later chunk of a split tile list: a list longer than
-                                     `head` is composited as a first chunk of `head` records, then
-                                     chunks of `chunk` records, in parallel, and merged exactly
-                                     (product rule of Eq. 2-4, stop rule re-applied where it falls
-                                     inside a chunk); 16..2^24, 0 = autotuned/default 512 */
-    int32_t head;                 /* records in a split list's first chunk, >= chunk; 0 = 4 * chunk */
+    int32_t chunk;                /* least records per chunk of a long tile list. A list longer than
+                                     `head` is composited by G warps per 8x4 pixel block (8 at tile
+                                     8, 2 at tile 16), one per depth-contiguous chunk of ceil(len / g)
+                                     records, g = min(G, ceil(len / chunk)), merged exactly (the
+                                     product rule of Eq. 2-4, the stop rule re-applied in the chunk
+                                     where it falls). 16..2^24, 0 = autotuned/default 512 */
+    int32_t head;                 /* a list longer than this is long, >= chunk; 0 = 4 * chunk.
+                                     At tile 32 no list is long. */
 } gs_render_opts;
 
 /* Caller-owned device outputs; a NULL plane is not written (and, for dcdx and
@@ -110,7 +112,7 @@ typedef struct {
  * normal is its shortest axis (the smallest of the fp32 log-scales, the first of equal
  * ones), turned to face the camera (n . (mean - camera centre) < 0), in camera
  * coordinates; normal = sum n_i a_i T_i, nv = -normal . (unit ray of the pixel centre).
- * Only gs_render_forward renders them, without splitting long tile lists; graphs, the
+ * Only gs_render_forward renders them, one warp per pixel block on every list; graphs, the
  * server, host outputs and GS_EMIT_BWD_STATE / GS_COUNT_PAIRS reject them. */
 typedef struct {
     float *rgb;    /* [3][H][W] */
@@ -250,7 +252,7 @@ gs_status gs_graph_destroy(gs_graph *graph);
 /* ---------------------------------------------------------------- autotuner
  * Times the forward for every tile in {8, 16, 32}, batch in {32, 64, 128, 256}
  * (pairs whose per-warp staging rings fit shared memory) and chunk in
- * {256, 512, 2048} (CUDA events, `iters` frames each, after one warm-up) and
+ * {256, 512, 1024} (CUDA events, `iters` frames each, after one warm-up) and
  * records the fastest in the context's cache, keyed by (W, H, N bucket, SH
  * degree); later calls with tile / batch / chunk = 0 use it. Synchronous.
  * Any output pointer may be NULL. */

@@ -360,149 +360,94 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
     for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(t)], 1u)] = (uint32_t)t;
 }
 
-// Compositing work plan. A tile whose list is longer than `head` is split into
-// depth-contiguous chunks: the first of `head` records, the others of `chunk`
-// (chunk_of / chunk_start / chunk_count); each chunk is a work item whose
-// per-pixel partial state goes to its own slot (a split tile's slots are
-// consecutive), and the split tile is finished front to back afterwards.
-// Items come in two waves, composited by two launches:
-//   wave A, items [0, n_tiles): the first chunk of every split tile (in split
-//     order), then the whole tiles, longest lists first;
-//   wave B, items [n_tiles, n_items): the later chunks, in slot order. They
-//     run after wave A, so they can leave out the pixels that already stopped
-//     in their tile's first chunk.
-//   items[i]       = (tile, start, end, slot | kWholeTile)
-//   split_tiles[s] = tile id of the s-th split tile, split_slot0[s] = its first slot
-//   slot_split[k]  = the split tile (index s) that slot k belongs to
-//   counts         = (n_items, n_split, n_slots, n_tiles = size of wave A)
-// One CTA; each warp takes 32 consecutive tiles at a time. A split tile gets
-// its split index and its slots from one packed counter, (splits << 32) +
-// slots, so that both come in the same order and the later chunks before a
-// tile's own number slot - split index. Whole tiles are bucketed by
-// floor(log2(length)), with one atomic per bucket and warp.
-// The plan's buffers hold max_split split tiles and max_slots slots, enough for
-// ranges that partition the K sorted instances. After a sort gave up
-// (kErrSortTimeout in *err) the ranges need not partition anything, so the plan
-// is left empty; and every write is checked against the capacities anyway: a
-// plan that would not fit is left empty with kErrCapacity set. Nothing is then
-// composited and the frame reports the error.
-__global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges, int n_tiles, uint32_t chunk,
-                                               uint32_t head, uint4 *__restrict__ items,
-                                               uint32_t *__restrict__ split_tiles,
-                                               uint32_t *__restrict__ split_slot0, uint32_t *__restrict__ slot_split,
-                                               uint32_t *__restrict__ counts, uint32_t *err, uint32_t max_split,
-                                               uint32_t max_slots)
-{
-    __shared__ unsigned long long s_alloc;  // (split tiles << 32) | slots handed out so far
-    __shared__ uint32_t s_bucket[33];       // whole tiles per bucket, then next free item per bucket
-    __shared__ bool s_skip;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
-    if (threadIdx.x == 0) {
-        s_alloc = 0ull;
-        s_skip = (*reinterpret_cast<volatile uint32_t *>(err) & kErrSortTimeout) != 0u;
-        if (s_skip) counts[0] = counts[1] = counts[2] = counts[3] = 0u;
-    }
-    if (threadIdx.x < 33) s_bucket[threadIdx.x] = 0u;
-    __syncthreads();
-    if (s_skip) return;
-    auto bucket_of = [](uint32_t len) { return len == 0 ? 32u : (uint32_t)__clz(len); };  // longer -> smaller
+// Compositing plan (one CTA). Every tile gets a bucket: the long tiles (list longer
+// than `head`) floor(log2(length)) in [0, 32), the others 32 + that (empty lists
+// last), so tile_order lists the long tiles first, each part longest first:
+// k_composite_long's CTAs take the long ones from the front, k_composite's the
+// others. plan = (n_long, 0 = the long tiles' work counter, n_short). Range loads
+// are issued four tiles per thread at a time; the bucket counts and cursors are
+// shared-memory atomics, one per bucket and warp (__match_any_sync). The order
+// within a bucket depends on the warps' timing, which no result depends on.
+constexpr int kPlanBuckets = 65;
+constexpr int kPlanUnroll = 4;
 
-    // pass 1: split tiles are placed; whole tiles are counted per bucket
-    for (int base = warp * 32; base < n_tiles; base += 1024) {
-        const int t = base + lane;
-        uint2 r = make_uint2(0u, 0u);
-        if (t < n_tiles) r = ranges[t];
-        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-        const uint32_t c = t < n_tiles ? chunk_count(len, head, chunk) : 0u;
-        const bool split = c > 1, whole = c == 1;
-        // split: exclusive prefix of slot counts over the warp's split lanes
-        const uint32_t smask = __ballot_sync(0xffffffffu, split);
-        uint32_t inc = split ? c : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += v;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
-        unsigned long long got = 0ull;
-        if (lane == 0 && smask)
-            got = atomicAdd(&s_alloc, ((unsigned long long)__popc(smask) << 32) | (unsigned long long)total);
-        got = __shfl_sync(0xffffffffu, got, 0);
-        if (split) {
-            const uint32_t sp = (uint32_t)(got >> 32) + (uint32_t)__popc(smask & lt);
-            const uint32_t slot = (uint32_t)(got & 0xffffffffull) + inc - c;
-            // written only if the whole tile fits (items hold n_tiles + max_slots entries)
-            if (sp < max_split && slot + c <= max_slots) {
-                split_tiles[sp] = (uint32_t)t;
-                split_slot0[sp] = slot;
-                items[sp] = make_uint4((uint32_t)t, r.x, r.x + head, slot);  // wave A: first chunk
-                const uint32_t later = (uint32_t)n_tiles + (slot - sp);      // wave B: later chunks before ours
-                for (uint32_t k = 0; k < c; ++k) {
-                    slot_split[slot + k] = sp;
-                    if (k == 0) continue;
-                    const uint32_t s0 = r.x + chunk_start(k, head, chunk);
-                    items[later + k - 1] = make_uint4((uint32_t)t, s0, min(r.y, s0 + chunk), slot + k);
-                }
-            }
-        }
-        const uint32_t b = whole ? bucket_of(len) : 64u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, b);
-        if (whole && lane == __ffs(peers) - 1) atomicAdd(&s_bucket[b], (uint32_t)__popc(peers));
-    }
+__device__ __forceinline__ uint32_t plan_bucket(uint2 r, uint32_t head)
+{
+    const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+    const uint32_t lg = len == 0 ? 32u : (uint32_t)__clz(len);  // longer -> smaller
+    return len > head ? lg : 32u + lg;
+}
+
+__global__ void __launch_bounds__(1024) k_plan(const uint2 *__restrict__ ranges, int n_tiles, uint32_t head,
+                                               uint32_t *__restrict__ order, uint32_t *__restrict__ plan,
+                                               const uint32_t *err)
+{
+    __shared__ uint32_t s_cnt[kPlanBuckets + 1];  // counts, then cursors; the last one is "no tile"
+    __shared__ bool s_skip;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    if (threadIdx.x == 0) s_skip = (*reinterpret_cast<const volatile uint32_t *>(err) & kErrSortTimeout) != 0u;
+    if (threadIdx.x <= kPlanBuckets) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
-    if ((uint32_t)(s_alloc >> 32) > max_split || (uint32_t)(s_alloc & 0xffffffffull) > max_slots) {
-        if (threadIdx.x == 0) {  // does not fit: nothing is composited, the frame reports it
-            counts[0] = counts[1] = counts[2] = counts[3] = 0u;
-            atomicOr(err, kErrCapacity);
-        }
+    if (s_skip) {
+        if (threadIdx.x < 3) plan[threadIdx.x] = 0u;
         return;
     }
-    if (threadIdx.x == 0) {
-        const uint32_t n_split = (uint32_t)(s_alloc >> 32), n_slots = (uint32_t)(s_alloc & 0xffffffffull);
-        uint32_t run = n_split;  // whole tiles follow the first chunks
-        for (int q = 0; q < 33; ++q) {
-            const uint32_t cnt = s_bucket[q];
-            s_bucket[q] = run;
-            run += cnt;
+    constexpr int kStride = 1024 * kPlanUnroll;
+    for (int base = threadIdx.x; base - (int)threadIdx.x < n_tiles; base += kStride) {
+        uint32_t bk[kPlanUnroll];
+#pragma unroll
+        for (int u = 0; u < kPlanUnroll; ++u) {
+            const int t = base + u * 1024;
+            bk[u] = t < n_tiles ? plan_bucket(ranges[t], head) : (uint32_t)kPlanBuckets;
         }
-        counts[0] = (uint32_t)n_tiles + n_slots - n_split;
-        counts[1] = n_split;
-        counts[2] = n_slots;
-        counts[3] = (uint32_t)n_tiles;
+#pragma unroll
+        for (int u = 0; u < kPlanUnroll; ++u) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, bk[u]);
+            if (bk[u] < (uint32_t)kPlanBuckets && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[bk[u]], __popc(peers));
+        }
     }
     __syncthreads();
-    // pass 2: whole tiles into their buckets
-    for (int base = warp * 32; base < n_tiles; base += 1024) {
-        const int t = base + lane;
-        uint2 r = make_uint2(0u, 0u);
-        if (t < n_tiles) r = ranges[t];
-        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-        const bool whole = t < n_tiles && chunk_count(len, head, chunk) == 1;
-        const uint32_t b = whole ? bucket_of(len) : 64u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, b);
-        const int leader = __ffs(peers) - 1;
-        uint32_t pos = 0;
-        if (whole && lane == leader) pos = atomicAdd(&s_bucket[b], (uint32_t)__popc(peers));
-        pos = __shfl_sync(0xffffffffu, pos, leader) + (uint32_t)__popc(peers & lt);
-        if (whole) items[pos] = make_uint4((uint32_t)t, r.x, r.x + len, kWholeTile);
+    if (threadIdx.x == 0) {
+        uint32_t run = 0, n_long = 0;
+        for (int q = 0; q < kPlanBuckets; ++q) {
+            const uint32_t c = s_cnt[q];
+            s_cnt[q] = run;
+            run += c;
+            if (q == 31) n_long = run;
+        }
+        plan[0] = n_long;
+        plan[1] = 0u;
+        plan[2] = (uint32_t)n_tiles - n_long;
+    }
+    __syncthreads();
+    for (int base = threadIdx.x; base - (int)threadIdx.x < n_tiles; base += kStride) {
+        uint32_t bk[kPlanUnroll];
+#pragma unroll
+        for (int u = 0; u < kPlanUnroll; ++u) {
+            const int t = base + u * 1024;
+            bk[u] = t < n_tiles ? plan_bucket(ranges[t], head) : (uint32_t)kPlanBuckets;
+        }
+#pragma unroll
+        for (int u = 0; u < kPlanUnroll; ++u) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, bk[u]);
+            const int leader = __ffs(peers) - 1;
+            uint32_t first = 0u;
+            if (bk[u] < (uint32_t)kPlanBuckets && lane == leader) first = atomicAdd(&s_cnt[bk[u]], __popc(peers));
+            first = __shfl_sync(0xffffffffu, first, leader);
+            if (bk[u] < (uint32_t)kPlanBuckets) order[first + __popc(peers & lt)] = (uint32_t)(base + u * 1024);
+        }
     }
 }
 
 }  // namespace
 
 // a split tile has > head >= chunk records and at most 2 + (len - head) / chunk slots
-int64_t plan_max_slots(int64_t max_k, int chunk) { return 3 * (max_k / chunk) + 2; }
-int64_t plan_max_items(int n_tiles, int64_t max_k, int chunk) { return n_tiles + plan_max_slots(max_k, chunk); }
-
-cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, int head, uint4 *items, uint32_t *split_tiles,
-                        uint32_t *split_slot0, uint32_t *slot_split, uint32_t *counts, uint32_t *err,
-                        int64_t max_split, int64_t max_slots, cudaStream_t s)
+cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int64_t head, uint32_t *order, uint32_t *plan,
+                        const uint32_t *err, cudaStream_t s)
 {
-    if (n_tiles <= 0) return cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 4, s);
-    k_plan<<<1, 1024, 0, s>>>(ranges, n_tiles, (uint32_t)chunk, (uint32_t)head, items, split_tiles, split_slot0,
-                              slot_split, counts, err, (uint32_t)std::min<int64_t>(max_split, 0xFFFFFFFFll),
-                              (uint32_t)std::min<int64_t>(max_slots, 0xFFFFFFFFll));
+    if (n_tiles <= 0) return cudaMemsetAsync(plan, 0, sizeof(uint32_t) * 3, s);
+    k_plan<<<1, 1024, 0, s>>>(ranges, n_tiles, (uint32_t)std::min<int64_t>(head, 0xFFFFFFFFll), order, plan, err);
     return cudaGetLastError();
 }
 

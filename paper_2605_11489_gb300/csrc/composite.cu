@@ -27,24 +27,27 @@
 // spans warps: a warp whose pixels are all saturated stops on its own. The
 // tile's list is read once per warp from L2 (DRAM once). Waits are bounded.
 //
-// Load balance: a tile whose list is longer than `chunk` records is split into
-// depth-contiguous chunks, one work item each, composited from the identity
-// state into per-pixel partial states (C, C_x, C_y, D, T, T_x, T_y). Two
-// segments a, b compose exactly as
+// Load balance. The plan (launch_plan) orders the tiles longest first and
+// separates the long ones (list longer than `head` records). k_composite takes
+// the short tiles, one CTA each. k_composite_long runs beside it on a second
+// stream: a persistent grid whose CTAs take long tiles from a counter, with G
+// warps per 8x4 pixel block (8 at tile 8, 2 at tile 16; at tile 32 no list is
+// long). Warp j of a block takes the j-th of g depth-contiguous chunks of the
+// list (g = min(G, ceil(len / chunk))) and composites it from the
+// identity state into a per-pixel partial state (C, C_x, C_y, D, T, T_x, T_y) in
+// shared memory. Two segments a, b compose exactly as
 //   C = Ca + Ta Cb,  C_x = Cxa + Txa Cb + Ta Cxb,  D = Da + Ta Db,
 //   T = Ta Tb,       T_x = Txa Tb + Ta Txb                     (product rule)
 // which equals the sequential result as long as no Gaussian of the tile was
 // cut off by the T < 1e-4 stop. T only decreases, so a pixel's stop falls in
 // chunk c exactly when c stopped locally or (prefix T) * (chunk T) < 1e-4.
-// Finishing a split tile takes two launches:
-//   k_rewalk: one pass per chunk, in parallel over all chunks. The lanes whose
-//     stop falls in this chunk fold the partial states in front of it into
-//     their exact prefix state and walk on from there through the same staged,
-//     masked warp pass, until they stop; they write their pixels.
-//   k_finish: one pass per split tile; every other pixel folds all chunks
-//     front to back and writes its result.
-// Both decide "stop in chunk c" from the same product chain of chunk T's, so
-// every pixel is written exactly once.
+// After one barrier, every warp follows that product chain for its pixels:
+//   - the warp of the chunk holding a pixel's stop folds the chunks in front
+//     of it into the exact prefix state and walks on from the chunk's start
+//     until the pixel stops (chunk 0 needs no walk: its state is exact);
+//   - the last chunk's warp writes the pixels that stop in no chunk, folding
+//     all chunks front to back;
+// so every pixel is written exactly once, by one warp, in one launch.
 #include "gsr_internal.cuh"
 #include <algorithm>
 
@@ -53,7 +56,7 @@ namespace {
 
 constexpr uint32_t kWaitTries = 1u << 22;
 constexpr int kStages = 3;
-constexpr int kPartialVals = 16;  // floats per pixel in a partial state
+constexpr int kPartialVals = 15;  // floats per pixel in a partial state
 constexpr int kMaxSmem = 227 * 1024;
 
 template <int BATCH>
@@ -328,36 +331,34 @@ __device__ __forceinline__ void write_final(const CompositeArgs &a, int px, int 
     }
 }
 
-// partial state of one pixel: planar [16][TILE*TILE] per slot, coalesced per value
-template <int TILE>
-__device__ __forceinline__ void write_partial(float *slot, int tid, const PixelAcc &s)
+// Partial state of one pixel over one chunk, in k_composite_long's shared memory:
+// planar [value][NT] per chunk (NT pixels of the tile), so a warp's 32 pixels
+// fall in 32 banks. Values: C[3], C_x[3], C_y[3], D, T, T_x, T_y, last, stopped.
+template <int NT>
+__device__ __forceinline__ void write_partial(float *part, int pix, const PixelAcc &s)
 {
-    constexpr int NT = TILE * TILE;
-    float v[kPartialVals] = {s.C[0], s.C[1], s.C[2], s.Cx[0], s.Cx[1], s.Cx[2], s.Cy[0], s.Cy[1], s.Cy[2],
-                             s.D, s.T, s.Tx, s.Ty, __uint_as_float(s.last), s.stopped ? 1.0f : 0.0f, 0.0f};
+    const float v[kPartialVals] = {s.C[0],  s.C[1], s.C[2], s.Cx[0], s.Cx[1], s.Cx[2], s.Cy[0],
+                                   s.Cy[1], s.Cy[2], s.D,   s.T,     s.Tx,    s.Ty,    __uint_as_float(s.last),
+                                   s.stopped ? 1.0f : 0.0f};
 #pragma unroll
-    for (int k = 0; k < kPartialVals; ++k) slot[k * NT + tid] = v[k];
+    for (int k = 0; k < kPartialVals; ++k) part[k * NT + pix] = v[k];
 }
 
-template <int TILE>
-__device__ __forceinline__ void read_partial(const float *slot, int tid, PixelAcc &q)
+template <int NT>
+__device__ __forceinline__ void read_partial(const float *part, int pix, PixelAcc &q)
 {
-    constexpr int NT = TILE * TILE;
-    float v[kPartialVals];
-#pragma unroll
-    for (int k = 0; k < kPartialVals; ++k) v[k] = slot[k * NT + tid];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        q.C[c] = v[c];
-        q.Cx[c] = v[3 + c];
-        q.Cy[c] = v[6 + c];
+        q.C[c] = part[c * NT + pix];
+        q.Cx[c] = part[(3 + c) * NT + pix];
+        q.Cy[c] = part[(6 + c) * NT + pix];
     }
-    q.D = v[9];
-    q.T = v[10];
-    q.Tx = v[11];
-    q.Ty = v[12];
-    q.last = __float_as_uint(v[13]);
-    q.stopped = v[14] != 0.0f;
+    q.D = part[9 * NT + pix];
+    q.T = part[10 * NT + pix];
+    q.Tx = part[11 * NT + pix];
+    q.Ty = part[12 * NT + pix];
+    q.last = __float_as_uint(part[13 * NT + pix]);
+    q.stopped = part[14 * NT + pix] != 0.0f;
 }
 
 // P <- P then Q (composition of two consecutive segments, product rule)
@@ -383,27 +384,16 @@ __device__ __forceinline__ void compose(PixelAcc &P, const PixelAcc &Q)
     if (STATE && Q.last) P.last = Q.last;
 }
 
+// The short tiles of the plan: CTA i composites tile_order[n_long + i], one warp
+// per 8x4 pixel block over the whole list.
 template <int TILE, int BATCH, bool GRAD, bool STATE, bool COUNT = false, bool NRM = false>
 __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t tile, s0, s1, slot = kWholeTile;
-    if (a.items) {
-        uint32_t idx = blockIdx.x;
-        if (a.wave == 1 && idx >= a.plan_counts[3]) return;
-        if (a.wave == 2) idx += a.plan_counts[3];
-        if (idx >= a.plan_counts[0]) return;
-        const uint4 it = a.items[idx];
-        tile = it.x;
-        s0 = it.y;
-        s1 = it.z;
-        slot = it.w;
-    } else {
-        tile = a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x;
-        const uint2 r = a.ranges[tile];
-        s0 = r.x;
-        s1 = r.y > r.x ? r.y : r.x;
-    }
+    if (blockIdx.x >= a.plan[2]) return;
+    const uint32_t tile = a.tile_order[a.plan[0] + blockIdx.x];
+    const uint2 r = a.ranges[tile];
+    const uint32_t s0 = r.x, s1 = r.y > r.x ? r.y : r.x;
     WarpRing<BATCH> &ring = reinterpret_cast<WarpRing<BATCH> *>(smem_raw)[threadIdx.x >> 5];
     ring_init(ring);
     uint32_t phase[kStages] = {};
@@ -413,16 +403,7 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
     const bool inside = px < a.width && py < a.height;
     PixelAcc s;
     acc_init(s, inside);
-    const uint32_t pos0 = s0 - a.ranges[tile].x;
-    // a later chunk (wave B) leaves out the pixels that stopped in the tile's
-    // first chunk: their stop is there, so no later partial state of theirs is read
-    bool skip = false;
-    if (slot != kWholeTile && pos0 >= (uint32_t)a.head) {
-        const uint32_t c = chunk_of(pos0, (uint32_t)a.head, (uint32_t)a.chunk);
-        skip = a.partial[(size_t)(slot - c) * kPartialVals * TILE * TILE + 14 * TILE * TILE + threadIdx.x] != 0.0f;
-        if (skip) s.done = true;
-    }
-    const bool ok = warp_span<BATCH, GRAD, STATE, COUNT, NRM>(a, px, py, bx0, by0, s0, s1, pos0, ring, phase, s);
+    const bool ok = warp_span<BATCH, GRAD, STATE, COUNT, NRM>(a, px, py, bx0, by0, s0, s1, 0u, ring, phase, s);
     if (!ok && (threadIdx.x & 31) == 0) atomicOr(a.err_word, kErrTmaTimeout);
     if (COUNT) {  // evaluated (inside a support rectangle) and blended pairs of this warp
         unsigned long long ne = s.n_eval, nb = s.n_blend;
@@ -436,130 +417,112 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
             atomicAdd(a.pair_counts + 1, nb);
         }
     }
-    if (slot == kWholeTile) {
-        if (inside) write_final<GRAD, STATE, NRM>(a, px, py, s);
-    } else if (!skip) {
-        write_partial<TILE>(a.partial + (size_t)slot * kPartialVals * TILE * TILE, threadIdx.x, s);
-    }
+    if (inside) write_final<GRAD, STATE, NRM>(a, px, py, s);
 }
 
-// Pixel `tid` of a split tile: does its stop fall in front of chunk c, in it,
-// or later? Follows the prefix product chain of the chunks' T exactly as the
-// fold in k_rewalk / k_finish does. Loads are issued four chunks at a time.
+// The long tiles of the plan (the load-balance note at the top): a persistent grid
+// whose CTAs take the next long tile from the plan's counter. Warp w owns pixel
+// block w % NB of the tile and chunk j = w / NB of its list; a tile of `len`
+// records has g = min(G, ceil(len / chunk)) chunks of ceil(len / g) records.
+// (Tried and slower on the 1M workload: a CTA per pixel block with 8, 12 or 16
+// chunk warps, and 16 chunk warps per block at tile 8.)
+constexpr int kLongBatch = 32;
 template <int TILE>
-__device__ __forceinline__ int stop_chunk_relation(const float *slot0, int tid, uint32_t c)
+__host__ __device__ constexpr int long_groups()  // G: warps per pixel block (16 warps per CTA)
 {
-    constexpr int NT = TILE * TILE;
-    constexpr size_t kSlot = (size_t)kPartialVals * NT;
-    float T = 1.0f;
-    for (uint32_t j0 = 0; j0 <= c; j0 += 4) {
-        float tj[4], sj[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const bool in = j0 + u <= c;
-            tj[u] = in ? slot0[(j0 + u) * kSlot + 10 * NT + tid] : 1.0f;
-            sj[u] = in ? slot0[(j0 + u) * kSlot + 14 * NT + tid] : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (j0 + u > c) break;
-            if (sj[u] != 0.0f || __fmul_rn(T, tj[u]) < kTMin) return j0 + u < c ? -1 : 0;
-            T = __fmul_rn(T, tj[u]);
-        }
-    }
-    return 1;  // -1: stop before c, 0: stop in c, 1: no stop up to and including c
+    return TILE == 8 ? 8 : 2;
+}
+template <int TILE>
+__host__ __device__ constexpr size_t long_smem_bytes()
+{
+    return sizeof(WarpRing<kLongBatch>) * (size_t)(TILE * TILE / 32) * long_groups<TILE>() +
+           sizeof(float) * kPartialVals * TILE * TILE * long_groups<TILE>();
 }
 
-// Split tiles, part 1 (one chunk per warp-item, all chunks in parallel): the
-// lanes whose stop falls in this chunk fold the partial states of the chunks
-// in front of it (exact prefix state), then walk the tile's records from the
-// chunk's start through the staged, masked warp pass until they stop, and
-// write their pixels. A lane whose walk ends the chunk without stopping (the
-// fold's product and the sequential one differ by rounding) walks on into the
-// next chunks, which continues the sequential pass exactly.
-template <int TILE, int BATCH, bool GRAD, bool STATE>
-__global__ void __launch_bounds__(TILE *TILE) k_rewalk(const CompositeArgs a)
+template <int TILE, bool GRAD, bool STATE>
+__global__ void __launch_bounds__(TILE *TILE *long_groups<TILE>()) k_composite_long(const CompositeArgs a)
 {
+    constexpr int NT = TILE * TILE, NB = NT / 32, G = long_groups<TILE>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int NT = TILE * TILE;
-    WarpRing<BATCH> &ring = reinterpret_cast<WarpRing<BATCH> *>(smem_raw)[threadIdx.x >> 5];
+    __shared__ uint32_t s_item;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t j = (uint32_t)(warp / NB);
+    const int pix = (warp % NB) * 32 + lane;  // the pixel's index in the tile, as k_composite's thread index
+    WarpRing<kLongBatch> &ring = reinterpret_cast<WarpRing<kLongBatch> *>(smem_raw)[warp];
+    // per chunk, planar [value][NT pixels]
+    float *const part = reinterpret_cast<float *>(smem_raw + sizeof(WarpRing<kLongBatch>) * NB * G);
     ring_init(ring);
     uint32_t phase[kStages] = {};
     bool ok = true;
-    const uint32_t n_slots = a.plan_counts[2];
-    const uint32_t chunk = (uint32_t)a.chunk;
-    for (uint32_t b = blockIdx.x; b < n_slots; b += gridDim.x) {
-        const uint32_t sp = a.slot_split[b];
-        const uint32_t tile = a.split_tiles[sp], first = a.split_slot0[sp];
+    const uint32_t n_long = a.plan[0];
+    const uint32_t chunk = (uint32_t)max(a.chunk, 1);
+    for (;;) {
+        __syncthreads();  // every warp is done with the previous tile's partial states
+        if (threadIdx.x == 0) s_item = atomicAdd(a.long_counter, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_long) break;
+        const uint32_t tile = a.tile_order[item];
         const uint2 r = a.ranges[tile];
-        const uint32_t c = b - first;
-        const uint32_t k0 = r.x + chunk_start(c, (uint32_t)a.head, chunk);
-        const float *slot0 = a.partial + (size_t)first * kPartialVals * NT;
+        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+        const uint32_t g = max(1u, min((uint32_t)G, (len + chunk - 1) / chunk));
+        const uint32_t cl = (len + g - 1) / g;
         const int tx = (int)(tile % (uint32_t)a.tiles_x), ty = (int)(tile / (uint32_t)a.tiles_x);
         int px, py, bx0, by0;
-        tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);
+        tile_pixel<TILE>(pix, tx, ty, px, py, bx0, by0);
         const bool inside = px < a.width && py < a.height;
-        const bool walk = inside && stop_chunk_relation<TILE>(slot0, threadIdx.x, c) == 0;
-        if (!__any_sync(0xffffffffu, walk)) continue;
-        PixelAcc P;
-        acc_init(P, walk);
-        if (c == 0) {  // the first chunk started from the identity: its partial state is exact
-            if (walk) {
-                read_partial<TILE>(slot0, threadIdx.x, P);
-                write_final<GRAD, STATE>(a, px, py, P);
-            }
-            continue;
-        }
-        if (walk && c > 0) {  // exact prefix state; the next chunk's loads overlap this fold
-            PixelAcc Qn;
-            read_partial<TILE>(slot0, threadIdx.x, Qn);
-            for (uint32_t j = 0; j < c; ++j) {
-                const PixelAcc Q = Qn;
-                if (j + 1 < c) read_partial<TILE>(slot0 + (size_t)(j + 1) * kPartialVals * NT, threadIdx.x, Qn);
-                compose<GRAD, STATE>(P, Q);
-            }
-        }
-        ok &= warp_span<BATCH, GRAD, STATE>(a, px, py, bx0, by0, k0, r.y, k0 - r.x, ring, phase, P);
-        if (walk) write_final<GRAD, STATE>(a, px, py, P);
-    }
-    if (!ok && (threadIdx.x & 31) == 0) atomicOr(a.err_word, kErrTmaTimeout);
-}
-
-// Split tiles, part 2 (one split tile per CTA): the pixels whose stop falls in
-// no chunk fold all chunks front to back and write their results; the next
-// chunk's partial state is loaded while the current one is folded.
-template <int TILE, bool GRAD, bool STATE>
-__global__ void __launch_bounds__(TILE *TILE) k_finish(const CompositeArgs a)
-{
-    constexpr int NT = TILE * TILE;
-    const uint32_t n_split = a.plan_counts[1];
-    const uint32_t chunk = (uint32_t)a.chunk;
-    for (uint32_t b = blockIdx.x; b < n_split; b += gridDim.x) {
-        const uint32_t tile = a.split_tiles[b];
-        const float *slot0 = a.partial + (size_t)a.split_slot0[b] * kPartialVals * NT;
-        const uint2 r = a.ranges[tile];
-        const uint32_t nch = chunk_count(r.y - r.x, (uint32_t)a.head, chunk);
-        const int tx = (int)(tile % (uint32_t)a.tiles_x), ty = (int)(tile / (uint32_t)a.tiles_x);
-        int px, py, bx0, by0;
-        tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);
-        if (px >= a.width || py >= a.height) continue;
-        PixelAcc P, Qn;
-        acc_init(P, true);
-        read_partial<TILE>(slot0, threadIdx.x, Qn);
-        bool stopped = false;
-        for (uint32_t c = 0; c < nch; ++c) {
-            const PixelAcc Q = Qn;
-            if (c + 1 < nch) read_partial<TILE>(slot0 + (size_t)(c + 1) * kPartialVals * NT, threadIdx.x, Qn);
-            if (Q.stopped || __fmul_rn(P.T, Q.T) < kTMin) {  // k_rewalk owns this pixel
-                stopped = true;
+        // phase 1: chunk j from the identity state
+        const uint32_t c0 = min(len, j * cl), c1 = min(len, c0 + cl);
+        PixelAcc s;
+        acc_init(s, inside && j < g);
+        if (j < g) ok &= warp_span<kLongBatch, GRAD, STATE>(a, px, py, bx0, by0, r.x + c0, r.x + c1, c0, ring, phase, s);
+        write_partial<NT>(part + (size_t)j * kPartialVals * NT, pix, s);
+        __syncthreads();
+        if (j >= g) continue;
+        // phase 2: the chunk holding the pixel's stop, from the product chain of the
+        // chunks' T (the same chain in every warp): -1 before j, 0 in j, 1 not up to j
+        int rel = 1;
+        float T = 1.0f;
+        for (uint32_t i = 0; i <= j; ++i) {
+            const float *pi = part + (size_t)i * kPartialVals * NT;
+            const float Ti = pi[10 * NT + pix];
+            if (pi[14 * NT + pix] != 0.0f || __fmul_rn(T, Ti) < kTMin) {
+                rel = i < j ? -1 : 0;
                 break;
             }
-            compose<GRAD, STATE>(P, Q);
+            T = __fmul_rn(T, Ti);
         }
-        if (!stopped) write_final<GRAD, STATE>(a, px, py, P);
+        if (inside && rel == 0 && j == 0) write_final<GRAD, STATE>(a, px, py, s);  // exact: from the identity
+        if (inside && rel == 1 && j == g - 1) {  // stops in no chunk: all chunks, front to back
+            PixelAcc P;
+            acc_init(P, true);
+            for (uint32_t i = 0; i < j; ++i) {
+                PixelAcc Q;
+                read_partial<NT>(part + (size_t)i * kPartialVals * NT, pix, Q);
+                compose<GRAD, STATE>(P, Q);
+            }
+            compose<GRAD, STATE>(P, s);
+            write_final<GRAD, STATE>(a, px, py, P);
+        }
+        // the stop falls in chunk j > 0: the exact prefix state, then a walk from the
+        // chunk's start until the pixel stops (on into later chunks if rounding has it
+        // stop later, which continues the sequential pass exactly)
+        const bool walk = inside && rel == 0 && j > 0;
+        if (__any_sync(0xffffffffu, walk)) {
+            PixelAcc P;
+            acc_init(P, walk);
+            if (walk)
+                for (uint32_t i = 0; i < j; ++i) {
+                    PixelAcc Q;
+                    read_partial<NT>(part + (size_t)i * kPartialVals * NT, pix, Q);
+                    compose<GRAD, STATE>(P, Q);
+                }
+            ok &= warp_span<kLongBatch, GRAD, STATE>(a, px, py, bx0, by0, r.x + c0, r.y, c0, ring, phase, P);
+            if (walk) write_final<GRAD, STATE>(a, px, py, P);
+        }
     }
+    if (!ok && lane == 0) atomicOr(a.err_word, kErrTmaTimeout);
 }
-
 // Serving: a persistent grid pulls (request, tile) items from a flat work list
 // described by per-request prefixes; every request's outputs and buffers are
 // its own. Items are handed out by an atomic counter (no waiting on anything).
@@ -640,14 +603,13 @@ cudaError_t launch_one(const CompositeArgs &a, unsigned nb, cudaStream_t s)
 }
 
 template <int TILE, int BATCH>
-cudaError_t launch_tb(const CompositeArgs &a, int64_t max_items, cudaStream_t s)
+cudaError_t launch_tb(const CompositeArgs &a, cudaStream_t s)
 {
     if constexpr (smem_bytes<TILE, BATCH>() > (size_t)kMaxSmem) {
         return cudaErrorInvalidValue;
     } else {
-        const unsigned nb = a.items ? (unsigned)max_items : (unsigned)(a.tiles_x * a.tiles_y);
+        const unsigned nb = (unsigned)(a.tiles_x * a.tiles_y);
         if (nb == 0) return cudaSuccess;
-        if (a.items && a.wave == 0) return cudaErrorInvalidValue;  // a plan runs as wave A, then wave B
         const bool grad = a.dcdx || a.dcdy;
         const bool state = a.final_T != nullptr;
         if (a.nrm_sorted) {  // the normal channel: no backward state, no census, whole tiles
@@ -666,43 +628,45 @@ cudaError_t launch_tb(const CompositeArgs &a, int64_t max_items, cudaStream_t s)
 }
 
 template <int TILE>
-cudaError_t launch_t(const CompositeArgs &a, int batch, int64_t max_items, cudaStream_t s)
+cudaError_t launch_t(const CompositeArgs &a, int batch, cudaStream_t s)
 {
     switch (batch) {
-    case 32: return launch_tb<TILE, 32>(a, max_items, s);
-    case 64: return launch_tb<TILE, 64>(a, max_items, s);
-    case 128: return launch_tb<TILE, 128>(a, max_items, s);
-    default: return launch_tb<TILE, 256>(a, max_items, s);
+    case 32: return launch_tb<TILE, 32>(a, s);
+    case 64: return launch_tb<TILE, 64>(a, s);
+    case 128: return launch_tb<TILE, 128>(a, s);
+    default: return launch_tb<TILE, 256>(a, s);
     }
 }
 
-// Grid of the split-tile passes: enough CTAs to fill the GPU a few times over,
-// each looping over its share of the (device-side counted) work.
-constexpr int64_t kMergeGridMax = 152 * 12;
+// CTAs of k_composite_long per SM (two of its 16-warp CTAs leave room for the short tiles' CTAs)
+constexpr int kLongCtasPerSm = 2;
 
 template <int TILE, bool GRAD, bool STATE>
-cudaError_t launch_merge_one(const CompositeArgs &a, int64_t max_split, int64_t max_slots, cudaStream_t s)
+cudaError_t launch_long_one(const CompositeArgs &a, int64_t max_long, cudaStream_t s)
 {
-    constexpr size_t smem = smem_bytes<TILE, 32>();
+    constexpr size_t smem = long_smem_bytes<TILE>();
     static bool done[64];
-    cudaError_t e = opt_in_smem(k_rewalk<TILE, 32, GRAD, STATE>, smem, done);
+    cudaError_t e = opt_in_smem(k_composite_long<TILE, GRAD, STATE>, smem, done);
     if (e != cudaSuccess) return e;
-    k_rewalk<TILE, 32, GRAD, STATE><<<(unsigned)std::min(max_slots, kMergeGridMax), TILE * TILE, smem, s>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_finish<TILE, GRAD, STATE><<<(unsigned)std::min(max_split, kMergeGridMax), TILE * TILE, 0, s>>>(a);
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(max_long, (int64_t)std::max(sms, 1) * kLongCtasPerSm);
+    if (grid <= 0) return cudaSuccess;
+    k_composite_long<TILE, GRAD, STATE><<<(unsigned)grid, TILE * TILE * long_groups<TILE>(), smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int TILE>
-cudaError_t launch_merge_t(const CompositeArgs &a, int64_t max_split, int64_t max_slots, cudaStream_t s)
+cudaError_t launch_long_t(const CompositeArgs &a, int64_t max_long, cudaStream_t s)
 {
+    static_assert(long_smem_bytes<TILE>() <= (size_t)kMaxSmem, "k_composite_long must fit shared memory");
     const bool grad = a.dcdx || a.dcdy;
     const bool state = a.final_T != nullptr;
-    if (grad && state) return launch_merge_one<TILE, true, true>(a, max_split, max_slots, s);
-    if (grad) return launch_merge_one<TILE, true, false>(a, max_split, max_slots, s);
-    if (state) return launch_merge_one<TILE, false, true>(a, max_split, max_slots, s);
-    return launch_merge_one<TILE, false, false>(a, max_split, max_slots, s);
+    if (grad && state) return launch_long_one<TILE, true, true>(a, max_long, s);
+    if (grad) return launch_long_one<TILE, true, false>(a, max_long, s);
+    if (state) return launch_long_one<TILE, false, true>(a, max_long, s);
+    return launch_long_one<TILE, false, false>(a, max_long, s);
 }
 
 template <int TILE>
@@ -730,35 +694,28 @@ bool composite_supported(int tile, int batch)
     return bytes <= (size_t)kMaxSmem;
 }
 
-cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, int64_t max_a, int64_t max_b,
-                             cudaStream_t s)
+cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, cudaStream_t s)
 {
     if (a.tiles_x == 0 || a.tiles_y == 0) return cudaSuccess;
-    auto one = [&](const CompositeArgs &w, int64_t n) {
-        switch (tile) {
-        case 8: return launch_t<8>(w, batch, n, s);
-        case 16: return launch_t<16>(w, batch, n, s);
-        default: return launch_t<32>(w, batch, n, s);
-        }
-    };
-    if (!a.items) return one(a, 0);
-    CompositeArgs w = a;
-    w.wave = 1;
-    cudaError_t e = one(w, max_a);
-    if (e != cudaSuccess) return e;
-    w.wave = 2;
-    return max_b > 0 ? one(w, max_b) : cudaSuccess;
-}
-
-cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, int64_t max_slots, cudaStream_t s)
-{
-    if (!a.items || max_split <= 0 || max_slots <= 0) return cudaSuccess;
     switch (tile) {
-    case 8: return launch_merge_t<8>(a, max_split, max_slots, s);
-    case 16: return launch_merge_t<16>(a, max_split, max_slots, s);
-    default: return launch_merge_t<32>(a, max_split, max_slots, s);
+    case 8: return launch_t<8>(a, batch, s);
+    case 16: return launch_t<16>(a, batch, s);
+    default: return launch_t<32>(a, batch, s);
     }
 }
+
+cudaError_t launch_composite_long(const CompositeArgs &a, int tile, int64_t max_long, cudaStream_t s)
+{
+    if (a.tiles_x == 0 || a.tiles_y == 0 || max_long <= 0) return cudaSuccess;
+    if (a.nrm_sorted || a.pair_counts) return cudaErrorInvalidValue;  // those frames have no long tiles
+    switch (tile) {
+    case 8: return launch_long_t<8>(a, max_long, s);
+    case 16: return launch_long_t<16>(a, max_long, s);
+    default: return cudaSuccess;
+    }
+}
+
+bool composite_long_supported(int tile) { return tile == 8 || tile == 16; }
 
 int composite_persistent_grid(int tile, int batch)
 {

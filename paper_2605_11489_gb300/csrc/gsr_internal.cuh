@@ -166,17 +166,13 @@ struct CompositeArgs {
     float *final_T, *final_Tx, *final_Ty;  // backward state (nullable)
     uint32_t *n_contrib;
     uint32_t *err_word;
-    const uint32_t *tile_order;  // tiles by decreasing list length (nullable = row-major)
-    // work plan (nullable: then one CTA per whole tile, in tile_order)
-    const uint4 *items;            // (tile, start, end, slot | kWholeTile)
-    const uint32_t *plan_counts;   // (n_items, n_split, n_slots, size of wave A)
-    const uint32_t *split_tiles;   // split tile ids
-    const uint32_t *split_slot0;   // first slot of each split tile
-    const uint32_t *slot_split;    // split tile index of each slot
-    int32_t wave;                  // items launched: 0 all, 1 wave A, 2 wave B
-    float *partial;                // [slot][16][TILE*TILE] per-pixel partial state of chunks
-    int32_t chunk;                 // records per later chunk of a split tile
-    int32_t head;                  // records in a split tile's first chunk (>= chunk)
+    // compositing plan (launch_plan): tile_order lists the long tiles (list > head records)
+    // first, then the others, each part longest first; plan = (n_long, long-tile work
+    // counter, n_short)
+    const uint32_t *tile_order;
+    const uint32_t *plan;
+    uint32_t *long_counter;        // plan + 1, handed out by k_composite_long's CTAs
+    int32_t chunk;                 // least records per chunk of a long tile
     unsigned long long *pair_counts;  // (evaluated, blended) pairs: the GS_COUNT_PAIRS census (nullable)
     // normal channel (nullable: the normal variant runs only when nrm_sorted is set, whole tiles only)
     const float4 *nrm_sorted;      // normals in sorted (instance) order, like rec
@@ -185,42 +181,28 @@ struct CompositeArgs {
     uint32_t give_up;              // diagnostic: each warp's first batch wait gives up without polling
                                    // (kErrTmaTimeout), then waits for its copies in flight
 };
-constexpr uint32_t kWholeTile = 0xFFFFFFFFu;
-// A tile list longer than `head` records (default kHeadChunks * chunk) is split
-// into a first chunk of `head` records and later chunks of `chunk` records.
-// Most pixels that saturate do so within the first records of a long list, so
-// a long first chunk lets the later chunks leave those pixels out.
+// Long tile lists. A list longer than `head` records (default kHeadChunks * chunk)
+// is composited by k_composite_long: G warps per 8x4 pixel block (8 at tile 8, 2 at
+// tile 16), each taking one of g = min(G, ceil(len / chunk)) depth-contiguous
+// chunks, merged exactly in shared memory. Shorter lists, and every list at tile
+// 32, take one warp per block (k_composite).
 constexpr int kHeadChunks = 4;
-// chunk index of list position `pos`, first position of chunk c, chunks of a list of `len`
-__host__ __device__ inline uint32_t chunk_of(uint32_t pos, uint32_t head, uint32_t chunk)
-{
-    return pos < head ? 0u : 1u + (pos - head) / chunk;
-}
-__host__ __device__ inline uint32_t chunk_start(uint32_t c, uint32_t head, uint32_t chunk)
-{
-    return c == 0 ? 0u : head + (c - 1) * chunk;
-}
-__host__ __device__ inline uint32_t chunk_count(uint32_t len, uint32_t head, uint32_t chunk)
-{
-    return len > head ? 1u + (len - head + chunk - 1) / chunk : 1u;
-}
-int64_t plan_max_slots(int64_t max_k, int chunk);
-int64_t plan_max_items(int n_tiles, int64_t max_k, int chunk);
-// The plan holds at most max_split split tiles and max_slots slots (frame_plan's sizes);
-// it is left empty after a sort timeout or when it would not fit (kErrCapacity in *err).
-cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int chunk, int head, uint4 *items, uint32_t *split_tiles,
-                        uint32_t *split_slot0, uint32_t *slot_split, uint32_t *counts, uint32_t *err,
-                        int64_t max_split, int64_t max_slots, cudaStream_t s);
-// merge of split tiles' chunks (after launch_composite with a plan)
-cudaError_t launch_merge(const CompositeArgs &a, int tile, int64_t max_split, int64_t max_slots, cudaStream_t s);
-// order tiles by decreasing list length (power-of-two buckets)
+// Plan of a frame's compositing: tile_order = the long tiles, then the others, each
+// part bucketed by floor(log2(length)), longest first; plan = (n_long, 0, n_short).
+// After a sort timeout (kErrSortTimeout in *err) nothing is planned (n_long = n_short
+// = 0): the ranges need not partition anything, and the frame reports the error.
+cudaError_t launch_plan(const uint2 *ranges, int n_tiles, int64_t head, uint32_t *order, uint32_t *plan,
+                        const uint32_t *err, cudaStream_t s);
+// order tiles by decreasing list length (power-of-two buckets), for the serving kernel
 cudaError_t launch_tile_order(const uint2 *ranges, int n_tiles, uint32_t *order, cudaStream_t s);
 bool composite_supported(int tile, int batch);
-// grid: one CTA per work item (bounded by max_items when a plan is given), else per tile
-// With a work plan (a.items): wave A over up to `max_a` items, then wave B over
-// up to `max_b`; without one: one CTA per tile.
-cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, int64_t max_a, int64_t max_b,
-                             cudaStream_t s);
+// The short tiles of a plan: one CTA per tile (grid n_tiles, CTAs past n_short exit).
+cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, cudaStream_t s);
+// The long tiles of a plan, up to max_long of them: a persistent grid of CTAs that take
+// tiles from the plan's work counter. No-op at tile 32 (its plan has no long tiles).
+cudaError_t launch_composite_long(const CompositeArgs &a, int tile, int64_t max_long, cudaStream_t s);
+// long tiles are composited apart at tile 8 and 16
+bool composite_long_supported(int tile);
 
 // serving: tiles of several requests from one (request, tile) work list
 struct ServeItem {  // one request's compositing description (device copy)

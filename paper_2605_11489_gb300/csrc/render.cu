@@ -75,6 +75,31 @@ struct Buf {
     T *as() const { return reinterpret_cast<T *>(p); }
 };
 
+// A second stream and its fork / join events: the long tiles are composited on it,
+// beside the short ones on the launch stream (also inside a graph capture, where
+// the events make the fork and join edges).
+struct ForkJoin {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ForkJoin() = default;
+    ForkJoin(const ForkJoin &) = delete;
+    ForkJoin &operator=(const ForkJoin &) = delete;
+    ~ForkJoin()
+    {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (s) cudaStreamDestroy(s);
+    }
+    cudaError_t ensure()
+    {
+        cudaError_t e = cudaSuccess;
+        if (!s && (e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if (!fork && (e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if (!join && (e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming)) != cudaSuccess) return e;
+        return e;
+    }
+};
+
 // All per-frame device buffers. Owned by a context (pooled), a state or a graph.
 struct Frame {
     Buf rec, bin, ntiles, bsums, boffs;
@@ -82,10 +107,11 @@ struct Frame {
     Buf dkeys[2], dvals[2], vsums, voffs, bsums2, boffs2;  // depth order of the visible Gaussians
     Buf keys64;                                     // (tile << 32 | depth bits) per instance, for a state view
     Buf ranges, order;
-    Buf items, split_tiles, split_slot0, slot_split, plan_counts, partial;  // compositing work plan
-    int chunk = 2048;
-    int head = 4 * 2048;  // records in a split list's first chunk
-    int64_t max_items = 0, max_split = 0, max_slots = 0;
+    Buf plan;             // (n_long, long-tile work counter, n_short): launch_plan
+    int chunk = 512;      // least records per chunk of a long tile list
+    int head = 4 * 512;   // a list longer than this is a long tile
+    int64_t max_long = 0; // long tiles the frame's capacity allows (0: none composited apart)
+    ForkJoin fork;        // the long tiles' stream beside the launch stream
     Buf fT, fTx, fTy, ncontrib;
     Buf nrm, nrm_sorted;  // the normal channel: per Gaussian, then in sorted (instance) order
     bool want_nrm = false;
@@ -354,8 +380,9 @@ gs_status frame_setup(Frame *f, const gs_scene *s, const gs_camera *c, const gs_
     f->tile = tile;
     f->batch = batch;
     if (chunk < 16 || chunk > (1 << 24)) return fail(GS_ERR_INVALID_ARG, "chunk must be 0 or 16..2^24");
-    const int64_t head = o->head ? (int64_t)o->head : (int64_t)kHeadChunks * chunk;
+    int64_t head = o->head ? (int64_t)o->head : (int64_t)kHeadChunks * chunk;
     if (head < chunk || head > (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "head must be 0 or chunk..2^30");
+    if (!composite_long_supported(tile)) head = 1ll << 30;  // tile 32: every list takes one warp per block
     f->chunk = chunk;
     f->head = (int)head;
     f->want_nrm = false;
@@ -407,24 +434,17 @@ gs_status frame_keys(Frame *f, int64_t cap)
     return GS_OK;
 }
 
-// Work-plan buffers for up to `cap` instances at the frame's tile size and
-// tile count (see plan_max_slots for the slot bound).
+// Plan and sort buffers for up to `cap` instances. At most cap / (head + 1) tiles
+// have lists longer than head.
 gs_status frame_plan(Frame *f, int64_t cap)
 {
-    const int64_t slots = plan_max_slots(cap, f->chunk);
-    f->max_slots = slots;
-    f->max_items = plan_max_items(f->n_tiles, cap, f->chunk);
-    f->max_split = std::min<int64_t>(f->n_tiles, cap / f->head + 1);
-    GSR_CUDA(f->items.ensure(sizeof(uint4) * (size_t)f->max_items));
-    GSR_CUDA(f->split_tiles.ensure(sizeof(uint32_t) * (size_t)f->max_split));
-    GSR_CUDA(f->split_slot0.ensure(sizeof(uint32_t) * (size_t)f->max_split));
-    GSR_CUDA(f->slot_split.ensure(sizeof(uint32_t) * (size_t)slots));
-    GSR_CUDA(f->plan_counts.ensure(sizeof(uint32_t) * 4));
+    f->max_long = f->head >= (1 << 30) ? 0 : std::min<int64_t>(f->n_tiles, cap / ((int64_t)f->head + 1) + 1);
+    GSR_CUDA(f->plan.ensure(sizeof(uint32_t) * 3));
+    if (f->max_long > 0) GSR_CUDA(f->fork.ensure());
     if (f->has_state) GSR_CUDA(f->keys64.ensure(sizeof(uint64_t) * (size_t)std::max<int64_t>(cap, 1)));
     // one scratch serves both sorts (they run one after the other): sized for
     // the larger of the instance capacity and the Gaussian count
     GSR_CUDA(f->sort_scr.ensure(sort_scratch_bytes(std::max<int64_t>(std::max<int64_t>(cap, f->n), 1))));
-    GSR_CUDA(f->partial.ensure(sizeof(float) * 16 * (size_t)f->tile * f->tile * (size_t)slots));
     return GS_OK;
 }
 
@@ -475,14 +495,9 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
     c.err_word = f->err_word ? f->err_word : f->counters.as<uint32_t>() + kCntErr;
     c.give_up = f->give_up ? 1u : 0u;
     c.tile_order = f->order.as<uint32_t>();
-    c.items = f->items.as<uint4>();
-    c.plan_counts = f->plan_counts.as<uint32_t>();
-    c.split_tiles = f->split_tiles.as<uint32_t>();
-    c.split_slot0 = f->split_slot0.as<uint32_t>();
-    c.slot_split = f->slot_split.as<uint32_t>();
-    c.partial = f->partial.as<float>();
+    c.plan = f->plan.as<uint32_t>();
+    c.long_counter = f->plan.as<uint32_t>() + 1;
     c.chunk = f->chunk;
-    c.head = f->head;
     if (f->count_pairs) c.pair_counts = reinterpret_cast<unsigned long long *>(f->counters.as<uint32_t>() + kCntPairs);
     if (f->want_nrm) {
         c.nrm_sorted = f->nrm_sorted.as<float4>();
@@ -537,13 +552,18 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
                            f->has_state ? f->keys64.as<uint64_t>() : nullptr, st,
                            f->want_nrm ? f->nrm.as<float4>() : nullptr,
                            f->want_nrm ? f->nrm_sorted.as<float4>() : nullptr));
-    GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->chunk, f->head, f->items.as<uint4>(),
-                         f->split_tiles.as<uint32_t>(), f->split_slot0.as<uint32_t>(), f->slot_split.as<uint32_t>(),
-                         f->plan_counts.as<uint32_t>(), err, f->max_split, f->max_slots, st));
+    GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->head, f->order.as<uint32_t>(),
+                         f->plan.as<uint32_t>(), err, st));
     GSR_CUDA(mark(mk, 7, st));
     const CompositeArgs ca = comp_args(f, out);
-    GSR_CUDA(launch_composite(ca, f->tile, f->batch, f->n_tiles, f->max_slots, st));
-    GSR_CUDA(launch_merge(ca, f->tile, f->max_split, f->max_slots, st));
+    if (f->max_long > 0) {  // long tiles on the second stream, beside the short ones
+        GSR_CUDA(cudaEventRecord(f->fork.fork, st));
+        GSR_CUDA(cudaStreamWaitEvent(f->fork.s, f->fork.fork, 0));
+        GSR_CUDA(launch_composite_long(ca, f->tile, f->max_long, f->fork.s));
+        GSR_CUDA(cudaEventRecord(f->fork.join, f->fork.s));
+    }
+    GSR_CUDA(launch_composite(ca, f->tile, f->batch, st));
+    if (f->max_long > 0) GSR_CUDA(cudaStreamWaitEvent(st, f->fork.join, 0));
     GSR_CUDA(mark(mk, 8, st));
     return GS_OK;
 }
@@ -569,8 +589,8 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
         return fail(GS_ERR_INVALID_ARG, "tile must be 8/16/32 and batch 32/64/128/256 with the warps' staging rings "
                                         "fitting shared memory");
     const bool state = (o->flags & GS_EMIT_BWD_STATE) != 0;
-    // the normal channel composites whole tile lists: its partial states would not fit the
-    // split-tile slots, so no list is split (first chunk 2^30 records)
+    // the normal channel composites every list with one warp per block (the long tiles'
+    // partial states keep no normal), so no list counts as long (head 2^30 records)
     const bool nrm = out->normal || out->nv;
     if (nrm && (o->flags & (GS_EMIT_BWD_STATE | GS_COUNT_PAIRS)))
         return fail(GS_ERR_INVALID_ARG, "the normal channel is rendered without GS_EMIT_BWD_STATE and GS_COUNT_PAIRS");
@@ -579,6 +599,8 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
         chunk = 1 << 24;
         on.head = 1 << 30;
     }
+    // the pair census counts the sequential pass: every list takes one warp per block
+    if (o->flags & GS_COUNT_PAIRS) on.head = 1 << 30;
     gs_status r = frame_setup(f, s, c, &on, tile, batch, chunk, state);
     f->count_pairs = (o->flags & GS_COUNT_PAIRS) != 0;
     if (r != GS_OK) return r;
@@ -644,9 +666,11 @@ gs_status context_warp_scratch(gs_context *ctx, size_t n_src, size_t n_dst, cuda
                                unsigned long long **best)
 {
     GSR_CUDA(ctx->warp_pos.ensure(sizeof(float2) * std::max<size_t>(n_src, 1)));
-    void *old = ctx->warp_best.p;
+    // a reallocation always grows the capacity (it may return the freed address again,
+    // so the pointer alone does not show it)
+    const size_t old_bytes = ctx->warp_best.bytes;
     GSR_CUDA(ctx->warp_best.ensure(sizeof(unsigned long long) * std::max<size_t>(n_dst, 1)));
-    if (ctx->warp_best.p != old || !ctx->warp_best_clean) {
+    if (ctx->warp_best.bytes != old_bytes || !ctx->warp_best_clean) {
         // every slot starts empty; the gather kernel leaves it so after each call
         GSR_CUDA(cudaMemsetAsync(ctx->warp_best.p, 0xFF, ctx->warp_best.bytes, st));
         ctx->warp_best_clean = true;
@@ -1109,7 +1133,7 @@ gs_status gs_autotune(gs_context *ctx, const gs_scene *scene, const gs_camera *c
     cudaEvent_t e0, e1;
     GSR_CUDA(cudaEventCreate(&e0));
     GSR_CUDA(cudaEventCreate(&e1));
-    const int tiles[3] = {8, 16, 32}, batches[4] = {32, 64, 128, 256}, chunks[3] = {256, 512, 2048};
+    const int tiles[3] = {8, 16, 32}, batches[4] = {32, 64, 128, 256}, chunks[3] = {256, 512, 1024};
     float best = 1e30f;
     int bt = kDefaultTile, bb = kDefaultBatch, bc = kDefaultChunk;
     for (int t : tiles)

@@ -149,11 +149,12 @@ def _dense_scene(n, seed, opaque=False):
 @pytest.mark.parametrize("chunk", [16, 64])
 @pytest.mark.parametrize("opaque", [False, True])
 def test_split_tiles_exact_merge(env, opaque, chunk):
-    """Chunked compositing of long tile lists (a first chunk of 4 * chunk
-    records, later chunks of `chunk`) against the unsplit pass and the oracle;
-    with opaque Gaussians the T < 1e-4 stop falls inside first and later
-    chunks: later chunks leave out pixels that stopped in the first, and a
-    later chunk holding a stop is re-walked from the exact prefix state."""
+    """Long tile lists (longer than head = 4 * chunk records) composited in
+    depth-contiguous chunks by several warps per 8x4 pixel block (g = min(G,
+    len / chunk) chunks, G = 8 at tile 8 and 2 at tile 16) and merged in shared
+    memory, against the unsplit pass and the oracle; with
+    opaque Gaussians the T < 1e-4 stop falls inside first and later chunks, and
+    a chunk holding a pixel's stop is re-walked from the exact prefix state."""
     api, O, ctx = env
     sc = _dense_scene(3000, 21 + opaque, opaque)
     cam = synth.tiny_camera(128, 96)

@@ -116,7 +116,7 @@ def test_autotune_picks_a_supported_config_and_caches_it(env):
     scene = api.Scene.from_arrays(sc)
     out = api.alloc_outputs(cam.width, cam.height)
     t, b, k, ms = ctx.autotune(scene, cam, out, iters=2)
-    assert t in (8, 16, 32) and b in (32, 64, 128, 256) and k in (256, 512, 2048) and ms > 0
+    assert t in (8, 16, 32) and b in (32, 64, 128, 256) and k in (256, 512, 1024) and ms > 0
     # tile = 0 / batch = 0 / chunk = 0 now resolve to the tuned choice
     o1 = ctx.forward(scene, cam)
     o2 = ctx.forward(scene, cam, tile=t, batch=b, chunk=k)
