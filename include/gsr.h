@@ -112,8 +112,13 @@ typedef struct {
  * normal is its shortest axis (the smallest of the fp32 log-scales, the first of equal
  * ones), turned to face the camera (n . (mean - camera centre) < 0), in camera
  * coordinates; normal = sum n_i a_i T_i, nv = -normal . (unit ray of the pixel centre).
- * Only gs_render_forward renders them, one warp per pixel block on every list; graphs, the
- * server, host outputs and GS_EMIT_BWD_STATE / GS_COUNT_PAIRS reject them. */
+ * depth_isect: RaDe-GS's ray-Gaussian intersection depth (Sec. 5.1). In the EWA ray space
+ * (u, v, z) of the projection (the same clamped Jacobian J), the densest point of Gaussian i
+ * along the ray of pixel p is the mean of z given (u, v) = p, affine in p:
+ *   z_i(p) = z_i + Sigma_{z,uv} (J W Sigma W^T J^T + 0.3 I)^-1 (p - mu2D_i),
+ * Sigma_{z,uv} the covariance of camera z with (u, v); depth_isect = sum z_i(p) a_i T_i.
+ * Only gs_render_forward renders these three, one warp per pixel block on every list;
+ * graphs, the server, host outputs and GS_EMIT_BWD_STATE / GS_COUNT_PAIRS reject them. */
 typedef struct {
     float *rgb;    /* [3][H][W] */
     float *dcdx;   /* [3][H][W]  dI/dx, Eq. 3 */
@@ -122,6 +127,7 @@ typedef struct {
     float *alpha;  /* [H][W]     1 - T_final */
     float *normal; /* [3][H][W]  sum n_i a_i T_i, camera coordinates */
     float *nv;     /* [H][W]     -normal . ray */
+    float *depth_isect; /* [H][W] sum z_i(p) a_i T_i, the intersection depth (above) */
 } gs_outputs;
 
 /* Per-parameter gradients, same layout and stride as gs_scene (caller-owned,

@@ -68,7 +68,7 @@ def lib():
             L.or_render.argtypes = [P, P, C.c_int] + [P] * 10
             L.or_render_pixels.argtypes = [P, P, C.c_int64, P, P, P, P, P, P]
             L.or_render_band.argtypes = [P, P, C.c_int, C.c_int, P, P, P, P, P]
-            L.or_render_normals.argtypes = [P, P, P, P, P, P, P]
+            L.or_render_normals.argtypes = [P, P, P, P, P, P, P, P]
             L.or_count_instances.restype = C.c_int64
             L.or_count_instances.argtypes = [P, P, C.c_int32]
             L.or_keys.argtypes = [P, P, C.c_int32, C.c_int64, P, P, P]
@@ -190,14 +190,18 @@ def render_normals(scene, cam) -> dict:
     - alpha [H, W].
     - nrm_amb [H, W]: 1 where a blended Gaussian's axis is within 1e-5 of perpendicular to its
       view direction, so that rounding may turn its normal either way.
-    - amb [H, W]: the render's decision flag."""
+    - amb [H, W]: the render's decision flag.
+    - depth_isect [H, W]: RaDe-GS's ray-Gaussian intersection depth, sum z_i(p) a_i T_i. z_i(p)
+      is the densest point of Gaussian i along the ray of pixel p in the EWA ray space (u, v,
+      camera z) of the projection: the mean of z given (u, v) = p, affine in p,
+      z_i(p) = z_i + Sigma_{z,uv} (Sigma2D + 0.3 I)^-1 (p - mu2D_i)."""
     s = _as_oscene(scene)
     H, W = cam.height, cam.width
     out = dict(normal=np.zeros((3, H, W)), nv=np.zeros((H, W)), alpha=np.zeros((H, W)),
-               nrm_amb=np.zeros((H, W), np.int32), amb=np.zeros((H, W), np.int32))
+               nrm_amb=np.zeros((H, W), np.int32), amb=np.zeros((H, W), np.int32), depth_isect=np.zeros((H, W)))
     st, cm = s.struct(), _cam(cam, (0.0, 0.0, 0.0))
     rc = lib().or_render_normals(C.byref(st), C.byref(cm),
-                                 *[_ptr(out[k]) for k in ("normal", "nv", "alpha", "nrm_amb", "amb")])
+                                 *[_ptr(out[k]) for k in ("normal", "nv", "alpha", "nrm_amb", "amb", "depth_isect")])
     if rc != 0:
         raise RuntimeError("or_render_normals failed: %d" % rc)
     return out

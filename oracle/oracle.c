@@ -15,6 +15,10 @@
  *   - the analytic image gradients dI/dx, dI/dy                           (Eq. 3)
  *     with the transmittance-gradient recursion                           (Eq. 4)
  *   - depth = sum z_i a_i T_i and alpha = 1 - T_final
+ *   - the RaDe-GS channels the paper renders depth and normals with (Sec. 5.1):
+ *     normals (shortest axis) and the ray-Gaussian intersection depth, the
+ *     conditional mean of camera z given the pixel in the EWA ray space
+ *     (cont_project, or_cont.rd)
  *   - the reverse-mode adjoint of all of the above (backward)
  *
  * Precision: FP64 for every continuous quantity. The discrete decisions (the
@@ -282,6 +286,7 @@ typedef struct {
     double rgb[3];
     int rgb_clamped[3];
     double nrm[3];  /* camera-space normal: the shortest axis, facing the camera (RaDe-GS, Sec. 5.1) */
+    double rd[2];   /* intersection depth's slope (dz/du, dz/dv) per pixel (RaDe-GS, Sec. 5.1) */
     int nrm_amb;    /* the axis is within 1e-5 of perpendicular to the view direction: orientation open */
 } or_cont;
 
@@ -347,6 +352,22 @@ static void cont_project(const or_scene *sc, const or_camera *cam, int64_t i, or
     P->ca = P->C / P->det;
     P->cb = -P->B / P->det;
     P->cc = P->A / P->det;
+    /* Intersection depth (RaDe-GS, which the paper renders depth with, Sec. 5.1). In the
+     * EWA ray space (u, v, z) -- image coordinates through the same clamped J, and camera
+     * z -- the Gaussian is N((u, v, z), [[J W Sig W^T J^T + 0.3 I, S_zuv^T], [S_zuv, .]]),
+     * S_zuv = (W Sig W^T J^T)_{z,:} the covariance of camera z with (u, v). Its densest
+     * point along the ray of image point p is the conditional mean of z given (u, v) = p:
+     *   z(p) = z + S_zuv (J W Sig W^T J^T + 0.3 I)^-1 (p - (u, v)),
+     * affine in p, with the slope rd = S_zuv . conic. */
+    double szuv[2];
+    for (int r = 0; r < 2; ++r) {
+        double acc = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) acc += W[8 + a] * P->Sig[3 * a + b] * P->T3[3 * r + b];
+        szuv[r] = acc;
+    }
+    P->rd[0] = szuv[0] * P->ca + szuv[1] * P->cb;
+    P->rd[1] = szuv[0] * P->cb + szuv[1] * P->cc;
     P->u = fx * tx / tz + cam->cx;
     P->v = fy * ty / tz + cam->cy;
     P->o = 1.0 / (1.0 + exp(-sc->logits[i]));
@@ -437,6 +458,7 @@ typedef struct {
 typedef struct {
     double rgb[3], gx[3], gy[3], depth, alpha, T, Tx, Ty;
     double normal[3];  /* sum of n_i a_i T_i (camera space) */
+    double depth_isect; /* sum of z_i(p) a_i T_i, the intersection depth (or_cont.rd) */
     int32_t nrm_amb;   /* a blended Gaussian's normal orientation is open (or_cont.nrm_amb) */
     double gx_abs[3], gy_abs[3]; /* the scale of an fp32 evaluation's error of dI/dx, dI/dy (below) */
     int32_t n_blended;
@@ -460,7 +482,7 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
     const double X = px + 0.5, Yp = py + 0.5;
     double T = 1.0, Tx = 0.0, Ty = 0.0, D = 0.0;
     double C[3] = {0, 0, 0}, Cx[3] = {0, 0, 0}, Cy[3] = {0, 0, 0}, Ax[3] = {0, 0, 0}, Ay[3] = {0, 0, 0};
-    double N[3] = {0, 0, 0};
+    double N[3] = {0, 0, 0}, Di = 0.0;
     int32_t nb = 0, amb = 0, namb = 0;
     uint32_t sig = 2166136261u;
     int64_t nt = 0;
@@ -502,6 +524,7 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
         }
         D += g->z * a * T;
         for (int c = 0; c < 3; ++c) N[c] += g->nrm[c] * a * T;  /* blended like the colour */
+        Di += (g->z + g->rd[0] * dx + g->rd[1] * dy) * a * T;
         namb |= g->nrm_amb;
         Tx = -ax * T + (1.0 - a) * Tx;                 /* Eq. 4 */
         Ty = -ay * T + (1.0 - a) * Ty;
@@ -519,6 +542,7 @@ static void composite_pixel(const or_cand *list, int64_t len, const or_cont *P, 
     out->depth = D;
     out->alpha = 1.0 - T;
     for (int c = 0; c < 3; ++c) out->normal[c] = N[c];
+    out->depth_isect = Di;
     out->nrm_amb = namb;
     out->T = T; out->Tx = Tx; out->Ty = Ty;
     out->n_blended = nb;
@@ -657,13 +681,13 @@ static int64_t max_bucket(const or_buckets *B)
 static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y0, int y1, double *rgb,
                        double *dcdx, double *dcdy, double *depth, double *alpha, double *final_T,
                        int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs, double *normal, double *nv,
-                       int32_t *nrm_amb);
+                       int32_t *nrm_amb, double *depth_isect);
 
 int or_render(const or_scene *sc, const or_camera *cam, int mode, double *rgb, double *dcdx, double *dcdy,
               double *depth, double *alpha, double *final_T, int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs)
 {
     return render_rows(sc, cam, mode, 0, cam->height, rgb, dcdx, dcdy, depth, alpha, final_T, n_blended, sig, amb, gabs,
-                       NULL, NULL, NULL);
+                       NULL, NULL, NULL, NULL);
 }
 
 /* Rows [y0, y1) of the frame (binned mode), written into full-size planes. */
@@ -673,22 +697,23 @@ int or_render_band(const or_scene *sc, const or_camera *cam, int y0, int y1, dou
     if (y0 < 0) y0 = 0;
     if (y1 > cam->height) y1 = cam->height;
     return render_rows(sc, cam, 1, y0, y1, rgb, dcdx, dcdy, depth, alpha, NULL, NULL, NULL, NULL, NULL, NULL, NULL,
-                       NULL);
+                       NULL, NULL);
 }
 
-/* The normal channel and the normal-view map (binned mode) with the colour's weights,
- * plus alpha and the orientation-ambiguity flag per pixel. */
+/* The RaDe-GS channels (binned mode) with the colour's weights: the normal channel, the
+ * normal-view map and the intersection depth, plus alpha and the orientation-ambiguity
+ * flag per pixel. */
 int or_render_normals(const or_scene *sc, const or_camera *cam, double *normal, double *nv, double *alpha,
-                      int32_t *nrm_amb, int32_t *amb)
+                      int32_t *nrm_amb, int32_t *amb, double *depth_isect)
 {
     return render_rows(sc, cam, 1, 0, cam->height, NULL, NULL, NULL, NULL, alpha, NULL, NULL, NULL, amb, NULL, normal,
-                       nv, nrm_amb);
+                       nv, nrm_amb, depth_isect);
 }
 
 static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y0, int y1, double *rgb,
                        double *dcdx, double *dcdy, double *depth, double *alpha, double *final_T,
                        int32_t *n_blended, uint32_t *sig, int32_t *amb, double *gabs, double *normal, double *nv,
-                       int32_t *nrm_amb)
+                       int32_t *nrm_amb, double *depth_isect)
 {
     const int W = cam->width, H = cam->height;
     const int64_t HW = (int64_t)W * H;
@@ -738,6 +763,7 @@ static int render_rows(const or_scene *sc, const or_camera *cam, int mode, int y
                     nv[p] = -(o.normal[0] * r[0] + o.normal[1] * r[1] + o.normal[2] * r[2]) / rn;
                 }
                 if (nrm_amb) nrm_amb[p] = o.nrm_amb;
+                if (depth_isect) depth_isect[p] = o.depth_isect;
             }
         }
         free(buf);

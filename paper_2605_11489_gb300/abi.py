@@ -59,7 +59,8 @@ class GsRenderOpts(C.Structure):
 
 class GsOutputs(C.Structure):
     _fields_ = [("rgb", C.c_void_p), ("dcdx", C.c_void_p), ("dcdy", C.c_void_p), ("depth", C.c_void_p),
-                ("alpha", C.c_void_p), ("normal", C.c_void_p), ("nv", C.c_void_p)]
+                ("alpha", C.c_void_p), ("normal", C.c_void_p), ("nv", C.c_void_p),
+                ("depth_isect", C.c_void_p)]
 
 
 class GsSceneGrads(C.Structure):

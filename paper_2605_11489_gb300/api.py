@@ -23,7 +23,9 @@ from . import abi
 from .abi import GsCamera, GsOutputs, GsRenderOpts, GsScene, GsSceneGrads, GsStateView, check
 
 OUTPUT_KEYS = ("rgb", "dcdx", "dcdy", "depth", "alpha")
-NORMAL_KEYS = ("normal", "nv")  # the normal channel and the normal-view map (plain forward only)
+# RaDe-GS channels (plain forward only): the normal channel, the normal-view map and the
+# ray-Gaussian intersection depth
+NORMAL_KEYS = ("normal", "nv", "depth_isect")
 
 
 def _stream_ptr(stream) -> int:
@@ -104,7 +106,8 @@ def _stats_dict(st) -> dict:
 
 def alloc_outputs(width, height, keys=OUTPUT_KEYS, device="cuda") -> dict:
     shp = {"rgb": (3, height, width), "dcdx": (3, height, width), "dcdy": (3, height, width),
-           "depth": (height, width), "alpha": (height, width), "normal": (3, height, width), "nv": (height, width)}
+           "depth": (height, width), "alpha": (height, width), "normal": (3, height, width), "nv": (height, width),
+           "depth_isect": (height, width)}
     return {k: torch.empty(shp[k], dtype=torch.float32, device=device) for k in keys}
 
 

@@ -279,8 +279,8 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
 // (with a thread per record, every lane's load and store touched its own line
 // and the L1 request path bound the kernel). Each thread takes four pieces, a
 // block apart, so their loads are in flight together. The pieces with e % 3 == 0
-// also write the tile ranges, (keys64 != NULL) the 64-bit keys and (nrm_sorted !=
-// NULL) the instance's normal.
+// also write the tile ranges, (keys64 != NULL) the 64-bit keys and (nrm_sorted, plane_sorted !=
+// NULL) the instance's normal and intersection-depth slope.
 constexpr int kRangeThreads = 256, kRangePer = 4;
 
 __global__ void __launch_bounds__(kRangeThreads)
@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(kRangeThreads)
              const uint32_t *__restrict__ counters, const GaussRec *__restrict__ rec,
              GaussRec *__restrict__ rec_sorted, uint2 *ranges, const uint4 *__restrict__ bin,
              uint64_t *__restrict__ keys64, const float4 *__restrict__ nrm, float4 *__restrict__ nrm_sorted,
+             const float2 *__restrict__ plane, float2 *__restrict__ plane_sorted,
              uint32_t n, uint32_t n_tiles)
 {
     // Indices and tile ids are checked against n and n_tiles: after a sort that gave up
@@ -330,6 +331,7 @@ __global__ void __launch_bounds__(kRangeThreads)
         }
         if (keys64) keys64[i] = ((uint64_t)t << 32) | (uint64_t)bin[g[k]].x;
         if (nrm_sorted) nrm_sorted[i] = __ldg(nrm + g[k]);
+        if (plane_sorted) plane_sorted[i] = __ldg(plane + g[k]);
     }
 }
 
@@ -499,7 +501,8 @@ cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int6
 
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
                           int64_t n, const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles,
-                          const uint4 *bin, uint64_t *keys64, cudaStream_t s, const float4 *nrm, float4 *nrm_sorted)
+                          const uint4 *bin, uint64_t *keys64, cudaStream_t s, const float4 *nrm, float4 *nrm_sorted,
+                          const float2 *plane, float2 *plane_sorted)
 {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess) return e;
@@ -507,7 +510,7 @@ cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint
     const int64_t per_block = (int64_t)kRangeThreads * kRangePer;
     const int64_t nb = (3 * max_k + per_block - 1) / per_block;
     k_ranges<<<(unsigned)nb, kRangeThreads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges, bin, keys64,
-                                                    nrm, nrm_sorted, (uint32_t)std::max<int64_t>(n, 1),
+                                                    nrm, nrm_sorted, plane, plane_sorted, (uint32_t)std::max<int64_t>(n, 1),
                                                     (uint32_t)n_tiles);
     return cudaGetLastError();
 }

@@ -75,6 +75,7 @@ struct PixelAcc {
     float T, Tx, Ty, D;
     float C[3], Cx[3], Cy[3];
     float N[3];  // normal channel (the NRM instantiations only)
+    float Di;    // intersection depth (the NRM instantiations only)
     uint32_t last;
     uint32_t n_eval, n_blend;  // pairs counted in the GS_COUNT_PAIRS instantiation only
     bool done, stopped;
@@ -86,6 +87,7 @@ __device__ __forceinline__ void acc_init(PixelAcc &s, bool inside)
     s.Tx = s.Ty = s.D = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) s.C[c] = s.Cx[c] = s.Cy[c] = s.N[c] = 0.0f;
+    s.Di = 0.0f;
     s.last = 0;
     s.done = !inside;
     s.stopped = false;
@@ -108,7 +110,8 @@ __device__ __forceinline__ void tile_pixel(int tid, int tile_x, int tile_y, int 
 // stops (the record would take T below 1e-4; it is not blended).
 template <bool GRAD, bool STATE, bool COUNT = false, bool NRM = false>
 __device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float4 &r1, const float4 &r2, float lx,
-                                      float ly, uint32_t pos, const float4 *nrm = nullptr)
+                                      float ly, uint32_t pos, const float4 *nrm = nullptr,
+                                      const float2 *plane = nullptr)
 {
     if (COUNT) ++s.n_eval;
     const AlphaEval e = eval_alpha(r0, r1, lx, ly);  // r0's centre relative to the block (block_centre)
@@ -127,6 +130,10 @@ __device__ __forceinline__ bool blend(PixelAcc &s, const float4 &r0, const float
         s.N[0] = __fmaf_rn(n.x, wgt, s.N[0]);
         s.N[1] = __fmaf_rn(n.y, wgt, s.N[1]);
         s.N[2] = __fmaf_rn(n.z, wgt, s.N[2]);
+        // the intersection depth at this pixel, z + (dz/du, dz/dv) . (p - mu2D), blended
+        // like the colour
+        const float2 pl = __ldg(plane);
+        s.Di = __fmaf_rn(__fmaf_rn(pl.x, e.dx, __fmaf_rn(pl.y, e.dy, r1.z)), wgt, s.Di);
     }
     if (GRAD) {
         const float ax = e.capped ? 0.0f : -__fmul_rn(al, e.ex);
@@ -264,7 +271,8 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
                     const float4 b0 = recs[kn].r0, b1 = recs[kn].r1, b2 = recs[kn].r2;
                     if (blend<GRAD, STATE, COUNT, NRM>(
                             s, a0, a1, a2, lx, ly, pos_b + k,
-                            NRM ? a.nrm_sorted + (s0 + (uint32_t)b * BATCH + k) : nullptr)) {
+                            NRM ? a.nrm_sorted + (s0 + (uint32_t)b * BATCH + k) : nullptr,
+                            NRM ? a.plane_sorted + (s0 + (uint32_t)b * BATCH + k) : nullptr)) {
                         s.done = true;
                         s.stopped = true;
                         break;
@@ -322,6 +330,7 @@ __device__ __forceinline__ void write_final(const CompositeArgs &a, int px, int 
             const float inv = rsqrtf(rx * rx + ry * ry + 1.0f);
             a.nv[p] = -(s.N[0] * rx + s.N[1] * ry + s.N[2]) * inv;
         }
+        if (a.depth_isect) a.depth_isect[p] = s.Di;
     }
     if (STATE) {
         a.final_T[p] = s.T;

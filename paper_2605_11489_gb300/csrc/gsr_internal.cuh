@@ -103,6 +103,7 @@ struct ProjectArgs {
     uint32_t *block_vis;   // per block of 1,024 Gaussians: visible Gaussians
     uint32_t *counters;    // visible count accumulates into kCntVisible / kCntSumV
     float4 *nrm;           // per Gaussian: camera-space normal (x, y, z, 0) of the visible ones (nullable)
+    float2 *plane;         // per Gaussian, with nrm: the intersection depth's slope (dz/du, dz/dv) per pixel
 };
 int project_blocks(int64_t n);
 // geometry (records without colour, bin, tile counts, block sums), then the SH
@@ -132,7 +133,8 @@ cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int6
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
                           int64_t n, const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles,
                           const uint4 *bin, uint64_t *keys64, cudaStream_t s, const float4 *nrm = nullptr,
-                          float4 *nrm_sorted = nullptr);
+                          float4 *nrm_sorted = nullptr, const float2 *plane = nullptr,
+                          float2 *plane_sorted = nullptr);
 
 // onesweep LSD radix sort of (keys, vals) on the low `bits` bits, K from counters[kCntEff]
 struct SortScratch {
@@ -176,7 +178,8 @@ struct CompositeArgs {
     unsigned long long *pair_counts;  // (evaluated, blended) pairs: the GS_COUNT_PAIRS census (nullable)
     // normal channel (nullable: the normal variant runs only when nrm_sorted is set, whole tiles only)
     const float4 *nrm_sorted;      // normals in sorted (instance) order, like rec
-    float *normal, *nv;
+    const float2 *plane_sorted;    // intersection-depth slopes in sorted order (with nrm_sorted)
+    float *normal, *nv, *depth_isect;
     float fx, fy, cx, cy;          // intrinsics: nv's pixel rays
     uint32_t give_up;              // diagnostic: each warp's first batch wait gives up without polling
                                    // (kErrTmaTimeout), then waits for its copies in flight

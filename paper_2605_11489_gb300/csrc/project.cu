@@ -80,6 +80,7 @@ struct Proj {
     float u, v, ca, cb, cc, o, z;  // u, v: the centre relative to the rectangle's first pixel centre
     uint32_t rlo, rhi, nt;
     float n[3];  // camera-space normal (with NRM only)
+    float pl[2]; // intersection-depth slope per pixel, (dz/du, dz/dv) (with NRM only)
 };
 
 // Error-free transformations (Dekker, Knuth): a * b = p + e and a + b = s + e exactly.
@@ -237,6 +238,15 @@ __device__ __forceinline__ void project_one(const CamParams &c, float mx, float 
         }
 #pragma unroll
         for (int r = 0; r < 3; ++r) P.n[r] = vm[4 * r] * nw0 + vm[4 * r + 1] * nw1 + vm[4 * r + 2] * nw2;
+        // RaDe-GS intersection depth: in the EWA ray space (u, v, z) the Gaussian's densest
+        // point along the pixel's ray is the mean of z given (u, v), affine in the pixel:
+        //   z(p) = z + Sigma_{z,uv} (Sigma2D + 0.3 I)^-1 (p - mu2D),
+        // Sigma_{z,uv} = (V2 . N0, V2 . N1) with V2 the camera-z row of W R S (the same
+        // clamped Jacobian as Sigma2D), and (Sigma2D + 0.3 I)^-1 the conic.
+        const float szu = F(V[6], N[0], F(V[7], N[1], M(V[8], N[2])));
+        const float szv = F(V[6], N[3], F(V[7], N[4], M(V[8], N[5])));
+        P.pl[0] = F(szu, P.ca, M(szv, P.cb));
+        P.pl[1] = F(szu, P.cb, M(szv, P.cc));
     }
 }
 
@@ -345,7 +355,10 @@ __global__ void __launch_bounds__(kGeomThreads, 1) k_project(ProjectArgs a)
             r.r2 = make_float4(0.0f, 0.0f, __uint_as_float(Q.rlo), __uint_as_float(Q.rhi));
             a.rec[i] = r;
             a.bin[i] = make_uint4(__float_as_uint(Q.z), Q.rlo, Q.rhi, 0u);
-            if (NRM) a.nrm[i] = make_float4(Q.n[0], Q.n[1], Q.n[2], 0.0f);
+            if (NRM) {
+                a.nrm[i] = make_float4(Q.n[0], Q.n[1], Q.n[2], 0.0f);
+                a.plane[i] = make_float2(Q.pl[0], Q.pl[1]);
+            }
         }
         a.ntiles[i] = Q.nt;
         my_tiles = Q.nt;

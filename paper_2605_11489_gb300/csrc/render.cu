@@ -113,7 +113,8 @@ struct Frame {
     int64_t max_long = 0; // long tiles the frame's capacity allows (0: none composited apart)
     ForkJoin fork;        // the long tiles' stream beside the launch stream
     Buf fT, fTx, fTy, ncontrib;
-    Buf nrm, nrm_sorted;  // the normal channel: per Gaussian, then in sorted (instance) order
+    Buf nrm, nrm_sorted;      // the normal channel: per Gaussian, then in sorted (instance) order
+    Buf plane, plane_sorted;  // the intersection depth's slopes, likewise
     bool want_nrm = false;
     Buf counters;
     int64_t n = 0, K = 0, key_cap = 0;
@@ -466,7 +467,10 @@ ProjectArgs proj_args(Frame *f, const gs_scene *s)
     a.block_sums = f->bsums.as<uint32_t>();
     a.block_vis = f->vsums.as<uint32_t>();
     a.counters = f->counters.as<uint32_t>();
-    if (f->want_nrm) a.nrm = f->nrm.as<float4>();
+    if (f->want_nrm) {
+        a.nrm = f->nrm.as<float4>();
+        a.plane = f->plane.as<float2>();
+    }
     return a;
 }
 
@@ -501,8 +505,10 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
     if (f->count_pairs) c.pair_counts = reinterpret_cast<unsigned long long *>(f->counters.as<uint32_t>() + kCntPairs);
     if (f->want_nrm) {
         c.nrm_sorted = f->nrm_sorted.as<float4>();
+        c.plane_sorted = f->plane_sorted.as<float2>();
         c.normal = out->normal;
         c.nv = out->nv;
+        c.depth_isect = out->depth_isect;
         c.fx = f->cam.fx;
         c.fy = f->cam.fy;
         c.cx = f->cam.cx;
@@ -551,7 +557,9 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
                            f->ranges.as<uint2>(), f->n_tiles, f->bin.as<uint4>(),
                            f->has_state ? f->keys64.as<uint64_t>() : nullptr, st,
                            f->want_nrm ? f->nrm.as<float4>() : nullptr,
-                           f->want_nrm ? f->nrm_sorted.as<float4>() : nullptr));
+                           f->want_nrm ? f->nrm_sorted.as<float4>() : nullptr,
+                           f->want_nrm ? f->plane.as<float2>() : nullptr,
+                           f->want_nrm ? f->plane_sorted.as<float2>() : nullptr));
     GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->head, f->order.as<uint32_t>(),
                          f->plan.as<uint32_t>(), err, st));
     GSR_CUDA(mark(mk, 7, st));
@@ -589,11 +597,13 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
         return fail(GS_ERR_INVALID_ARG, "tile must be 8/16/32 and batch 32/64/128/256 with the warps' staging rings "
                                         "fitting shared memory");
     const bool state = (o->flags & GS_EMIT_BWD_STATE) != 0;
-    // the normal channel composites every list with one warp per block (the long tiles'
-    // partial states keep no normal), so no list counts as long (head 2^30 records)
-    const bool nrm = out->normal || out->nv;
+    // the RaDe-GS channels (normal, nv, intersection depth) composite every list with one
+    // warp per block (the long tiles' partial states keep neither), so no list counts as
+    // long (head 2^30 records)
+    const bool nrm = out->normal || out->nv || out->depth_isect;
     if (nrm && (o->flags & (GS_EMIT_BWD_STATE | GS_COUNT_PAIRS)))
-        return fail(GS_ERR_INVALID_ARG, "the normal channel is rendered without GS_EMIT_BWD_STATE and GS_COUNT_PAIRS");
+        return fail(GS_ERR_INVALID_ARG,
+                    "normal, nv and depth_isect are rendered without GS_EMIT_BWD_STATE and GS_COUNT_PAIRS");
     gs_render_opts on = *o;
     if (nrm) {
         chunk = 1 << 24;
@@ -607,7 +617,10 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
     f->err_word = ctx->err.as<uint32_t>();
     f->give_up = ctx->give_up;
     f->want_nrm = nrm;
-    if (nrm) GSR_CUDA(f->nrm.ensure(sizeof(float4) * (size_t)std::max<int64_t>(s->n, 1)));
+    if (nrm) {
+        GSR_CUDA(f->nrm.ensure(sizeof(float4) * (size_t)std::max<int64_t>(s->n, 1)));
+        GSR_CUDA(f->plane.ensure(sizeof(float2) * (size_t)std::max<int64_t>(s->n, 1)));
+    }
     uint32_t *cnt = f->counters.as<uint32_t>();
     Marks mk;
     mk.mask = timing_mask(o->flags);
@@ -643,7 +656,10 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
         if (r != GS_OK) return r;
     }
     if ((r = frame_plan(f, f->K)) != GS_OK) return r;
-    if (nrm) GSR_CUDA(f->nrm_sorted.ensure(sizeof(float4) * (size_t)std::max<int64_t>(f->K, 1)));
+    if (nrm) {
+        GSR_CUDA(f->nrm_sorted.ensure(sizeof(float4) * (size_t)std::max<int64_t>(f->K, 1)));
+        GSR_CUDA(f->plane_sorted.ensure(sizeof(float2) * (size_t)std::max<int64_t>(f->K, 1)));
+    }
     // counters[kCntEff] was clamped to kMaxInstances; K fits, so it equals K.
     r = enqueue_after_scan(f, out, f->K, st, mk);
     if (r != GS_OK || !f->count_pairs) return r;
@@ -780,8 +796,8 @@ gs_status gs_render_forward_to_host(gs_context *ctx, const gs_scene *scene, cons
                                     const gs_render_opts *opts, const gs_outputs *host_out, gs_stream stream)
 {
     if (!ctx || !host_out || !cam || !opts) return fail(GS_ERR_INVALID_ARG, "NULL argument");
-    if (host_out->normal || host_out->nv)
-        return fail(GS_ERR_INVALID_ARG, "host outputs carry no normal channel (render it with gs_render_forward)");
+    if (host_out->normal || host_out->nv || host_out->depth_isect)
+        return fail(GS_ERR_INVALID_ARG, "host outputs carry no RaDe-GS channel (render it with gs_render_forward)");
     gs_status r = check_cam(cam);
     if (r != GS_OK) return r;
     GSR_CUDA(cudaSetDevice(ctx->device));
@@ -906,7 +922,8 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
     if (!graph) return fail(GS_ERR_INVALID_ARG, "graph is NULL");
     *graph = nullptr;
     if (!ctx || !opts || !out) return fail(GS_ERR_INVALID_ARG, "NULL argument");
-    if (out->normal || out->nv) return fail(GS_ERR_INVALID_ARG, "graphs do not render the normal channel");
+    if (out->normal || out->nv || out->depth_isect)
+        return fail(GS_ERR_INVALID_ARG, "graphs do not render the RaDe-GS channels");
     gs_status r = check_scene(scene);
     if (r != GS_OK) return r;
     if ((r = check_cam(cam)) != GS_OK) return r;

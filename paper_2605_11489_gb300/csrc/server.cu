@@ -623,7 +623,8 @@ gs_status gs_server_submit(gs_server *S, int32_t scene_id, const gs_camera *cam,
     gs_status r = check_cam(cam);
     if (r != GS_OK) return r;
     if (opts->flags & GS_EMIT_BWD_STATE) return fail(GS_ERR_INVALID_ARG, "serving does not keep backward state");
-    if (out->normal || out->nv) return fail(GS_ERR_INVALID_ARG, "serving does not render the normal channel");
+    if (out->normal || out->nv || out->depth_isect)
+        return fail(GS_ERR_INVALID_ARG, "serving does not render the RaDe-GS channels");
     if ((opts->tile && opts->tile != kServeTile) || (opts->batch && opts->batch != kServeBatch))
         return fail(GS_ERR_INVALID_ARG, "serving renders with tile 16, batch 64");
     Request *q = new Request();

@@ -1,8 +1,12 @@
-"""GPU parity of the normal channel and the normal-view map against the oracle, through the
-C ABI (gs_render_forward with gs_outputs.normal / .nv).
+"""GPU parity of the RaDe-GS channels against the oracle, through the C ABI
+(gs_render_forward with gs_outputs.normal / .nv / .depth_isect).
 
-- The normal is the one RaDe-GS renders (the paper's depth and normal maps, Sec. 5.1).
+- The normal and the ray-Gaussian intersection depth are the ones RaDe-GS renders (the
+  paper's depth and normal maps, Sec. 5.1).
 - The normal-view map Nv is the one the super-sampling takes (Sec. 4.1).
+- The intersection depth is held to the depth channel's bar (gpu_util.check_depth): 2e-4
+  relative to max(1, |depth|) on >= 99.99 % of the pixels, 5e-3 of the alpha-cut flip
+  scale on all.
 
 Bar: the colour's.
 - The normal is the same alpha-weighted sum with unit vectors in place of colours, so its
@@ -17,7 +21,7 @@ import pytest
 
 from paper_2605_11489_gb300 import synth
 
-from gpu_util import check_colour
+from gpu_util import check_colour, check_depth
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +54,9 @@ def _check(got, ref):
     assert ok.mean() > 0.99
     check_colour(got["normal"][:, ok], ref["normal"][:, ok], "normal")
     check_colour(got["nv"][ok], ref["nv"][ok], "nv")
+    check_depth(got["depth_isect"][ok], ref["depth_isect"][ok], ref["alpha"][ok])
+    # the intersection depth really leaves the centre depth: slopes are in play
+    assert np.abs(got["depth_isect"] - got["depth"]).max() > 1e-3
 
 
 @pytest.mark.parametrize("tile", [8, 16, 32])
