@@ -5,7 +5,7 @@ path (projection + SH colour, scan, key duplication, radix sort, tile ranges,
 compositing with dC/dx, dC/dy, depth and alpha), replayed as a captured CUDA
 graph with the frame's camera (the fixed-resolution stream path), with
 --frames-in-flight frames (default 4) rendering concurrently on their own streams
-(api.FrameStream). The scene is
+(api.FrameStream over the C ABI's gs_frame_stream_*). The scene is
 resident in HBM before timing starts and is larger than L2, so steps do not
 reuse each other's inputs from cache.
 
@@ -849,20 +849,15 @@ def measure_render(args, name, ctx, stream, sc, cams, world, rank, local_rank, f
     fs.synchronize()
     fs.stats(reset=True)
 
-    def timed_replays(frame_stream, two):
-        """Times args.steps frames (CUDA events on `stream`, which joins every slot's stream);
-        with two=False the slots' graphs replay on one stream, one frame at a time."""
+    def timed_replays(frame_stream):
+        """Times args.steps frames (CUDA events on `stream`: every slot's first frame waits
+        for the start event, and the end event waits for every slot's last frame)."""
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for k in range(frame_stream.slots):
-            frame_stream.streams[k].wait_event(e0)
+        frame_stream.follow(stream)
         for i in range(args.steps):
-            cam = cams[(args.warmup + i) % len(cams)]
-            if two:
-                frame_stream.render(cam)
-            else:
-                frame_stream.graphs[i % frame_stream.slots].render(cam, stream=stream)
+            frame_stream.render(cams[(args.warmup + i) % len(cams)])
         frame_stream.join(stream)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -874,7 +869,7 @@ def measure_render(args, name, ctx, stream, sc, cams, world, rank, local_rank, f
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    ms = timed_replays(fs, True)
+    ms = timed_replays(fs)
     if world > 1:
         torch.distributed.barrier()
     if smi:
@@ -890,16 +885,22 @@ def measure_render(args, name, ctx, stream, sc, cams, world, rank, local_rank, f
     # sharing the GPU with the other frames in flight)
     composite_ms_in_flight = (sum(x["stage_ms"]["composite"] * x["timed_frames"] for x in sts)
                               / max(1, sum(x["timed_frames"] for x in sts)))
-    # the same replays one frame at a time on one stream: a timed region of its own, where
-    # the compositing events measure the kernel alone (the roofline's launch duration)
-    ms_one = slowest_rank(timed_replays(fs, False), world, "cuda")
-    sts1 = fs.stats(reset=True)
+    fs.close()
+    # the same replays one frame at a time (a one-slot frame stream): a timed region of its
+    # own, where the compositing events measure the kernel alone (the roofline's launch
+    # duration)
+    fs1 = api.FrameStream(ctx, scene, cams[0], capacity, tile, batch, chunk, timed="composite", slots=1)
+    for i in range(args.warmup):
+        fs1.render(cams[i % len(cams)])
+    fs1.synchronize()
+    fs1.stats(reset=True)
+    ms_one = slowest_rank(timed_replays(fs1), world, "cuda")
+    sts1 = fs1.stats(reset=True)
     composite_ms_alone = (sum(x["stage_ms"]["composite"] * x["timed_frames"] for x in sts1)
                           / max(1, sum(x["timed_frames"] for x in sts1)))
-    fs.synchronize()
+    fs1.close()
     one_stream = {"value": job_throughput(W * H * args.steps, world, ms_one * 1e-3), "unit": "Mpix/s",
                   "ms_per_step": ms_one / args.steps}
-    fs.close()
 
     # per-stage times: a replay of the camera path with events at every stage boundary
     staged = ctx.graph(scene, cams[0], out, capacity=capacity, tile=tile, batch=batch, chunk=chunk, timed=True,
@@ -952,24 +953,26 @@ def measure_render(args, name, ctx, stream, sc, cams, world, rank, local_rank, f
     stage_roofline = {k: {kk: v[kk] for kk in ("bound", "achieved", "unit", "frac")}
                       for k, v in ((s_, roofline(s_)) for s_ in abi.STAGES)}
 
-    # end to end through the public API: each frame's camera from the host, all five output
-    # planes back to pinned host memory, every step (api.HostFrameStream: graph replay with
-    # the copies of one frame overlapping the next frame's render); plus, for context, the
-    # one-frame synchronous call gs_render_forward_to_host
+    # end to end through the C ABI's frame stream (gs_frame_stream_*, wrapped by
+    # api.HostFrameStream): each frame's camera from the host, all five output planes back to
+    # pinned host memory (one host set per slot), every step, with one frame's copies
+    # overlapping the other slots' renders; plus, for context, the one-frame synchronous call
+    # gs_render_forward_to_host
     e2e = None
     if not args.no_e2e:
+        nh = args.frames_in_flight
         hosts = [{k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in out.items()}
-                 for _ in range(2)]
+                 for _ in range(nh)]
         hfs = api.HostFrameStream(ctx, scene, cams[0], capacity, tile, batch, chunk, slots=args.frames_in_flight)
         for i in range(3):
-            hfs.render(cams[i % len(cams)], hosts[i % 2])
+            hfs.render(cams[i % len(cams)], hosts[i % nh])
         hfs.synchronize()
         e2e_steps = min(args.steps, 60)
         if world > 1:
             torch.distributed.barrier()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
-            hfs.render(cams[i % len(cams)], hosts[i % 2])
+            hfs.render(cams[i % len(cams)], hosts[i % nh])
         hfs.synchronize()
         dt = slowest_rank(time.perf_counter() - t0, world, "cuda")
         hfs.close()
@@ -983,9 +986,9 @@ def measure_render(args, name, ctx, stream, sc, cams, world, rank, local_rank, f
         dt_sync = slowest_rank(time.perf_counter() - t0, world, "cuda")
         e2e = {"value": job_throughput(W * H * e2e_steps, world, dt), "unit": "Mpix/s",
                "h2d_bytes_per_step": GS_CAMERA_BYTES, "d2h_bytes_per_step": 11 * W * H * 4,
-               "path": "api.HostFrameStream: graph replay per frame with the camera from the host, "
-                       "--frames-in-flight frames on their own streams, D2H of rgb, dC/dx, dC/dy, depth, "
-                       "alpha into pinned host memory, copies overlapping the next renders",
+               "path": "gs_frame_stream_submit (C ABI; api.HostFrameStream): graph replay per frame with the "
+                       "camera from the host, --frames-in-flight frames on their own streams, D2H of rgb, dC/dx, "
+                       "dC/dy, depth, alpha into pinned host memory, copies overlapping the other frames' renders",
                "sync_call": {"value": job_throughput(W * H * n_sync, world, dt_sync), "unit": "Mpix/s",
                              "path": "gs_render_forward_to_host per frame (plain forward + D2H, synchronous)"}}
 
@@ -1059,7 +1062,7 @@ def measure_render(args, name, ctx, stream, sc, cams, world, rank, local_rank, f
     return {"value": value, "ms_per_step": ms / args.steps, "frames_per_s": 1e3 * args.steps * world / ms,
             "config": {"workload": name, "desc": WORKLOADS[name]["desc"], "width": W, "height": H,
                        "gaussians": sc.n, "sh_degree": sc.deg, "tile": tile, "batch": batch, "chunk": chunk,
-                       "path": "CUDA graph replay per frame, %d frames in flight (api.FrameStream)"
+                       "path": "CUDA graph replay per frame, %d frames in flight (gs_frame_stream_* via api.FrameStream)"
                                % args.frames_in_flight, "frames_in_flight": args.frames_in_flight,
                        "l2": "inputs larger than L2 (scene %.0f MB)" % (sc.nbytes() / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -255,6 +255,49 @@ gs_status gs_graph_check(gs_graph *graph, gs_stream stream, int64_t *max_instanc
 gs_status gs_graph_stats(gs_graph *graph, gs_stream stream, int reset, gs_frame_stats *stats);
 gs_status gs_graph_destroy(gs_graph *graph);
 
+/* ---------------------------------------------------------------- frames in flight
+ * A frame stream renders a camera sequence with `slots` frames in flight: one captured
+ * graph (as gs_graph_create) and one high-priority stream per slot. Frame f (numbered
+ * from 0 in submission order) goes to slot f % slots and renders into that slot's device
+ * planes. Consecutive frames are independent, so one frame's compositing runs beside
+ * the next frames' projection and sorts.
+ *
+ * outs: `slots` caller-owned device output sets (W x H of cam0, fp32, the layouts of
+ *   gs_outputs; each non-NULL plane is rendered, and every set names the same planes;
+ *   the RaDe-GS channels are not rendered here). They must outlive the stream.
+ * opts, capacity: as gs_graph_create (capacity 0 = 4 N); timing flags apply to every slot.
+ *
+ * submit: enqueues the frame with camera `cam` (the resolution of cam0) and returns its
+ *   number in *frame. If `host` is not NULL, each of its non-NULL planes receives a copy
+ *   of the same device plane (cudaMemcpyAsync on the slot's stream, after the render;
+ *   pinned host memory lets it overlap, pageable memory makes it synchronous). Slot k
+ *   renders again only after its previous frame's copies and any release (below). The
+ *   call does not wait for the GPU.
+ * join: makes stream `consumer` wait until frame f has rendered (and its host copies are done).
+ * release: frame f's slot renders its next frame only after the work enqueued on
+ *   `consumer` so far (the consumer's reads of the frame's planes). Without a release, the
+ *   slot is rewritten `slots` frames later, stream-ordered after its own earlier work.
+ * wait: the host waits for frame f (its render and copies).
+ * For join, release and wait, f must be among the last `slots` submitted frames
+ * (GS_ERR_INVALID_ARG otherwise).
+ * synchronize: waits for every submitted frame; returns the first error any slot's frames
+ *   raised since the last call (GS_ERR_CAPACITY for instances beyond capacity,
+ *   GS_ERR_TIMEOUT for a bounded wait that gave up), like gs_graph_check.
+ * stats: gs_graph_stats of slot `slot`.
+ * destroy: waits for every frame, then frees the graphs, streams and events (not outs). */
+typedef struct gs_frame_stream gs_frame_stream;
+gs_status gs_frame_stream_create(gs_context *ctx, const gs_scene *scene, const gs_camera *cam0,
+                                 const gs_render_opts *opts, const gs_outputs *outs, int32_t slots,
+                                 int64_t capacity, gs_frame_stream **fs);
+gs_status gs_frame_stream_submit(gs_frame_stream *fs, const gs_camera *cam, const gs_outputs *host,
+                                 int64_t *frame);
+gs_status gs_frame_stream_join(gs_frame_stream *fs, int64_t frame, gs_stream consumer);
+gs_status gs_frame_stream_release(gs_frame_stream *fs, int64_t frame, gs_stream consumer);
+gs_status gs_frame_stream_wait(gs_frame_stream *fs, int64_t frame);
+gs_status gs_frame_stream_synchronize(gs_frame_stream *fs);
+gs_status gs_frame_stream_stats(gs_frame_stream *fs, int32_t slot, int reset, gs_frame_stats *stats);
+gs_status gs_frame_stream_destroy(gs_frame_stream *fs);
+
 /* ---------------------------------------------------------------- autotuner
  * Times the forward for every tile in {8, 16, 32}, batch in {32, 64, 128, 256}
  * (pairs whose per-warp staging rings fit shared memory) and chunk in

@@ -35,7 +35,10 @@ ENTRY_POINTS = (
     "gs_context_create", "gs_context_destroy", "gs_render_forward", "gs_render_forward_to_host",
     "gs_render_backward", "gs_state_view_get", "gs_context_stats", "gs_context_check", "gs_context_debug_waits",
     "gs_state_free", "gs_graph_create",
-    "gs_graph_render", "gs_graph_check", "gs_graph_stats", "gs_graph_destroy", "gs_autotune", "gs_server_create", "gs_server_load_scene",
+    "gs_graph_render", "gs_graph_check", "gs_graph_stats", "gs_graph_destroy", "gs_frame_stream_create",
+    "gs_frame_stream_submit", "gs_frame_stream_join", "gs_frame_stream_release", "gs_frame_stream_wait",
+    "gs_frame_stream_synchronize", "gs_frame_stream_stats", "gs_frame_stream_destroy",
+    "gs_autotune", "gs_server_create", "gs_server_load_scene",
     "gs_server_submit", "gs_server_poll", "gs_server_cancel", "gs_server_drain", "gs_server_destroy",
     "gs_sort_pairs_static", "gs_warp", "gs_gai_upsample", "gs_last_error", "gs_version",
 )
@@ -125,6 +128,15 @@ def _declare(L):
         "gs_graph_check": [P, P, C.POINTER(I64)],
         "gs_graph_destroy": [P],
         "gs_graph_stats": [P, P, C.c_int, C.POINTER(GsFrameStats)],
+        "gs_frame_stream_create": [P, C.POINTER(GsScene), C.POINTER(GsCamera), C.POINTER(GsRenderOpts),
+                                   C.POINTER(GsOutputs), I32, I64, C.POINTER(P)],
+        "gs_frame_stream_submit": [P, C.POINTER(GsCamera), C.POINTER(GsOutputs), C.POINTER(I64)],
+        "gs_frame_stream_join": [P, I64, P],
+        "gs_frame_stream_release": [P, I64, P],
+        "gs_frame_stream_wait": [P, I64],
+        "gs_frame_stream_synchronize": [P],
+        "gs_frame_stream_stats": [P, I32, C.c_int, C.POINTER(GsFrameStats)],
+        "gs_frame_stream_destroy": [P],
         "gs_context_stats": [P, P, C.c_int, C.POINTER(GsFrameStats)],
         "gs_context_check": [P, P],
         "gs_context_debug_waits": [P, I32],

@@ -430,16 +430,17 @@ def gai_upsample(weights, rgb, dcdx, dcdy, out=None, stream=None):
 
 # ----------------------------------------------------------------------------- frames to the host
 class FrameStream:
-    """Renders a camera sequence on the device with `slots` frames in flight (default 2).
-    - One captured graph per slot, each with its own output buffers and its own stream, takes
-      the frames in turn. Consecutive frames are independent, so one frame's compositing runs
-      beside the next frames' projection and sorts.
-    - `render(cam)` returns the slot k that frame goes to. Its planes are `outs[k]`, complete
-      once `rendered[k]` has fired; make a stream wait on that event before reading them.
+    """Renders a camera sequence on the device with `slots` frames in flight (default 2),
+    through the C ABI's frame stream (gs_frame_stream_*).
+    - One captured graph per slot, each with its own output buffers (`outs[k]`) and its own
+      high-priority stream, takes the frames in turn. Consecutive frames are independent,
+      so one frame's compositing runs beside the next frames' projection and sorts.
+    - `render(cam)` returns the slot k that frame goes to. `wait_for(k, stream)` makes a
+      stream wait until slot k's latest frame has rendered; then `outs[k]` may be read there.
     - A consumer that reads `outs[k]` on its own stream calls `release(k, stream)` when it
       has enqueued those reads. The next frame rendered into slot k then waits for them.
       Without a release, slot k is rewritten `slots` frames later.
-    Every computation runs in libgsr.so."""
+    Every computation, stream and event lives in libgsr.so."""
 
     def __init__(self, ctx: "Context", scene: "Scene", cam0, capacity: int, tile=0, batch=0, chunk=0,
                  keys=OUTPUT_KEYS, timed=False, slots=2):
@@ -447,112 +448,79 @@ class FrameStream:
         self.slots = n = int(slots)
         if n < 1:
             raise ValueError("slots must be >= 1")
-        self.streams = [torch.cuda.Stream() for _ in range(n)]
+        self.ctx, self.scene = ctx, scene  # keep alive
         self.outs = [alloc_outputs(W, H, tuple(keys)) for _ in range(n)]
-        self.graphs = [ctx.graph(scene, cam0, self.outs[k], capacity=capacity, tile=tile, batch=batch, chunk=chunk,
-                                 timed=timed, stream=self.streams[k]) for k in range(n)]
-        self.rendered = [torch.cuda.Event() for _ in range(n)]
-        self.released = [None] * n
-        self.t = 0
+        sets = (GsOutputs * n)(*[outputs_struct(o) for o in self.outs])
+        op = opts_struct(tile, batch, (0.0, 0.0, 0.0), timed=timed, chunk=chunk)
+        h = C.c_void_p()
         torch.cuda.synchronize()
+        check(abi.lib().gs_frame_stream_create(ctx.h, C.byref(scene.struct()), C.byref(camera_struct(cam0)),
+                                               C.byref(op), sets, n, int(capacity), C.byref(h)))
+        self.h = h
+        self.frame = [-1] * n  # the latest frame number of each slot
 
-    def render(self, cam) -> int:
-        k = self.t % self.slots
-        if self.released[k] is not None:
-            self.streams[k].wait_event(self.released[k])
-            self.released[k] = None
-        self.graphs[k].render(cam, stream=self.streams[k])
-        self.rendered[k].record(self.streams[k])
-        self.t += 1
+    def render(self, cam, host_out: dict = None) -> int:
+        """Enqueue frame `cam`; with `host_out` (pinned fp32 CPU tensors keyed like `outs`)
+        its planes are also copied there after the render."""
+        f = C.c_int64()
+        ho = C.byref(outputs_struct(host_out)) if host_out is not None else None
+        check(abi.lib().gs_frame_stream_submit(self.h, C.byref(camera_struct(cam)), ho, C.byref(f)))
+        k = f.value % self.slots
+        self.frame[k] = f.value
         return k
 
+    def wait_for(self, k: int, stream) -> None:
+        check(abi.lib().gs_frame_stream_join(self.h, self.frame[k], _stream_ptr(stream)))
+
     def release(self, k: int, stream) -> None:
-        ev = torch.cuda.Event()
-        ev.record(stream)
-        self.released[k] = ev
+        check(abi.lib().gs_frame_stream_release(self.h, self.frame[k], _stream_ptr(stream)))
+
+    def follow(self, stream) -> None:
+        """Every slot's next frame waits for the work enqueued on `stream` so far."""
+        for k in range(self.slots):
+            if self.frame[k] >= 0:
+                self.release(k, stream)
 
     def join(self, stream) -> None:
         """Makes `stream` wait for every frame submitted so far."""
         for k in range(self.slots):
-            stream.wait_event(self.rendered[k])
+            if self.frame[k] >= 0:
+                self.wait_for(k, stream)
 
     def synchronize(self) -> None:
         """Waits for every submitted frame; raises if a frame overflowed the graphs'
-        instance capacity."""
-        for k in range(self.slots):
-            self.streams[k].synchronize()
-            self.graphs[k].check(stream=self.streams[k])
+        instance capacity or a bounded wait gave up."""
+        check(abi.lib().gs_frame_stream_synchronize(self.h))
 
     def stats(self, reset=False) -> list:
-        return [self.graphs[k].stats(reset=reset, stream=self.streams[k]) for k in range(self.slots)]
+        out = []
+        for k in range(self.slots):
+            st = abi.GsFrameStats()
+            check(abi.lib().gs_frame_stream_stats(self.h, k, int(reset), C.byref(st)))
+            out.append(_stats_dict(st))
+        return out
 
     def close(self) -> None:
-        self.synchronize()
-        for g in self.graphs:
-            g.close()
+        if self.h:
+            self.synchronize()
+            abi.lib().gs_frame_stream_destroy(self.h)
+            self.h = C.c_void_p(0)
 
 
-class HostFrameStream:
-    """Renders a camera sequence into HOST planes (pinned memory), with each frame's
-    device-to-host copies overlapping the next frame's render.
-    - Frames render by graph replay with `slots` frames in flight (default 2): one captured
-      graph per slot, each with its own device output buffers and high-priority stream, takes
-      the frames in turn.
-    - A copy stream moves each finished frame's planes, in frame order, to the caller's host
-      buffers while the next frames render.
-    - Events order the streams. A device buffer is rendered into again only after its
-      previous copy has completed.
-    The caller owns the host buffers and must not touch a frame's buffers until
-    `synchronize()` (or until two later frames have been submitted and synchronised). Every
-    computation runs in libgsr.so; the copies are cudaMemcpyAsync."""
+class HostFrameStream(FrameStream):
+    """Renders a camera sequence into HOST planes (pinned memory) through the C ABI's frame
+    stream: each frame's device-to-host copies run on its slot's stream right after its
+    render, beside the other slots' renders. The caller owns the host buffers and must not
+    touch a frame's buffers until `synchronize()`."""
 
     def __init__(self, ctx: "Context", scene: "Scene", cam0, capacity: int, tile=0, batch=0, chunk=0,
                  keys=OUTPUT_KEYS, slots=2):
-        W, H = cam0.width, cam0.height
-        self.keys = tuple(keys)
-        self.slots = n = int(slots)
-        if n < 1:
-            raise ValueError("slots must be >= 1")
-        self.rs = [torch.cuda.Stream(priority=-1) for _ in range(n)]
-        self.cs = torch.cuda.Stream()
-        self.outs = [alloc_outputs(W, H, self.keys) for _ in range(n)]
-        self.graphs = [ctx.graph(scene, cam0, self.outs[k], capacity=capacity, tile=tile, batch=batch,
-                                 chunk=chunk, stream=self.rs[k]) for k in range(n)]
-        self.rendered = [torch.cuda.Event() for _ in range(n)]
-        self.copied = [torch.cuda.Event() for _ in range(n)]
-        self.used = [False] * n
-        self.t = 0
-        torch.cuda.synchronize()
+        super().__init__(ctx, scene, cam0, capacity, tile, batch, chunk, keys, False, slots)
 
-    def render(self, cam, host_out: dict):
+    def render(self, cam, host_out: dict) -> int:
         """Enqueue frame `cam`; its planes land in `host_out` (pinned fp32 CPU tensors of
         the output shapes, keyed like the device outputs)."""
-        k = self.t % self.slots
-        if self.used[k]:
-            self.rs[k].wait_event(self.copied[k])
-        self.graphs[k].render(cam, stream=self.rs[k])
-        self.rendered[k].record(self.rs[k])
-        self.cs.wait_event(self.rendered[k])
-        with torch.cuda.stream(self.cs):
-            for key in self.keys:
-                host_out[key].copy_(self.outs[k][key], non_blocking=True)
-        self.copied[k].record(self.cs)
-        self.used[k] = True
-        self.t += 1
-
-    def synchronize(self):
-        """Waits for every submitted frame's copies; raises if a frame overflowed the
-        graphs' instance capacity."""
-        for k in range(self.slots):
-            self.rs[k].synchronize()
-        self.cs.synchronize()
-        for k in range(self.slots):
-            self.graphs[k].check(stream=self.rs[k])
-
-    def close(self):
-        self.synchronize()
-        for g in self.graphs:
-            g.close()
+        return super().render(cam, host_out)
 
 
 # ----------------------------------------------------------------------------- pipeline

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgsr.so")
-SOURCES = ["project.cu", "binning.cu", "sort.cu", "composite.cu", "backward.cu", "render.cu", "server.cu", "warp.cu", "gai.cu",
+SOURCES = ["project.cu", "binning.cu", "sort.cu", "composite.cu", "backward.cu", "render.cu", "server.cu", "frames.cu",
+           "warp.cu", "gai.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-ftz=false", "-prec-div=true",

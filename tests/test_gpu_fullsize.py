@@ -66,7 +66,7 @@ def _stream_frames(api, ctx, scene, cams, frames, config, slots=BENCH_SLOTS):
     for f, target in seq:
         k = fs.render(cams[f])
         if target:
-            copy.wait_event(fs.rendered[k])
+            fs.wait_for(k, copy)
             with torch.cuda.stream(copy):
                 kept[f] = {key: v.clone() for key, v in fs.outs[k].items()}
             fs.release(k, copy)

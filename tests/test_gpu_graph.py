@@ -149,9 +149,10 @@ def test_host_frame_stream_equals_plain_forward(env):
             assert torch.equal(h[k], ref[k].cpu()), k
 
 
-@pytest.mark.parametrize("slots", [2, 3])
+@pytest.mark.parametrize("slots", [2, 3, 4])
 def test_frame_stream_frames_in_flight(env, slots):
-    """api.FrameStream: one graph and stream per slot take the frames in turn. A consumer on
+    """api.FrameStream (the C ABI's gs_frame_stream_*): one graph and stream per slot take
+    the frames in turn. A consumer on
     its own stream copies each frame's planes out and releases the slot; every copy equals
     the plain forward of its camera bit for bit, so neither the overlap of consecutive
     frames nor the reuse of a slot `slots` frames later disturbs a frame."""
@@ -166,7 +167,7 @@ def test_frame_stream_frames_in_flight(env, slots):
     copies = []
     for cam in cams:
         k = fs.render(cam)
-        consumer.wait_event(fs.rendered[k])
+        fs.wait_for(k, consumer)
         with torch.cuda.stream(consumer):
             copies.append({key: v.clone() for key, v in fs.outs[k].items()})
         fs.release(k, consumer)
@@ -178,3 +179,70 @@ def test_frame_stream_frames_in_flight(env, slots):
         torch.cuda.synchronize()
         for key in ref:
             assert torch.equal(got[key], ref[key]), key
+
+
+def test_frame_stream_c_abi_contract(env):
+    """gs_frame_stream_* directly through ctypes: frame numbers, the window of frames that
+    join / release / wait accept, host planes the stream does not render, the RaDe-GS
+    channels, wait() making a frame's host copy readable, and an instance overflow reported
+    once by synchronize."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2605_11489_gb300 import abi
+
+    api, ctx = env
+    L = abi.lib()
+    sc = synth.tiny_scene(4096, 0)
+    cams = synth.jittered_tiny_cameras(6, 31)
+    scene = api.Scene.from_arrays(sc)
+    W, H = cams[0].width, cams[0].height
+    slots = 3
+    outs = [api.alloc_outputs(W, H, ("rgb", "alpha")) for _ in range(slots)]
+    sets = (abi.GsOutputs * slots)(*[api.outputs_struct(o) for o in outs])
+    op = api.opts_struct(16, 64)
+    h = C.c_void_p()
+    abi.check(L.gs_frame_stream_create(ctx.h, C.byref(scene.struct()), C.byref(api.camera_struct(cams[0])),
+                                       C.byref(op), sets, slots, 200_000, C.byref(h)))
+    try:
+        host = {"rgb": torch.empty(3, H, W).pin_memory(), "alpha": torch.empty(H, W).pin_memory()}
+        f = C.c_int64()
+        nums = []
+        for cam in cams[:5]:
+            abi.check(L.gs_frame_stream_submit(h, C.byref(api.camera_struct(cam)), None, C.byref(f)))
+            nums.append(f.value)
+        assert nums == [0, 1, 2, 3, 4]
+        for bad in (-1, 0, 1, 5):  # outside the last `slots` frames (2, 3, 4)
+            assert L.gs_frame_stream_wait(h, bad) == abi.GS_ERR_INVALID_ARG
+            assert L.gs_frame_stream_join(h, bad, None) == abi.GS_ERR_INVALID_ARG
+            assert L.gs_frame_stream_release(h, bad, None) == abi.GS_ERR_INVALID_ARG
+        # a host plane the stream does not render, and a RaDe-GS plane
+        d = torch.empty(H, W).pin_memory()
+        for hs in ({"depth": d}, {"rgb": host["rgb"], "depth_isect": d}):
+            assert L.gs_frame_stream_submit(h, C.byref(api.camera_struct(cams[5])),
+                                            C.byref(api.outputs_struct(hs)), C.byref(f)) == abi.GS_ERR_INVALID_ARG
+        # frame 5 with its planes copied to the host: readable after wait(5)
+        abi.check(L.gs_frame_stream_submit(h, C.byref(api.camera_struct(cams[5])),
+                                           C.byref(api.outputs_struct(host)), C.byref(f)))
+        assert f.value == 5
+        abi.check(L.gs_frame_stream_wait(h, 5))
+        ref = ctx.forward(scene, cams[5], tile=16, batch=64)
+        torch.cuda.synchronize()
+        assert torch.equal(host["rgb"], ref["rgb"].cpu()) and torch.equal(host["alpha"], ref["alpha"].cpu())
+        assert torch.equal(outs[5 % slots]["rgb"], ref["rgb"])
+        abi.check(L.gs_frame_stream_synchronize(h))
+    finally:
+        L.gs_frame_stream_destroy(h)
+    # an instance overflow: reported by synchronize, once
+    h = C.c_void_p()
+    abi.check(L.gs_frame_stream_create(ctx.h, C.byref(scene.struct()), C.byref(api.camera_struct(cams[0])),
+                                       C.byref(op), sets, slots, 1_000, C.byref(h)))
+    try:
+        abi.check(L.gs_frame_stream_submit(h, C.byref(api.camera_struct(cams[0])), None, C.byref(f)))
+        assert L.gs_frame_stream_synchronize(h) == abi.GS_ERR_CAPACITY
+        assert L.gs_frame_stream_synchronize(h) == abi.GS_OK  # reported once
+    finally:
+        L.gs_frame_stream_destroy(h)
+    with pytest.raises(abi.GsError):  # the RaDe-GS channels are not rendered by frame streams
+        api.FrameStream(ctx, scene, cams[0], 200_000, 16, 64, slots=slots, keys=("rgb", "nv"))
