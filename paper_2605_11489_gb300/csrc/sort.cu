@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(KeyT) == 8 ? 3 : 4)
     const uint32_t part = s_part;
     if (part >= nparts) return;
     const uint32_t base = part * kPart;
+    const uint32_t hist_d = hist[tid];  // this thread's digit's global count, loaded early
 
     KeyT k[kItems];
     uint32_t v[kItems], rk[kItems];
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(KeyT) == 8 ? 3 : 4)
         cnt += c;
     }
     uint32_t cexcl, hexcl;
-    block_excl_scan2(cnt, hist[tid], cexcl, hexcl, s_tmp);
+    block_excl_scan2(cnt, hist_d, cexcl, hexcl, s_tmp);
     // decoupled lookback for this digit, kLook predecessors per round trip:
     // their words are loaded together and summed newest first until an
     // inclusive prefix is met; a word not yet published is re-read on its own.
