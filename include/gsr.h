@@ -51,7 +51,10 @@ typedef enum {
     GS_ERR_CUDA = -3,          /* a CUDA runtime call failed */
     GS_ERR_TIMEOUT = -4,       /* a bounded device wait gave up */
     GS_ERR_CAPACITY = -5,      /* instance list exceeded a fixed capacity */
-    GS_ERR_CANCELLED = -6      /* request cancelled or server shut down */
+    GS_ERR_CANCELLED = -6,     /* request cancelled or server shut down */
+    GS_ERR_INTERNAL = -7       /* an internal failure: the server's scheduler stopped, or (in
+                                  a GSR_DEBUG build) a device index check fired; see
+                                  gs_last_error */
 } gs_status;
 
 typedef struct gs_context gs_context;

@@ -11,7 +11,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgsr.so")
+# GSR_DEBUG=1 loads the GSR_DEBUG build (build.build(debug=True)), whose device index guards
+# report kErrBounds as GS_ERR_INTERNAL
+LIB_PATH = os.path.join(HERE, "libgsr_debug.so" if os.environ.get("GSR_DEBUG") == "1" else "libgsr.so")
 
 GS_OK = 0
 GS_NOT_READY = 1
@@ -21,6 +23,7 @@ GS_ERR_CUDA = -3
 GS_ERR_TIMEOUT = -4
 GS_ERR_CAPACITY = -5
 GS_ERR_CANCELLED = -6
+GS_ERR_INTERNAL = -7
 GS_EMIT_BWD_STATE = 1
 GS_TIME_STAGES = 2
 GS_TIME_COMPOSITE = 8
@@ -28,7 +31,8 @@ GS_COUNT_PAIRS = 4
 STAGES = ("project", "scan", "compact", "depth_sort", "duplicate", "tile_sort", "ranges", "composite")
 
 STATUS_NAMES = {0: "GS_OK", 1: "GS_NOT_READY", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_OOM", -3: "GS_ERR_CUDA",
-                -4: "GS_ERR_TIMEOUT", -5: "GS_ERR_CAPACITY", -6: "GS_ERR_CANCELLED"}
+                -4: "GS_ERR_TIMEOUT", -5: "GS_ERR_CAPACITY", -6: "GS_ERR_CANCELLED",
+                -7: "GS_ERR_INTERNAL"}
 
 # every entry point declared in include/gsr.h
 ENTRY_POINTS = (

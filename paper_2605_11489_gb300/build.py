@@ -17,6 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgsr.so")
+DEBUG_LIB = os.path.join(HERE, "libgsr_debug.so")
 SOURCES = ["project.cu", "binning.cu", "sort.cu", "composite.cu", "backward.cu", "render.cu", "server.cu", "frames.cu",
            "warp.cu", "gai.cu",
            "noalloc.cu"]
@@ -39,8 +40,13 @@ def _stale(obj: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, debug: bool = False) -> str:
+    """Compiles libgsr.so (or, with debug=True, libgsr_debug.so: the same sources with
+    -DGSR_DEBUG, whose device index guards record kErrBounds; objects in _build/debug)."""
+    bdir = os.path.join(BUILD, "debug") if debug else BUILD
+    lib = DEBUG_LIB if debug else LIB
+    flags = FLAGS + (["-DGSR_DEBUG"] if debug else [])
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
@@ -49,14 +55,14 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     todo = []
     for s in srcs:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(bdir, s.replace(".cu", ".o"))
         objs.append(obj)
         if _stale(obj, [src, *headers, __file__]):
             todo.append((src, obj))
 
     def compile_one(job):
         src, obj = job
-        cmd = [nvcc, *FLAGS, "-c", src, "-o", obj + ".tmp"]
+        cmd = [nvcc, *flags, "-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
@@ -67,14 +73,14 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
 
     with ThreadPoolExecutor(max_workers=jobs or min(8, os.cpu_count() or 4)) as ex:
         list(ex.map(compile_one, todo))
-    if todo or not os.path.exists(LIB) or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if todo or not os.path.exists(lib) or _stale(lib, objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "static", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
                                                             const uint32_t *__restrict__ block_offs, int tile_shift,
                                                             int tiles_x, uint32_t *__restrict__ keys,
                                                             uint32_t *__restrict__ vals, unsigned long long capacity,
-                                                            uint32_t *counters, uint32_t *__restrict__ hist, int passes,
+                                                            uint32_t *err, uint32_t *__restrict__ hist, int passes,
                                                             uint32_t n)
 {
     constexpr int kWarps = kProjThreads / 32, kPerWarp = 128;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         uint32_t idx = i0 + g < V ? dvals[i0 + g] : 0u;
-        if (idx >= n) idx = 0u;  // (an unsorted depth order, see k_sorted_counts): no tiles
+        if (!GSR_IN_BOUNDS(idx, n, err)) idx = 0u;  // (an unsorted depth order, see k_sorted_counts): no tiles
         cnt[g] = i0 + g < V && dvals[i0 + g] < n ? ntiles[idx] : 0u;
         uint32_t org = 0, wid = 1;
         if (cnt[g]) {
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
             overflow = true;
         }
     }
-    if (overflow) atomicOr(&counters[kCntErr], kErrCapacity);
+    if (overflow) atomicOr(err, kErrCapacity);
     flush_hist(s_hist, hist, passes * 256);
 }
 
@@ -285,7 +285,7 @@ constexpr int kRangeThreads = 256, kRangePer = 4;
 
 __global__ void __launch_bounds__(kRangeThreads)
     k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-             const uint32_t *__restrict__ counters, const GaussRec *__restrict__ rec,
+             const uint32_t *__restrict__ counters, uint32_t *err, const GaussRec *__restrict__ rec,
              GaussRec *__restrict__ rec_sorted, uint2 *ranges, const uint4 *__restrict__ bin,
              uint64_t *__restrict__ keys64, const float4 *__restrict__ nrm, float4 *__restrict__ nrm_sorted,
              const float2 *__restrict__ plane, float2 *__restrict__ plane_sorted,
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kRangeThreads)
     for (int k = 0; k < kRangePer; ++k) {
         const uint32_t e = e0 + (uint32_t)k * kRangeThreads;
         g[k] = e < P ? vals[e / 3u] : 0u;
-        if (g[k] >= n) g[k] = 0u;
+        if (!GSR_IN_BOUNDS(g[k], n, err)) g[k] = 0u;
     }
     if (rec_sorted) {
 #pragma unroll
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kRangeThreads)
         if (e >= P || e % 3u != 0u) continue;
         const uint32_t i = e / 3u;
         const uint32_t t = keys[i];
-        if (t < n_tiles) {
+        if (GSR_IN_BOUNDS(t, n_tiles, err)) {
             if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
             if (i == K - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
         }
@@ -483,8 +483,9 @@ cudaError_t launch_compact(const uint32_t *ntiles, const uint4 *bin, const uint3
 cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int64_t max_v, const uint32_t *ntiles,
                              const uint4 *bin, uint32_t *bsums, uint32_t *boffs, int tile_shift, int tiles_x,
                              uint32_t *keys, uint32_t *vals, int64_t capacity, uint32_t *counters, uint32_t *hist,
-                             int passes, cudaStream_t s)
+                             int passes, cudaStream_t s, uint32_t *err)
 {
+    if (!err) err = counters + kCntErr;
     if (passes < 0 || passes > 2) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 8 * 256, s);
     if (e != cudaSuccess) return e;
@@ -495,21 +496,22 @@ cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int6
     k_scan_plain<<<1, kScanThreads, 0, s>>>(bsums, nb, boffs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_duplicate<<<nb, kProjThreads, 0, s>>>(dvals, vcount, ntiles, bin, boffs, tile_shift, tiles_x, keys, vals,
-                                            (unsigned long long)capacity, counters, hist, passes, (uint32_t)max_v);
+                                            (unsigned long long)capacity, err, hist, passes, (uint32_t)max_v);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
+cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, uint32_t *counters, int64_t max_k,
                           int64_t n, const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles,
                           const uint4 *bin, uint64_t *keys64, cudaStream_t s, const float4 *nrm, float4 *nrm_sorted,
-                          const float2 *plane, float2 *plane_sorted)
+                          const float2 *plane, float2 *plane_sorted, uint32_t *err)
 {
+    if (!err) err = counters + kCntErr;
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess) return e;
     if (max_k <= 0) return cudaSuccess;
     const int64_t per_block = (int64_t)kRangeThreads * kRangePer;
     const int64_t nb = (3 * max_k + per_block - 1) / per_block;
-    k_ranges<<<(unsigned)nb, kRangeThreads, 0, s>>>(keys, vals, counters, rec, rec_sorted, ranges, bin, keys64,
+    k_ranges<<<(unsigned)nb, kRangeThreads, 0, s>>>(keys, vals, counters, err, rec, rec_sorted, ranges, bin, keys64,
                                                     nrm, nrm_sorted, plane, plane_sorted, (uint32_t)std::max<int64_t>(n, 1),
                                                     (uint32_t)n_tiles);
     return cudaGetLastError();

@@ -308,6 +308,7 @@ __device__ __forceinline__ void write_final(const CompositeArgs &a, int px, int 
 {
     const int64_t HW = (int64_t)a.width * a.height;
     const int64_t p = (int64_t)py * a.width + px;
+    if (!GSR_IN_BOUNDS(p, HW, a.err_word)) return;
     if (a.rgb)
 #pragma unroll
         for (int c = 0; c < 3; ++c) a.rgb[c * HW + p] = __fmaf_rn(s.T, a.bg[c], s.C[c]);
@@ -401,6 +402,7 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (blockIdx.x >= a.plan[2]) return;
     const uint32_t tile = a.tile_order[a.plan[0] + blockIdx.x];
+    if (!GSR_IN_BOUNDS(tile, (uint32_t)(a.tiles_x * a.tiles_y), a.err_word)) return;
     const uint2 r = a.ranges[tile];
     const uint32_t s0 = r.x, s1 = r.y > r.x ? r.y : r.x;
     WarpRing<BATCH> &ring = reinterpret_cast<WarpRing<BATCH> *>(smem_raw)[threadIdx.x >> 5];

@@ -122,6 +122,7 @@ gs_status gs_frame_stream_create(gs_context *ctx, const gs_scene *scene, const g
 
 gs_status gs_frame_stream_submit(gs_frame_stream *fs, const gs_camera *cam, const gs_outputs *host, int64_t *frame)
 {
+    gsr::NvtxRange nvtx_("gsr.frame_stream_submit");
     if (!fs || !cam) return fail(GS_ERR_INVALID_ARG, "NULL argument");
     const int k = (int)(fs->next % fs->slots);
     const gs_outputs &dev = fs->outs[k];

@@ -137,6 +137,7 @@ extern "C" gs_status gs_gai_upsample(const gs_gai_weights *w, const float *rgb, 
                                      const float *dcdy, int32_t channels, int32_t width, int32_t height, float *out,
                                      gs_stream stream)
 {
+    gsr::NvtxRange nvtx_("gsr.gai_upsample");
     using namespace gsr;
     if (!w || !w->wc || !w->wt) return fail(GS_ERR_INVALID_ARG, "gs_gai_upsample: weights are NULL");
     const int S = w->scale, C = w->features;

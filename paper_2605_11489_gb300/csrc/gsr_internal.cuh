@@ -7,6 +7,8 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gsr.h"
 
 namespace gsr {
@@ -19,12 +21,50 @@ constexpr float kTMin = 1e-4f;              // stop before T would fall below 1e
 constexpr int kProjThreads = 256;           // projection block: 256 threads x 4 Gaussians
 constexpr int kProjPerBlock = kProjThreads * 4;
 
+// NVTX range over a host scope (the entry points and the stages of a frame's enqueue), so
+// that a profiler shows which stage launched which kernels. NVTX3 is header-only: without a
+// profiler attached a range is two calls that return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+// Consecutive stages in one scope: next() ends the current range and starts the next.
+struct NvtxStages {
+    explicit NvtxStages(const char *first) { nvtxRangePushA(first); }
+    void next(const char *name)
+    {
+        nvtxRangePop();
+        nvtxRangePushA(name);
+    }
+    ~NvtxStages() { nvtxRangePop(); }
+    NvtxStages(const NvtxStages &) = delete;
+    NvtxStages &operator=(const NvtxStages &) = delete;
+};
+
 // Error bits written by kernels into a device status word.
 enum : uint32_t {
     kErrSortTimeout = 1u,       // radix-sort lookback gave up waiting
     kErrTmaTimeout = 2u,        // compositing waited too long for a staged batch
     kErrCapacity = 4u,          // instance list exceeded the buffers' capacity
+    kErrBounds = 8u,            // a GSR_DEBUG index check fired (the access was skipped)
 };
+
+// Index guards. In every build the guarded access is skipped when i >= n. A GSR_DEBUG build
+// also raises kErrBounds in the kernel's error word, so that a guard that fires is seen (the
+// build's stand-in for a memory checker; nothing traps).
+#ifdef GSR_DEBUG
+__device__ __forceinline__ bool gsr_in_bounds(uint64_t i, uint64_t n, uint32_t *err)
+{
+    if (i < n) return true;
+    if (err) atomicOr(err, kErrBounds);
+    return false;
+}
+#define GSR_IN_BOUNDS(i, n, err) ::gsr::gsr_in_bounds((uint64_t)(i), (uint64_t)(n), (err))
+#else
+#define GSR_IN_BOUNDS(i, n, err) ((uint64_t)(i) < (uint64_t)(n))
+#endif
 
 // ---------------------------------------------------------------- device-side camera
 struct CamParams {
@@ -127,14 +167,16 @@ cudaError_t launch_compact(const uint32_t *ntiles, const uint4 *bin, const uint3
 cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int64_t max_v, const uint32_t *ntiles,
                              const uint4 *bin, uint32_t *bsums, uint32_t *boffs, int tile_shift, int tiles_x,
                              uint32_t *keys, uint32_t *vals, int64_t capacity, uint32_t *counters, uint32_t *hist,
-                             int passes, cudaStream_t s);
+                             int passes, cudaStream_t s, uint32_t *err = nullptr);
 // K5: per-tile [start, end) from the sorted tile keys, the records gathered into
 // sorted order, and (keys64 != NULL) each instance's (tile << 32 | depth bits)
-cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, const uint32_t *counters, int64_t max_k,
+cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, uint32_t *counters, int64_t max_k,
                           int64_t n, const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles,
                           const uint4 *bin, uint64_t *keys64, cudaStream_t s, const float4 *nrm = nullptr,
                           float4 *nrm_sorted = nullptr, const float2 *plane = nullptr,
-                          float2 *plane_sorted = nullptr);
+                          float2 *plane_sorted = nullptr, uint32_t *err = nullptr);
+// (launch_duplicate, launch_ranges: `err` is the error word for kErrCapacity and kErrBounds,
+// by default counters + kCntErr)
 
 // onesweep LSD radix sort of (keys, vals) on the low `bits` bits, K from counters[kCntEff]
 struct SortScratch {

@@ -532,6 +532,7 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     SortScratch scr;
     sort_scratch_carve(f->sort_scr.p, std::max<int64_t>(f->key_cap, f->n), &scr);
     // K3a, K4a: the visible Gaussians in depth order
+    NvtxStages nvtx_stage("gsr.depth_sort");
     GSR_CUDA(launch_compact(f->ntiles.as<uint32_t>(), f->bin.as<uint4>(), f->voffs.as<uint32_t>(), f->n,
                             f->dkeys[0].as<uint32_t>(), f->dvals[0].as<uint32_t>(), scr.hist, st));
     GSR_CUDA(mark(mk, 3, st));
@@ -540,12 +541,13 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     int dres = 0;
     GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, err, f->n, 32, scr, &dres, st, true, f->give_up));
     GSR_CUDA(mark(mk, 4, st));
+    nvtx_stage.next("gsr.tile_keys_sort");
     // K3b, K4b: tile keys in depth order, then stable by tile
     const int tbits = f->bits - 32;
     GSR_CUDA(launch_duplicate(dv[dres], cnt + kCntVisible, f->n, f->ntiles.as<uint32_t>(), f->bin.as<uint4>(),
                               f->bsums2.as<uint32_t>(), f->boffs2.as<uint32_t>(), f->cam.tile_shift, f->tiles_x,
                               f->keys[0].as<uint32_t>(), f->vals[0].as<uint32_t>(), f->key_cap, cnt, scr.hist,
-                              sort_passes(tbits), st));
+                              sort_passes(tbits), st, err));
     GSR_CUDA(mark(mk, 5, st));
     uint32_t *kk[2] = {f->keys[0].as<uint32_t>(), f->keys[1].as<uint32_t>()};
     uint32_t *vv[2] = {f->vals[0].as<uint32_t>(), f->vals[1].as<uint32_t>()};
@@ -553,16 +555,18 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     GSR_CUDA(launch_sort32(kk, vv, cnt + kCntEff, err, max_k, tbits, scr, &res, st, true, f->give_up));
     f->sorted = res;
     GSR_CUDA(mark(mk, 6, st));
+    nvtx_stage.next("gsr.ranges_plan");
     GSR_CUDA(launch_ranges(kk[res], vv[res], cnt, max_k, f->n, f->rec.as<GaussRec>(), f->rec_sorted.as<GaussRec>(),
                            f->ranges.as<uint2>(), f->n_tiles, f->bin.as<uint4>(),
                            f->has_state ? f->keys64.as<uint64_t>() : nullptr, st,
                            f->want_nrm ? f->nrm.as<float4>() : nullptr,
                            f->want_nrm ? f->nrm_sorted.as<float4>() : nullptr,
                            f->want_nrm ? f->plane.as<float2>() : nullptr,
-                           f->want_nrm ? f->plane_sorted.as<float2>() : nullptr));
+                           f->want_nrm ? f->plane_sorted.as<float2>() : nullptr, err));
     GSR_CUDA(launch_plan(f->ranges.as<uint2>(), f->n_tiles, f->head, f->order.as<uint32_t>(),
                          f->plan.as<uint32_t>(), err, st));
     GSR_CUDA(mark(mk, 7, st));
+    nvtx_stage.next("gsr.composite");
     const CompositeArgs ca = comp_args(f, out);
     if (f->max_long > 0) {  // long tiles on the second stream, beside the short ones
         GSR_CUDA(cudaEventRecord(f->fork.fork, st));
@@ -583,6 +587,7 @@ gs_status err_status(uint32_t err)
     if (err & kErrSortTimeout) return fail(GS_ERR_TIMEOUT, "radix sort lookback wait gave up");
     if (err & kErrTmaTimeout) return fail(GS_ERR_TIMEOUT, "compositing batch wait gave up");
     if (err & kErrCapacity) return fail(GS_ERR_CAPACITY, "instance count exceeded capacity");
+    if (err & kErrBounds) return fail(GS_ERR_INTERNAL, "a device index check fired (GSR_DEBUG build)");
     return GS_OK;
 }
 
@@ -631,7 +636,10 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
     GSR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * kCntSlots, st));
     GSR_CUDA(mark(mk, 0, st));
     const ProjectArgs pa = proj_args(f, s);
-    GSR_CUDA(launch_project(pa, st));
+    {
+        NvtxRange nvtx_("gsr.project_scan");
+        GSR_CUDA(launch_project(pa, st));
+    }
     GSR_CUDA(mark(mk, 1, st));
     GSR_CUDA(launch_scan_blocks(pa.block_sums, pa.block_vis, project_blocks(s->n), f->boffs.as<uint32_t>(),
                                 f->voffs.as<uint32_t>(), cnt, kMaxInstances, st));
@@ -758,6 +766,7 @@ gs_status gs_context_destroy(gs_context *ctx)
 gs_status gs_render_forward(gs_context *ctx, const gs_scene *scene, const gs_camera *cam, const gs_render_opts *opts,
                             const gs_outputs *out, gs_fwd_state **state, gs_stream stream)
 {
+    gsr::NvtxRange nvtx_("gsr.forward");
     if (state) *state = nullptr;
     if (!ctx || !opts || !out) return fail(GS_ERR_INVALID_ARG, "ctx, opts and out must be non-NULL");
     gs_status r = check_scene(scene);
@@ -795,6 +804,7 @@ gs_status gs_render_forward(gs_context *ctx, const gs_scene *scene, const gs_cam
 gs_status gs_render_forward_to_host(gs_context *ctx, const gs_scene *scene, const gs_camera *cam,
                                     const gs_render_opts *opts, const gs_outputs *host_out, gs_stream stream)
 {
+    gsr::NvtxRange nvtx_("gsr.forward_to_host");
     if (!ctx || !host_out || !cam || !opts) return fail(GS_ERR_INVALID_ARG, "NULL argument");
     if (host_out->normal || host_out->nv || host_out->depth_isect)
         return fail(GS_ERR_INVALID_ARG, "host outputs carry no RaDe-GS channel (render it with gs_render_forward)");
@@ -828,6 +838,7 @@ gs_status gs_render_forward_to_host(gs_context *ctx, const gs_scene *scene, cons
 gs_status gs_render_backward(gs_context *ctx, const gs_fwd_state *state, const gs_scene *scene,
                              const gs_outputs *grad_in, const gs_scene_grads *grads, gs_stream stream)
 {
+    gsr::NvtxRange nvtx_("gsr.backward");
     if (!ctx || !state || !grad_in || !grads) return fail(GS_ERR_INVALID_ARG, "NULL argument");
     gs_status r = check_scene(scene);
     if (r != GS_OK) return r;
@@ -973,6 +984,7 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
             GSR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * kCntPerFrame, s2));
             GSR_CUDA(mark(evs, 0, s2));
             g->proj_args = proj_args(f, scene);
+            NvtxRange nvtx_("gsr.project_scan");
             GSR_CUDA(launch_project(g->proj_args, s2));
             GSR_CUDA(mark(evs, 1, s2));
             GSR_CUDA(launch_scan_blocks(g->proj_args.block_sums, g->proj_args.block_vis, project_blocks(scene->n),
@@ -1046,6 +1058,7 @@ gs_status gs_graph_create(gs_context *ctx, const gs_scene *scene, const gs_camer
 
 gs_status gs_graph_render(gs_graph *g, const gs_camera *cam, gs_stream stream)
 {
+    gsr::NvtxRange nvtx_("gsr.graph_render");
     if (!g || !cam) return fail(GS_ERR_INVALID_ARG, "NULL argument");
     if (cam->width != g->f->W || cam->height != g->f->H) return fail(GS_ERR_INVALID_ARG, "resolution differs from the graph's");
     gs_status r = check_cam(cam);

@@ -23,7 +23,11 @@
 // GSR_FAULT=enqueue:<k> makes the k-th admission's first launch fail;
 // GSR_FAULT=wait:<k> runs the k-th admitted request's kernels with waits that give
 // up at once (its sort lookbacks and compositing batch waits), so that request
-// finishes with GS_ERR_TIMEOUT through its device error word, others proceed.
+// finishes with GS_ERR_TIMEOUT through its device error word, others proceed;
+// GSR_FAULT=thread:<k> makes the scheduler thread throw (a host exception) before its
+// k-th admission. The thread catches whatever escapes its loop: it waits for the GPU work
+// it has enqueued (so no kernel still writes a caller's planes), finishes every request
+// not yet done with GS_ERR_INTERNAL, and stops; later submits fail with GS_ERR_INTERNAL.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,6 +39,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -220,8 +225,8 @@ struct gs_server {
     uint32_t *d_work = nullptr;
     int comp_grid = 0;
     int alloc_count = 0, enqueue_count = 0, admit_count = 0;
-    int fault_alloc = -1, fault_enqueue = -1, fault_wait = -1;
-    std::atomic<uint32_t> thread_err{0};
+    int fault_alloc = -1, fault_enqueue = -1, fault_wait = -1, fault_thread = -1;
+    bool dead = false;       // the scheduler stopped on a failure (thread_msg)
     std::string thread_msg;
 };
 
@@ -393,7 +398,7 @@ CompositeArgs slot_comp_args(Slot &sl)
     return c;
 }
 
-void scheduler(gs_server *S)
+void scheduler_loop(gs_server *S)
 {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
@@ -416,8 +421,11 @@ void scheduler(gs_server *S)
             progressed = true;
         }
         // 1. admit queued requests into free slots
+        NvtxStages nvtx_stage("gsr.serve.admit");
         for (int si = 0; si < (int)S->slots.size() && !S->queue.empty(); ++si) {
             if (S->slots[si].req) continue;
+            if (S->fault_thread >= 0 && S->admit_count == S->fault_thread)
+                throw std::runtime_error("injected scheduler failure (GSR_FAULT=thread)");
             Request *r = S->queue.front();
             S->queue.pop_front();
             gs_status st = admit(S, si, r);
@@ -428,6 +436,7 @@ void scheduler(gs_server *S)
             progressed = true;
         }
         // 2. requests whose scan finished: read K, ask for sort memory in arrival order
+        nvtx_stage.next("gsr.serve.sort");
         for (Slot &sl : S->slots) {
             if (!sl.req || sl.req->stage != Stage::Scan) continue;
             if (cudaEventQuery(sl.ev_scan) != cudaSuccess) continue;
@@ -469,6 +478,7 @@ void scheduler(gs_server *S)
             progressed = true;
         }
         // 3b. launch one compositing batch over every sorted request
+        nvtx_stage.next("gsr.serve.composite");
         if (!S->comp_busy) {
             int n = 0;
             uint32_t total = 0;
@@ -527,6 +537,43 @@ void scheduler(gs_server *S)
     }
 }
 
+// The scheduler stopped on a failure: wait for the GPU work it enqueued, then finish every
+// request that is not done with GS_ERR_INTERNAL and free what they held. Later submits fail.
+void scheduler_failed(gs_server *S, const char *what)
+{
+    std::lock_guard<std::mutex> g(S->mu);
+    cudaSetDevice(S->device);
+    for (Slot &sl : S->slots)
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (S->comp_stream) cudaStreamSynchronize(S->comp_stream);
+    S->dead = true;
+    S->thread_msg = what;
+    const std::string msg = std::string("the server's scheduler stopped: ") + what;
+    for (Slot &sl : S->slots) {
+        if (!sl.req) continue;
+        Request *r = sl.req;
+        slot_free(S, sl);
+        finish(S, r, fail(GS_ERR_INTERNAL, msg));
+    }
+    for (Request *r : S->queue) finish(S, r, fail(GS_ERR_INTERNAL, msg));
+    S->queue.clear();
+    S->sort_wait.clear();  // their slots were freed above
+    S->comp_slots.clear();
+    S->comp_busy = false;
+    S->cv_done.notify_all();
+}
+
+void scheduler(gs_server *S)
+{
+    try {
+        scheduler_loop(S);
+    } catch (const std::exception &e) {
+        scheduler_failed(S, e.what());
+    } catch (...) {
+        scheduler_failed(S, "unknown exception");
+    }
+}
+
 }  // namespace
 }  // namespace gsr
 
@@ -547,6 +594,7 @@ gs_status gs_server_create(int device, size_t sort_budget_bytes, int max_infligh
     S->fault_alloc = fault_at("alloc");
     S->fault_enqueue = fault_at("enqueue");
     S->fault_wait = fault_at("wait");
+    S->fault_thread = fault_at("thread");
     cudaError_t e = S->arena.init(sort_budget_bytes);
     S->slots.resize(max_inflight);
     for (Slot &sl : S->slots) {
@@ -642,6 +690,10 @@ gs_status gs_server_submit(gs_server *S, int32_t scene_id, const gs_camera *cam,
             delete q;
             return fail(GS_ERR_CANCELLED, "server is shutting down");
         }
+        if (S->dead) {
+            delete q;
+            return fail(GS_ERR_INTERNAL, "the server's scheduler stopped: " + S->thread_msg);
+        }
         q->scene = scene_id;
         q->id = S->next_id++;
         S->all[q->id] = q;
@@ -690,6 +742,7 @@ gs_status gs_server_drain(gs_server *S)
     if (!S) return fail(GS_ERR_INVALID_ARG, "NULL server");
     std::unique_lock<std::mutex> lk(S->mu);
     S->cv_done.wait(lk, [&] { return S->pending == 0; });
+    if (S->dead) return fail(GS_ERR_INTERNAL, "the server's scheduler stopped: " + S->thread_msg);
     return GS_OK;
 }
 

@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(KeyT) == 8 ? 3 : 4)
         const KeyT key = s_keys[i];
         const uint32_t d = (uint32_t)(key >> shift) & 0xFFu;
         const uint32_t g = s_base[d] + (i - s_start[d]);
-        if (g < K) {
+        if (GSR_IN_BOUNDS(g, K, err)) {
             kout[g] = key;
             vout[g] = s_vals[i];
         }

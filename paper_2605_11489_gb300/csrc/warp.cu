@@ -349,6 +349,7 @@ gs_status check_warp_args(const gs_camera *src, const gs_camera *dst, const gs_w
 extern "C" gs_status gs_warp(gs_context *ctx, const gs_camera *src, const gs_camera *dst, const gs_warp_input *in,
                              const gs_warp_output *out, gs_stream stream)
 {
+    gsr::NvtxRange nvtx_("gsr.warp");
     using namespace gsr;
     if (!ctx) return fail(GS_ERR_INVALID_ARG, "ctx is NULL");
     gs_status r = check_warp_args(src, dst, in, out);

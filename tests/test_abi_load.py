@@ -67,3 +67,19 @@ def test_product_never_imports_oracle():
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "oracle.c" not in txt, f
+
+
+def test_debug_build_compiles_and_exports_every_declared_symbol():
+    """The GSR_DEBUG build (device index guards that raise kErrBounds) cross-compiles for
+    sm_103a from the same sources and exports the same entry points."""
+    import ctypes
+
+    from paper_2605_11489_gb300 import build as b
+
+    path = b.build(debug=True)
+    assert path.endswith("libgsr_debug.so") and os.path.exists(path)
+    L = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(L, name), name
+    L.gs_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in L.gs_version()

@@ -177,3 +177,45 @@ def test_injected_host_failure_ends_only_its_request(env, fault):
     assert sum(1 for s in sts if s != 0) == 1, sts
     assert sts[int(fault.split(":")[1])] != 0
     srv.close()
+
+
+def test_scheduler_thread_failure_fails_pending_requests_and_later_submits(env):
+    """GSR_FAULT=thread:2: the scheduler thread throws before its third admission. With one
+    in-flight slot, requests 0 and 1 complete first (and equal the plain forward); every
+    other request finishes with GS_ERR_INTERNAL once the thread has waited for its GPU
+    work; later submits and drain report GS_ERR_INTERNAL; destroy still returns."""
+    api, ctx = env
+    import torch
+
+    from paper_2605_11489_gb300 import abi
+
+    scene = api.Scene.from_arrays(synth.tiny_scene(4096, 10))
+    cam = synth.tiny_camera()
+    old = os.environ.get("GSR_FAULT")
+    os.environ["GSR_FAULT"] = "thread:2"
+    try:
+        srv = api.Server(sort_budget_bytes=64 << 20, max_inflight=1)
+    finally:
+        if old is None:
+            del os.environ["GSR_FAULT"]
+        else:
+            os.environ["GSR_FAULT"] = old
+    try:
+        sid = srv.load_scene(scene)
+        outs = [api.alloc_outputs(cam.width, cam.height) for _ in range(6)]
+        rids = [srv.submit(sid, cam, o) for o in outs]
+        sts = [_wait(srv, r)[0] for r in rids]
+        assert sts == [abi.GS_OK, abi.GS_OK] + [abi.GS_ERR_INTERNAL] * 4, sts
+        ref = ctx.forward(scene, cam, tile=16, chunk=1 << 24)
+        torch.cuda.synchronize()
+        for o in outs[:2]:
+            for k in ref:
+                assert torch.equal(o[k], ref[k]), k
+        with pytest.raises(abi.GsError) as e:
+            srv.submit(sid, cam, outs[0])
+        assert e.value.status == abi.GS_ERR_INTERNAL
+        with pytest.raises(abi.GsError) as e:
+            srv.drain()
+        assert e.value.status == abi.GS_ERR_INTERNAL
+    finally:
+        srv.close()
