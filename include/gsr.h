@@ -100,12 +100,12 @@ typedef struct {
     uint32_t flags;               /* GS_EMIT_* */
     int32_t chunk;                /* least records per chunk of a long tile list. A list longer than
                                      `head` is composited by G warps per 8x4 pixel block (8 at tile
-                                     8, 2 at tile 16), one per depth-contiguous chunk of ceil(len / g)
-                                     records, g = min(G, ceil(len / chunk)), merged exactly (the
-                                     product rule of Eq. 2-4, the stop rule re-applied in the chunk
-                                     where it falls). 16..2^24, 0 = autotuned/default 512 */
-    int32_t head;                 /* a list longer than this is long, >= chunk; 0 = 4 * chunk.
-                                     At tile 32 no list is long. */
+                                     8 while lists average at most 1,024 records, else 16), one per
+                                     depth-contiguous chunk of ceil(len / g) records, g = min(G,
+                                     ceil(len / chunk)), merged exactly (the product rule of Eq. 2-4,
+                                     the stop rule re-applied in the chunk where it falls).
+                                     16..2^24, 0 = autotuned/default 512 */
+    int32_t head;                 /* a list longer than this is long, >= chunk; 0 = 4 * chunk */
 } gs_render_opts;
 
 /* Caller-owned device outputs; a NULL plane is not written (and, for dcdx and

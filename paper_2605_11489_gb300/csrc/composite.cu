@@ -30,10 +30,10 @@
 // Load balance. The plan (launch_plan) orders the tiles longest first and
 // separates the long ones (list longer than `head` records). k_composite takes
 // the short tiles, one CTA each. k_composite_long runs beside it on a second
-// stream: a persistent grid whose CTAs take long tiles from a counter, with G
-// warps per 8x4 pixel block (8 at tile 8, 2 at tile 16; at tile 32 no list is
-// long). Warp j of a block takes the j-th of g depth-contiguous chunks of the
-// list (g = min(G, ceil(len / chunk))) and composites it from the
+// stream: a persistent grid whose 16-warp CTAs take (long tile, group of 8x4 pixel
+// blocks) items from a counter, with G warps per block (8 for a two-block group,
+// 16 for a one-block group). Warp j of a block takes the j-th of g depth-contiguous
+// chunks of the list (g = min(G, ceil(len / chunk))) and composites it from the
 // identity state into a per-pixel partial state (C, C_x, C_y, D, T, T_x, T_y) in
 // shared memory. Two segments a, b compose exactly as
 //   C = Ca + Ta Cb,  C_x = Cxa + Txa Cb + Ta Cxb,  D = Da + Ta Db,
@@ -432,48 +432,45 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(const CompositeArgs a)
 }
 
 // The long tiles of the plan (the load-balance note at the top): a persistent grid
-// whose CTAs take the next long tile from the plan's counter. Warp w owns pixel
-// block w % NB of the tile and chunk j = w / NB of its list; a tile of `len`
-// records has g = min(G, ceil(len / chunk)) chunks of ceil(len / g) records.
-// (Tried and slower on the 1M workload: a CTA per pixel block with 8, 12 or 16
-// chunk warps, and 16 chunk warps per block at tile 8.)
+// whose CTAs of kLongWarps warps take (long tile, group of BPC pixel blocks) items from the
+// plan's counter. Warp w owns pixel block w % BPC of the group and chunk j = w / BPC of the
+// tile's list; a list of `len` records has g = min(G, ceil(len / chunk)) chunks of
+// ceil(len / g) records, G = kLongWarps / BPC. BPC = 2 (a whole 8x8 tile, 8 chunk warps per
+// block) measured best on lists of a few hundred records on average; BPC = 1 (16 chunk warps
+// per block) serves longer lists and the larger tiles.
 constexpr int kLongBatch = 32;
-template <int TILE>
-__host__ __device__ constexpr int long_groups()  // G: warps per pixel block (16 warps per CTA)
-{
-    return TILE == 8 ? 8 : 2;
-}
-template <int TILE>
+constexpr int kLongWarps = 16;
 __host__ __device__ constexpr size_t long_smem_bytes()
 {
-    return sizeof(WarpRing<kLongBatch>) * (size_t)(TILE * TILE / 32) * long_groups<TILE>() +
-           sizeof(float) * kPartialVals * TILE * TILE * long_groups<TILE>();
+    return sizeof(WarpRing<kLongBatch>) * (size_t)kLongWarps + sizeof(float) * kPartialVals * 32 * kLongWarps;
 }
 
-template <int TILE, bool GRAD, bool STATE>
-__global__ void __launch_bounds__(TILE *TILE *long_groups<TILE>()) k_composite_long(const CompositeArgs a)
+template <int TILE, int BPC, bool GRAD, bool STATE>
+__global__ void __launch_bounds__(kLongWarps * 32) k_composite_long(const CompositeArgs a)
 {
-    constexpr int NT = TILE * TILE, NB = NT / 32, G = long_groups<TILE>();
+    constexpr int NB = TILE * TILE / 32, G = kLongWarps / BPC, NP = BPC * 32, GROUPS = NB / BPC;
+    static_assert(NB % BPC == 0 && kLongWarps % BPC == 0, "blocks per CTA must divide the tile and the CTA");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t s_item;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t j = (uint32_t)(warp / NB);
-    const int pix = (warp % NB) * 32 + lane;  // the pixel's index in the tile, as k_composite's thread index
+    const uint32_t j = (uint32_t)(warp / BPC);
+    const int q = (warp % BPC) * 32 + lane;  // the pixel's index within the group's NP pixels
     WarpRing<kLongBatch> &ring = reinterpret_cast<WarpRing<kLongBatch> *>(smem_raw)[warp];
-    // per chunk, planar [value][NT pixels]
-    float *const part = reinterpret_cast<float *>(smem_raw + sizeof(WarpRing<kLongBatch>) * NB * G);
+    // per chunk, planar [value][NP pixels]
+    float *const part = reinterpret_cast<float *>(smem_raw + sizeof(WarpRing<kLongBatch>) * kLongWarps);
     ring_init(ring);
     uint32_t phase[kStages] = {};
     bool ok = true;
-    const uint32_t n_long = a.plan[0];
+    const uint32_t n_items = a.plan[0] * (uint32_t)GROUPS;
     const uint32_t chunk = (uint32_t)max(a.chunk, 1);
     for (;;) {
-        __syncthreads();  // every warp is done with the previous tile's partial states
+        __syncthreads();  // every warp is done with the previous item's partial states
         if (threadIdx.x == 0) s_item = atomicAdd(a.long_counter, 1u);
         __syncthreads();
         const uint32_t item = s_item;
-        if (item >= n_long) break;
-        const uint32_t tile = a.tile_order[item];
+        if (item >= n_items) break;
+        const uint32_t tile = a.tile_order[item / GROUPS];
+        const int pix = (int)(item % GROUPS) * NP + q;  // the pixel's index in the tile, as in k_composite
         const uint2 r = a.ranges[tile];
         const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
         const uint32_t g = max(1u, min((uint32_t)G, (len + chunk - 1) / chunk));
@@ -487,7 +484,7 @@ __global__ void __launch_bounds__(TILE *TILE *long_groups<TILE>()) k_composite_l
         PixelAcc s;
         acc_init(s, inside && j < g);
         if (j < g) ok &= warp_span<kLongBatch, GRAD, STATE>(a, px, py, bx0, by0, r.x + c0, r.x + c1, c0, ring, phase, s);
-        write_partial<NT>(part + (size_t)j * kPartialVals * NT, pix, s);
+        write_partial<NP>(part + (size_t)j * kPartialVals * NP, q, s);
         __syncthreads();
         if (j >= g) continue;
         // phase 2: the chunk holding the pixel's stop, from the product chain of the
@@ -495,9 +492,9 @@ __global__ void __launch_bounds__(TILE *TILE *long_groups<TILE>()) k_composite_l
         int rel = 1;
         float T = 1.0f;
         for (uint32_t i = 0; i <= j; ++i) {
-            const float *pi = part + (size_t)i * kPartialVals * NT;
-            const float Ti = pi[10 * NT + pix];
-            if (pi[14 * NT + pix] != 0.0f || __fmul_rn(T, Ti) < kTMin) {
+            const float *pi = part + (size_t)i * kPartialVals * NP;
+            const float Ti = pi[10 * NP + q];
+            if (pi[14 * NP + q] != 0.0f || __fmul_rn(T, Ti) < kTMin) {
                 rel = i < j ? -1 : 0;
                 break;
             }
@@ -509,7 +506,7 @@ __global__ void __launch_bounds__(TILE *TILE *long_groups<TILE>()) k_composite_l
             acc_init(P, true);
             for (uint32_t i = 0; i < j; ++i) {
                 PixelAcc Q;
-                read_partial<NT>(part + (size_t)i * kPartialVals * NT, pix, Q);
+                read_partial<NP>(part + (size_t)i * kPartialVals * NP, q, Q);
                 compose<GRAD, STATE>(P, Q);
             }
             compose<GRAD, STATE>(P, s);
@@ -525,7 +522,7 @@ __global__ void __launch_bounds__(TILE *TILE *long_groups<TILE>()) k_composite_l
             if (walk)
                 for (uint32_t i = 0; i < j; ++i) {
                     PixelAcc Q;
-                    read_partial<NT>(part + (size_t)i * kPartialVals * NT, pix, Q);
+                    read_partial<NP>(part + (size_t)i * kPartialVals * NP, q, Q);
                     compose<GRAD, STATE>(P, Q);
                 }
             ok &= warp_span<kLongBatch, GRAD, STATE>(a, px, py, bx0, by0, r.x + c0, r.y, c0, ring, phase, P);
@@ -652,33 +649,35 @@ cudaError_t launch_t(const CompositeArgs &a, int batch, cudaStream_t s)
 // CTAs of k_composite_long per SM (two of its 16-warp CTAs leave room for the short tiles' CTAs)
 constexpr int kLongCtasPerSm = 2;
 
-template <int TILE, bool GRAD, bool STATE>
+template <int TILE, int BPC, bool GRAD, bool STATE>
 cudaError_t launch_long_one(const CompositeArgs &a, int64_t max_long, cudaStream_t s)
 {
-    constexpr size_t smem = long_smem_bytes<TILE>();
+    constexpr size_t smem = long_smem_bytes();
     static bool done[64];
-    cudaError_t e = opt_in_smem(k_composite_long<TILE, GRAD, STATE>, smem, done);
+    cudaError_t e = opt_in_smem(k_composite_long<TILE, BPC, GRAD, STATE>, smem, done);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int64_t grid = std::min<int64_t>(max_long, (int64_t)std::max(sms, 1) * kLongCtasPerSm);
+    const int64_t items = max_long * (TILE * TILE / 32 / BPC);
+    const int64_t grid = std::min<int64_t>(items, (int64_t)std::max(sms, 1) * kLongCtasPerSm);
     if (grid <= 0) return cudaSuccess;
-    k_composite_long<TILE, GRAD, STATE><<<(unsigned)grid, TILE * TILE * long_groups<TILE>(), smem, s>>>(a);
+    k_composite_long<TILE, BPC, GRAD, STATE><<<(unsigned)grid, kLongWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int TILE>
-cudaError_t launch_long_t(const CompositeArgs &a, int64_t max_long, cudaStream_t s)
+template <int TILE, int BPC>
+cudaError_t launch_long_tb(const CompositeArgs &a, int64_t max_long, cudaStream_t s)
 {
-    static_assert(long_smem_bytes<TILE>() <= (size_t)kMaxSmem, "k_composite_long must fit shared memory");
     const bool grad = a.dcdx || a.dcdy;
     const bool state = a.final_T != nullptr;
-    if (grad && state) return launch_long_one<TILE, true, true>(a, max_long, s);
-    if (grad) return launch_long_one<TILE, true, false>(a, max_long, s);
-    if (state) return launch_long_one<TILE, false, true>(a, max_long, s);
-    return launch_long_one<TILE, false, false>(a, max_long, s);
+    if (grad && state) return launch_long_one<TILE, BPC, true, true>(a, max_long, s);
+    if (grad) return launch_long_one<TILE, BPC, true, false>(a, max_long, s);
+    if (state) return launch_long_one<TILE, BPC, false, true>(a, max_long, s);
+    return launch_long_one<TILE, BPC, false, false>(a, max_long, s);
 }
+
+static_assert(long_smem_bytes() <= (size_t)kMaxSmem, "k_composite_long must fit shared memory");
 
 template <int TILE>
 int persistent_grid()
@@ -720,13 +719,11 @@ cudaError_t launch_composite_long(const CompositeArgs &a, int tile, int64_t max_
     if (a.tiles_x == 0 || a.tiles_y == 0 || max_long <= 0) return cudaSuccess;
     if (a.nrm_sorted || a.pair_counts) return cudaErrorInvalidValue;  // those frames have no long tiles
     switch (tile) {
-    case 8: return launch_long_t<8>(a, max_long, s);
-    case 16: return launch_long_t<16>(a, max_long, s);
-    default: return cudaSuccess;
+    case 8: return a.long_bpc == 2 ? launch_long_tb<8, 2>(a, max_long, s) : launch_long_tb<8, 1>(a, max_long, s);
+    case 16: return launch_long_tb<16, 1>(a, max_long, s);
+    default: return launch_long_tb<32, 1>(a, max_long, s);
     }
 }
-
-bool composite_long_supported(int tile) { return tile == 8 || tile == 16; }
 
 int composite_persistent_grid(int tile, int batch)
 {

@@ -217,6 +217,7 @@ struct CompositeArgs {
     const uint32_t *plan;
     uint32_t *long_counter;        // plan + 1, handed out by k_composite_long's CTAs
     int32_t chunk;                 // least records per chunk of a long tile
+    int32_t long_bpc;              // pixel blocks per k_composite_long CTA: 2 (8 chunk warps each) or 1 (16)
     unsigned long long *pair_counts;  // (evaluated, blended) pairs: the GS_COUNT_PAIRS census (nullable)
     // normal channel (nullable: the normal variant runs only when nrm_sorted is set, whole tiles only)
     const float4 *nrm_sorted;      // normals in sorted (instance) order, like rec
@@ -227,10 +228,10 @@ struct CompositeArgs {
                                    // (kErrTmaTimeout), then waits for its copies in flight
 };
 // Long tile lists. A list longer than `head` records (default kHeadChunks * chunk)
-// is composited by k_composite_long: G warps per 8x4 pixel block (8 at tile 8, 2 at
-// tile 16), each taking one of g = min(G, ceil(len / chunk)) depth-contiguous
-// chunks, merged exactly in shared memory. Shorter lists, and every list at tile
-// 32, take one warp per block (k_composite).
+// is composited by k_composite_long: G warps per 8x4 pixel block (8 when a CTA takes
+// two blocks, 16 when it takes one), each taking one of g = min(G, ceil(len / chunk))
+// depth-contiguous chunks, merged exactly in shared memory. Shorter lists take one
+// warp per block (k_composite).
 constexpr int kHeadChunks = 4;
 // Plan of a frame's compositing: tile_order = the long tiles, then the others, each
 // part bucketed by floor(log2(length)), longest first; plan = (n_long, 0, n_short).
@@ -244,10 +245,9 @@ bool composite_supported(int tile, int batch);
 // The short tiles of a plan: one CTA per tile (grid n_tiles, CTAs past n_short exit).
 cudaError_t launch_composite(const CompositeArgs &a, int tile, int batch, cudaStream_t s);
 // The long tiles of a plan, up to max_long of them: a persistent grid of CTAs that take
-// tiles from the plan's work counter. No-op at tile 32 (its plan has no long tiles).
+// (tile, pixel-block group) items from the plan's work counter (a.long_bpc blocks a group:
+// 2 only at tile 8).
 cudaError_t launch_composite_long(const CompositeArgs &a, int tile, int64_t max_long, cudaStream_t s);
-// long tiles are composited apart at tile 8 and 16
-bool composite_long_supported(int tile);
 
 // serving: tiles of several requests from one (request, tile) work list
 struct ServeItem {  // one request's compositing description (device copy)

@@ -111,6 +111,7 @@ struct Frame {
     int chunk = 512;      // least records per chunk of a long tile list
     int head = 4 * 512;   // a list longer than this is a long tile
     int64_t max_long = 0; // long tiles the frame's capacity allows (0: none composited apart)
+    int long_bpc = 2;     // pixel blocks per long-tile CTA (composite.cu)
     ForkJoin fork;        // the long tiles' stream beside the launch stream
     Buf fT, fTx, fTy, ncontrib;
     Buf nrm, nrm_sorted;      // the normal channel: per Gaussian, then in sorted (instance) order
@@ -350,6 +351,9 @@ namespace gsr {
 namespace {
 
 constexpr int kDefaultTile = 16, kDefaultBatch = 32, kDefaultChunk = 512;
+// average records per tile (capacity / tiles) up to which a tile-8 long-tile CTA takes the
+// whole tile
+constexpr int64_t kLongBpcAvgMax = 1024;
 
 // tile / batch / chunk: explicit options win, then the autotuner's cache for
 // (W, H, N bucket, SH degree), then the defaults.
@@ -381,9 +385,8 @@ gs_status frame_setup(Frame *f, const gs_scene *s, const gs_camera *c, const gs_
     f->tile = tile;
     f->batch = batch;
     if (chunk < 16 || chunk > (1 << 24)) return fail(GS_ERR_INVALID_ARG, "chunk must be 0 or 16..2^24");
-    int64_t head = o->head ? (int64_t)o->head : (int64_t)kHeadChunks * chunk;
+    const int64_t head = o->head ? (int64_t)o->head : (int64_t)kHeadChunks * chunk;
     if (head < chunk || head > (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "head must be 0 or chunk..2^30");
-    if (!composite_long_supported(tile)) head = 1ll << 30;  // tile 32: every list takes one warp per block
     f->chunk = chunk;
     f->head = (int)head;
     f->want_nrm = false;
@@ -440,6 +443,9 @@ gs_status frame_keys(Frame *f, int64_t cap)
 gs_status frame_plan(Frame *f, int64_t cap)
 {
     f->max_long = f->head >= (1 << 30) ? 0 : std::min<int64_t>(f->n_tiles, cap / ((int64_t)f->head + 1) + 1);
+    // a long-tile CTA takes a whole 8x8 tile (8 chunk warps per block) while lists hold a few
+    // hundred records on average; with longer lists, and at larger tiles, one block (16)
+    f->long_bpc = (f->tile == 8 && cap <= kLongBpcAvgMax * (int64_t)f->n_tiles) ? 2 : 1;
     GSR_CUDA(f->plan.ensure(sizeof(uint32_t) * 3));
     if (f->max_long > 0) GSR_CUDA(f->fork.ensure());
     if (f->has_state) GSR_CUDA(f->keys64.ensure(sizeof(uint64_t) * (size_t)std::max<int64_t>(cap, 1)));
@@ -501,6 +507,7 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
     c.tile_order = f->order.as<uint32_t>();
     c.plan = f->plan.as<uint32_t>();
     c.long_counter = f->plan.as<uint32_t>() + 1;
+    c.long_bpc = f->long_bpc;
     c.chunk = f->chunk;
     if (f->count_pairs) c.pair_counts = reinterpret_cast<unsigned long long *>(f->counters.as<uint32_t>() + kCntPairs);
     if (f->want_nrm) {

@@ -151,8 +151,7 @@ def _dense_scene(n, seed, opaque=False):
 def test_split_tiles_exact_merge(env, opaque, chunk):
     """Long tile lists (longer than head = 4 * chunk records) composited in
     depth-contiguous chunks by several warps per 8x4 pixel block (g = min(G,
-    len / chunk) chunks, G = 8 at tile 8 and 2 at tile 16) and merged in shared
-    memory, against the unsplit pass and the oracle; with
+    len / chunk) chunks, G = 8 or 16) and merged in shared memory, against the unsplit pass and the oracle; with
     opaque Gaussians the T < 1e-4 stop falls inside first and later chunks, and
     a chunk holding a pixel's stop is re-walked from the exact prefix state."""
     api, O, ctx = env
@@ -162,7 +161,7 @@ def test_split_tiles_exact_merge(env, opaque, chunk):
     ref = O.render(sc, cam, bg=bg)
     if opaque:
         assert (ref["final_T"] < 2e-4).mean() > 0.02  # the stop is reached in many pixels
-    for tile in (8, 16):
+    for tile in (8, 16, 32):
         whole = _render(api, ctx, sc, cam, bg=bg, tile=tile, chunk=1 << 24)
         split, st = _render(api, ctx, sc, cam, bg=bg, tile=tile, chunk=chunk, state=True)
         v = st.view()
