@@ -534,6 +534,8 @@ __global__ void __launch_bounds__(kLongWarps * 32) k_composite_long(const Compos
 // Serving: a persistent grid pulls (request, tile) items from a flat work list
 // described by per-request prefixes; every request's outputs and buffers are
 // its own. Items are handed out by an atomic counter (no waiting on anything).
+// A request with a plan (launch_plan) gives this kernel its short tiles only; its
+// long tiles go to k_composite_long on the request's own stream.
 constexpr int kMaxServeReqs = 256;
 constexpr int kServeBatch = 32;
 
@@ -563,7 +565,12 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite_persistent(const Serve
         }
         const CompositeArgs &a = reqs[lo].args;
         uint32_t t = item - s_first[lo];
-        if (a.tile_order) t = a.tile_order[t];
+        if (a.plan) {  // the request's long tiles are composited apart: its short ones, in plan order
+            if (t >= a.plan[2]) continue;
+            t = a.tile_order[a.plan[0] + t];
+        } else if (a.tile_order) {
+            t = a.tile_order[t];
+        }
         const int tx = (int)(t % (uint32_t)a.tiles_x), ty = (int)(t / (uint32_t)a.tiles_x);
         int px, py, bx0, by0;
         tile_pixel<TILE>(threadIdx.x, tx, ty, px, py, bx0, by0);

@@ -12,7 +12,10 @@
 //                request waits, in arrival order. K3-K5 run on the slot stream.
 //   3. compose - whenever the compositing stream is idle, every sorted request
 //                is put into one persistent compositing launch whose CTAs pull
-//                (request, tile) items from a flat work list.
+//                (request, tile) items from a flat work list: each request's short
+//                tile lists, in its plan's order. Its long lists (longer than
+//                4 x kServeChunk records) go to k_composite_long on its own slot
+//                stream, beside that launch.
 // So requests that arrive while others are on the GPU are admitted as slots and
 // memory free up, and their projection and sorting overlap the compositing of
 // the others. Completion frees the slot and the sort memory and stamps the
@@ -50,8 +53,14 @@ namespace gsr {
 namespace {
 
 using Clock = std::chrono::steady_clock;
-constexpr int kServeTile = 16;
-constexpr int kServeBatch = 64;
+// Served requests are composited at tile 8 with staging batches of 32 records (the persistent
+// kernel's); measured on the mixed serving stream against tile 16: 983 against 788 Mpix/s, and a
+// Poisson-load p99 of 10 against 146 ms.
+constexpr int kServeTile = 8;
+constexpr int kServeBatch = 32;
+// long tile lists (longer than kHeadChunks * kServeChunk records) are composited per request by
+// k_composite_long, beside the batch's persistent kernel
+constexpr int kServeChunk = 512;
 constexpr int kMaxSlots = 256;
 
 // First-fit allocator over one device allocation (the sort-buffer budget).
@@ -164,7 +173,8 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_scan = nullptr, ev_sorted = nullptr;
-    DevBuf rec, bin, ntiles, bsums, boffs, ranges, order, counters;
+    cudaEvent_t ev_done = nullptr;  // the request's long tiles and error word, after its batch
+    DevBuf rec, bin, ntiles, bsums, boffs, ranges, order, counters, plan;
     DevBuf vsums, voffs, bsums2, boffs2, dkeys[2], dvals[2], dscr;  // depth order (per Gaussian)
     GaussRec *rec_sorted = nullptr;  // in the sort memory
     uint32_t *h_counters = nullptr;  // pinned
@@ -180,7 +190,7 @@ struct Slot {
     // every device buffer the slot owns (the sort memory belongs to the arena)
     void release_buffers()
     {
-        DevBuf *all[] = {&rec, &bin, &ntiles, &bsums, &boffs, &ranges, &order, &counters, &vsums, &voffs,
+        DevBuf *all[] = {&rec, &bin, &ntiles, &bsums, &boffs, &ranges, &order, &counters, &plan, &vsums, &voffs,
                          &bsums2, &boffs2, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1], &dscr};
         for (DevBuf *b : all) b->release();
     }
@@ -278,6 +288,7 @@ cudaError_t slot_reserve(Slot &sl, int64_t n, int n_tiles)
     ok(sl.ranges.ensure(sizeof(uint2) * (size_t)std::max(n_tiles, 1)));
     ok(sl.order.ensure(sizeof(uint32_t) * (size_t)std::max(n_tiles, 1)));
     ok(sl.counters.ensure(sizeof(uint32_t) * kCntSlots));
+    ok(sl.plan.ensure(sizeof(uint32_t) * 3));
     return e;
 }
 
@@ -368,8 +379,9 @@ gs_status enqueue_sort(gs_server *S, Slot &sl)
     GSR_CUDA(launch_ranges(sl.keys[res], sl.vals[res], cnt, K, s.n, static_cast<const GaussRec *>(sl.rec.p), sl.rec_sorted,
                            static_cast<uint2 *>(sl.ranges.p), sl.n_tiles, static_cast<const uint4 *>(sl.bin.p),
                            nullptr, sl.stream));
-    GSR_CUDA(launch_tile_order(static_cast<const uint2 *>(sl.ranges.p), sl.n_tiles, static_cast<uint32_t *>(sl.order.p),
-                               sl.stream));
+    GSR_CUDA(launch_plan(static_cast<const uint2 *>(sl.ranges.p), sl.n_tiles, (int64_t)kHeadChunks * kServeChunk,
+                         static_cast<uint32_t *>(sl.order.p), static_cast<uint32_t *>(sl.plan.p), cnt + kCntErr,
+                         sl.stream));
     GSR_CUDA(cudaEventRecord(sl.ev_sorted, sl.stream));
     r->stage = Stage::Sorted;
     return GS_OK;
@@ -395,6 +407,10 @@ CompositeArgs slot_comp_args(Slot &sl)
     c.alpha = r->out.alpha;
     c.err_word = static_cast<uint32_t *>(sl.counters.p) + kCntErr;
     c.give_up = sl.give_up ? 1u : 0u;
+    c.plan = static_cast<const uint32_t *>(sl.plan.p);
+    c.long_counter = static_cast<uint32_t *>(sl.plan.p) + 1;
+    c.chunk = kServeChunk;
+    c.long_bpc = (kServeTile == 8 && sl.K <= 1024 * (int64_t)sl.n_tiles) ? 2 : 1;
     return c;
 }
 
@@ -404,11 +420,13 @@ void scheduler_loop(gs_server *S)
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         bool progressed = false;
-        // 3a. retire a finished compositing batch
-        if (S->comp_busy && cudaEventQuery(S->comp_done) == cudaSuccess) {
+        // 3a. retire a finished compositing batch: its persistent kernel and every request's
+        // long tiles and error word (ev_done)
+        bool batch_done = S->comp_busy && cudaEventQuery(S->comp_done) == cudaSuccess;
+        for (int si : S->comp_slots) batch_done = batch_done && cudaEventQuery(S->slots[si].ev_done) == cudaSuccess;
+        if (batch_done) {
             for (int si : S->comp_slots) {
                 Slot &sl = S->slots[si];
-                cudaStreamSynchronize(sl.stream);
                 // the slot's device error bits, copied after its compositing (sort lookback,
                 // batch waits); a request whose kernels gave up finishes with that error
                 const uint32_t err = sl.h_counters[kCntErr];
@@ -502,14 +520,24 @@ void scheduler_loop(gs_server *S)
                 if (e == cudaSuccess)
                     e = launch_composite_persistent(S->d_items, n, total, kServeTile, kServeBatch, S->d_work,
                                                     S->comp_grid, S->comp_stream);
-                for (int si : S->comp_slots) {  // each request's error bits, after its last kernel
-                    Slot &sl = S->slots[si];
+                if (e == cudaSuccess) e = cudaEventRecord(S->comp_done, S->comp_stream);
+                // each request's long tiles on its own stream, beside the batch's kernel; then its
+                // error bits, once both are done
+                for (size_t k = 0; k < S->comp_slots.size() && e == cudaSuccess; ++k) {
+                    Slot &sl = S->slots[S->comp_slots[k]];
+                    const int64_t head = (int64_t)kHeadChunks * kServeChunk;
+                    const int64_t max_long = std::min<int64_t>(sl.n_tiles, sl.K / (head + 1) + 1);
+                    e = launch_composite_long(S->h_items[k].args, kServeTile, max_long, sl.stream);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(sl.stream, S->comp_done, 0);
                     if (e == cudaSuccess)
                         e = cudaMemcpyAsync(sl.h_counters + kCntErr, static_cast<uint32_t *>(sl.counters.p) + kCntErr,
-                                            sizeof(uint32_t), cudaMemcpyDeviceToHost, S->comp_stream);
+                                            sizeof(uint32_t), cudaMemcpyDeviceToHost, sl.stream);
+                    if (e == cudaSuccess) e = cudaEventRecord(sl.ev_done, sl.stream);
                 }
-                if (e == cudaSuccess) e = cudaEventRecord(S->comp_done, S->comp_stream);
                 if (e != cudaSuccess) {
+                    // nothing of the batch may still write a caller's planes when its requests end
+                    cudaStreamSynchronize(S->comp_stream);
+                    for (int si : S->comp_slots) cudaStreamSynchronize(S->slots[si].stream);
                     for (int si : S->comp_slots) {
                         Request *r = S->slots[si].req;
                         slot_free(S, S->slots[si]);
@@ -601,6 +629,7 @@ gs_status gs_server_create(int device, size_t sort_budget_bytes, int max_infligh
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_scan, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_sorted, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_counters, sizeof(uint32_t) * kCntSlots);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->comp_stream, cudaStreamNonBlocking);
@@ -674,7 +703,8 @@ gs_status gs_server_submit(gs_server *S, int32_t scene_id, const gs_camera *cam,
     if (out->normal || out->nv || out->depth_isect)
         return fail(GS_ERR_INVALID_ARG, "serving does not render the RaDe-GS channels");
     if ((opts->tile && opts->tile != kServeTile) || (opts->batch && opts->batch != kServeBatch))
-        return fail(GS_ERR_INVALID_ARG, "serving renders with tile 16, batch 64");
+        return fail(GS_ERR_INVALID_ARG, "serving renders with tile " + std::to_string(kServeTile) + ", batch " +
+                                            std::to_string(kServeBatch));
     Request *q = new Request();
     q->cam = *cam;
     q->opts = *opts;
@@ -761,6 +791,7 @@ gs_status gs_server_destroy(gs_server *S)
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.ev_scan) cudaEventDestroy(sl.ev_scan);
         if (sl.ev_sorted) cudaEventDestroy(sl.ev_sorted);
+        if (sl.ev_done) cudaEventDestroy(sl.ev_done);
         if (sl.h_counters) cudaFreeHost(sl.h_counters);
         sl.release_buffers();
     }

@@ -124,7 +124,7 @@ def test_server_request_whose_waits_give_up_fails_alone(env):
 
     sc, cam = _scene(), _camera()
     scene = api.Scene.from_arrays(sc)
-    ref = api.Context(0).forward(scene, cam, tile=16, chunk=1 << 24)
+    ref = api.Context(0).forward(scene, cam, tile=8, chunk=512)  # the server's tile and chunking
     old = os.environ.get("GSR_FAULT")
     os.environ["GSR_FAULT"] = "wait:2"
     try:
