@@ -302,9 +302,11 @@ gs_status gs_frame_stream_stats(gs_frame_stream *fs, int32_t slot, int reset, gs
 gs_status gs_frame_stream_destroy(gs_frame_stream *fs);
 
 /* ---------------------------------------------------------------- autotuner
- * Times the forward for every tile in {8, 16, 32}, batch in {32, 64, 128, 256}
+ * Times the render for every tile in {8, 16, 32}, batch in {32, 64, 128, 256}
  * (pairs whose per-warp staging rings fit shared memory) and chunk in
- * {256, 512, 1024} (CUDA events, `iters` frames each, after one warm-up) and
+ * {256, 512, 1024}: one plain forward gives the configuration's instance count,
+ * which sizes a graph (as gs_graph_create), whose replays of `cam` are timed
+ * (CUDA events, `iters` frames one at a time, after one warm-up). It
  * records the fastest in the context's cache, keyed by (W, H, N bucket, SH
  * degree); later calls with tile / batch / chunk = 0 use it. Synchronous.
  * Any output pointer may be NULL. */

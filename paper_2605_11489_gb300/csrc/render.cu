@@ -1171,6 +1171,9 @@ gs_status gs_autotune(gs_context *ctx, const gs_scene *scene, const gs_camera *c
     GSR_CUDA(cudaEventCreate(&e0));
     GSR_CUDA(cudaEventCreate(&e1));
     const int tiles[3] = {8, 16, 32}, batches[4] = {32, 64, 128, 256}, chunks[3] = {256, 512, 1024};
+    gs_outputs planes = *out;  // timed on the standard planes (graphs render no RaDe-GS channel)
+    planes.normal = planes.nv = planes.depth_isect = nullptr;
+    out = &planes;
     float best = 1e30f;
     int bt = kDefaultTile, bb = kDefaultBatch, bc = kDefaultChunk;
     for (int t : tiles)
@@ -1181,13 +1184,23 @@ gs_status gs_autotune(gs_context *ctx, const gs_scene *scene, const gs_camera *c
                 o.tile = t;
                 o.batch = b;
                 o.chunk = c;
-                r = gs_render_forward(ctx, scene, cam, &o, out, nullptr, stream);  // warm-up
+                // one plain forward gives this configuration's instance count, which sizes a
+                // graph; the graph's replays are timed, as frames are rendered in streams
+                r = gs_render_forward(ctx, scene, cam, &o, out, nullptr, stream);
                 if (r != GS_OK) break;
+                const int64_t K =
+                    (int64_t)ctx->h_counters[kCntTotal] | ((int64_t)ctx->h_counters[kCntTotalHi] << 32);
+                gs_graph *g = nullptr;
+                r = gs_graph_create(ctx, scene, cam, &o, out, std::min<int64_t>(K + K / 4 + 4096, kMaxInstances),
+                                    stream, &g);
+                if (r != GS_OK) break;
+                r = gs_graph_render(g, cam, stream);  // warm-up
                 cudaEventRecord(e0, st);
-                for (int it = 0; it < iters && r == GS_OK; ++it)
-                    r = gs_render_forward(ctx, scene, cam, &o, out, nullptr, stream);
+                for (int it = 0; it < iters && r == GS_OK; ++it) r = gs_graph_render(g, cam, stream);
                 cudaEventRecord(e1, st);
                 cudaEventSynchronize(e1);
+                if (r == GS_OK) r = gs_graph_check(g, stream, nullptr);
+                gs_graph_destroy(g);
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 ms /= iters;
