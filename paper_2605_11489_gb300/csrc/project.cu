@@ -325,44 +325,71 @@ __global__ void __launch_bounds__(256) k_colour(ProjectArgs a)
     r[9] = fmaxf(col[2] + 0.5f, 0.0f);  // r2.y
 }
 
-// One Gaussian per thread, kProjPerBlock (1,024) per block -- the unit of the
-// per-block tile and visibility sums the scan reads. A warp reads 128
-// contiguous bytes of every plane. (Four Gaussians per thread with 16-byte
-// loads needed 80 registers and left the SMs at ~36 % warp occupancy.)
-constexpr int kGeomThreads = kProjPerBlock;
+// Two Gaussians per thread, 512 apart (each warp reads 128 contiguous bytes of every plane),
+// kProjPerBlock (1,024) per block -- the unit of the per-block tile and visibility sums the
+// scan reads. Both Gaussians' parameters are loaded before either is projected, so the
+// second one's loads are in flight during the first one's arithmetic; two 512-thread blocks
+// share an SM. (One Gaussian per thread in 1,024-thread blocks, one block per SM at 54
+// registers, stalled on those loads; four Gaussians per thread with 16-byte loads needed
+// 80 registers and left the SMs at ~36 % warp occupancy.)
+constexpr int kGeomPer = 2;
+constexpr int kGeomThreads = kProjPerBlock / kGeomPer;
+
+struct GaussIn {
+    float mx, my, mz, ls0, ls1, ls2, qw, qx, qy, qz, logit;
+};
 
 template <bool NRM>
-__global__ void __launch_bounds__(kGeomThreads, 1) k_project(ProjectArgs a)
+__device__ __forceinline__ void project_store(const ProjectArgs &a, int64_t i, const GaussIn &g, uint32_t &tiles,
+                                              uint32_t &vis)
 {
-    const int64_t i = (int64_t)blockIdx.x * kGeomThreads + threadIdx.x;
     const int64_t n4 = (a.n + 3) & ~(int64_t)3;  // ntiles is read 4 at a time: its padding is written 0
+    tiles = vis = 0u;
+    if (i >= n4) return;
+    Proj Q;
+    Q.vis = false;
+    Q.nt = 0;
+    if (i < a.n)
+        project_one<NRM>(a.cam, g.mx, g.my, g.mz, g.ls0, g.ls1, g.ls2, g.qw, g.qx, g.qy, g.qz, g.logit, Q);
+    if (Q.vis) {  // colour left 0 for k_colour
+        GaussRec r;
+        r.r0 = make_float4(Q.u, Q.v, Q.ca, Q.cb);
+        r.r1 = make_float4(Q.cc, Q.o, Q.z, 0.0f);
+        r.r2 = make_float4(0.0f, 0.0f, __uint_as_float(Q.rlo), __uint_as_float(Q.rhi));
+        a.rec[i] = r;
+        a.bin[i] = make_uint4(__float_as_uint(Q.z), Q.rlo, Q.rhi, 0u);
+        if (NRM) {
+            a.nrm[i] = make_float4(Q.n[0], Q.n[1], Q.n[2], 0.0f);
+            a.plane[i] = make_float2(Q.pl[0], Q.pl[1]);
+        }
+    }
+    a.ntiles[i] = Q.nt;
+    tiles = Q.nt;
+    vis = Q.vis ? 1u : 0u;
+}
+
+template <bool NRM>
+__global__ void __launch_bounds__(kGeomThreads, 2) k_project(ProjectArgs a)
+{
+    const int64_t i0 = (int64_t)blockIdx.x * kProjPerBlock + threadIdx.x;
+    const int64_t np = a.n_pad;
+    GaussIn g[kGeomPer];
+#pragma unroll
+    for (int k = 0; k < kGeomPer; ++k) {
+        const int64_t i = i0 + (int64_t)k * kGeomThreads;
+        const bool in = i < a.n;
+        auto ld = [&](const float *base, int row) { return in ? __ldg(base + (int64_t)row * np + i) : 0.0f; };
+        g[k] = GaussIn{ld(a.means, 0),  ld(a.means, 1), ld(a.means, 2), ld(a.log_scales, 0), ld(a.log_scales, 1),
+                       ld(a.log_scales, 2), ld(a.quats, 0), ld(a.quats, 1), ld(a.quats, 2), ld(a.quats, 3),
+                       ld(a.logits, 0)};
+    }
     uint32_t my_tiles = 0, my_vis = 0;
-    if (i < n4) {
-        Proj Q;
-        Q.vis = false;
-        Q.nt = 0;
-        if (i < a.n) {
-            const int64_t np = a.n_pad;
-            auto ld = [&](const float *base, int row) { return __ldg(base + (int64_t)row * np + i); };
-            project_one<NRM>(a.cam, ld(a.means, 0), ld(a.means, 1), ld(a.means, 2), ld(a.log_scales, 0),
-                        ld(a.log_scales, 1), ld(a.log_scales, 2), ld(a.quats, 0), ld(a.quats, 1), ld(a.quats, 2),
-                        ld(a.quats, 3), ld(a.logits, 0), Q);
-        }
-        if (Q.vis) {  // colour left 0 for k_colour
-            GaussRec r;
-            r.r0 = make_float4(Q.u, Q.v, Q.ca, Q.cb);
-            r.r1 = make_float4(Q.cc, Q.o, Q.z, 0.0f);
-            r.r2 = make_float4(0.0f, 0.0f, __uint_as_float(Q.rlo), __uint_as_float(Q.rhi));
-            a.rec[i] = r;
-            a.bin[i] = make_uint4(__float_as_uint(Q.z), Q.rlo, Q.rhi, 0u);
-            if (NRM) {
-                a.nrm[i] = make_float4(Q.n[0], Q.n[1], Q.n[2], 0.0f);
-                a.plane[i] = make_float2(Q.pl[0], Q.pl[1]);
-            }
-        }
-        a.ntiles[i] = Q.nt;
-        my_tiles = Q.nt;
-        my_vis = Q.vis ? 1u : 0u;
+#pragma unroll
+    for (int k = 0; k < kGeomPer; ++k) {
+        uint32_t t, v;
+        project_store<NRM>(a, i0 + (int64_t)k * kGeomThreads, g[k], t, v);
+        my_tiles += t;
+        my_vis += v;
     }
     // block sum of tiles touched -> per-block sums for the instance-offset scan
     __shared__ uint32_t s_warp[2][kGeomThreads / 32];

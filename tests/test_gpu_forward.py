@@ -174,8 +174,11 @@ def test_split_tiles_exact_merge(env, opaque, chunk):
             assert d < 2e-5, (k, d)
 
 
-def test_split_tiles_backward_state(env):
-    """The backward pass over a split frame equals the backward over the unsplit one."""
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_split_tiles_backward_state(env, tile):
+    """The backward pass over a frame whose long lists were composited in chunks (the
+    long-tile kernel's two-block and one-block groups, at every tile size) equals the
+    backward over the unsplit one."""
     api, O, ctx = env
     import torch
 
@@ -185,7 +188,7 @@ def test_split_tiles_backward_state(env):
     gi = {k: torch.from_numpy(v).cuda() for k, v in synth.upstream_grads(96, 64, 2).items()}
     grads = []
     for chunk in (1 << 24, 64, 16):
-        out, st = ctx.forward(scene, cam, state=True, chunk=chunk)
+        out, st = ctx.forward(scene, cam, state=True, chunk=chunk, tile=tile)
         g = ctx.backward(st, scene, gi)
         st.free()
         grads.append([t.clone() for t in g])
