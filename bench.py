@@ -4,7 +4,7 @@ A step renders one frame of the workload's camera path through the whole hot
 path (projection + SH colour, scan, key duplication, radix sort, tile ranges,
 compositing with dC/dx, dC/dy, depth and alpha), replayed as a captured CUDA
 graph with the frame's camera (the fixed-resolution stream path), with
---frames-in-flight frames (default 4) rendering concurrently on their own streams
+--frames-in-flight frames (default 6) rendering concurrently on their own streams
 (api.FrameStream over the C ABI's gs_frame_stream_*). The scene is
 resident in HBM before timing starts and is larger than L2, so steps do not
 reuse each other's inputs from cache.
@@ -1100,7 +1100,7 @@ def main():
     ap.add_argument("--no-normals", action="store_true", help="skip the normal-channel timing")
     ap.add_argument("--no-legs", action="store_true",
                     help="the headline workload only (without the 6M and serving legs of the default line)")
-    ap.add_argument("--frames-in-flight", type=int, default=4,
+    ap.add_argument("--frames-in-flight", type=int, default=6,
                     help="frames rendered concurrently, one graph and stream each (api.FrameStream)")
     args = ap.parse_args()
     if args.warmup < 3:

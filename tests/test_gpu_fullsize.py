@@ -5,7 +5,7 @@ against the FP64 oracle:
     sort of the whole instance list (the 1M frames at the default tile and at the
     benchmark's tile 8; the 6M frame at 480x270);
   - every pixel of whole frames rendered the way bench.py times them: captured
-    graphs replayed through api.FrameStream with 4 frames in flight, at the
+    graphs replayed through api.FrameStream with 6 frames in flight, at the
     autotuner's tile / batch / chunk (what bench.py picks) and at tile 8, batch
     128, chunk 2048, against the oracle's binned render of the same frame, at the
     stated bars of gpu_util (colour 2e-4 on >= 99.99 % and 5e-3 on all, depth the
@@ -21,7 +21,7 @@ from gpu_util import check_render
 
 pytestmark = pytest.mark.gpu
 
-BENCH_SLOTS = 4  # bench.py's default --frames-in-flight
+BENCH_SLOTS = 6  # bench.py's default --frames-in-flight
 
 
 @pytest.fixture(scope="module")
