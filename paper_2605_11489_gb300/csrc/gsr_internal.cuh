@@ -192,13 +192,15 @@ int sort_passes(int bits);
 // hist_ready: scr.hist already holds the digit histograms of the keys (built
 // by launch_duplicate), so the histogram pass is skipped. give_up: every
 // lookback gives up at once (diagnostic; sets kErrSortTimeout, output unsorted).
+// wide: partitions of 512 threads with 8 keys each instead of 256 with 16 (the faster
+// shape for the depth sort of the visible Gaussians; the narrow one for the tile keys).
 cudaError_t launch_sort(uint64_t *keys[2], uint32_t *vals[2], const uint32_t *counters, uint32_t *err_word,
                         int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s,
-                        bool hist_ready = false, bool give_up = false);
+                        bool hist_ready = false, bool give_up = false, bool wide = false);
 // The same over 32-bit keys; the element count is the device word *count.
 cudaError_t launch_sort32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *count, uint32_t *err_word,
                           int64_t max_k, int bits, const SortScratch &scr, int *result, cudaStream_t s,
-                          bool hist_ready, bool give_up = false);
+                          bool hist_ready, bool give_up = false, bool wide = false);
 
 struct CompositeArgs {
     const GaussRec *rec;  // records in sorted (instance) order: tile t's list is rec[ranges[t].x, ranges[t].y)

@@ -546,7 +546,7 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     uint32_t *dk[2] = {f->dkeys[0].as<uint32_t>(), f->dkeys[1].as<uint32_t>()};
     uint32_t *dv[2] = {f->dvals[0].as<uint32_t>(), f->dvals[1].as<uint32_t>()};
     int dres = 0;
-    GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, err, f->n, 32, scr, &dres, st, true, f->give_up));
+    GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, err, f->n, 32, scr, &dres, st, true, f->give_up, true));
     GSR_CUDA(mark(mk, 4, st));
     nvtx_stage.next("gsr.tile_keys_sort");
     // K3b, K4b: tile keys in depth order, then stable by tile

@@ -366,7 +366,7 @@ gs_status enqueue_sort(gs_server *S, Slot &sl)
                             static_cast<uint32_t *>(sl.voffs.p), s.n, dk[0], dv[0], dscr.hist, sl.stream));
     int dres = 0;
     GSR_CUDA(launch_sort32(dk, dv, cnt + kCntVisible, cnt + kCntErr, s.n, 32, dscr, &dres, sl.stream, true,
-                           sl.give_up));
+                           sl.give_up, true));
     const int tbits = sl.bits - 32;
     GSR_CUDA(launch_duplicate(dv[dres], cnt + kCntVisible, s.n, static_cast<uint32_t *>(sl.ntiles.p),
                               static_cast<uint4 *>(sl.bin.p), static_cast<uint32_t *>(sl.bsums2.p),
