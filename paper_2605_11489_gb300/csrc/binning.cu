@@ -121,6 +121,19 @@ __device__ __forceinline__ uint32_t block_excl(uint32_t mine, uint32_t *s_warp, 
 }
 
 // Adds a block's digit histograms (shared, `n` bins) into the global ones.
+// floor(a / b) for a < 2^16 and 1 <= b < 2^16 (a key's position in its Gaussian's tile
+// rectangle and the rectangle's width; at most 65,536 tiles): a single-precision estimate,
+// with exact operands and a relative error under 2^-22, is within 1/64 of a / b, so at most
+// one off; the remainder corrects it.
+__device__ __forceinline__ uint32_t div_small(uint32_t a, uint32_t b)
+{
+    uint32_t q = (uint32_t)__fmul_rz((float)a, __frcp_rn((float)b));
+    const int r = (int)a - (int)(q * b);
+    if (r < 0) --q;
+    else if (r >= (int)b) ++q;
+    return q;
+}
+
 __device__ __forceinline__ void flush_hist(const uint32_t *s_hist, uint32_t *hist, int n)
 {
     __syncthreads();
@@ -144,12 +157,16 @@ __global__ void __launch_bounds__(kProjThreads) k_compact(const uint32_t *__rest
     uint4 nt = make_uint4(0, 0, 0, 0);
     if (i0 < n) nt = *reinterpret_cast<const uint4 *>(ntiles + i0);
     const uint32_t vis[4] = {nt.x != 0u, nt.y != 0u, nt.z != 0u, nt.w != 0u};
+    // the visible Gaussians' depth keys are loaded before the block scan's barrier
+    uint32_t zk[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) zk[g] = vis[g] ? bin[i0 + g].x : 0u;
     uint32_t total;
     uint32_t off = vis_offs[blockIdx.x] + block_excl(vis[0] + vis[1] + vis[2] + vis[3], s_warp, total);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         if (!vis[g]) continue;
-        const uint32_t z = bin[i0 + g].x;
+        const uint32_t z = zk[g];
         dkeys[off] = z;
         dvals[off] = (uint32_t)(i0 + g);
         ++off;
@@ -246,15 +263,14 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
     const unsigned long long base = (unsigned long long)block_offs[blockIdx.x] + warp_first;
     bool overflow = false;
     for (uint32_t e = (uint32_t)lane; e < T; e += 32) {
-        int lo = 0, hi = kPerWarp;  // last j with s_pre[j] <= e (it has a nonzero count)
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (s_pre[warp][mid] <= e) lo = mid + 1;
-            else hi = mid;
-        }
-        const int j = lo - 1;
+        // the last j with s_pre[j] <= e (it has a nonzero count, as s_pre[kPerWarp] = T > e):
+        // seven fixed halving steps, s_pre[0] = 0 <= e throughout
+        int j = 0;
+#pragma unroll
+        for (int step = kPerWarp / 2; step >= 1; step >>= 1)
+            if (s_pre[warp][j + step] <= e) j += step;
         const uint32_t li = e - s_pre[warp][j], w = s_wid[warp][j], org = s_org[warp][j];
-        const uint32_t q = li / w;
+        const uint32_t q = div_small(li, w);
         const uint32_t tile = ((org >> 16) + q) * (uint32_t)tiles_x + (org & 0xFFFFu) + (li - q * w);
         const unsigned long long off = base + e;
         if (off < capacity) {
