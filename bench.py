@@ -747,9 +747,9 @@ def run_pipeline(args):
                 "hr_mpix_s": 16 * W * H * fps / 1e6,
                 "serial": {"frames_per_s": 1e3 * args.steps * world / ms_serial, "ms_per_step": ms_serial / args.steps},
                 "speedup_vs_serial": ms_serial / ms, "clocks": clocks,
-                # per frame: the render graph's kernels (15 + 2 tile-sort passes), 2 interpolations,
+                # per frame: the render graph's kernels (13 + 2 tile-sort passes), 2 interpolations,
                 # 2 warps x 2
-                "gpu_launches": args.steps * (15 + 2 + 2 + 4)}
+                "gpu_launches": args.steps * (13 + 2 + 2 + 4)}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -1074,9 +1074,9 @@ def measure_render(args, name, ctx, stream, sc, cams, world, rank, local_rank, f
             "roofline": roof, "stage_roofline": stage_roofline, "clocks": clocks, "e2e": e2e,
             "cpu_baseline": cpu,
             # kernels per frame: projection, colour, block scan, compaction, 4 depth-sort
-            # passes, tile-count sums, their scan, duplication, `tile_passes` tile-sort
-            # passes, ranges, plan, the long-tile and the short-tile compositing kernels
-            "gpu_launches": args.steps * (15 + tile_passes)}
+            # passes, duplication, `tile_passes` tile-sort passes, ranges, plan, the long-tile
+            # and the short-tile compositing kernels
+            "gpu_launches": args.steps * (13 + tile_passes)}
 
 
 def main():

@@ -88,14 +88,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const uint32_t *__
     }
 }
 
-// Plain exclusive scan of per-block sums (K3b's counts in depth order).
-__global__ void __launch_bounds__(kScanThreads) k_scan_plain(const uint32_t *__restrict__ sums, int nb,
-                                                             uint32_t *__restrict__ offs)
-{
-    __shared__ unsigned long long s_warp[kScanThreads / 32];
-    block_scan_counts(sums, nb, offs, s_warp);
-}
-
 // Block-wide exclusive prefix of one value per thread (256 threads) and the
 // block total.
 __device__ __forceinline__ uint32_t block_excl(uint32_t mine, uint32_t *s_warp, uint32_t &total)
@@ -176,63 +168,114 @@ __global__ void __launch_bounds__(kProjThreads) k_compact(const uint32_t *__rest
     flush_hist(s_hist, hist, 4 * 256);
 }
 
-// K3b, first half: per 1,024 depth-sorted Gaussians (256 threads x 4), the
-// sum of their tile counts.
-// An index >= n (only possible when the depth sort gave up and left its output
-// unsorted, holes included) counts as a Gaussian with no tiles.
-__global__ void __launch_bounds__(kProjThreads) k_sorted_counts(const uint32_t *__restrict__ dvals,
-                                                                const uint32_t *__restrict__ vcount,
-                                                                const uint32_t *__restrict__ ntiles,
-                                                                uint32_t *__restrict__ sums, uint32_t n)
+// K3b's lookback words: word 0 the partition ticket, then per partition of 1,024 sorted
+// Gaussians its tile count (flag kDupAgg) or the inclusive prefix of the counts (kDupPre).
+constexpr unsigned long long kDupAgg = 1ull << 62;
+constexpr unsigned long long kDupPre = 2ull << 62;
+constexpr unsigned long long kDupFlags = 3ull << 62;
+constexpr unsigned long long kDupVal = kDupAgg - 1ull;
+constexpr uint32_t kDupMaxSpins = 1u << 22;
+
+__device__ __forceinline__ unsigned long long ld_vol64(const unsigned long long *p)
 {
-    __shared__ uint32_t s_warp[kProjThreads / 32];
-    const uint32_t V = *vcount;
-    const uint32_t i0 = (blockIdx.x * kProjThreads + threadIdx.x) * 4;
-    uint32_t mine = 0;
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        const uint32_t idx = i0 + g < V ? dvals[i0 + g] : n;
-        if (idx < n) mine += ntiles[idx];
-    }
-    uint32_t total;
-    block_excl(mine, s_warp, total);
-    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+__device__ __forceinline__ void st_vol64(unsigned long long *p, unsigned long long v)
+{
+    *reinterpret_cast<volatile unsigned long long *>(p) = v;
 }
 
-// K3b, second half: every depth-sorted Gaussian's keys, key = tile id (32-bit)
-// and value = Gaussian index, for every tile of its support rectangle (rows,
-// then columns), at offsets continuing the scan of K3b's block sums; counts
-// the tile digits. Keys past `capacity` are not written (the overflow bit is
-// set). Each warp owns 128 consecutive sorted Gaussians and deals their keys
-// out to consecutive lanes, so that the stores are coalesced: lane l emits the
-// warp's keys l, l + 32, ..., finding each key's Gaussian by a binary search
-// over the warp's prefix of tile counts.
+// Decoupled lookback of partition `part` (called by one whole warp): publishes the
+// partition's count, reads up to 32 predecessors' words per round trip and sums them, newest
+// first, up to the nearest inclusive prefix, then publishes its own inclusive prefix. Returns
+// the exclusive prefix on every lane. A partition only waits for partitions that drew earlier
+// tickets, which are running or done; each wait is still bounded: after max_spins polls it
+// sets kErrSortTimeout and takes the sum so far (the keys then land at wrong offsets, in
+// bounds). max_spins = 0 gives up before the first look (a diagnostic setting).
+__device__ unsigned long long dup_lookback(unsigned long long *st, uint32_t part, uint32_t count,
+                                           uint32_t max_spins, uint32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    if (part == 0) {
+        if (lane == 0) st_vol64(st, kDupPre | count);
+        return 0ull;
+    }
+    if (lane == 0) st_vol64(st + part, kDupAgg | count);
+    unsigned long long excl = 0ull;
+    int p = (int)part - 1;  // the newest predecessor not yet summed
+    uint32_t spins = 0;
+    bool gave_up = max_spins == 0u;
+    while (!gave_up) {
+        const int q = p - lane;
+        const unsigned long long w = q >= 0 ? ld_vol64(st + q) : kDupPre;  // before partition 0: 0
+        const uint32_t ready = __ballot_sync(0xffffffffu, (w & kDupFlags) != 0ull);
+        const uint32_t pre = __ballot_sync(0xffffffffu, (w & kDupFlags) == kDupPre);
+        const int lim = pre ? __ffs(pre) - 1 : 31;  // lanes 0..lim are summed
+        const uint32_t need = lim == 31 ? 0xffffffffu : (2u << lim) - 1u;
+        if ((ready & need) != need) {
+            if (++spins > max_spins) {
+                gave_up = true;
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        unsigned long long v = lane <= lim ? (w & kDupVal) : 0ull;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pre) break;
+        p -= 32;
+    }
+    if (gave_up && lane == 0) atomicOr(err, kErrSortTimeout);
+    if (lane == 0) st_vol64(st + part, kDupPre | ((excl + count) & kDupVal));
+    return excl;
+}
+
+// K3b: every depth-sorted Gaussian's keys, key = tile id (32-bit) and value = Gaussian
+// index, for every tile of its support rectangle (rows, then columns), in depth order; counts
+// the tile digits. Keys past `capacity` are not written (the overflow bit is set). One pass:
+// each block takes a partition of 1,024 sorted Gaussians by ticket, sums their tile counts and
+// finds the partition's offset by decoupled lookback (`look`). Each warp owns 128 consecutive
+// sorted Gaussians and deals their keys out to consecutive lanes, so that the stores are
+// coalesced: lane l emits the warp's keys l, l + 32, ..., finding each key's Gaussian by a
+// search over the warp's prefix of tile counts.
+// An index >= n (only possible when the depth sort gave up and left its output unsorted,
+// holes included) counts as a Gaussian with no tiles.
 __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__restrict__ dvals,
                                                             const uint32_t *__restrict__ vcount,
                                                             const uint32_t *__restrict__ ntiles,
                                                             const uint4 *__restrict__ bin,
-                                                            const uint32_t *__restrict__ block_offs, int tile_shift,
+                                                            unsigned long long *__restrict__ look, int tile_shift,
                                                             int tiles_x, uint32_t *__restrict__ keys,
                                                             uint32_t *__restrict__ vals, unsigned long long capacity,
                                                             uint32_t *err, uint32_t *__restrict__ hist, int passes,
-                                                            uint32_t n)
+                                                            uint32_t n, uint32_t max_spins)
 {
     constexpr int kWarps = kProjThreads / 32, kPerWarp = 128;
     __shared__ uint32_t s_warp[kWarps];
     __shared__ uint32_t s_hist[2 * 256];
+    __shared__ uint32_t s_part;
+    __shared__ unsigned long long s_base;
     __shared__ uint32_t s_pre[kWarps][kPerWarp + 1];  // exclusive prefix of tile counts, then the warp's total
     __shared__ uint32_t s_idx[kWarps][kPerWarp];      // Gaussian index
     __shared__ uint32_t s_org[kWarps][kPerWarp];      // first tile of its rectangle: tx | ty << 16
     __shared__ uint32_t s_wid[kWarps][kPerWarp];      // width of its rectangle in tiles
     for (int i = threadIdx.x; i < 2 * 256; i += kProjThreads) s_hist[i] = 0;
+    if (threadIdx.x == 0) s_part = (uint32_t)atomicAdd(look, 1ull);
+    __syncthreads();
+    const uint32_t part = s_part;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t V = *vcount;
-    const uint32_t i0 = (blockIdx.x * kProjThreads + threadIdx.x) * 4;
+    // a partition past the visible Gaussians has no keys, nor has any later ticket's: none
+    // of them is waited for
+    if ((unsigned long long)part * kProjPerBlock >= V) return;
+    const uint32_t i0 = (part * kProjThreads + threadIdx.x) * 4;
     uint32_t cnt[4], mine = 0;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         uint32_t idx = i0 + g < V ? dvals[i0 + g] : 0u;
-        if (!GSR_IN_BOUNDS(idx, n, err)) idx = 0u;  // (an unsorted depth order, see k_sorted_counts): no tiles
+        if (!GSR_IN_BOUNDS(idx, n, err)) idx = 0u;  // (an unsorted depth order): no tiles
         cnt[g] = i0 + g < V && dvals[i0 + g] < n ? ntiles[idx] : 0u;
         uint32_t org = 0, wid = 1;
         if (cnt[g]) {
@@ -249,6 +292,10 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
     }
     uint32_t total;
     const uint32_t excl = block_excl(mine, s_warp, total);  // (block-wide; includes a barrier)
+    if (warp == 0) {
+        const unsigned long long b = dup_lookback(look + 1, part, total, max_spins, err);
+        if (lane == 0) s_base = b;
+    }
     // the warp's offsets: prefix within the warp, the warp's first key's global offset
     const uint32_t warp_first = __shfl_sync(0xffffffffu, excl, 0);
     uint32_t run = excl - warp_first;
@@ -259,8 +306,9 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
     }
     if (lane == 31) s_pre[warp][kPerWarp] = run;
     __syncwarp();
+    __syncthreads();  // s_base
     const uint32_t T = s_pre[warp][kPerWarp];
-    const unsigned long long base = (unsigned long long)block_offs[blockIdx.x] + warp_first;
+    const unsigned long long base = s_base + warp_first;
     bool overflow = false;
     for (uint32_t e = (uint32_t)lane; e < T; e += 32) {
         // the last j with s_pre[j] <= e (it has a nonzero count, as s_pre[kPerWarp] = T > e):
@@ -497,9 +545,9 @@ cudaError_t launch_compact(const uint32_t *ntiles, const uint4 *bin, const uint3
 }
 
 cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int64_t max_v, const uint32_t *ntiles,
-                             const uint4 *bin, uint32_t *bsums, uint32_t *boffs, int tile_shift, int tiles_x,
-                             uint32_t *keys, uint32_t *vals, int64_t capacity, uint32_t *counters, uint32_t *hist,
-                             int passes, cudaStream_t s, uint32_t *err)
+                             const uint4 *bin, unsigned long long *look, int tile_shift, int tiles_x, uint32_t *keys,
+                             uint32_t *vals, int64_t capacity, uint32_t *counters, uint32_t *hist, int passes,
+                             cudaStream_t s, uint32_t *err, bool give_up)
 {
     if (!err) err = counters + kCntErr;
     if (passes < 0 || passes > 2) return cudaErrorInvalidValue;
@@ -507,14 +555,15 @@ cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int6
     if (e != cudaSuccess) return e;
     const int nb = project_blocks(max_v);
     if (nb == 0) return cudaSuccess;
-    k_sorted_counts<<<nb, kProjThreads, 0, s>>>(dvals, vcount, ntiles, bsums, (uint32_t)max_v);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_scan_plain<<<1, kScanThreads, 0, s>>>(bsums, nb, boffs);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_duplicate<<<nb, kProjThreads, 0, s>>>(dvals, vcount, ntiles, bin, boffs, tile_shift, tiles_x, keys, vals,
-                                            (unsigned long long)capacity, err, hist, passes, (uint32_t)max_v);
+    e = cudaMemsetAsync(look, 0, duplicate_look_bytes(max_v), s);
+    if (e != cudaSuccess) return e;
+    k_duplicate<<<nb, kProjThreads, 0, s>>>(dvals, vcount, ntiles, bin, look, tile_shift, tiles_x, keys, vals,
+                                            (unsigned long long)capacity, err, hist, passes, (uint32_t)max_v,
+                                            give_up ? 0u : kDupMaxSpins);
     return cudaGetLastError();
 }
+
+size_t duplicate_look_bytes(int64_t max_v) { return sizeof(unsigned long long) * ((size_t)project_blocks(max_v) + 1); }
 
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, uint32_t *counters, int64_t max_k,
                           int64_t n, const GaussRec *rec, GaussRec *rec_sorted, uint2 *ranges, int n_tiles,

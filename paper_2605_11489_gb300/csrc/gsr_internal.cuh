@@ -45,7 +45,7 @@ struct NvtxStages {
 
 // Error bits written by kernels into a device status word.
 enum : uint32_t {
-    kErrSortTimeout = 1u,       // radix-sort lookback gave up waiting
+    kErrSortTimeout = 1u,       // a radix-sort or duplication lookback gave up waiting
     kErrTmaTimeout = 2u,        // compositing waited too long for a staged batch
     kErrCapacity = 4u,          // instance list exceeded the buffers' capacity
     kErrBounds = 8u,            // a GSR_DEBUG index check fired (the access was skipped)
@@ -163,11 +163,13 @@ cudaError_t launch_compact(const uint32_t *ntiles, const uint4 *bin, const uint3
                            uint32_t *dkeys, uint32_t *dvals, uint32_t *hist, cudaStream_t s);
 // K3b: tile keys (u32) + indices of the depth-sorted Gaussians dvals[0, *vcount),
 // in that order; `hist` (cleared here) gets the tile sort's `passes` (<= 2)
-// digit histograms. bsums/boffs: per 1,024 sorted Gaussians, >= project_blocks(max_v).
+// digit histograms. look: duplicate_look_bytes(max_v) bytes of lookback words (cleared
+// here). give_up: the lookback gives up at once (diagnostic; sets kErrSortTimeout).
 cudaError_t launch_duplicate(const uint32_t *dvals, const uint32_t *vcount, int64_t max_v, const uint32_t *ntiles,
-                             const uint4 *bin, uint32_t *bsums, uint32_t *boffs, int tile_shift, int tiles_x,
-                             uint32_t *keys, uint32_t *vals, int64_t capacity, uint32_t *counters, uint32_t *hist,
-                             int passes, cudaStream_t s, uint32_t *err = nullptr);
+                             const uint4 *bin, unsigned long long *look, int tile_shift, int tiles_x, uint32_t *keys,
+                             uint32_t *vals, int64_t capacity, uint32_t *counters, uint32_t *hist, int passes,
+                             cudaStream_t s, uint32_t *err = nullptr, bool give_up = false);
+size_t duplicate_look_bytes(int64_t max_v);
 // K5: per-tile [start, end) from the sorted tile keys, the records gathered into
 // sorted order, and (keys64 != NULL) each instance's (tile << 32 | depth bits)
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, uint32_t *counters, int64_t max_k,

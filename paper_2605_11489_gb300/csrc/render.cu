@@ -104,7 +104,7 @@ struct ForkJoin {
 struct Frame {
     Buf rec, bin, ntiles, bsums, boffs;
     Buf keys[2], vals[2], sort_scr, rec_sorted;     // tile keys (u32) and Gaussian indices, per instance
-    Buf dkeys[2], dvals[2], vsums, voffs, bsums2, boffs2;  // depth order of the visible Gaussians
+    Buf dkeys[2], dvals[2], vsums, voffs, dlook;  // depth order of the visible Gaussians
     Buf keys64;                                     // (tile << 32 | depth bits) per instance, for a state view
     Buf ranges, order;
     Buf plan;             // (n_long, long-tile work counter, n_short): launch_plan
@@ -410,8 +410,7 @@ gs_status frame_setup(Frame *f, const gs_scene *s, const gs_camera *c, const gs_
     }
     GSR_CUDA(f->vsums.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
     GSR_CUDA(f->voffs.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
-    GSR_CUDA(f->bsums2.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
-    GSR_CUDA(f->boffs2.ensure(sizeof(uint32_t) * (size_t)std::max(nb, 1)));
+    GSR_CUDA(f->dlook.ensure(duplicate_look_bytes(std::max<int64_t>(s->n, 1))));
     GSR_CUDA(f->ranges.ensure(sizeof(uint2) * (size_t)f->n_tiles));
     GSR_CUDA(f->order.ensure(sizeof(uint32_t) * (size_t)f->n_tiles));
     GSR_CUDA(f->counters.ensure(sizeof(uint32_t) * kCntSlots));
@@ -552,9 +551,9 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     // K3b, K4b: tile keys in depth order, then stable by tile
     const int tbits = f->bits - 32;
     GSR_CUDA(launch_duplicate(dv[dres], cnt + kCntVisible, f->n, f->ntiles.as<uint32_t>(), f->bin.as<uint4>(),
-                              f->bsums2.as<uint32_t>(), f->boffs2.as<uint32_t>(), f->cam.tile_shift, f->tiles_x,
+                              f->dlook.as<unsigned long long>(), f->cam.tile_shift, f->tiles_x,
                               f->keys[0].as<uint32_t>(), f->vals[0].as<uint32_t>(), f->key_cap, cnt, scr.hist,
-                              sort_passes(tbits), st, err));
+                              sort_passes(tbits), st, err, f->give_up));
     GSR_CUDA(mark(mk, 5, st));
     uint32_t *kk[2] = {f->keys[0].as<uint32_t>(), f->keys[1].as<uint32_t>()};
     uint32_t *vv[2] = {f->vals[0].as<uint32_t>(), f->vals[1].as<uint32_t>()};

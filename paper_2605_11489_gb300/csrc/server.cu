@@ -175,7 +175,7 @@ struct Slot {
     cudaEvent_t ev_scan = nullptr, ev_sorted = nullptr;
     cudaEvent_t ev_done = nullptr;  // the request's long tiles and error word, after its batch
     DevBuf rec, bin, ntiles, bsums, boffs, ranges, order, counters, plan;
-    DevBuf vsums, voffs, bsums2, boffs2, dkeys[2], dvals[2], dscr;  // depth order (per Gaussian)
+    DevBuf vsums, voffs, dlook, dkeys[2], dvals[2], dscr;  // depth order (per Gaussian)
     GaussRec *rec_sorted = nullptr;  // in the sort memory
     uint32_t *h_counters = nullptr;  // pinned
     void *sort_mem = nullptr;        // from the arena
@@ -191,7 +191,7 @@ struct Slot {
     void release_buffers()
     {
         DevBuf *all[] = {&rec, &bin, &ntiles, &bsums, &boffs, &ranges, &order, &counters, &plan, &vsums, &voffs,
-                         &bsums2, &boffs2, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1], &dscr};
+                         &dlook, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1], &dscr};
         for (DevBuf *b : all) b->release();
     }
 };
@@ -278,8 +278,9 @@ cudaError_t slot_reserve(Slot &sl, int64_t n, int n_tiles)
     ok(sl.rec.ensure(sizeof(GaussRec) * (size_t)n1));
     ok(sl.bin.ensure(sizeof(uint4) * (size_t)n1));
     ok(sl.ntiles.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(n4, 4)));
-    DevBuf *per_block[] = {&sl.bsums, &sl.boffs, &sl.vsums, &sl.voffs, &sl.bsums2, &sl.boffs2};
+    DevBuf *per_block[] = {&sl.bsums, &sl.boffs, &sl.vsums, &sl.voffs};
     for (DevBuf *b : per_block) ok(b->ensure(sizeof(uint32_t) * (size_t)nb));
+    ok(sl.dlook.ensure(duplicate_look_bytes(n1)));
     for (int k = 0; k < 2; ++k) {
         ok(sl.dkeys[k].ensure(sizeof(uint32_t) * (size_t)n1));
         ok(sl.dvals[k].ensure(sizeof(uint32_t) * (size_t)n1));
@@ -369,9 +370,9 @@ gs_status enqueue_sort(gs_server *S, Slot &sl)
                            sl.give_up, true));
     const int tbits = sl.bits - 32;
     GSR_CUDA(launch_duplicate(dv[dres], cnt + kCntVisible, s.n, static_cast<uint32_t *>(sl.ntiles.p),
-                              static_cast<uint4 *>(sl.bin.p), static_cast<uint32_t *>(sl.bsums2.p),
-                              static_cast<uint32_t *>(sl.boffs2.p), sl.cam.tile_shift, sl.cam.tiles_x, sl.keys[0],
-                              sl.vals[0], K, cnt, scr.hist, sort_passes(tbits), sl.stream));
+                              static_cast<uint4 *>(sl.bin.p), static_cast<unsigned long long *>(sl.dlook.p),
+                              sl.cam.tile_shift, sl.cam.tiles_x, sl.keys[0], sl.vals[0], K, cnt, scr.hist,
+                              sort_passes(tbits), sl.stream, nullptr, sl.give_up));
     int res = 0;
     GSR_CUDA(launch_sort32(sl.keys, sl.vals, cnt + kCntEff, cnt + kCntErr, K, tbits, scr, &res, sl.stream, true,
                            sl.give_up));
