@@ -21,8 +21,10 @@
 // - the three input planes and their one-pixel halo are staged in shared memory (zero
 //   outside the image);
 // - each thread evaluates M x + b for two pixels 16 apart, one row of their S x S blocks at
-//   a time, so each weight of M (in the kernel-parameter constant bank) is fetched once
-//   for both pixels;
+//   a time. The two pixels' inputs and sums sit in register pairs, and each weight of M is
+//   stored twice in the kernel-parameter constant bank, so one 64-bit constant load and one
+//   packed FMA (fma.rn.f32x2, two IEEE fmas, the same results as two scalar ones) serve both
+//   pixels;
 // - each block row is written as S contiguous floats (one 16-byte store at S = 4).
 #include <cuda_runtime.h>
 
@@ -38,11 +40,32 @@ constexpr int kGaiPx = 2;                              // pixels per thread, kGa
 constexpr int kGaiThreads = kGaiTX * kGaiTY / kGaiPx;  // 128
 constexpr int kHaloX = kGaiTX + 2, kHaloY = kGaiTY + 2;
 
+// M and b with every entry duplicated ({m, m}): the operand of a packed FMA over two pixels
 template <int S>
 struct GaiParams {
-    float M[S * S][27];
-    float b[S * S];
+    float2 M[S * S][27];
+    float2 b[S * S];
 };
+
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+// two fmas, lane by lane: (a.x * b.x + c.x, a.y * b.y + c.y), each rounded once
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 
 template <int S>
 __global__ void __launch_bounds__(kGaiThreads, 6) k_gai(const GaiParams<S> w, const float *__restrict__ rgb,
@@ -67,15 +90,15 @@ __global__ void __launch_bounds__(kGaiThreads, 6) k_gai(const GaiParams<S> w, co
             tile[2][ly][lx] = ok ? dcdy[g] : 0.f;
         }
         __syncthreads();
-        float in[kGaiPx][27];
+        static_assert(kGaiPx == 2, "the packed FMA takes the thread's two pixels");
+        unsigned long long in[27];  // {pixel 0, pixel 1}
 #pragma unroll
-        for (int p = 0; p < kGaiPx; ++p)
+        for (int q = 0; q < 3; ++q)
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) in[p][9 * q + 3 * i + j] = tile[q][ty + j][tx + p * kHalf + i];
+                for (int j = 0; j < 3; ++j)
+                    in[9 * q + 3 * i + j] = pack2(tile[q][ty + j][tx + i], tile[q][ty + j][tx + kHalf + i]);
         // one row v of the S x S blocks at a time: every weight is fetched once for both pixels
 #pragma unroll
         for (int v = 0; v < S; ++v) {
@@ -83,14 +106,12 @@ __global__ void __launch_bounds__(kGaiThreads, 6) k_gai(const GaiParams<S> w, co
 #pragma unroll
             for (int u = 0; u < S; ++u) {
                 const int s = u * S + v;
+                unsigned long long a2 = pack2(w.b[s].x, w.b[s].y);
 #pragma unroll
-                for (int p = 0; p < kGaiPx; ++p) acc[p][u] = w.b[s];
-#pragma unroll
-                for (int k = 0; k < 27; ++k) {
-                    const float m = w.M[s][k];
-#pragma unroll
-                    for (int p = 0; p < kGaiPx; ++p) acc[p][u] = __fmaf_rn(m, in[p][k], acc[p][u]);
-                }
+                for (int k = 0; k < 27; ++k) a2 = fma2(pack2(w.M[s][k].x, w.M[s][k].y), in[k], a2);
+                const float2 r = unpack2(a2);
+                acc[0][u] = r.x;
+                acc[1][u] = r.y;
             }
 #pragma unroll
             for (int p = 0; p < kGaiPx; ++p) {
@@ -118,8 +139,11 @@ cudaError_t launch_gai_s(const std::vector<double> &M, const std::vector<double>
 {
     GaiParams<S> p;
     for (int s = 0; s < S * S; ++s) {
-        for (int k = 0; k < 27; ++k) p.M[s][k] = (float)M[(size_t)s * 27 + k];
-        p.b[s] = (float)b[s];
+        for (int k = 0; k < 27; ++k) {
+            const float m = (float)M[(size_t)s * 27 + k];
+            p.M[s][k] = make_float2(m, m);
+        }
+        p.b[s] = make_float2((float)b[s], (float)b[s]);
     }
     const dim3 grid((W + kGaiTX - 1) / kGaiTX, (H + kGaiTY - 1) / kGaiTY);  // kGaiThreads threads each
     k_gai<S><<<grid, kGaiThreads, 0, st>>>(p, rgb, dcdx, dcdy, W, H, channels, out);
