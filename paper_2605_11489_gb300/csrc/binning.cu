@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(kProjThreads) k_duplicate(const uint32_t *__re
 // and the L1 request path bound the kernel). Each thread takes four pieces, a
 // block apart, so their loads are in flight together. The pieces with e % 3 == 0
 // also write the tile ranges, (keys64 != NULL) the 64-bit keys and (nrm_sorted, plane_sorted !=
-// NULL) the instance's normal and intersection-depth slope.
+// NULL) the instance's normal and intersection-depth slope. With rec_sorted NULL (compositing
+// then gathers each batch's records by index) a thread takes whole instances instead.
 constexpr int kRangeThreads = 256, kRangePer = 4;
 
 __global__ void __launch_bounds__(kRangeThreads)
@@ -359,7 +360,10 @@ __global__ void __launch_bounds__(kRangeThreads)
     // (kErrSortTimeout) the keys are not sorted and may hold stale words, and the frame is
     // reported as failed, but nothing is read or written out of bounds.
     const uint32_t K = counters[kCntEff];
-    const uint32_t P = 3u * K;  // 16-byte pieces (K < 2^30)
+    // work units: three 16-byte pieces per instance when the records are gathered, else the
+    // instances themselves
+    const uint32_t per = rec_sorted ? 3u : 1u;
+    const uint32_t P = per * K;  // (K < 2^30)
     const uint32_t e0 = blockIdx.x * (kRangeThreads * kRangePer) + threadIdx.x;
     const float4 *src = reinterpret_cast<const float4 *>(rec);
     float4 *dst = reinterpret_cast<float4 *>(rec_sorted);
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(kRangeThreads)
 #pragma unroll
     for (int k = 0; k < kRangePer; ++k) {
         const uint32_t e = e0 + (uint32_t)k * kRangeThreads;
-        g[k] = e < P ? vals[e / 3u] : 0u;
+        g[k] = e < P ? vals[e / per] : 0u;
         if (!GSR_IN_BOUNDS(g[k], n, err)) g[k] = 0u;
     }
     if (rec_sorted) {
@@ -386,8 +390,8 @@ __global__ void __launch_bounds__(kRangeThreads)
 #pragma unroll
     for (int k = 0; k < kRangePer; ++k) {
         const uint32_t e = e0 + (uint32_t)k * kRangeThreads;
-        if (e >= P || e % 3u != 0u) continue;
-        const uint32_t i = e / 3u;
+        if (e >= P || e % per != 0u) continue;
+        const uint32_t i = e / per;
         const uint32_t t = keys[i];
         if (GSR_IN_BOUNDS(t, n_tiles, err)) {
             if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
@@ -575,7 +579,7 @@ cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *vals, uint32_t *
     if (e != cudaSuccess) return e;
     if (max_k <= 0) return cudaSuccess;
     const int64_t per_block = (int64_t)kRangeThreads * kRangePer;
-    const int64_t nb = (3 * max_k + per_block - 1) / per_block;
+    const int64_t nb = ((rec_sorted ? 3 : 1) * max_k + per_block - 1) / per_block;
     k_ranges<<<(unsigned)nb, kRangeThreads, 0, s>>>(keys, vals, counters, err, rec, rec_sorted, ranges, bin, keys64,
                                                     nrm, nrm_sorted, plane, plane_sorted, (uint32_t)std::max<int64_t>(n, 1),
                                                     (uint32_t)n_tiles);

@@ -15,9 +15,12 @@
 // GB300 layout: one CTA per work item (a tile, or a chunk of a long tile
 // list), one pixel per thread, and every warp an independent 8x4 pixel block
 // with its own shared-memory ring of kStages batches of BATCH records and its
-// own mbarriers. Lane 0 stages the next batches of the tile's (contiguous,
-// sorted) records with one TMA bulk copy per batch (cp.async.bulk, completion
-// counted on the warp's mbarrier) while the warp blends the current one; per
+// own mbarriers. The next batches are staged while the warp blends the current
+// one: from the tile's contiguous sorted records (the frames that keep that copy:
+// backward state, normal channels, the server), lane 0 issues one TMA bulk copy
+// per batch (cp.async.bulk, completion counted on the warp's mbarrier); in a
+// plain forward every lane gathers its batch positions' records by Gaussian
+// index (cp.async, one group per batch), so no sorted copy is made. Per
 // group of 32 records, each lane forms the mask of block pixels inside one
 // record's rectangle, and a warp-wide bit transpose of those masks gives each
 // lane the records whose rectangle holds its own pixel; it blends only these,
@@ -159,6 +162,16 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// gather mode: one 16-byte piece global -> shared (through L2), per-lane groups
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // 32x32 bit-matrix transpose across a warp: lane j holds row j (bit L = column
 // L); returns column `lane` (bit j = row j's bit `lane`). Five butterfly stages,
 // each swapping the off-diagonal blocks of the next-smaller block size.
@@ -200,9 +213,28 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
     const int nbatches = (int)((total + BATCH - 1) / BATCH);
     if (__all_sync(0xffffffffu, s.done) || nbatches == 0) return true;
 
-    // batch b -> ring slot b % kStages; lane 0 issues one bulk copy per batch
+    // batch b -> ring slot b % kStages. Sorted records: lane 0 issues one bulk copy per batch,
+    // counted on the slot's mbarrier. Gather mode: each lane copies the records of its batch
+    // positions (lane, lane + 32, ...) by index, three 16-byte pieces each, as one cp.async
+    // group per batch; every lane commits exactly one group per batch slot (empty past the
+    // list), so waiting for all but the newest kStages - 1 groups waits for batch b.
+    const bool gather = a.rec_index != nullptr;
     auto issue = [&](int b) {
-        if (lane == 0) {
+        if (gather) {
+            const int buf = b % kStages;
+            const uint32_t start = s0 + (uint32_t)b * BATCH;
+            const uint32_t cnt = min((uint32_t)BATCH, s1 - start);
+            for (uint32_t j = (uint32_t)lane; j < cnt; j += 32u) {
+                uint32_t g = __ldg(a.vals + start + j);
+                if (!GSR_IN_BOUNDS(g, a.n_gauss, a.err_word)) g = 0u;
+                const float4 *src = reinterpret_cast<const float4 *>(a.rec_index + g);
+                float4 *dst = reinterpret_cast<float4 *>(&ring.rec[buf][j]);
+                cp_async16(dst, src);
+                cp_async16(dst + 1, src + 1);
+                cp_async16(dst + 2, src + 2);
+            }
+            cp_async_commit();
+        } else if (lane == 0) {
             const int buf = b % kStages;
             const uint32_t start = s0 + (uint32_t)b * BATCH;
             const uint32_t cnt = min((uint32_t)BATCH, s1 - start);
@@ -216,19 +248,28 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
     const float lx = block_px(px), ly = block_py(py);
     bool ok = true;
 
-    for (int b = 0; b < kStages - 1 && b < nbatches; ++b) issue(b);
+    for (int b = 0; b < kStages - 1; ++b) {
+        if (b < nbatches) issue(b);
+        else if (gather) cp_async_commit();
+    }
     int b = 0;
     const uint32_t first_tries = a.give_up ? 0u : kWaitTries;
     for (; b < nbatches; ++b) {
         const int buf = b % kStages;
-        __syncwarp();  // the lanes' writes of block centres into the slot precede its refill
+        __syncwarp();  // the lanes' reads and writes of block centres in the slot precede its refill
         if (b + kStages - 1 < nbatches) issue(b + kStages - 1);
-        if (!mbar_wait_bounded(&ring.bar[buf], phase[buf], first_tries)) ok = false;
-        if (!__all_sync(0xffffffffu, ok)) {  // batch b is still in flight: drained below
-            ok = false;                      // (the same on every lane, so the drain is too)
-            break;
+        else if (gather) cp_async_commit();
+        if (gather) {
+            cp_async_wait<kStages - 1>();  // this lane's copies of batch b have landed
+            __syncwarp();                  // and every other lane's
+        } else {
+            if (!mbar_wait_bounded(&ring.bar[buf], phase[buf], first_tries)) ok = false;
+            if (!__all_sync(0xffffffffu, ok)) {  // batch b is still in flight: drained below
+                ok = false;                      // (the same on every lane, so the drain is too)
+                break;
+            }
+            phase[buf] ^= 1u;
         }
-        phase[buf] ^= 1u;
         const uint32_t cnt = min((uint32_t)BATCH, s1 - (s0 + (uint32_t)b * BATCH));
         GaussRec *recs = ring.rec[buf];  // this warp's own staged copy
         const uint32_t pos_b = pos0 + (uint32_t)b * BATCH + 1u;
@@ -294,6 +335,11 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
     // CTA exits: after a warp finishes batch b - 1 early, batches b .. b + kStages - 2 are in
     // flight; after a wait on batch b gives up, batches b .. b + kStages - 1 are (b's own copy
     // included). Each is waited for with the full bound.
+    if (gather) {
+        cp_async_wait<0>();  // the copies issued ahead of an early exit, before the slots are reused
+        __syncwarp();
+        return ok;
+    }
     const int in_flight_end = ok ? b + kStages - 1 : b + kStages;
     for (int q = b; q < nbatches && q < in_flight_end; ++q) {
         if (!mbar_wait_bounded(&ring.bar[q % kStages], phase[q % kStages], kWaitTries)) ok = false;

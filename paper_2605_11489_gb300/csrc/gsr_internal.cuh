@@ -206,7 +206,12 @@ cudaError_t launch_sort32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *
 
 struct CompositeArgs {
     const GaussRec *rec;  // records in sorted (instance) order: tile t's list is rec[ranges[t].x, ranges[t].y)
-    const uint32_t *vals;
+    const uint32_t *vals;  // the Gaussian index of each instance, sorted like rec
+    // gather mode (rec_index set, rec unused): the records by Gaussian index, each batch
+    // gathered through vals; indices >= n_gauss (possible only after a sort gave up) read
+    // record 0
+    const GaussRec *rec_index;
+    uint32_t n_gauss;
     const uint2 *ranges;
     int32_t width, height, tiles_x, tiles_y;
     float bg[3];

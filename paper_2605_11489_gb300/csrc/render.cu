@@ -479,11 +479,22 @@ ProjectArgs proj_args(Frame *f, const gs_scene *s)
     return a;
 }
 
+// A plain forward (no backward state, no normal channels) composites from the records by
+// Gaussian index, each warp gathering its batches through the sorted indices, so K5 does
+// not copy the records into instance order. The backward and the normal channels read that
+// sorted copy (and the normal path its sorted normals).
+bool gather_records(const Frame *f) { return !f->has_state && !f->want_nrm; }
+
 CompositeArgs comp_args(Frame *f, const gs_outputs *out)
 {
     CompositeArgs c{};
-    c.rec = f->rec_sorted.as<GaussRec>();
     c.vals = f->vals[f->sorted].as<uint32_t>();
+    if (gather_records(f)) {
+        c.rec_index = f->rec.as<GaussRec>();
+        c.n_gauss = (uint32_t)std::max<int64_t>(f->n, 1);
+    } else {
+        c.rec = f->rec_sorted.as<GaussRec>();
+    }
     c.ranges = f->ranges.as<uint2>();
     c.width = f->W;
     c.height = f->H;
@@ -562,7 +573,8 @@ gs_status enqueue_after_scan(Frame *f, const gs_outputs *out, int64_t max_k, cud
     f->sorted = res;
     GSR_CUDA(mark(mk, 6, st));
     nvtx_stage.next("gsr.ranges_plan");
-    GSR_CUDA(launch_ranges(kk[res], vv[res], cnt, max_k, f->n, f->rec.as<GaussRec>(), f->rec_sorted.as<GaussRec>(),
+    GSR_CUDA(launch_ranges(kk[res], vv[res], cnt, max_k, f->n, f->rec.as<GaussRec>(),
+                           gather_records(f) ? nullptr : f->rec_sorted.as<GaussRec>(),
                            f->ranges.as<uint2>(), f->n_tiles, f->bin.as<uint4>(),
                            f->has_state ? f->keys64.as<uint64_t>() : nullptr, st,
                            f->want_nrm ? f->nrm.as<float4>() : nullptr,
