@@ -218,14 +218,30 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
     // positions (lane, lane + 32, ...) by index, three 16-byte pieces each, as one cp.async
     // group per batch; every lane commits exactly one group per batch slot (empty past the
     // list), so waiting for all but the newest kStages - 1 groups waits for batch b.
+    // The indices of the next batch to gather are loaded when the current one is issued, so
+    // they arrive while the warp blends.
     const bool gather = a.rec_index != nullptr;
+    uint32_t next_idx[BATCH / 32];
+    auto load_idx = [&](int b) {
+        const uint32_t start = s0 + (uint32_t)b * BATCH;
+        const uint32_t cnt = b < nbatches ? min((uint32_t)BATCH, s1 - start) : 0u;
+#pragma unroll
+        for (int w = 0; w < BATCH / 32; ++w) {
+            const uint32_t j = (uint32_t)(w * 32 + lane);
+            next_idx[w] = j < cnt ? __ldg(a.vals + start + j) : 0u;
+        }
+    };
+    if (gather) load_idx(0);
     auto issue = [&](int b) {
         if (gather) {
             const int buf = b % kStages;
             const uint32_t start = s0 + (uint32_t)b * BATCH;
             const uint32_t cnt = min((uint32_t)BATCH, s1 - start);
-            for (uint32_t j = (uint32_t)lane; j < cnt; j += 32u) {
-                uint32_t g = __ldg(a.vals + start + j);
+#pragma unroll
+            for (int w = 0; w < BATCH / 32; ++w) {
+                const uint32_t j = (uint32_t)(w * 32 + lane);
+                if (j >= cnt) break;
+                uint32_t g = next_idx[w];
                 if (!GSR_IN_BOUNDS(g, a.n_gauss, a.err_word)) g = 0u;
                 const float4 *src = reinterpret_cast<const float4 *>(a.rec_index + g);
                 float4 *dst = reinterpret_cast<float4 *>(&ring.rec[buf][j]);
@@ -234,6 +250,7 @@ __device__ __forceinline__ bool warp_span(const CompositeArgs &a, int px, int py
                 cp_async16(dst + 2, src + 2);
             }
             cp_async_commit();
+            load_idx(b + 1);
         } else if (lane == 0) {
             const int buf = b % kStages;
             const uint32_t start = s0 + (uint32_t)b * BATCH;
