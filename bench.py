@@ -771,8 +771,9 @@ def algorithmic(stage, w, deg, n, K_avg, V_avg, tile_passes, pixels, pairs):
         return "hbm", (4.0 + 4.0 + 12.0) * V_avg + 8.0 * K_avg
     if stage == "tile_sort":
         return "hbm", K_avg * 16 * tile_passes
-    if stage == "ranges":  # key + value read, 48-byte record gathered and written, per instance
-        return "hbm", (4.0 + 4.0 + 48.0 + 48.0) * K_avg
+    if stage == "ranges":  # plain forwards: the sorted tile key read per instance (compositing
+        # gathers the records by index, so no sorted record copy is made); the ranges are tiny
+        return "hbm", 4.0 * K_avg
     # composite: FP32 FLOP of the per-pair work, an FMA counted as 2: 16 per evaluated pair
     # (alpha: offset, quadratic form, exponent, opacity), 38 more per blended pair (the
     # Eq. 2-4 updates of colour, depth, T and the x/y gradient terms), on the census' counts

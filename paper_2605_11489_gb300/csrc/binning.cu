@@ -369,10 +369,13 @@ __global__ void __launch_bounds__(kRangeThreads)
     float4 *dst = reinterpret_cast<float4 *>(rec_sorted);
     float4 v[kRangePer];
     uint32_t g[kRangePer];
+    // the Gaussian index is read only for what needs it (the record copy, the 64-bit keys,
+    // the normals): a plain forward's ranges read the keys alone
+    const bool need_g = rec_sorted || keys64 || nrm_sorted || plane_sorted;
 #pragma unroll
     for (int k = 0; k < kRangePer; ++k) {
         const uint32_t e = e0 + (uint32_t)k * kRangeThreads;
-        g[k] = e < P ? vals[e / per] : 0u;
+        g[k] = e < P && need_g ? vals[e / per] : 0u;
         if (!GSR_IN_BOUNDS(g[k], n, err)) g[k] = 0u;
     }
     if (rec_sorted) {
