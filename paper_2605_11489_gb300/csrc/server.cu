@@ -6,8 +6,8 @@
 //   1. admit   - a free in-flight slot takes it; projection + scan (K1, K2) run
 //                on the slot's own stream and the instance count K is copied back.
 //   2. sort    - once K is known the request's sort buffers (tile keys and
-//                values, both ping-pong halves, sorted records, sort scratch:
-//                about 66 B per instance) are
+//                values, both ping-pong halves, sort scratch: about 18 B per
+//                instance; compositing gathers the records by index) are
 //                taken from a fixed byte budget; if the budget is short the
 //                request waits, in arrival order. K3-K5 run on the slot stream.
 //   3. compose - whenever the compositing stream is idle, every sorted request
@@ -25,7 +25,7 @@
 // allocation fail (that request finishes with GS_ERR_OOM, others proceed);
 // GSR_FAULT=enqueue:<k> makes the k-th admission's first launch fail;
 // GSR_FAULT=wait:<k> runs the k-th admitted request's kernels with waits that give
-// up at once (its sort lookbacks and compositing batch waits), so that request
+// up at once (its sort and duplication lookbacks), so that request
 // finishes with GS_ERR_TIMEOUT through its device error word, others proceed;
 // GSR_FAULT=thread:<k> makes the scheduler thread throw (a host exception) before its
 // k-th admission. The thread catches whatever escapes its loop: it waits for the GPU work
@@ -176,7 +176,7 @@ struct Slot {
     cudaEvent_t ev_done = nullptr;  // the request's long tiles and error word, after its batch
     DevBuf rec, bin, ntiles, bsums, boffs, ranges, order, counters, plan;
     DevBuf vsums, voffs, dlook, dkeys[2], dvals[2], dscr;  // depth order (per Gaussian)
-    GaussRec *rec_sorted = nullptr;  // in the sort memory
+    uint32_t n_gauss = 1;            // the scene's Gaussians (bounds the gathered indices)
     uint32_t *h_counters = nullptr;  // pinned
     void *sort_mem = nullptr;        // from the arena
     Request *req = nullptr;
@@ -262,7 +262,7 @@ size_t sort_bytes(int64_t K)
 {
     const int64_t k = std::max<int64_t>(K, 1);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return 4 * up(sizeof(uint32_t) * k) + up(sizeof(GaussRec) * k) + up(sort_scratch_bytes(k));
+    return 4 * up(sizeof(uint32_t) * k) + up(sort_scratch_bytes(k));
 }
 
 // The slot's per-Gaussian and per-tile buffers for n Gaussians and n_tiles tiles.
@@ -355,8 +355,7 @@ gs_status enqueue_sort(gs_server *S, Slot &sl)
     p += up(sizeof(uint32_t) * k1);
     sl.vals[1] = reinterpret_cast<uint32_t *>(p);
     p += up(sizeof(uint32_t) * k1);
-    sl.rec_sorted = reinterpret_cast<GaussRec *>(p);
-    p += up(sizeof(GaussRec) * k1);
+    sl.n_gauss = (uint32_t)std::max<int64_t>(s.n, 1);
     SortScratch scr, dscr;
     sort_scratch_carve(p, k1, &scr);
     sort_scratch_carve(sl.dscr.p, std::max<int64_t>(s.n, 1), &dscr);
@@ -377,7 +376,7 @@ gs_status enqueue_sort(gs_server *S, Slot &sl)
     GSR_CUDA(launch_sort32(sl.keys, sl.vals, cnt + kCntEff, cnt + kCntErr, K, tbits, scr, &res, sl.stream, true,
                            sl.give_up));
     sl.sorted = res;
-    GSR_CUDA(launch_ranges(sl.keys[res], sl.vals[res], cnt, K, s.n, static_cast<const GaussRec *>(sl.rec.p), sl.rec_sorted,
+    GSR_CUDA(launch_ranges(sl.keys[res], sl.vals[res], cnt, K, s.n, static_cast<const GaussRec *>(sl.rec.p), nullptr,
                            static_cast<uint2 *>(sl.ranges.p), sl.n_tiles, static_cast<const uint4 *>(sl.bin.p),
                            nullptr, sl.stream));
     GSR_CUDA(launch_plan(static_cast<const uint2 *>(sl.ranges.p), sl.n_tiles, (int64_t)kHeadChunks * kServeChunk,
@@ -392,7 +391,8 @@ CompositeArgs slot_comp_args(Slot &sl)
 {
     Request *r = sl.req;
     CompositeArgs c{};
-    c.rec = sl.rec_sorted;
+    c.rec_index = static_cast<const GaussRec *>(sl.rec.p);  // gathered by index through vals
+    c.n_gauss = sl.n_gauss;
     c.vals = sl.vals[sl.sorted];
     c.tile_order = static_cast<const uint32_t *>(sl.order.p);
     c.ranges = static_cast<const uint2 *>(sl.ranges.p);

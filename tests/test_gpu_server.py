@@ -101,7 +101,7 @@ def test_poll_before_ready_and_drain(env):
     from paper_2605_11489_gb300 import abi
 
     scene = api.Scene.from_arrays(synth.clustered_scene(200_000, 6, (2.0, 2.0, 2.0), 8, 3))
-    srv = api.Server(sort_budget_bytes=4 << 30, max_inflight=4)  # ~0.8 GB of sort memory per request at tile 8
+    srv = api.Server(sort_budget_bytes=4 << 30, max_inflight=4)  # ~0.2 GB of sort memory per request at tile 8
     sid = srv.load_scene(scene)
     cam = synth.make_camera((0.5, 0.3, 4.0), (1, 1, 1), (0, 1, 0), 480, 270)
     rids = [srv.submit(sid, cam, api.alloc_outputs(480, 270)) for _ in range(16)]
@@ -140,7 +140,7 @@ def test_admission_waits_for_budget_and_rejects_oversized(env):
 
     scene = api.Scene.from_arrays(synth.tiny_scene(4096, 8))
     cam = synth.tiny_camera()
-    # about 6,700 instances * ~75 B: one request's sort memory is ~0.5 MB
+    # about 6,700 instances * ~18 B plus alignment: one request's sort memory is ~0.15 MB
     srv = api.Server(sort_budget_bytes=1 << 20, max_inflight=8)
     sid = srv.load_scene(scene)
     outs = [api.alloc_outputs(cam.width, cam.height) for _ in range(10)]
