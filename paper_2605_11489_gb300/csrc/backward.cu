@@ -105,10 +105,10 @@ __global__ void __launch_bounds__(32) k_composite_bwd(const BackwardArgs a)
         const int64_t beg = end - kBwdBatch > 0 ? end - kBwdBatch : 0;
         const int cnt = (int)(end - beg);
         __syncwarp();
-        for (int t = lane; t < cnt; t += 32) {  // the tile's contiguous sorted records
+        for (int t = lane; t < cnt; t += 32) {  // the tile's records, gathered by index like the forward's
             const uint32_t idx = a.vals[range.x + beg + t];
             s_idx[t] = idx;
-            GaussRec r = a.rec_sorted[range.x + beg + t];
+            GaussRec r = a.rec[idx < a.n ? idx : 0u];
             if (idx >= a.n) r.r2.z = r.r2.w = __uint_as_float(0xFFFFFFFFu);  // no pixel: never blended
             s_rec[t] = r;
         }

@@ -17,10 +17,10 @@
 // with its own shared-memory ring of kStages batches of BATCH records and its
 // own mbarriers. The next batches are staged while the warp blends the current
 // one: from the tile's contiguous sorted records (the frames that keep that copy:
-// backward state, normal channels, the server), lane 0 issues one TMA bulk copy
-// per batch (cp.async.bulk, completion counted on the warp's mbarrier); in a
-// plain forward every lane gathers its batch positions' records by Gaussian
-// index (cp.async, one group per batch), so no sorted copy is made. Per
+// the normal channels), lane 0 issues one TMA bulk copy per batch (cp.async.bulk,
+// completion counted on the warp's mbarrier); in every other frame each lane
+// gathers its batch positions' records by Gaussian index (cp.async, one group
+// per batch), so no sorted copy is made. Per
 // group of 32 records, each lane forms the mask of block pixels inside one
 // record's rectangle, and a warp-wide bit transpose of those masks gives each
 // lane the records whose rectangle holds its own pixel; it blends only these,

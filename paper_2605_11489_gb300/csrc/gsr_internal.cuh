@@ -271,8 +271,7 @@ int composite_persistent_grid(int tile, int batch);
 // backward
 struct BackwardArgs {
     // compositing side
-    const GaussRec *rec;
-    const GaussRec *rec_sorted;  // the records in sorted (instance) order, as the forward gathered them
+    const GaussRec *rec;  // the records by Gaussian index, read through vals as the forward gathered them
     const uint32_t *vals;
     const uint2 *ranges;
     int32_t width, height, tiles_x, tiles_y, tile;

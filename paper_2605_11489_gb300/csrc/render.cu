@@ -431,8 +431,6 @@ gs_status frame_keys(Frame *f, int64_t cap)
     GSR_CUDA(f->keys[1].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(cap, 1)));
     GSR_CUDA(f->vals[0].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(cap, 1)));
     GSR_CUDA(f->vals[1].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(cap, 1)));
-
-    GSR_CUDA(f->rec_sorted.ensure(sizeof(GaussRec) * (size_t)std::max<int64_t>(cap, 1)));
     f->key_cap = cap;
     return GS_OK;
 }
@@ -479,11 +477,11 @@ ProjectArgs proj_args(Frame *f, const gs_scene *s)
     return a;
 }
 
-// A plain forward (no backward state, no normal channels) composites from the records by
-// Gaussian index, each warp gathering its batches through the sorted indices, so K5 does
-// not copy the records into instance order. The backward and the normal channels read that
-// sorted copy (and the normal path its sorted normals).
-bool gather_records(const Frame *f) { return !f->has_state && !f->want_nrm; }
+// A frame without the normal channels composites from the records by Gaussian index, each
+// warp gathering its batches through the sorted indices, so K5 does not copy the records
+// into instance order (the backward reads them by index too). The normal channels' K5 pass
+// gathers the sorted normals and slopes, and the records with them.
+bool gather_records(const Frame *f) { return !f->want_nrm; }
 
 CompositeArgs comp_args(Frame *f, const gs_outputs *out)
 {
@@ -681,6 +679,9 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
         r = frame_keys(f, f->K);
         if (r != GS_OK) return r;
     }
+    // the sorted record copy, for the frames whose K5 makes one (the normal channels)
+    if (!gather_records(f))
+        GSR_CUDA(f->rec_sorted.ensure(sizeof(GaussRec) * (size_t)std::max<int64_t>(f->key_cap, 1)));
     if ((r = frame_plan(f, f->K)) != GS_OK) return r;
     if (nrm) {
         GSR_CUDA(f->nrm_sorted.ensure(sizeof(float4) * (size_t)std::max<int64_t>(f->K, 1)));
@@ -872,7 +873,6 @@ gs_status gs_render_backward(gs_context *ctx, const gs_fwd_state *state, const g
     GSR_CUDA(cudaMemsetAsync(ctx->g2d.p, 0, sizeof(float) * 10 * (size_t)f->n, st));
     BackwardArgs b{};
     b.rec = f->rec.as<GaussRec>();
-    b.rec_sorted = f->rec_sorted.as<GaussRec>();
     b.vals = f->vals[f->sorted].as<uint32_t>();
     b.ranges = f->ranges.as<uint2>();
     b.width = f->W;
