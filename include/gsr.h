@@ -226,12 +226,17 @@ gs_status gs_state_view_get(const gs_fwd_state *state, gs_state_view *view);
  * GS_ERR_TIMEOUT when a bounded wait gave up), then clears it. */
 gs_status gs_context_check(gs_context *ctx, gs_stream stream);
 /* Diagnostic for testing the failure path without a stuck GPU: with
- * give_up != 0, every bounded device wait of the context's later plain forwards
- * gives up at once instead of after its ~4M polls (each radix-sort lookback
- * before its first look, each warp's first compositing batch wait before its
- * first poll; a warp that gave up still waits, with the normal bound, for the
- * copies it has in flight). Those frames report GS_ERR_TIMEOUT through
- * gs_context_check; 0 restores the normal bound. */
+ * give_up = 1, every bounded device wait of the context's later plain forwards
+ * gives up at once instead of after its ~4M polls (each radix-sort and
+ * duplication lookback before its first look, each warp's first compositing
+ * batch wait before its first poll; a warp that gave up still waits, with the
+ * normal bound, for the copies it has in flight). A sort that gave up leaves
+ * nothing planned, so compositing then waits on nothing; give_up = 2 makes only
+ * the compositing batch waits give up, which are polled in the frames that
+ * stage batches by TMA bulk copies (those with the normal channels; the others
+ * gather with cp.async and have no poll). Those frames report GS_ERR_TIMEOUT
+ * through gs_context_check; 0 restores the normal bound. Other values:
+ * GS_ERR_INVALID_ARG. */
 gs_status gs_context_debug_waits(gs_context *ctx, int32_t give_up);
 /* Synchronises `stream` and returns the context's frame statistics (plain
  * forward calls); `reset` != 0 clears them afterwards. */

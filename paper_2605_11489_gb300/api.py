@@ -295,10 +295,11 @@ class Context:
         returns the status code (0 = GS_OK) without raising."""
         return abi.lib().gs_context_check(self.h, _stream_ptr(stream))
 
-    def debug_waits(self, give_up: bool) -> None:
-        """Diagnostic (gs_context_debug_waits): make every bounded device wait of the later
-        plain forwards give up at once, to exercise the GS_ERR_TIMEOUT path."""
-        check(abi.lib().gs_context_debug_waits(self.h, 1 if give_up else 0))
+    def debug_waits(self, give_up) -> None:
+        """Diagnostic (gs_context_debug_waits): make the bounded device waits of the later
+        plain forwards give up at once, to exercise the GS_ERR_TIMEOUT path: 1 (or True)
+        every wait, 2 compositing's batch waits only, 0 (or False) none."""
+        check(abi.lib().gs_context_debug_waits(self.h, int(give_up)))
 
     def graph(self, scene: Scene, cam, out: dict, capacity=0, tile=0, batch=0, bg=(0.0, 0.0, 0.0), timed=False,
               stream=None, chunk=0, head=0):

@@ -129,7 +129,8 @@ struct Frame {
     // device word the sort and compositing kernels raise their error bits in: the
     // context's sticky word for plain frames, the frame's counters for graphs
     uint32_t *err_word = nullptr;
-    bool give_up = false;  // diagnostic: every bounded wait gives up at once
+    bool give_up = false;            // diagnostic: the sorts' and duplication's lookbacks give up at once
+    bool give_up_composite = false;  // diagnostic: compositing's first batch wait gives up at once
 };
 
 // Per-stage CUDA-event timer: a ring of event sets, one set of kBounds events
@@ -299,7 +300,7 @@ struct gs_context {
     std::vector<Frame *> pool;
     uint32_t *h_counters = nullptr;  // pinned: kCntSlots words, then the sticky error word's copy
     Buf err;                         // device: error bits of plain frames, kept until reported
-    bool give_up = false;            // gs_context_debug_waits
+    int give_up = 0;                 // gs_context_debug_waits: 0, 1 (every wait) or 2 (compositing's)
     Buf g2d;
     Buf host_planes;
     Buf warp_pos, warp_best;    // frame-interpolation warp: landing positions, depth-test slots
@@ -511,7 +512,7 @@ CompositeArgs comp_args(Frame *f, const gs_outputs *out)
         c.n_contrib = f->ncontrib.as<uint32_t>();
     }
     c.err_word = f->err_word ? f->err_word : f->counters.as<uint32_t>() + kCntErr;
-    c.give_up = f->give_up ? 1u : 0u;
+    c.give_up = f->give_up_composite ? 1u : 0u;
     c.tile_order = f->order.as<uint32_t>();
     c.plan = f->plan.as<uint32_t>();
     c.long_counter = f->plan.as<uint32_t>() + 1;
@@ -636,7 +637,8 @@ gs_status forward_plain(gs_context *ctx, const gs_scene *s, const gs_camera *c, 
     f->count_pairs = (o->flags & GS_COUNT_PAIRS) != 0;
     if (r != GS_OK) return r;
     f->err_word = ctx->err.as<uint32_t>();
-    f->give_up = ctx->give_up;
+    f->give_up = ctx->give_up == 1;
+    f->give_up_composite = ctx->give_up != 0;
     f->want_nrm = nrm;
     if (nrm) {
         GSR_CUDA(f->nrm.ensure(sizeof(float4) * (size_t)std::max<int64_t>(s->n, 1)));
@@ -769,7 +771,8 @@ gs_status gs_context_check(gs_context *ctx, gs_stream stream)
 gs_status gs_context_debug_waits(gs_context *ctx, int32_t give_up)
 {
     if (!ctx) return fail(GS_ERR_INVALID_ARG, "ctx is NULL");
-    ctx->give_up = give_up != 0;
+    if (give_up < 0 || give_up > 2) return fail(GS_ERR_INVALID_ARG, "give_up must be 0, 1 or 2");
+    ctx->give_up = give_up;
     return GS_OK;
 }
 

@@ -1,8 +1,8 @@
 """Bounded device waits and device errors, through the C ABI, without a stuck GPU.
 
-Every wait in the kernels (the radix sort's decoupled lookback, the compositing
-warps' staged-batch waits) gives up after a bounded number of polls and raises
-an error bit instead of spinning. A diagnostic setting (gs_context_debug_waits,
+Every wait in the kernels (the radix sort's and the duplication's decoupled
+lookbacks, the compositing warps' staged-batch waits) gives up after a bounded
+number of polls and raises an error bit instead of spinning. A diagnostic setting (gs_context_debug_waits,
 or GSR_FAULT=wait:<k> in the server) makes them give up at once, so that the
 failure path runs deterministically on a healthy GPU: the frame must report
 GS_ERR_TIMEOUT, nothing may be read or written out of bounds, and the context
@@ -70,6 +70,39 @@ def test_forward_wait_gives_up_reports_timeout_and_context_recovers(env):
         for k in out:
             assert torch.equal(out[k], ref[k]), k
         check_render(out, O.render(sc, cam), grad_frac=GRAD_FRAC_STRESS)  # a close-range stress scene
+    finally:
+        torch.cuda.synchronize()
+        ctx.close()
+        ref_ctx.close()
+
+
+def test_compositing_batch_wait_gives_up_and_context_recovers(env):
+    """Level 2 of the diagnostic makes only compositing's batch waits give up, so the
+    sorts finish and the plan is made. Frames with the normal channels stage their batches
+    by TMA bulk copies into each warp's mbarrier ring: every warp's first wait gives up,
+    waits (bounded) for the copies it has in flight, and the frame reports
+    GS_ERR_TIMEOUT. The same frame then renders exactly as on a fresh context."""
+    abi, api, O = env
+    import torch
+
+    sc, cam = _scene(), _camera()
+    scene = api.Scene.from_arrays(sc)
+    keys = api.OUTPUT_KEYS + api.NORMAL_KEYS
+    ref_ctx = api.Context(0)
+    ref = ref_ctx.forward(scene, cam, keys=keys)
+    ctx = api.Context(0)
+    try:
+        with pytest.raises(abi.GsError) as ei:
+            ctx.debug_waits(3)
+        assert ei.value.status == abi.GS_ERR_INVALID_ARG
+        ctx.debug_waits(2)
+        ctx.forward(scene, cam, keys=keys)
+        assert ctx.check() == abi.GS_ERR_TIMEOUT
+        ctx.debug_waits(0)
+        out = ctx.forward(scene, cam, keys=keys)
+        assert ctx.check() == abi.GS_OK
+        for k in out:
+            assert torch.equal(out[k], ref[k]), k
     finally:
         torch.cuda.synchronize()
         ctx.close()
