@@ -70,7 +70,9 @@ def check_depth(got, ref_depth, ref_alpha, frac=COLOUR_FRAC):
 
 
 def grad_bound(ref, rms, rel=GRAD_REL):
-    """The survey's reading of "1e-3 relative": 1e-3 * max(|g|, 1e-2 * rms)."""
+    """A 1e-3 relative bar on a gradient value, with a floor of 1e-2 of the channel's rms so
+    that values near zero are not held to an absolute bar finer than fp32 rounding:
+    1e-3 * max(|g|, 1e-2 * rms)."""
     return rel * np.maximum(np.abs(ref), GRAD_RMS_FLOOR * rms)
 
 
